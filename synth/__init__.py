@@ -93,19 +93,22 @@ def arrowhead(beta: float, m: int = 20000, n: int = 50) -> np.ndarray:
 def known_answer(m: int, n: int, seed: int, kappa_r: float = 1e3):
     """(X, Q0, R0) with X = Q0 R0 in exact arithmetic.
 
-    Q0 has orthonormal columns; R0 is upper triangular with a positive
-    diagonal geometric from 1 to 1/kappa_r and N(0, 0.1^2) entries above it.
+    Q0 has orthonormal columns; R0 = diag(d) (I + T) is upper triangular with
+    a positive diagonal d geometric from 1 to 1/kappa_r and T strictly upper
+    with N(0, 0.09/n) entries.
     The positive-diagonal thin QR is unique, so R must equal R0 and Q must
     equal Q0 up to the conditioning of the problem.
     """
     q0 = orthonormal(m, n, seed)
     g = rng(seed + 2)
-    r0 = np.triu(0.1 * g.standard_normal((n, n)), 1)
+    # R0 = diag(d) (I + T) with T strictly upper, N(0, 0.3^2/n) entries: the
+    # unit factor stays well conditioned, so kappa(R0) stays near kappa_r.
+    t = np.triu(g.standard_normal((n, n)), 1) * (0.3 / math.sqrt(max(n, 1)))
     if n > 1:
         d = np.power(float(kappa_r), -np.arange(n) / (n - 1))
     else:
         d = np.ones(1)
-    r0 += np.diag(d)
+    r0 = d[:, None] * (np.eye(n) + t)
     x = np.asfortranarray(q0 @ r0)
     return x, q0, np.asfortranarray(r0)
 

@@ -1,0 +1,430 @@
+"""Pins for the CPU oracle: each routine is checked against something other
+than itself -- exact integer arithmetic, LAPACK (numpy/scipy), brute force in
+50-digit arithmetic (mpmath), closed forms, published test vectors and the
+paper's error bounds.  A dropped term, a wrong sign or index, or a transposed
+operand in the oracle fails at least one of these.  No GPU is used."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import synth
+
+U = 2.0 ** -53
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _int_upper(n, seed, diag=(1, 3)):
+    g = np.random.default_rng(seed)
+    r = np.triu(g.integers(-4, 5, size=(n, n)), 1).astype(np.float64)
+    r += np.diag(g.integers(diag[0], diag[1] + 1, size=n).astype(np.float64))
+    return np.asfortranarray(r)
+
+
+# ------------------------------------------------------------ Gram, TRMM ---
+
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (130, 17), (257, 40)])
+def test_gram_exact_on_integers(m, n):
+    x = synth.integer_matrix(m, n, seed=m * 31 + n)
+    xi = x.astype(np.int64)
+    assert np.array_equal(oracle.gram(x), (xi.T @ xi).astype(np.float64))
+
+
+def test_gram_is_xtx_not_xxt():
+    x = synth.integer_matrix(9, 4, seed=3)
+    g = oracle.gram(x)
+    assert g.shape == (4, 4)
+    assert np.array_equal(g, g.T)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16])
+def test_trmm_upper_exact(n):
+    a = _int_upper(n, 1)
+    b = _int_upper(n, 2)
+    ref = (np.triu(a).astype(np.int64) @ np.triu(b).astype(np.int64)).astype(np.float64)
+    assert np.array_equal(oracle.trmm_upper(a, b), ref)
+
+
+# -------------------------------------------------------------- Cholesky ---
+
+@pytest.mark.parametrize("n", [1, 3, 8, 24])
+def test_cholesky_recovers_integer_factor_exactly(n):
+    # G = R^T R with an integer R of positive diagonal: every quantity of the
+    # column Cholesky is an exact integer, so R comes back bit for bit.
+    r = _int_upper(n, 10 + n, diag=(1, 4))
+    g = (r.T.astype(np.int64) @ r.astype(np.int64)).astype(np.float64)
+    rr, st, _ = oracle.cholesky(g)
+    assert st == 0
+    assert np.array_equal(rr, r)
+
+
+def test_cholesky_brute_force_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    g0 = np.random.default_rng(5).standard_normal((6, 6))
+    g = g0.T @ g0 + 0.1 * np.eye(6)
+    r, st, _ = oracle.cholesky(g)
+    assert st == 0
+    ref = mpmath.cholesky(mpmath.matrix(g.tolist()))  # lower L with G = L L^T
+    ref_r = np.array([[float(ref[j, i]) for j in range(6)] for i in range(6)])
+    assert np.max(np.abs(r - ref_r)) <= 1e-13 * np.max(np.abs(ref_r))
+
+
+def test_cholesky_breakdown_status_and_column():
+    g = np.diag([4.0, 1.0, -1.0, 2.0])
+    _, st, info = oracle.cholesky(g, raise_on_error=False)
+    assert st == oracle.CHOL_BREAKDOWN and info == 2
+    g = np.array([[1.0, 2.0], [2.0, 1.0]])  # indefinite: radicand 1 - 4 < 0 at column 1
+    _, st, info = oracle.cholesky(g, raise_on_error=False)
+    assert st == oracle.CHOL_BREAKDOWN and info == 1
+    g = np.array([[np.nan]])
+    _, st, info = oracle.cholesky(g, raise_on_error=False)
+    assert st == oracle.CHOL_BREAKDOWN and info == 0
+
+
+# ------------------------------------------------------------------ TRSM ---
+
+@pytest.mark.parametrize("m,n", [(1, 1), (11, 4), (200, 33)])
+def test_trsm_exact_on_unit_integer_factor(m, n):
+    # R integer upper with diagonal +-1, Q integer: X = Q R exactly and the
+    # substitution X R^{-1} reproduces Q exactly.
+    g = np.random.default_rng(m + n)
+    r = np.triu(g.integers(-3, 4, size=(n, n)), 1).astype(np.float64)
+    r += np.diag(g.choice([-1.0, 1.0], size=n))
+    q = g.integers(-5, 6, size=(m, n)).astype(np.float64)
+    x = (q.astype(np.int64) @ r.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(oracle.trsm(x, r), q)
+
+
+def test_trsm_matches_lapack_triangular_solve():
+    g = np.random.default_rng(9)
+    n, m = 12, 50
+    r = np.triu(g.standard_normal((n, n))) + 4 * np.eye(n)
+    x = g.standard_normal((m, n))
+    ref = scipy.linalg.solve_triangular(r.T, x.T, lower=True).T  # X R^{-1}
+    assert np.max(np.abs(oracle.trsm(x, r) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------------------ GEPP ---
+
+def _rational_gepp(a):
+    """Exact GEPP over the rationals (first-index tie-break)."""
+    a = [[Fraction(int(v)) for v in row] for row in a]
+    m, n = len(a), len(a[0])
+    piv = []
+    for k in range(min(m, n)):
+        p = max(range(k, m), key=lambda i: (abs(a[i][k]), -i))
+        piv.append(p)
+        a[k], a[p] = a[p], a[k]
+        for i in range(k + 1, m):
+            a[i][k] = a[i][k] / a[k][k]
+            for j in range(k + 1, n):
+                a[i][j] -= a[i][k] * a[k][j]
+    return a, piv
+
+
+@pytest.mark.parametrize("m,n,seed", [(5, 5, 1), (9, 4, 2), (16, 8, 3), (8, 8, 4)])
+def test_gepp_brute_force_rational(m, n, seed):
+    x = synth.integer_matrix(m, n, seed, lo=-6, hi=6)
+    x[:, 0] += 50.0 * np.eye(m, n)[:, 0]  # keep it nonsingular
+    ex, piv = _rational_gepp(x)
+    lu, ipiv, st, _ = oracle.gepp(x)
+    assert st == 0
+    assert list(ipiv) == piv
+    ref = np.array([[float(v) for v in row] for row in ex])
+    assert np.max(np.abs(lu - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_gepp_tie_break_smallest_index():
+    x = np.array([[1.0, 2.0], [-3.0, 1.0], [3.0, 5.0], [2.0, 0.0]])
+    lu, ipiv, st, _ = oracle.gepp(x)
+    assert ipiv[0] == 1  # |-3| == |3|: the first one wins
+
+
+def test_gepp_matches_lapack_getrf():
+    # well conditioned, so that LAPACK's blocked summation order and ours
+    # agree to a few ulps; the pivot sequence must be identical
+    x = synth.svd_matrix(300, 20, 10.0, 11)
+    lu, ipiv, st, _ = oracle.gepp(x)
+    lu_ref, piv_ref = scipy.linalg.lu_factor(x)
+    assert np.array_equal(ipiv, piv_ref[:20])
+    assert np.max(np.abs(lu - lu_ref[:, :20])) <= 1e-13
+
+
+def test_gepp_backward_error_eq_elu():
+    # |P X - M N| <= 1.02 n u |M||N|  (eq. (elu))
+    x = synth.svd_matrix(400, 24, 1e8, 12)
+    lu, ipiv, st, _ = oracle.gepp(x)
+    px = x.copy()
+    for k, p in enumerate(ipiv):
+        px[[k, p]] = px[[p, k]]
+    mm, nn = oracle.unit_lower(lu), oracle.upper(lu)
+    err = np.abs(px - mm @ nn)
+    bound = 1.02 * 24 * U * (np.abs(mm) @ np.abs(nn))
+    assert np.all(err <= bound + 1e-300)
+    assert np.max(np.abs(mm)) <= 1.0
+
+
+def test_gepp_zero_pivot_reported():
+    x = np.array([[1.0, 2.0], [2.0, 4.0], [3.0, 6.0]])
+    _, _, st, info = oracle.gepp(x, raise_on_error=False)
+    assert st == oracle.LU_ZERO_PIVOT and info == 1
+
+
+# ----------------------------------------------------------- Householder ---
+
+@pytest.mark.parametrize("s,n", [(1, 1), (6, 3), (40, 17), (128, 64)])
+def test_householder_r_matches_lapack_including_signs(s, n):
+    a = np.random.default_rng(s * n).standard_normal((s, n))
+    r = oracle.householder_r(a)
+    r_ref = np.linalg.qr(a, mode="r")  # dgeqrf: beta = -sign(alpha) ||x||
+    assert np.allclose(r, np.triu(r_ref[:n]), rtol=0, atol=1e-13 * np.max(np.abs(r_ref)))
+
+
+def test_householder_r_invariant_rtr_equals_ata():
+    a = synth.svd_matrix(64, 10, 1e5, 4)
+    r = oracle.householder_r(a)
+    assert np.allclose(r.T @ r, a.T @ a, atol=1e-14)
+    assert np.array_equal(r, np.triu(r))
+
+
+def test_householder_skips_zero_subcolumn():
+    a = np.array([[-2.0, 1.0], [0.0, 3.0], [0.0, 4.0]])
+    r = oracle.householder_r(a)
+    assert r[0, 0] == -2.0 and r[0, 1] == 1.0       # H_0 = I
+    assert abs(abs(r[1, 1]) - 5.0) < 1e-15           # ||(3, 4)|| = 5, beta = -5
+    assert r[1, 1] < 0
+
+
+# --------------------------------------------------------------- sketches ---
+
+def test_sketch_dense_exact_on_integers():
+    g = np.random.default_rng(3)
+    S = g.integers(-3, 4, size=(7, 50)).astype(np.float64)
+    x = g.integers(-5, 6, size=(50, 6)).astype(np.float64)
+    ref = (S.astype(np.int64) @ x.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(oracle.sketch_dense(S, x), ref)
+
+
+def test_sketch_sparse_equals_dense_definition():
+    s, m, zeta = 16, 300, 4  # 1/sqrt(4) = 1/2: exact
+    rows, signs = oracle.sparse_sign_pattern(s, m, zeta, seed=77)
+    x = synth.integer_matrix(m, 5, 8)
+    S = oracle.sparse_to_dense(s, m, zeta, rows, signs)
+    y1 = oracle.sketch_sparse(s, zeta, rows, signs, x)
+    y2 = oracle.sketch_dense(S, x)
+    ref = (2 * S).astype(np.int64) @ x.astype(np.int64) / 2.0
+    assert np.array_equal(y1, ref) and np.array_equal(y2, ref)
+
+
+def _kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                v = [int(t, 16) for t in line.split()]
+                rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,out", _kat())
+def test_philox_known_answers(ctr, key, out):
+    assert list(oracle.philox4x32_10(ctr, key)) == out
+
+
+def test_ln_and_cossin_definitions_are_accurate():
+    xs = np.concatenate([np.arange(1, 2 ** 23, 9973) * 2.0 ** -23, [2.0 ** -23, 0.5, 1.0]])
+    for x in xs.astype(np.float32):
+        assert abs(oracle.ln_f32(float(x)) - math.log(float(x))) <= 4e-7 * max(1.0, abs(math.log(float(x))))
+    for u in np.arange(0, 2 ** 23, 7919) * 2.0 ** -23:
+        c, s = oracle.cossin_2pi_f32(float(np.float32(u)))
+        assert abs(c - math.cos(2 * math.pi * u)) < 1e-6
+        assert abs(s - math.sin(2 * math.pi * u)) < 1e-6
+    assert oracle.ln_f32(1.0) == 0.0
+    assert oracle.cossin_2pi_f32(0.0) == (1.0, 0.0)
+
+
+def test_gaussian_sketch_statistics():
+    from scipy import stats
+    z = np.array([oracle.gauss_entry(123, r, i) for r in range(8) for i in range(4000)])
+    assert abs(z.mean()) < 0.03 and abs(z.var() - 1.0) < 0.04
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    S = oracle.gaussian_sketch_matrix(32, 1000, 5)
+    assert abs(np.mean(np.sum(S * S, axis=0)) - 1.0) < 0.05  # column norms ~ 1 (N(0, 1/s))
+    # the same (seed, r, i) always gives the same entry
+    assert oracle.gauss_entry(123, 5, 17) == oracle.gauss_entry(123, 5, 17)
+    assert oracle.gauss_entry(123, 5, 17) != oracle.gauss_entry(124, 5, 17)
+
+
+def test_sparse_sign_pattern_properties():
+    s, m, zeta = 64, 5000, 8
+    rows, signs = oracle.sparse_sign_pattern(s, m, zeta, seed=3)
+    r = rows.reshape(m, zeta)
+    assert all(len(set(rr)) == zeta for rr in r)
+    assert set(np.unique(signs)) == {-1, 1}
+    counts = np.bincount(rows, minlength=s)
+    from scipy import stats
+    assert stats.chisquare(counts).pvalue > 1e-3
+    S = oracle.sparse_to_dense(s, m, zeta, rows, signs)
+    assert np.allclose(np.sum(S * S, axis=0), 1.0)
+    # zeta == s forces the fallback path; it must still give distinct rows
+    rows2, _ = oracle.sparse_sign_pattern(8, 20, 8, seed=1)
+    assert all(sorted(rr) == list(range(8)) for rr in rows2.reshape(20, 8))
+
+
+@pytest.mark.parametrize("kind", ["gauss", "sparse"])
+def test_sketch_is_an_embedding_eq_s2(kind):
+    # For X with orthonormal columns, the singular values of S X lie in
+    # [sqrt(1-eps), sqrt(1+eps)] with eps = 0.5 (eq. (s2)), with high probability.
+    # For a Gaussian S the extreme singular values sit near 1 +- sqrt(n/s), so
+    # eps = 0.5 needs s >~ 20 n; s = 32 n here.
+    m, n, s = 3000, 8, 256
+    x = synth.orthonormal(m, n, 21)
+    if kind == "gauss":
+        y = oracle.sketch_dense(oracle.gaussian_sketch_matrix(s, m, 9), x)
+    else:
+        rows, signs = oracle.sparse_sign_pattern(s, m, 8, 9)
+        y = oracle.sketch_sparse(s, 8, rows, signs, x)
+    sv = np.linalg.svd(y, compute_uv=False)
+    assert sv.max() <= math.sqrt(1.5) and sv.min() >= math.sqrt(0.5)
+
+
+def test_sketch_precond_r1_is_r_factor_of_sketch():
+    # R1 = R0 N is the R-factor of Y up to row signs; after the sign fix it is
+    # the positive-diagonal one: R1^T R1 = Y^T Y and R1 = D R_householder(Y).
+    y = synth.svd_matrix(64, 12, 1e4, 31)
+    r1, st, _ = oracle.sketch_precond(y)
+    rh = np.linalg.qr(y, mode="r")
+    rh = np.sign(np.diag(rh))[:, None] * rh
+    assert np.all(np.diag(r1) > 0) and np.array_equal(r1, np.triu(r1))
+    assert np.max(np.abs(r1 - rh)) <= 1e-10 * np.max(np.abs(rh))
+
+
+# ---------------------------------------------------------------- drivers ---
+
+def _mp_qr(x):
+    """Positive-diagonal thin QR in 50-digit arithmetic (Cholesky of the exact Gram)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    X = mpmath.matrix(x.tolist())
+    G = X.T * X
+    L = mpmath.cholesky(G)
+    R = L.T
+    Q = X * R ** -1
+    m, n = x.shape
+    return (np.array([[float(Q[i, j]) for j in range(n)] for i in range(m)]),
+            np.array([[float(R[i, j]) for j in range(n)] for i in range(n)]))
+
+
+def _drivers(s):
+    return {
+        "cholqr2": lambda x: oracle.cholqr2(x),
+        "lc2": lambda x: oracle.lc2(x),
+        "rclupp": lambda x: oracle.rclupp(x, S=synth.gaussian_sketch(s, x.shape[0], 4)),
+        "rcluppr": lambda x: oracle.rcluppr(x, S=synth.gaussian_sketch(s, x.shape[0], 4)),
+        "rclupp_sparse": lambda x: oracle.rclupp(x, sparse=(s, 4) + oracle.sparse_sign_pattern(s, x.shape[0], 4, 4)),
+        "rcluppr_sparse": lambda x: oracle.rcluppr(x, sparse=(s, 4) + oracle.sparse_sign_pattern(s, x.shape[0], 4, 4)),
+    }
+
+
+@pytest.mark.parametrize("name", list(_drivers(16)))
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_drivers_brute_force_small(name, n):
+    x = synth.svd_matrix(40, n, 1e3, 100 + n)
+    q_ref, r_ref = _mp_qr(x)
+    q, r, st = _drivers(max(2 * n, 4))[name](x)
+    assert st == 0
+    assert np.max(np.abs(r - r_ref)) <= 1e-12 * np.max(np.abs(r_ref))
+    assert np.max(np.abs(q - q_ref)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(_drivers(64)))
+def test_drivers_known_answer(name):
+    x, q0, r0 = synth.known_answer(2000, 24, seed=8, kappa_r=1e4)
+    q, r, st = _drivers(64)[name](x)
+    assert st == 0
+    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+    assert np.linalg.norm(r - r0) / np.linalg.norm(r0) <= 1e-12 * 1e4
+    assert np.max(np.abs(q - q0)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(_drivers(100)))
+def test_drivers_agree_with_householder_up_to_signs(name):
+    x = synth.svd_matrix(2000, 50, 1e6, 13)
+    q, r, st = _drivers(100)[name](x)
+    qh, rh = np.linalg.qr(x)
+    d = np.sign(np.diag(rh))
+    rh, qh = d[:, None] * rh, qh * d[None, :]
+    assert np.linalg.norm(r - rh) / np.linalg.norm(rh) <= 1e-15 * 1e6 * 10
+    assert np.linalg.norm(q - qh) <= 1e-15 * 1e6 * 10
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10])
+def test_singular_values_of_r_closed_form(kappa):
+    # X = U diag(sigma) V^T: R has the singular values sigma (R^T R = V S^2 V^T).
+    m, n = 3000, 20
+    x = synth.svd_matrix(m, n, kappa, 41)
+    q, r, st = oracle.rclupp(x, S=synth.gaussian_sketch(40, m, 2))
+    sv = np.linalg.svd(r, compute_uv=False)
+    sigma = np.power(kappa, -np.arange(n) / (n - 1))
+    assert np.max(np.abs(sv - sigma) / sigma) <= 1e-15 * kappa * 100
+
+
+def _thm41_bounds(m, n, x, eps=0.5):
+    h = 1.0 / (0.78 / math.sqrt(1 + eps) - 0.1 / math.sqrt(1 - eps))
+    orth = 6 * (m * n * U + n * (n + 1) * U)
+    res = (4.36 / math.sqrt(1 - eps) * h * n * math.sqrt(n) * U * np.linalg.norm(x, "fro")
+           + 3.02 / math.sqrt(1 - eps) * h * n * n * U * np.linalg.norm(x, 2))
+    return orth, res
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e8, 1e12])
+@pytest.mark.parametrize("algo", ["rclupp", "rcluppr"])
+def test_theorem_4_1_bounds(kappa, algo):
+    m, n, s = 4096, 64, 128
+    x = synth.svd_matrix(m, n, kappa, 51)
+    S = synth.gaussian_sketch(s, m, 52)
+    q, r, st = getattr(oracle, algo)(x, S=S)
+    orth_b, res_b = _thm41_bounds(m, n, x)
+    assert oracle.orthogonality(q) <= orth_b
+    assert np.linalg.norm(q @ r - x, "fro") <= res_b
+
+
+def test_cholqr2_lemma_3_1_and_breakdown():
+    m, n = 4096, 32
+    x = synth.svd_matrix(m, n, 1e3, 61)
+    q, r, st = oracle.cholqr2(x)
+    assert oracle.orthogonality(q) <= 6 * (m * n * U + n * (n + 1) * U)
+    assert np.linalg.norm(q @ r - x, "fro") <= 5 * n ** 2.5 * U * np.linalg.norm(x, 2)
+    # kappa beyond u^{-1/2}: CholeskyQR2 breaks down (Section 2.2)
+    _, _, st = oracle.cholqr2(synth.svd_matrix(m, n, 1e12, 62), raise_on_error=False)
+    assert st == oracle.CHOL_BREAKDOWN
+
+
+def test_lc2_lemma_3_3():
+    m, n = 4096, 32
+    x = synth.svd_matrix(m, n, 1e6, 71)
+    q, r, st = oracle.lc2(x)
+    assert oracle.orthogonality(q) <= 6.5 * (m * n * U + n * (n + 1) * U)
+    assert np.linalg.norm(q @ r - x, "fro") <= 4.09 * n * n * U * np.linalg.norm(x, 2)
+
+
+def test_rcluppr_robust_on_arrowhead_section_5_1_3():
+    # The arrowhead matrix of Section 5.1.3: RCLUPPr stays accurate where
+    # CholeskyQR2 breaks down.
+    x = synth.arrowhead(1e-10, m=2000, n=20)
+    q, r, st = oracle.rcluppr(x, S=synth.gaussian_sketch(40, 2000, 3))
+    assert st == 0 and oracle.orthogonality(q) < 1e-12 and oracle.residual(x, q, r) < 1e-14
+    _, _, st2 = oracle.cholqr2(x, raise_on_error=False)
+    assert st2 == oracle.CHOL_BREAKDOWN
+
+
+def test_stacked_lower_section_5_1_2():
+    x = synth.stacked_lower(-0.8, copies=40, nb=20)
+    for algo in ("rclupp", "rcluppr"):
+        q, r, st = getattr(oracle, algo)(x, S=synth.gaussian_sketch(40, x.shape[0], 3))
+        assert st == 0 and oracle.orthogonality(q) < 1e-12 and oracle.residual(x, q, r) < 1e-14
