@@ -1,0 +1,206 @@
+/*
+ * rclupp.h -- C ABI of the GB300 (sm_103a) library for the QR factorization
+ * of tall-skinny matrices by randomized CholeskyQR with LU partial pivoting.
+ *
+ * Paper: "A new randomized CholeskyQR based on LU decomposition with partial
+ * pivoting" (arXiv 2412.06551).  The problem (Section 1): X in R^{m x n},
+ * m >= n, rank(X) = n; compute X = Q R with Q (m x n) orthonormal columns and
+ * R (n x n) upper triangular.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major FP64: element (i, j) of a matrix A with
+ *     leading dimension lda is A[i + j*lda], lda >= number of rows.
+ *   - Matrix pointers are DEVICE pointers owned by the caller, unless an
+ *     argument says "host".  The library never frees them.
+ *   - The handle owns its stream binding and a device workspace that grows
+ *     on demand (cudaMalloc) and is released by rclupp_destroy.
+ *   - Every call is enqueued on the handle's stream and is synchronous with
+ *     respect to its returned status: the function returns after the GPU work
+ *     has finished, so a numerical status (breakdown, zero pivot) can be
+ *     returned.  Entry points marked "async" only enqueue.
+ *   - On any status other than RCLUPP_OK the contents of the outputs are
+ *     unspecified.  Argument errors are detected before any GPU work.
+ *   - R outputs are n x n upper triangular with the strict lower triangle set
+ *     to zero and a positive diagonal (the unique thin QR).
+ *   - Q may alias X for rclupp_factor and cholqr2_factor (every tall pass is
+ *     row-local).  For rclupp_r_factor and lc2_factor aliasing makes the
+ *     handle allocate an m x n workspace for the LU factor.
+ */
+#ifndef RCLUPP_H
+#define RCLUPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rclupp_handle_s *rclupp_handle_t;
+
+typedef enum {
+    RCLUPP_OK = 0,
+    RCLUPP_ERR_ARG = -1,            /* invalid argument (sizes, pointers, leading dims) */
+    RCLUPP_ERR_CHOL_BREAKDOWN = -2, /* a Cholesky radicand was <= 0 or NaN (info: column) */
+    RCLUPP_ERR_LU_ZERO_PIVOT = -3,  /* zero pivot in an LU factorization: rank < n */
+    RCLUPP_ERR_NONFINITE = -4,      /* non-finite value met where a finite one is required */
+    RCLUPP_ERR_CUDA = -5,           /* a CUDA runtime call failed */
+    RCLUPP_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+    RCLUPP_ERR_NOMEM = -7,          /* workspace allocation failed */
+    RCLUPP_ERR_UNSUPPORTED = -8     /* size or option outside what this build supports */
+} rclupp_status_t;
+
+typedef enum {
+    RCLUPP_SKETCH_GAUSSIAN = 0,   /* S = G / sqrt(s), G standard Gaussian (Section 3) */
+    RCLUPP_SKETCH_SPARSE_SIGN = 1 /* zeta distinct rows per column, +-1/sqrt(zeta)   */
+} rclupp_sketch_kind_t;
+
+typedef enum {
+    RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
+    RCLUPP_PREC_SKETCH_BF16 = 1, /* Gaussian sketch on tensor cores: bf16 S, bf16 X, fp32 sum */
+    RCLUPP_PREC_SKETCH_FP32 = 2  /* bf16 S, X split into three bf16 terms, fp32 sum          */
+} rclupp_precision_t;
+
+/* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
+ *   kind  : Gaussian or sparse-sign.
+ *   s     : sketch size, n <= s <= 4096 (the paper uses s = O(n), e.g. n+1 or 2n).
+ *   zeta  : nonzeros per column for the sparse-sign sketch (1 <= zeta <= s, <= 16).
+ *   seed  : key of the counter-based generator (Philox4x32-10) for S.
+ *   prec  : precision of the sketch product (rclupp_precision_t).
+ *   S/lds : optional explicit dense sketch (DEVICE, s x m, column-major); when
+ *           non-NULL it replaces the generated one (kind and seed are ignored).
+ * The generated S: entry (r, i) depends only on (seed, r, i), so S is never
+ * stored.  Gaussian: Philox4x32-10 with counter (i mod 2^32, i div 2^32,
+ * r div 4, 0x53474155) and key = seed; words (w0, w1) serve rows 4b, 4b+1 and
+ * (w2, w3) rows 4b+2, 4b+3 by the Box-Muller transform, evaluated in binary32
+ * with series for ln and sin/cos; S = z / sqrt(s).  Sparse-sign: Philox words
+ * with counter (i mod 2^32, i div 2^32, block, 0x53535047) propose rows
+ * floor(w s / 2^32), duplicates skipped, sign from the lowest bit. */
+typedef struct {
+    int32_t kind;
+    int32_t zeta;
+    int64_t s;
+    uint64_t seed;
+    int32_t prec;
+    int32_t reserved;
+    const double *S;
+    int64_t lds;
+} rclupp_opts_t;
+
+/* Diagnostic output of a factorization (may be NULL). */
+typedef struct {
+    int32_t status;      /* same as the return value */
+    int32_t failed_step; /* 0 none; 1 sketch LU; 2 tall LU; 3 first Cholesky;
+                            4 second Cholesky; 5 third Cholesky (LC2 / CholeskyQR2) */
+    int64_t info;        /* failing column for breakdown / zero pivot, else -1 */
+} rclupp_info_t;
+
+/* ---- handle -------------------------------------------------------------- */
+
+/* Create a handle bound to the CUDA stream `stream` (a cudaStream_t; NULL =
+ * the legacy default stream) on the current device.  Allocates a small
+ * status buffer; the workspace is allocated lazily.  Errors: ERR_ARG (NULL
+ * out-pointer), ERR_CUDA, ERR_NOMEM. */
+rclupp_status_t rclupp_create(rclupp_handle_t *handle, void *stream);
+/* Release the handle and its workspace (synchronizes its stream first). */
+rclupp_status_t rclupp_destroy(rclupp_handle_t handle);
+/* Rebind the handle to another stream of the same device. */
+rclupp_status_t rclupp_set_stream(rclupp_handle_t handle, void *stream);
+/* Bytes of device workspace currently held by the handle. */
+rclupp_status_t rclupp_workspace_bytes(rclupp_handle_t handle, size_t *bytes);
+/* Human-readable name of a status code (static string). */
+const char *rclupp_status_string(int status);
+
+/* ---- algorithm drivers -------------------------------------------------- */
+
+/* [Q, R] = RCLUPP(X) -- Algorithm 6 (RCLUPP), Section 1:
+ *   X_s = S X; [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M); R1 = R0 N
+ *   (diagonal signs of R1 normalised); Q1 = X R1^{-1};
+ *   [Q, Z] = CholeskyQR2(Q1); R = Z R1  (evaluated R3 = R2 R1, R = R4 R3).
+ * X: m x n (ldx >= m); Q: m x n (ldq >= m), may alias X; R: n x n (ldr >= n).
+ * opts: sketch options (NULL = Gaussian, s = 2n, seed 0, FP64).
+ * Requires 1 <= n <= 256, n <= m, n <= s.  Errors: ERR_ARG, ERR_UNSUPPORTED,
+ * ERR_LU_ZERO_PIVOT (sketch rank-deficient), ERR_CHOL_BREAKDOWN, ERR_CUDA,
+ * ERR_NOMEM, ERR_TIMEOUT. */
+rclupp_status_t rclupp_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                              int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                              double *R, int64_t ldr, rclupp_info_t *info);
+
+/* [Q, R] = RCLUPPr(X) -- Algorithm 7 (RCLUPPr), Section 4.4:
+ *   [M, N, P] = LU(X) (tall, partial pivoting over all m rows); M_s = S M;
+ *   R0 = R of HouseholderQR(M_s); R1 = R0 N (signs normalised);
+ *   Q1 = X R1^{-1}; [Q, Z] = CholeskyQR2(Q1); R = Z R1.
+ * Same arguments and errors as rclupp_factor; X is not modified. */
+rclupp_status_t rclupp_r_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                                int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                                double *R, int64_t ldr, rclupp_info_t *info);
+
+/* [Q, R] = CholeskyQR2(X) -- Algorithm 2 (Section 2.1).  No sketch.
+ * Breaks down (ERR_CHOL_BREAKDOWN) when kappa_2(X) approaches u^{-1/2}. */
+rclupp_status_t cholqr2_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                               int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
+                               rclupp_info_t *info);
+
+/* [Q, R] = LC2(X) -- Algorithm 4 (Section 2.3): [M, N, P] = LU(X);
+ * S = chol(M^T M); R1 = S N (signs normalised); Q1 = X R1^{-1};
+ * [Q, Z] = CholeskyQR(Q1); R = Z R1. */
+rclupp_status_t lc2_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                           int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
+                           rclupp_info_t *info);
+
+/* ---- individual steps of the tall path (each is one row of the path) ---- */
+
+/* Y = S A (s x n, ldy >= s): the sketch of Algorithm 6 step 1 (S X) and of
+ * Algorithm 7 step 2 (S M).  unit_lower != 0 reads A as the unit-lower
+ * trapezoidal factor of an in-place LU (ones on the diagonal, zeros above).
+ * Sum order is a fixed split over row chunks and a fixed-order reduction, so
+ * results are bitwise reproducible for a given device. */
+rclupp_status_t rclupp_sketch(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                              int64_t lda, int32_t unit_lower, const rclupp_opts_t *opts,
+                              double *Y, int64_t ldy);
+
+/* G = A^T A (n x n, ldg >= n, both triangles written): Algorithm 1 step 1,
+ * C1/C5 of Theorem 4.1; unit_lower as in rclupp_sketch (LC2's M^T M). */
+rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                            int64_t lda, int32_t unit_lower, double *G, int64_t ldg);
+
+/* Q = A R^{-1} by substitution (eq. (ewy), C3, C7) and, when G != NULL,
+ * G = Q^T Q (C1, C5) in the same pass.  R: n x n upper, nonzero diagonal.
+ * Q may alias A. */
+rclupp_status_t rclupp_trsm_gram(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                                 int64_t lda, const double *R, int64_t ldr, double *Q, int64_t ldq,
+                                 double *G, int64_t ldg);
+
+/* Upper Cholesky factor of an SPD n x n G (Algorithm 1 step 2; C2, C6).
+ * Returns ERR_CHOL_BREAKDOWN with *col (if non-NULL) = failing column. */
+rclupp_status_t rclupp_cholesky(rclupp_handle_t handle, int64_t n, const double *G, int64_t ldg,
+                                double *R, int64_t ldr, int64_t *col);
+
+/* C = A B for upper-triangular n x n A, B (eq. (ey), C4, C8). */
+rclupp_status_t rclupp_trmm_upper(rclupp_handle_t handle, int64_t n, const double *A, int64_t lda,
+                                  const double *B, int64_t ldb, double *C, int64_t ldc);
+
+/* Tall LU with partial pivoting, in place (Algorithm 4 step 1, Algorithm 7
+ * step 1): on return the strict lower part of A holds M (unit diagonal
+ * implied), its top n x n upper triangle holds N, and ipiv (DEVICE, n int32)
+ * holds 0-based row interchanges (row k swapped with ipiv[k] >= k).  The
+ * pivot is the first row of largest magnitude (smallest index on ties).
+ * Returns ERR_LU_ZERO_PIVOT with *col = k for a zero pivot. */
+rclupp_status_t rclupp_tall_lupp(rclupp_handle_t handle, int64_t m, int64_t n, double *A,
+                                 int64_t lda, int32_t *ipiv, int64_t *col);
+
+/* R1 from a sketched s x n matrix Y (Algorithm 6 steps 2-4): LU with partial
+ * pivoting of Y, R-factor of the Householder QR of M, R1 = R0 N, diagonal
+ * signs normalised.  Y is not modified.  Errors: ERR_LU_ZERO_PIVOT. */
+rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t n,
+                                      const double *Y, int64_t ldy, double *R1, int64_t ldr);
+
+/* R-factor of the Householder QR of an s x n matrix A (Algorithm 5 step 2,
+ * Algorithm 6 step 3): LAPACK larfg sign convention, A not modified. */
+rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t n,
+                                     const double *A, int64_t lda, double *R, int64_t ldr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCLUPP_H */

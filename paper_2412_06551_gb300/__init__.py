@@ -1,0 +1,380 @@
+"""GB300 (sm_103a) tall-skinny QR by randomized CholeskyQR with LU partial
+pivoting (RCLUPP, RCLUPPr) plus CholeskyQR2 and LC2 -- Python binding.
+
+The computation lives in ``librclupp.so`` (hand-written CUDA kernels behind
+the C ABI of ``include/rclupp.h``).  This module only marshals arguments:
+it takes torch CUDA tensors (float64), passes their device pointers,
+leading dimensions and the current torch stream to the C entry points of the
+same names, and turns status codes into exceptions.  There is no CPU path:
+without the compiled library on a CUDA device every call raises.
+
+Matrices are column-major: an m x n tensor with strides (1, ld), ld >= m,
+e.g. ``torch.empty((n, m), dtype=torch.float64, device="cuda").t()``.
+Row-major inputs are copied to column-major first (``colmajor``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = [
+    "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
+    "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32",
+    "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
+    "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
+    "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
+    "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r",
+]
+
+SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN = 0, 1
+PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32 = 0, 1, 2
+
+
+class Status:
+    OK = 0
+    ERR_ARG = -1
+    ERR_CHOL_BREAKDOWN = -2
+    ERR_LU_ZERO_PIVOT = -3
+    ERR_NONFINITE = -4
+    ERR_CUDA = -5
+    ERR_TIMEOUT = -6
+    ERR_NOMEM = -7
+    ERR_UNSUPPORTED = -8
+
+
+class Opts(ctypes.Structure):
+    """rclupp_opts_t: sketch kind, zeta, s, seed, precision, optional explicit S."""
+    _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_int32), ("s", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    """rclupp_info_t: status, failed step, failing column."""
+    _fields_ = [("status", ctypes.c_int32), ("failed_step", ctypes.c_int32), ("info", ctypes.c_int64)]
+
+
+class RclupError(RuntimeError):
+    def __init__(self, fn: str, status: int, info: "Info | None" = None):
+        msg = "%s: %s (status %d)" % (fn, _status_string(status), status)
+        if info is not None and info.failed_step:
+            msg += ", step %d, column %d" % (info.failed_step, info.info)
+        super().__init__(msg)
+        self.status = status
+        self.info = info
+
+
+# ------------------------------------------------------------------ loading
+
+_lock = threading.Lock()
+_lib = None
+
+_P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+_SIGNATURES = {
+    "rclupp_create": ([ctypes.POINTER(_P), _P], _I32),
+    "rclupp_destroy": ([_P], _I32),
+    "rclupp_set_stream": ([_P, _P], _I32),
+    "rclupp_workspace_bytes": ([_P, ctypes.POINTER(ctypes.c_size_t)], _I32),
+    "rclupp_status_string": ([_I32], ctypes.c_char_p),
+    "rclupp_factor": ([_P, _I64, _I64, _P, _I64, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
+                       ctypes.POINTER(Info)], _I32),
+    "rclupp_r_factor": ([_P, _I64, _I64, _P, _I64, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
+                         ctypes.POINTER(Info)], _I32),
+    "cholqr2_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
+    "lc2_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
+    "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
+    "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
+    "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_cholesky": ([_P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_int64)], _I32),
+    "rclupp_trmm_upper": ([_P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_tall_lupp": ([_P, _I64, _I64, _P, _I64, _P, ctypes.POINTER(ctypes.c_int64)], _I32),
+    "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGNATURES)
+
+
+def load(build: bool = True):
+    """Load librclupp.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("librclupp.so is missing; run __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _status_string(status: int) -> str:
+    try:
+        return load(build=False).rclupp_status_string(status).decode()
+    except Exception:
+        return "status"
+
+
+# ------------------------------------------------------------------ tensors
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(t):
+    """(tensor, ld) with t column-major (strides (1, ld)); copies when needed."""
+    torch = _torch()
+    if t.dtype != torch.float64:
+        raise TypeError("float64 tensors required")
+    if not t.is_cuda:
+        raise TypeError("CUDA tensors required (the library has no CPU path)")
+    if t.dim() != 2:
+        raise ValueError("2-D tensors required")
+    m, n = t.shape
+    if t.stride(0) == 1 and (n == 1 or t.stride(1) >= max(1, m)):
+        return t, max(t.stride(1), max(1, m)) if n > 1 else max(1, m)
+    c = t.t().contiguous().t()
+    return c, max(1, m)
+
+
+def empty_colmajor(m: int, n: int, device=None):
+    torch = _torch()
+    return torch.empty((n, m), dtype=torch.float64, device=device or "cuda").t()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Handle:
+    """Owns an rclupp handle (workspace + status buffer) on one device."""
+
+    def __init__(self, device=None):
+        torch = _torch()
+        self.device = torch.device(device or "cuda", torch.cuda.current_device()) \
+            if device is None else torch.device(device)
+        self._lib = load()
+        h = _P()
+        with torch.cuda.device(self.device):
+            st = self._lib.rclupp_create(ctypes.byref(h), _P(torch.cuda.current_stream().cuda_stream))
+        if st != Status.OK:
+            raise RclupError("rclupp_create", st)
+        self._h = h
+
+    def bind(self):
+        torch = _torch()
+        self._lib.rclupp_set_stream(self._h, _P(torch.cuda.current_stream(self.device).cuda_stream))
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t(0)
+        self._lib.rclupp_workspace_bytes(self._h, ctypes.byref(v))
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rclupp_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles = {}
+
+
+def _handle(t) -> Handle:
+    idx = t.device.index
+    h = _handles.get(idx)
+    if h is None:
+        h = Handle(t.device)
+        _handles[idx] = h
+    return h
+
+
+def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None):
+    o = Opts()
+    o.kind = int(kind)
+    o.zeta = int(zeta)
+    o.s = int(s if s is not None else 2 * n)
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    o.prec = int(prec)
+    if S is not None:
+        S, lds = colmajor(S)
+        o.S = S.data_ptr()
+        o.lds = lds
+    else:
+        o.S = None
+        o.lds = 0
+    return o, S
+
+
+def _raise(fn, st, info=None, check=True):
+    if st != Status.OK and check:
+        raise RclupError(fn, st, info)
+
+
+# -------------------------------------------------------------- drivers
+
+def _factor(fn_name, X, sketch=True, Q=None, R=None, check=True, **kw):
+    X, ldx = colmajor(X)
+    m, n = X.shape
+    Q = empty_colmajor(m, n, X.device) if Q is None else Q
+    Q, ldq = colmajor(Q)
+    R = empty_colmajor(n, n, X.device) if R is None else R
+    R, ldr = colmajor(R)
+    h = _handle(X)
+    info = Info()
+    lib = load()
+    if sketch:
+        o, S_keep = _opts(n=n, **kw)
+        st = getattr(lib, fn_name)(h.bind(), m, n, _ptr(X), ldx, ctypes.byref(o), _ptr(Q), ldq,
+                                   _ptr(R), ldr, ctypes.byref(info))
+    else:
+        st = getattr(lib, fn_name)(h.bind(), m, n, _ptr(X), ldx, _ptr(Q), ldq, _ptr(R), ldr,
+                                   ctypes.byref(info))
+    _raise(fn_name, st, info, check)
+    return Q, R, info
+
+
+def rclupp_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
+                  Q=None, R=None, check=True):
+    """[Q, R] = RCLUPP(X) (Algorithm 6).  Returns (Q, R, Info)."""
+    return _factor("rclupp_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
+                   prec=prec, S=S)
+
+
+def rclupp_r_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
+                    Q=None, R=None, check=True):
+    """[Q, R] = RCLUPPr(X) (Algorithm 7).  Returns (Q, R, Info)."""
+    return _factor("rclupp_r_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
+                   prec=prec, S=S)
+
+
+def cholqr2_factor(X, *, Q=None, R=None, check=True):
+    """[Q, R] = CholeskyQR2(X) (Algorithm 2).  Returns (Q, R, Info)."""
+    return _factor("cholqr2_factor", X, False, Q, R, check)
+
+
+def lc2_factor(X, *, Q=None, R=None, check=True):
+    """[Q, R] = LC2(X) (Algorithm 4).  Returns (Q, R, Info)."""
+    return _factor("lc2_factor", X, False, Q, R, check)
+
+
+# ---------------------------------------------------------------- steps
+
+def rclupp_sketch(A, *, s, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
+                  unit_lower=False, Y=None):
+    """Y = S A (s x n)."""
+    A, lda = colmajor(A)
+    m, n = A.shape
+    Y = empty_colmajor(s, n, A.device) if Y is None else Y
+    Y, ldy = colmajor(Y)
+    o, S_keep = _opts(kind=kind, s=s, zeta=zeta, seed=seed, prec=prec, S=S, n=n)
+    st = load().rclupp_sketch(_handle(A).bind(), m, n, _ptr(A), lda, int(bool(unit_lower)),
+                              ctypes.byref(o), _ptr(Y), ldy)
+    _raise("rclupp_sketch", st)
+    return Y
+
+
+def rclupp_gram(A, *, unit_lower=False, G=None):
+    """G = A^T A."""
+    A, lda = colmajor(A)
+    m, n = A.shape
+    G = empty_colmajor(n, n, A.device) if G is None else G
+    G, ldg = colmajor(G)
+    st = load().rclupp_gram(_handle(A).bind(), m, n, _ptr(A), lda, int(bool(unit_lower)), _ptr(G),
+                            ldg)
+    _raise("rclupp_gram", st)
+    return G
+
+
+def rclupp_trsm_gram(A, R, *, Q=None, gram=True):
+    """Q = A R^{-1} and (when gram) G = Q^T Q.  Returns (Q, G or None)."""
+    A, lda = colmajor(A)
+    R, ldr = colmajor(R)
+    m, n = A.shape
+    Q = empty_colmajor(m, n, A.device) if Q is None else Q
+    Q, ldq = colmajor(Q)
+    G = empty_colmajor(n, n, A.device) if gram else None
+    ldg = colmajor(G)[1] if gram else 1
+    st = load().rclupp_trsm_gram(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(R), ldr, _ptr(Q), ldq,
+                                 _ptr(G), ldg)
+    _raise("rclupp_trsm_gram", st)
+    return Q, G
+
+
+def rclupp_cholesky(G, *, check=True):
+    """Upper R with G = R^T R.  Returns (R, status, column)."""
+    G, ldg = colmajor(G)
+    n = G.shape[0]
+    R = empty_colmajor(n, n, G.device)
+    col = ctypes.c_int64(-1)
+    st = load().rclupp_cholesky(_handle(G).bind(), n, _ptr(G), ldg, _ptr(R), n, ctypes.byref(col))
+    _raise("rclupp_cholesky", st, None, check)
+    return R, st, int(col.value)
+
+
+def rclupp_trmm_upper(A, B):
+    """C = triu(A) triu(B)."""
+    A, lda = colmajor(A)
+    B, ldb = colmajor(B)
+    n = A.shape[0]
+    C = empty_colmajor(n, n, A.device)
+    st = load().rclupp_trmm_upper(_handle(A).bind(), n, _ptr(A), lda, _ptr(B), ldb, _ptr(C), n)
+    _raise("rclupp_trmm_upper", st)
+    return C
+
+
+def rclupp_tall_lupp(A, *, check=True):
+    """In-place tall LU with partial pivoting on a column-major copy of A.
+    Returns (LU, ipiv (int32, device), status, column)."""
+    torch = _torch()
+    A, lda = colmajor(A)
+    LU = A.clone(memory_format=torch.preserve_format)
+    LU, ldl = colmajor(LU)
+    m, n = LU.shape
+    ipiv = torch.zeros(n, dtype=torch.int32, device=A.device)
+    col = ctypes.c_int64(-1)
+    st = load().rclupp_tall_lupp(_handle(A).bind(), m, n, _ptr(LU), ldl, _ptr(ipiv), ctypes.byref(col))
+    _raise("rclupp_tall_lupp", st, None, check)
+    return LU, ipiv, st, int(col.value)
+
+
+def rclupp_sketch_precond(Y):
+    """R1 from a sketched matrix (Algorithm 6 steps 2-4, signs normalised)."""
+    Y, ldy = colmajor(Y)
+    s, n = Y.shape
+    R1 = empty_colmajor(n, n, Y.device)
+    st = load().rclupp_sketch_precond(_handle(Y).bind(), s, n, _ptr(Y), ldy, _ptr(R1), n)
+    _raise("rclupp_sketch_precond", st)
+    return R1
+
+
+def rclupp_householder_r(A):
+    """R-factor of the Householder QR of A (LAPACK larfg convention)."""
+    A, lda = colmajor(A)
+    s, n = A.shape
+    R = empty_colmajor(n, n, A.device)
+    st = load().rclupp_householder_r(_handle(A).bind(), s, n, _ptr(A), lda, _ptr(R), n)
+    _raise("rclupp_householder_r", st)
+    return R

@@ -1,0 +1,494 @@
+// C ABI of the library (declared in include/rclupp.h): handles, workspace,
+// argument checks, and the drivers that sequence the tall passes and the
+// small factorizations in the order the algorithm boxes fix.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/rclupp.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace rq;
+
+struct rclupp_handle_s {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    DevStatus *d_status = nullptr;
+    DevStatus *h_status = nullptr;  // pinned
+};
+
+namespace {
+
+constexpr int kMaxN = 256;
+constexpr int64_t kMaxS = 4096;
+
+// Carves aligned sub-buffers out of the handle's workspace.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <class T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Device buffers of one factorization.
+struct Bufs {
+    double *part;
+    double *Y;
+    double *W;
+    double *RP[5];
+    double *rinv[5];
+    double *G;
+    void *lu;
+    int32_t *ipiv;
+    double *LUbuf;
+};
+
+Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *total) {
+    Carver c(base);
+    Bufs b;
+    const int n_pad = pad16(n);
+    const size_t part = std::max(gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0));
+    b.part = c.take<double>(part);
+    b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
+    b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
+    for (int i = 0; i < 5; ++i) {
+        b.RP[i] = c.take<double>(size_t(n_pad) * n_pad);
+        b.rinv[i] = c.take<double>(n_pad);
+    }
+    b.G = c.take<double>(size_t(n) * n);
+    b.lu = c.take<char>(lu_scratch_bytes(m, n));
+    b.ipiv = c.take<int32_t>(n);
+    b.LUbuf = need_lu_copy ? c.take<double>(size_t(m) * n) : nullptr;
+    *total = c.off + 256;
+    return b;
+}
+
+rclupp_status_t from_cuda(cudaError_t e) { return e == cudaSuccess ? RCLUPP_OK : RCLUPP_ERR_CUDA; }
+
+rclupp_status_t ensure_ws(rclupp_handle_t h, size_t bytes) {
+    if (h->ws_bytes >= bytes) return RCLUPP_OK;
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RCLUPP_ERR_NOMEM;
+    }
+    h->ws_bytes = bytes;
+    return RCLUPP_OK;
+}
+
+Bufs prepare(rclupp_handle_t h, int64_t m, int n, int64_t s, bool need_lu_copy,
+             rclupp_status_t *status) {
+    size_t total = 0;
+    carve(nullptr, m, n, s, need_lu_copy, &total);
+    *status = ensure_ws(h, total);
+    Bufs b{};
+    if (*status != RCLUPP_OK) return b;
+    b = carve(h->ws, m, n, s, need_lu_copy, &total);
+    if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
+        *status = RCLUPP_ERR_CUDA;
+    return b;
+}
+
+// Waits for the stream and converts the device status.
+rclupp_status_t finish(rclupp_handle_t h, rclupp_status_t launch_status, rclupp_info_t *info,
+                       int64_t *col) {
+    if (launch_status == RCLUPP_OK) {
+        if (cudaMemcpyAsync(h->h_status, h->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                            h->stream) != cudaSuccess)
+            launch_status = RCLUPP_ERR_CUDA;
+    }
+    const cudaError_t se = cudaStreamSynchronize(h->stream);
+    rclupp_status_t st = launch_status;
+    int step = 0;
+    long long inf = -1;
+    if (st == RCLUPP_OK && se != cudaSuccess) st = RCLUPP_ERR_CUDA;
+    if (st == RCLUPP_OK && h->h_status->code != 0) {
+        st = static_cast<rclupp_status_t>(h->h_status->code);
+        step = h->h_status->step;
+        inf = h->h_status->info;
+    }
+    if (info) {
+        info->status = st;
+        info->failed_step = step;
+        info->info = inf;
+    }
+    if (col) *col = inf;
+    return st;
+}
+
+bool bad_ld(int64_t ld, int64_t rows) { return ld < std::max<int64_t>(rows, 1); }
+
+rclupp_status_t check_common(rclupp_handle_t h, int64_t m, int64_t n, const void *X, int64_t ldx,
+                             const void *Q, int64_t ldq, const void *R, int64_t ldr) {
+    if (!h || !X || !Q || !R) return RCLUPP_ERR_ARG;
+    if (n < 1 || m < n) return RCLUPP_ERR_ARG;
+    if (bad_ld(ldx, m) || bad_ld(ldq, m) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    return RCLUPP_OK;
+}
+
+rclupp_opts_t resolve_opts(const rclupp_opts_t *opts, int64_t n) {
+    rclupp_opts_t o;
+    std::memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    else {
+        o.kind = RCLUPP_SKETCH_GAUSSIAN;
+        o.s = 2 * n;
+        o.zeta = 8;
+        o.seed = 0;
+        o.prec = RCLUPP_PREC_FP64;
+    }
+    return o;
+}
+
+rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
+    if (o.s < n || o.s > kMaxS) return o.s < n ? RCLUPP_ERR_ARG : RCLUPP_ERR_UNSUPPORTED;
+    if (o.kind != RCLUPP_SKETCH_GAUSSIAN && o.kind != RCLUPP_SKETCH_SPARSE_SIGN) return RCLUPP_ERR_ARG;
+    if (o.S && o.lds < o.s) return RCLUPP_ERR_ARG;
+    if (o.kind == RCLUPP_SKETCH_SPARSE_SIGN && !o.S) {
+        if (o.zeta < 1 || o.zeta > o.s) return RCLUPP_ERR_ARG;
+        if (o.zeta > 16) return RCLUPP_ERR_UNSUPPORTED;
+        const size_t smem = size_t(round_up(o.s, 64)) * 32 * 8 + 64 * 33 * 8 + 64 * 16 * 4;
+        if (smem > 220 * 1024) return RCLUPP_ERR_UNSUPPORTED;
+    }
+    if (o.prec != RCLUPP_PREC_FP64) return RCLUPP_ERR_UNSUPPORTED;
+    (void)m;
+    return RCLUPP_OK;
+}
+
+#define RQ_TRY(expr)                                     \
+    do {                                                 \
+        const cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return RCLUPP_ERR_CUDA;   \
+    } while (0)
+
+// Steps 5-7 of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
+// b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
+// R = R4 (R2 R1).
+rclupp_status_t precond_then_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
+                                     const double *X, int64_t ldx, double *Q, int64_t ldq,
+                                     double *R, int64_t ldr) {
+    cudaStream_t s = h->stream;
+    DevStatus *st = h->d_status;
+    const int np = pad16(n);
+    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, st, 3, s));
+    RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
+    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[3], b.rinv[3], nullptr, 0, st, 4, s));
+    RQ_TRY(launch_trmm_upper(b.RP[3], np, b.RP[2], np, n, R, ldr, s));  // R = R4 R3
+    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, nullptr, 0, b.part, st, s));
+    return RCLUPP_OK;
+}
+
+// copy an m x n matrix (device to device, possibly different leading dims)
+cudaError_t copy_matrix(double *dst, int64_t ldd, const double *src, int64_t lds, int64_t m,
+                        int64_t n, cudaStream_t s) {
+    return cudaMemcpy2DAsync(dst, size_t(ldd) * 8, src, size_t(lds) * 8, size_t(m) * 8, size_t(n),
+                             cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+rclupp_status_t rclupp_create(rclupp_handle_t *handle, void *stream) {
+    if (!handle) return RCLUPP_ERR_ARG;
+    *handle = nullptr;
+    rclupp_handle_s *h = new (std::nothrow) rclupp_handle_s();
+    if (!h) return RCLUPP_ERR_NOMEM;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaMalloc(&h->d_status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&h->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->d_status) cudaFree(h->d_status);
+        delete h;
+        return RCLUPP_ERR_CUDA;
+    }
+    cudaMemset(h->d_status, 0, sizeof(DevStatus));
+    *handle = h;
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_destroy(rclupp_handle_t h) {
+    if (!h) return RCLUPP_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    delete h;
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_set_stream(rclupp_handle_t h, void *stream) {
+    if (!h) return RCLUPP_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_workspace_bytes(rclupp_handle_t h, size_t *bytes) {
+    if (!h || !bytes) return RCLUPP_ERR_ARG;
+    *bytes = h->ws_bytes;
+    return RCLUPP_OK;
+}
+
+const char *rclupp_status_string(int status) {
+    switch (status) {
+        case RCLUPP_OK: return "ok";
+        case RCLUPP_ERR_ARG: return "invalid argument";
+        case RCLUPP_ERR_CHOL_BREAKDOWN: return "Cholesky breakdown";
+        case RCLUPP_ERR_LU_ZERO_PIVOT: return "zero pivot in LU";
+        case RCLUPP_ERR_NONFINITE: return "non-finite value";
+        case RCLUPP_ERR_CUDA: return "CUDA error";
+        case RCLUPP_ERR_TIMEOUT: return "device wait timed out";
+        case RCLUPP_ERR_NOMEM: return "out of device memory";
+        case RCLUPP_ERR_UNSUPPORTED: return "unsupported size or option";
+        default: return "unknown status";
+    }
+}
+
+rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
+                              int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                              double *R, int64_t ldr, rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    const rclupp_opts_t o = resolve_opts(opts, n);
+    if ((st = check_opts(o, m, n)) != RCLUPP_OK) return st;
+    Bufs b = prepare(h, m, int(n), o.s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaStream_t s = h->stream;
+    DevStatus *ds = h->d_status;
+    const int ni = int(n), si = int(o.s);
+    rclupp_status_t ls = RCLUPP_OK;
+    do {
+        // X_s = S X (step 1)
+        if (launch_sketch(X, ldx, m, ni, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
+                          ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        // [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M); R1 = R0 N (steps 2-4)
+        if (launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s) !=
+            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        ls = precond_then_cholqr2(h, b, m, ni, X, ldx, Q, ldq, R, ldr);
+    } while (0);
+    return finish(h, ls, info, nullptr);
+}
+
+rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
+                                int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                                double *R, int64_t ldr, rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    const rclupp_opts_t o = resolve_opts(opts, n);
+    if ((st = check_opts(o, m, n)) != RCLUPP_OK) return st;
+    const bool alias = (Q == X);
+    Bufs b = prepare(h, m, int(n), o.s, alias, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaStream_t s = h->stream;
+    DevStatus *ds = h->d_status;
+    const int ni = int(n), si = int(o.s);
+    double *L = alias ? b.LUbuf : Q;
+    const int64_t ldl = alias ? m : ldq;
+    rclupp_status_t ls = RCLUPP_OK;
+    do {
+        if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        // [M, N, P] = LU(X) (step 1)
+        if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        // M_s = S M (step 2)
+        if (launch_sketch(L, ldl, m, ni, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s,
+                          b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        // R0 = R of HouseholderQR(M_s); R1 = R0 N (steps 3-4)
+        if (launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        ls = precond_then_cholqr2(h, b, m, ni, X, ldx, Q, ldq, R, ldr);
+    } while (0);
+    return finish(h, ls, info, nullptr);
+}
+
+rclupp_status_t cholqr2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
+                               int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
+                               rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaStream_t s = h->stream;
+    DevStatus *ds = h->d_status;
+    const int ni = int(n), np = pad16(ni);
+    rclupp_status_t ls = RCLUPP_OK;
+    do {
+        // [Q1, R1] = CholeskyQR(X)
+        if (launch_gram(X, ldx, m, ni, 0, b.G, n, b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_cholesky(b.G, n, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 3, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        // [Q, Z] = CholeskyQR(Q1)
+        if (launch_trsm_gram(X, ldx, m, ni, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, ds, s) !=
+            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_cholesky(b.G, n, ni, b.W, b.RP[1], b.rinv[1], nullptr, 0, ds, 4, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        // R = Z R1
+        if (launch_trmm_upper(b.RP[1], np, b.RP[0], np, ni, R, ldr, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_trsm_gram(Q, ldq, m, ni, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, ds, s) !=
+            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+    } while (0);
+    return finish(h, ls, info, nullptr);
+}
+
+rclupp_status_t lc2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X, int64_t ldx,
+                           double *Q, int64_t ldq, double *R, int64_t ldr, rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    const bool alias = (Q == X);
+    Bufs b = prepare(h, m, int(n), n, alias, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaStream_t s = h->stream;
+    DevStatus *ds = h->d_status;
+    const int ni = int(n), np = pad16(ni);
+    double *L = alias ? b.LUbuf : Q;
+    const int64_t ldl = alias ? m : ldq;
+    rclupp_status_t ls = RCLUPP_OK;
+    do {
+        if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        // [M, N, P] = LU(X)
+        if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        // G = M^T M; S = chol(G); R1 = S N
+        if (launch_gram(L, ldl, m, ni, 1, b.G, n, b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_cholesky(b.G, n, ni, b.W, b.RP[4], b.rinv[4], nullptr, 0, ds, 3, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_lc2_r1(b.RP[4], np, L, ldl, ni, b.RP[0], b.rinv[0], s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
+        if (launch_trsm_gram(X, ldx, m, ni, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, ds, s) !=
+            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_cholesky(b.G, n, ni, b.W, b.RP[1], b.rinv[1], nullptr, 0, ds, 4, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_trmm_upper(b.RP[1], np, b.RP[0], np, ni, R, ldr, s) != cudaSuccess) {
+            ls = RCLUPP_ERR_CUDA; break; }
+        if (launch_trsm_gram(Q, ldq, m, ni, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, ds, s) !=
+            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
+    } while (0);
+    return finish(h, ls, info, nullptr);
+}
+
+// ---- individual steps ----
+
+rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const double *A, int64_t lda,
+                              int32_t unit_lower, const rclupp_opts_t *opts, double *Y,
+                              int64_t ldy) {
+    if (!h || !A || !Y || n < 1 || m < 1 || bad_ld(lda, m)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    const rclupp_opts_t o = resolve_opts(opts, n);
+    rclupp_status_t st = check_opts(o, m, n);
+    if (st != RCLUPP_OK) return st;
+    if (bad_ld(ldy, o.s)) return RCLUPP_ERR_ARG;
+    Bufs b = prepare(h, m, int(n), o.s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed,
+                                        o.S, o.lds, Y, ldy, b.part, h->d_status, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_gram(rclupp_handle_t h, int64_t m, int64_t n, const double *A, int64_t lda,
+                            int32_t unit_lower, double *G, int64_t ldg) {
+    if (!h || !A || !G || n < 1 || m < 1 || bad_ld(lda, m) || bad_ld(ldg, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e =
+        launch_gram(A, lda, m, int(n), unit_lower, G, ldg, b.part, h->d_status, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_trsm_gram(rclupp_handle_t h, int64_t m, int64_t n, const double *A,
+                                 int64_t lda, const double *R, int64_t ldr, double *Q, int64_t ldq,
+                                 double *G, int64_t ldg) {
+    if (!h || !A || !R || !Q || n < 1 || m < 1 || bad_ld(lda, m) || bad_ld(ldr, n) || bad_ld(ldq, m))
+        return RCLUPP_ERR_ARG;
+    if (G && bad_ld(ldg, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaError_t e = launch_pad_upper(R, ldr, int(n), b.RP[0], b.rinv[0], h->stream);
+    if (e == cudaSuccess)
+        e = launch_trsm_gram(A, lda, m, int(n), b.RP[0], b.rinv[0], Q, ldq, G, ldg, b.part,
+                             h->d_status, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_cholesky(rclupp_handle_t h, int64_t n, const double *G, int64_t ldg,
+                                double *R, int64_t ldr, int64_t *col) {
+    if (!h || !G || !R || n < 1 || bad_ld(ldg, n) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, n, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_cholesky(G, ldg, int(n), b.W, b.RP[0], b.rinv[0], R, ldr,
+                                          h->d_status, 3, h->stream);
+    return finish(h, from_cuda(e), nullptr, col);
+}
+
+rclupp_status_t rclupp_trmm_upper(rclupp_handle_t h, int64_t n, const double *A, int64_t lda,
+                                  const double *B, int64_t ldb, double *C, int64_t ldc) {
+    if (!h || !A || !B || !C || n < 1 || bad_ld(lda, n) || bad_ld(ldb, n) || bad_ld(ldc, n))
+        return RCLUPP_ERR_ARG;
+    if (n > kMaxN) return RCLUPP_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
+        return RCLUPP_ERR_CUDA;
+    const cudaError_t e = launch_trmm_upper(A, lda, B, ldb, int(n), C, ldc, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_tall_lupp(rclupp_handle_t h, int64_t m, int64_t n, double *A, int64_t lda,
+                                 int32_t *ipiv, int64_t *col) {
+    if (!h || !A || !ipiv || n < 1 || m < n || bad_ld(lda, m)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_tall_lupp(A, lda, m, int(n), ipiv, b.lu, h->d_status, 2, h->stream);
+    return finish(h, from_cuda(e), nullptr, col);
+}
+
+rclupp_status_t rclupp_sketch_precond(rclupp_handle_t h, int64_t s, int64_t n, const double *Y,
+                                      int64_t ldy, double *R1, int64_t ldr) {
+    if (!h || !Y || !R1 || n < 1 || s < n || bad_ld(ldy, s) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || s > kMaxS) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, s, int(n), s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_sketch_precond(Y, ldy, int(s), int(n), b.W, b.RP[0], b.rinv[0], R1,
+                                                ldr, h->d_status, 1, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_householder_r(rclupp_handle_t h, int64_t s, int64_t n, const double *A,
+                                     int64_t lda, double *R, int64_t ldr) {
+    if (!h || !A || !R || n < 1 || s < n || bad_ld(lda, s) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || s > kMaxS) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, s, int(n), s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_householder_r(A, lda, int(s), int(n), b.W, R, ldr, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Host-side launchers of the library's kernels (internal interface between
+// the C-ABI layer and the kernel translation units).  All pointers are
+// device pointers; every launcher enqueues on `stream` and returns the CUDA
+// launch status.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rq {
+
+// Number of streaming multiprocessors of the current device (cached).
+int num_sms();
+
+// Builds a 2-D TMA descriptor for a column-major FP64 matrix (rows x cols,
+// leading dimension ld) with a box of box_rows x box_cols.  Returns false
+// when the matrix does not meet TMA's alignment rules (16-byte base address,
+// 16-byte multiple stride) or the encoder is unavailable; callers then use
+// plain loads.
+bool make_tma_map(CUtensorMap *map, const double *A, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols);
+
+// ---- tall passes (tall.cu) ----
+struct TallPlan {
+    int bm;          // rows per tile
+    int ncb;         // columns per tile slice (TMA box width)
+    int64_t chunk;   // rows per CTA (multiple of bm)
+    int grid_x;      // CTAs along the rows
+};
+
+// Row partition of an m-row pass for a kernel with `ctas_per_sm` resident
+// CTAs, rows per tile bm, and `ytiles` independent column/output tiles.
+TallPlan plan_rows(int64_t m, int bm, int ctas_per_sm, int ytiles);
+
+// Partial-sum buffer sizes (doubles).
+size_t gram_partials_doubles(int64_t m, int n);
+size_t sketch_partials_doubles(int64_t m, int n, int64_t s, int kind);
+
+// G = A^T A into G (ldg), partial buffer `part` of gram_partials_doubles().
+cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit_lower, double *G,
+                        int64_t ldg, double *part, DevStatus *st, cudaStream_t stream);
+
+// Q = A R^{-1} with R given as a padded upper factor RP (n_pad x n_pad,
+// ld n_pad, zeros elsewhere) and rinv[n_pad] = 1 / diag; optionally G = Q^T Q.
+cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                             const double *rinv, double *Q, int64_t ldq, double *G, int64_t ldg,
+                             double *part, DevStatus *st, cudaStream_t stream);
+
+// Y = S A (s x n, ldy); kind 0 Gaussian (generated from seed, or explicit S
+// when S != nullptr), kind 1 sparse-sign.
+cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int kind,
+                          int64_t s, int zeta, uint64_t seed, const double *S, int64_t lds,
+                          double *Y, int64_t ldy, double *part, DevStatus *st,
+                          cudaStream_t stream);
+
+// Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
+cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,
+                             cudaStream_t stream);
+
+
+// ---- tall LU with partial pivoting (lu.cu) ----
+size_t lu_scratch_bytes(int64_t m, int n);
+cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *ipiv,
+                             void *scratch, DevStatus *st, int step_id, cudaStream_t stream);
+
+// ---- small dense factorizations on one CTA (small.cu) ----
+// R1 from the sketch Y (s x n): LU with partial pivoting, Householder R of
+// M, R1 = R0 N, diagonal signs normalised.  Writes R1 into RP/rinv (padded)
+// and, when R1 != nullptr, into R1 (ld ldr).  W: s*n*2 doubles scratch.
+cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, double *W,
+                                  double *RP, double *rinv, double *R1, int64_t ldr,
+                                  DevStatus *st, int step_id, cudaStream_t stream);
+
+// RCLUPPr's R1 from the sketched factor M_s (s x n): Householder R of M_s,
+// R1 = R0 N with N the top of the in-place tall LU (lda), signs normalised.
+// W: 2*s*n scratch.
+cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const double *LU,
+                              int64_t lda, double *W, double *RP, double *rinv,
+                              cudaStream_t stream);
+
+// R-factor of the Householder QR of A (s x n) into R (ldr); W: s*n scratch.
+cudaError_t launch_householder_r(const double *A, int64_t lda, int s, int n, double *W, double *R,
+                                 int64_t ldr, cudaStream_t stream);
+
+// Upper Cholesky of G (n x n); writes padded RP/rinv and, when R != nullptr,
+// R (ldr).  W: n*n scratch.  Breakdown -> status with step_id and column.
+cudaError_t launch_cholesky(const double *G, int64_t ldg, int n, double *W, double *RP,
+                            double *rinv, double *R, int64_t ldr, DevStatus *st, int step_id,
+                            cudaStream_t stream);
+
+// C = triu(A) triu(B) (n x n), written to C (ldc) with zeros below the diagonal.
+cudaError_t launch_trmm_upper(const double *A, int64_t lda, const double *B, int64_t ldb, int n,
+                              double *C, int64_t ldc, cudaStream_t stream);
+
+// LC2's R1 = Sc N with N read from the top of an in-place LU (lda), signs
+// normalised; output padded RP/rinv.
+cudaError_t launch_lc2_r1(const double *Sc, int64_t lds, const double *LU, int64_t lda, int n,
+                          double *RP, double *rinv, cudaStream_t stream);
+
+}  // namespace rq

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point that include/rclupp.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2412_06551_gb300 as rq
+from paper_2412_06551_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdrs = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+            if f.endswith(".h")]
+    names = set()
+    for h in hdrs:
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for mt in re.finditer(r"\b(?:rclupp_status_t|const char \*)\s*\*?\s*(\w+)\s*\(", txt):
+            names.add(mt.group(1))
+    return names
+
+
+def test_library_builds_and_loads():
+    path = _build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    assert lib is not None
+
+
+def test_every_declared_symbol_is_exported():
+    declared = _declared()
+    assert {"rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor"} <= declared
+    lib = ctypes.CDLL(_build.build())
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    assert set(rq.exported_symbols()) == _declared()
+
+
+def test_status_strings_without_gpu():
+    lib = rq.load()
+    assert lib.rclupp_status_string(0) == b"ok"
+    assert lib.rclupp_status_string(-2) == b"Cholesky breakdown"
+
+
+def test_argument_errors_before_any_gpu_work():
+    # NULL handle / bad sizes are rejected on the host, with no CUDA call.
+    lib = rq.load()
+    info = rq.Info()
+    st = lib.cholqr2_factor(None, 10, 4, None, 10, None, 10, None, 4, ctypes.byref(info))
+    assert st == rq.Status.ERR_ARG
+    assert lib.rclupp_create(None, None) == rq.Status.ERR_ARG
+
+
+def test_no_cpu_fallback_in_the_binding():
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((8, 2), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        rq.cholqr2_factor(x)
