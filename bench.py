@@ -1,0 +1,423 @@
+"""Benchmark: FP64 RCLUPP, RCLUPPr, CholeskyQR2 and LC2 side by side on one
+tall-skinny matrix (m = 2^20, n = 128, Gaussian sketch s = 256).
+
+One step = the four factorizations of the same resident X through the C ABI
+(every row of the tall path runs: Gaussian sketch, tall LU with partial
+pivoting, sketch of M, small LU / Householder / Cholesky, fused TRSM + Gram
+passes, final TRSM).  Metric: TSQR GFLOP/s in the 2 m n^2 model, summed over
+the four factorizations.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own matrix (replicas, weak
+scaling, no collective on the data path); timing is the max over ranks.
+--impl reference times the CPU oracle (the plain FP64 C implementation) on a
+bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+M, N, S_SKETCH, KAPPA = 1 << 20, 128, 256, 1e4
+SEED_X, SEED_S = synth.kappa_seed(1, 0), synth.kappa_seed(1, 0) + 7
+PATHS = ["rclupp", "rcluppr", "cholqr2", "lc2"]
+# algorithmic FP64 flops per factorization (leading terms, 2-flop FMAs):
+#   RCLUPP  : sketch 2smn + 2 x (TRSM mn^2 + Gram mn^2) + final TRSM mn^2
+#   RCLUPPr : + tall LU mn^2 (the sketch of M replaces the sketch of X)
+#   CholeskyQR2: Gram + (TRSM + Gram) + TRSM = 4 mn^2;  LC2: LU + 4 mn^2
+ALGO_FLOPS = {
+    "rclupp": lambda m, n, s: 2 * s * m * n + 5 * m * n * n,
+    "rcluppr": lambda m, n, s: 2 * s * m * n + 6 * m * n * n,
+    "cholqr2": lambda m, n, s: 4 * m * n * n,
+    "lc2": lambda m, n, s: 5 * m * n * n,
+}
+SAMPLE_M = 1 << 15  # rows of the CPU-oracle sample
+METRIC = "TSQR GFLOP/s (2mn^2 model) & roofline fraction, mixed vs FP64 at equal ||Q^T Q - I||"
+FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9  # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+
+
+def workload_config():
+    return {
+        "workload": "FP64 RCLUPP + RCLUPPr + CholeskyQR2 + LC2 side by side, one tall-skinny X",
+        "m": M, "n": N, "s": S_SKETCH, "sketch": "gaussian N(0,1/s), generated on the fly",
+        "kappa": KAPPA, "matrix": "U diag(sigma) V^T, sigma geometric 1 .. 1/kappa",
+        "seed_x": SEED_X, "seed_s": SEED_S,
+        "l2": "input 1.07 GB > 129 MB L2, no flush between steps",
+        "parallelism": "replicas",
+    }
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--accuracy-sweep", action="store_true",
+                   help="also report orthogonality/residual at kappa 1e10 and 1e15")
+    p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "sketch_gauss", "sketch_sparse",
+                                      "lu", "rclupp"],
+                   help="run one kernel class on an m x n matrix instead (profiler captures)")
+    p.add_argument("--m", type=int, default=1 << 18)
+    p.add_argument("--n", type=int, default=N)
+    p.add_argument("--reps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample_step(x, S):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.rclupp(x, S=S)
+    oracle.rcluppr(x, S=S)
+    oracle.cholqr2(x)
+    oracle.lc2(x)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_inputs():
+    xs = synth.svd_matrix(SAMPLE_M, N, KAPPA, SEED_X)
+    Ss = synth.gaussian_sketch(S_SKETCH, SAMPLE_M, SEED_S)
+    return xs, Ss
+
+
+def cpu_baseline(repeats=1):
+    import oracle
+    xs, Ss = oracle_sample_inputs()
+    t = min(oracle_sample_step(xs, Ss) for _ in range(repeats))
+    model = len(PATHS) * 2.0 * SAMPLE_M * N * N
+    return {
+        "value": model / t / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+        "sample": "the four factorizations on a %d x %d row sample of the same construction "
+                  "(kappa %.0e, Gaussian s=%d), %.2f s per sample" % (SAMPLE_M, N, KAPPA, S_SKETCH, t),
+    }
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    xs, Ss = oracle_sample_inputs()
+    for _ in range(args.warmup):
+        oracle_sample_step(xs, Ss)
+    times = [oracle_sample_step(xs, Ss) for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    model = len(PATHS) * 2.0 * SAMPLE_M * N * N
+    val = model / t / 1e9
+    sample = "the four factorizations on a %d x %d row sample of the workload" % (SAMPLE_M, N)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU ---
+
+def to_dev(a, torch, device):
+    a = np.asfortranarray(a)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()
+
+
+def run_paths(rq, X, outs, torch):
+    Qs, Rs = outs
+    rq.rclupp_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[0], R=Rs[0])
+    rq.rclupp_r_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[1], R=Rs[1])
+    rq.cholqr2_factor(X, Q=Qs[2], R=Rs[2])
+    rq.lc2_factor(X, Q=Qs[3], R=Rs[3])
+
+
+def accuracy(torch, X, Q, R):
+    n = Q.shape[1]
+    eye = torch.eye(n, dtype=torch.float64, device=Q.device)
+    orth = float(torch.linalg.norm(Q.t() @ Q - eye))
+    res = float(torch.linalg.norm(Q @ R - X) / torch.linalg.norm(X))
+    return orth, res
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", torch.cuda.current_device())
+    import paper_2412_06551_gb300 as rq
+    rq.load()
+
+    x = synth.svd_matrix(M, N, KAPPA, SEED_X + rank)
+    X = to_dev(x, torch, device)
+    Qs = [rq.empty_colmajor(M, N, device) for _ in PATHS]
+    Rs = [rq.empty_colmajor(N, N, device) for _ in PATHS]
+    stream = torch.cuda.current_stream(device)
+
+    for _ in range(max(3, args.warmup)):
+        run_paths(rq, X, (Qs, Rs), torch)
+    torch.cuda.synchronize()
+
+    # per-path times (untimed for the metric; one pass each)
+    path_ms = {}
+    for i, name in enumerate(PATHS):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if name == "rclupp":
+            rq.rclupp_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[0], R=Rs[0])
+        elif name == "rcluppr":
+            rq.rclupp_r_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[1], R=Rs[1])
+        elif name == "cholqr2":
+            rq.cholqr2_factor(X, Q=Qs[2], R=Rs[2])
+        else:
+            rq.lc2_factor(X, Q=Qs[3], R=Rs[3])
+        e1.record(stream)
+        e1.synchronize()
+        path_ms[name] = e0.elapsed_time(e1)
+
+    # ---- timed region (device-resident inputs) ----
+    sampler = ClockSampler(local) if rank == 0 else None
+    rq.profile_reset()
+    rq.profile_enable(True)
+    launches0 = rq.kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run_paths(rq, X, (Qs, Rs), torch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = rq.kernel_launches() - launches0
+    rq.profile_enable(False)
+    prof = rq.profile_read()
+    clocks = sampler.stop() if sampler else None
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    model_flops = len(PATHS) * 2.0 * M * N * N
+    value = world * model_flops * args.steps / (t_ms / 1e3) / 1e9
+
+    # ---- end to end: pinned host X in, Q and R of every path out ----
+    xh = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T)).pin_memory()
+    Xd = torch.empty((N, M), dtype=torch.float64, device=device)
+    qh = [torch.empty((N, M), dtype=torch.float64).pin_memory() for _ in PATHS]
+    rh = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in PATHS]
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        Xd.copy_(xh, non_blocking=True)
+        run_paths(rq, Xd.t(), (Qs, Rs), torch)
+        for i in range(len(PATHS)):
+            qh[i].copy_(Qs[i].t(), non_blocking=True)
+            rh[i].copy_(Rs[i].t(), non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = M * N * 8
+    d2h = len(PATHS) * (M * N * 8 + N * N * 8)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # accuracy of the timed run (same X) and optional kappa sweep
+    acc = {}
+    for i, name in enumerate(PATHS):
+        o, r = accuracy(torch, X, Qs[i], Rs[i])
+        acc[name] = {"orth": o, "res": r}
+    sweep = {}
+    if args.accuracy_sweep:
+        for k_i, kap in ((1, 1e10), (2, 1e15)):
+            xk = to_dev(synth.svd_matrix(M, N, kap, synth.kappa_seed(1, k_i)), torch, device)
+            row = {}
+            for name, fn in (("rclupp", lambda Z: rq.rclupp_factor(Z, s=S_SKETCH, seed=SEED_S, check=False)),
+                             ("rcluppr", lambda Z: rq.rclupp_r_factor(Z, s=S_SKETCH, seed=SEED_S, check=False)),
+                             ("cholqr2", lambda Z: rq.cholqr2_factor(Z, check=False)),
+                             ("lc2", lambda Z: rq.lc2_factor(Z, check=False))):
+                Q, R, info = fn(xk)
+                if info.status != 0:
+                    row[name] = {"status": int(info.status), "step": int(info.failed_step)}
+                else:
+                    o, r = accuracy(torch, xk, Q, R)
+                    row[name] = {"orth": o, "res": r}
+            sweep["%.0e" % kap] = row
+            del xk
+
+    # dominant kernel: largest share of the timed kernel time
+    tot = {k: v for k, v in prof.items() if v[0] > 0}
+    dom = max(tot, key=lambda k: tot[k][1])
+    dom_launches, dom_ms = tot[dom]
+    avg_ms = dom_ms / dom_launches
+    per_launch_flops = {
+        "trsm_gram": M * (2.0 * N * N + N),
+        "trsm": M * 1.0 * N * N,
+        "gram": M * 1.0 * N * (N + 1),
+        "sketch_gauss": 2.0 * S_SKETCH * M * N,
+    }
+    ach = per_launch_flops.get(dom, float("nan")) / (avg_ms / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
+                "avg_launch_ms": avg_ms, "launches": dom_launches}
+    kernel_share = {k: round(v[1] / sum(w[1] for w in tot.values()), 4) for k, v in tot.items()}
+
+    paths = {}
+    for name in PATHS:
+        f = ALGO_FLOPS[name](M, N, S_SKETCH)
+        t = path_ms[name] / 1e3
+        paths[name] = {"ms": path_ms[name], "gflops_2mn2": 2.0 * M * N * N / t / 1e9,
+                       "fp64_gflops": f / t / 1e9, "roofline_frac": f / t / 1e9 / FP64_PEAK_GFLOPS,
+                       **acc[name]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(), "roofline": roofline, "kernel_share": kernel_share,
+        "paths": paths, "gpu_launches": int(launches),
+        "e2e": {"value": world * model_flops / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "clocks": clocks,
+    }
+    if sweep:
+        line["accuracy_sweep"] = sweep
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_case(args):
+    """One kernel class on a smaller matrix (for profiler captures)."""
+    import torch
+    import paper_2412_06551_gb300 as rq
+    m, n = args.m, args.n
+    x = synth.svd_matrix(m, n, KAPPA, SEED_X) if m <= (1 << 20) else \
+        np.asfortranarray(synth.rng(SEED_X).standard_normal((m, n)))
+    device = torch.device("cuda", 0)
+    X = to_dev(x, torch, device)
+    R = to_dev(np.triu(synth.rng(3).standard_normal((n, n))) / math.sqrt(n) + 2 * np.eye(n), torch,
+               device)
+    for _ in range(args.reps):
+        if args.case == "trsm_gram":
+            rq.rclupp_trsm_gram(X, R)
+        elif args.case == "trsm":
+            rq.rclupp_trsm_gram(X, R, gram=False)
+        elif args.case == "gram":
+            rq.rclupp_gram(X)
+        elif args.case == "sketch_gauss":
+            rq.rclupp_sketch(X, s=2 * n, seed=1)
+        elif args.case == "sketch_sparse":
+            rq.rclupp_sketch(X, s=2 * n, kind=rq.SKETCH_SPARSE_SIGN, zeta=8, seed=1)
+        elif args.case == "lu":
+            rq.rclupp_tall_lupp(X)
+        elif args.case == "rclupp":
+            rq.rclupp_factor(X, s=2 * n, seed=1)
+    torch.cuda.synchronize()
+    print("case %s m=%d n=%d reps=%d done" % (args.case, m, n, args.reps))
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,22 @@ rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t
 rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t n,
                                      const double *A, int64_t lda, double *R, int64_t ldr);
 
+/* ---- instrumentation (no counterpart in the paper) ----------------------
+ * Launch accounting and per-kernel timing for benchmarks.  Every kernel the
+ * library launches increments a process-wide counter.  When profiling is
+ * enabled, a CUDA event pair is recorded on the launching stream around each
+ * kernel; rclupp_profile_get synchronizes on the recorded events and returns,
+ * for one kernel class (0 <= kid < 13), the number of timed launches, their
+ * summed duration in milliseconds and the class name (static string).
+ * Classes: 0 sketch_gauss, 1 sketch_sparse, 2 gram, 3 trsm_gram (fused
+ * TRSM + Gram), 4 trsm, 5 reduce, 6 lu_col, 7 lu_trailing, 8 lu_u12,
+ * 9 small_precond, 10 cholesky, 11 trmm, 12 pad.  Returns ERR_ARG for an
+ * invalid class. */
+void rclupp_profile_enable(int enable);
+void rclupp_profile_reset(void);
+int rclupp_profile_get(int kid, long long *launches, double *total_ms, const char **name);
+unsigned long long rclupp_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

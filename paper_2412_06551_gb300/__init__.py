@@ -27,6 +27,7 @@ __all__ = [
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
     "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r",
+    "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
 ]
 
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN = 0, 1
@@ -93,7 +94,42 @@ _SIGNATURES = {
     "rclupp_tall_lupp": ([_P, _I64, _I64, _P, _I64, _P, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_profile_enable": ([ctypes.c_int], None),
+    "rclupp_profile_reset": ([], None),
+    "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)], _I32),
+    "rclupp_kernel_launches": ([], ctypes.c_ulonglong),
 }
+
+KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
+                  "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad"]
+
+
+def profile_enable(on: bool = True) -> None:
+    """Time every kernel launch with CUDA events on its stream (benchmarks)."""
+    load().rclupp_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    load().rclupp_profile_reset()
+
+
+def profile_read() -> dict:
+    """{class name: (timed launches, total ms)} for every kernel class."""
+    lib = load()
+    out = {}
+    for kid in range(len(KERNEL_CLASSES)):
+        n = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0.0)
+        name = ctypes.c_char_p()
+        lib.rclupp_profile_get(kid, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(name))
+        out[name.value.decode()] = (int(n.value), float(ms.value))
+    return out
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().rclupp_kernel_launches())
 
 
 def library_path() -> str:

@@ -100,3 +100,39 @@ cudaError_t launch_lc2_r1(const double *Sc, int64_t lds, const double *LU, int64
                           double *RP, double *rinv, cudaStream_t stream);
 
 }  // namespace rq
+
+namespace rq {
+
+// ---- launch accounting and per-kernel timing (prof.cu) ----
+// Kernel classes timed by the optional profiler.
+enum KernelId : int {
+    KID_SKETCH_GAUSS = 0,
+    KID_SKETCH_SPARSE,
+    KID_GRAM,
+    KID_TRSM_GRAM,
+    KID_TRSM,
+    KID_REDUCE,
+    KID_LU_COL,
+    KID_LU_TRAILING,
+    KID_LU_U12,
+    KID_SMALL_PRECOND,
+    KID_CHOLESKY,
+    KID_TRMM,
+    KID_PAD,
+    KID_COUNT
+};
+
+// Every kernel launch of the library goes through these two calls: the
+// launch counter is always kept; when profiling is enabled an event pair
+// brackets the launch on its stream.
+void prof_begin(int kid, cudaStream_t stream);
+void prof_end(int kid, cudaStream_t stream);
+
+#define RQ_LAUNCH(KID, STREAM, ...)       \
+    do {                                  \
+        ::rq::prof_begin((KID), (STREAM)); \
+        __VA_ARGS__;                      \
+        ::rq::prof_end((KID), (STREAM));   \
+    } while (0)
+
+}  // namespace rq

@@ -222,8 +222,8 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
     cudaFuncSetAttribute(k_lu_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax));
     int64_t chunk;
     int g = lu_grid(m, chunk);
-    k_lu_trailing<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, 0, 0, chunk, cands, ticket, ipiv, st,
-                                                step_id);
+    RQ_LAUNCH(KID_LU_TRAILING, stream, k_lu_trailing<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, 0, 0, chunk, cands, ticket, ipiv, st,
+                                                step_id));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int k0 = 0; k0 < n; k0 += kLuNB) {
         const int pe = std::min(n, k0 + kLuNB);
@@ -231,18 +231,18 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
             const int64_t rows = m - k - 1;
             if (rows <= 0) break;
             g = lu_grid(rows, chunk);
-            k_lu_col<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, k, pe, chunk, cands, ticket, ipiv,
-                                                   st, step_id);
+            RQ_LAUNCH(KID_LU_COL, stream, k_lu_col<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, k, pe, chunk, cands, ticket, ipiv,
+                                                   st, step_id));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (pe < n) {
-            k_lu_u12<<<1, kLuThreads, 0, stream>>>(A, lda, n, k0, pe);
+            RQ_LAUNCH(KID_LU_U12, stream, k_lu_u12<<<1, kLuThreads, 0, stream>>>(A, lda, n, k0, pe));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             const int64_t rows = m - pe;
             g = lu_grid(rows, chunk);
             const size_t sm = size_t(pe - k0) * (n - pe) * sizeof(double);
-            k_lu_trailing<<<g, kLuThreads, sm, stream>>>(A, lda, m, n, k0, pe, chunk, cands, ticket,
-                                                         ipiv, st, step_id);
+            RQ_LAUNCH(KID_LU_TRAILING, stream, k_lu_trailing<<<g, kLuThreads, sm, stream>>>(A, lda, m, n, k0, pe, chunk, cands, ticket,
+                                                         ipiv, st, step_id));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }

@@ -222,16 +222,16 @@ __global__ void __launch_bounds__(kSmallThreads)
 cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, double *W,
                                   double *RP, double *rinv, double *R1, int64_t ldr,
                                   DevStatus *st, int step_id, cudaStream_t stream) {
-    k_small_precond<<<1, kSmallThreads, 0, stream>>>(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1,
-                                                     ldr, st, step_id);
+    RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_small_precond<<<1, kSmallThreads, 0, stream>>>(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1,
+                                                     ldr, st, step_id));
     return cudaGetLastError();
 }
 
 cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const double *LU,
                               int64_t lda, double *W, double *RP, double *rinv,
                               cudaStream_t stream) {
-    k_small_precond<<<1, kSmallThreads, 0, stream>>>(Ms, ldm, s, n, 1, LU, lda, W, RP, rinv,
-                                                     nullptr, 0, nullptr, 0);
+    RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_small_precond<<<1, kSmallThreads, 0, stream>>>(Ms, ldm, s, n, 1, LU, lda, W, RP, rinv,
+                                                     nullptr, 0, nullptr, 0));
     return cudaGetLastError();
 }
 
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kSmallThreads)
 
 cudaError_t launch_householder_r(const double *A, int64_t lda, int s, int n, double *W, double *R,
                                  int64_t ldr, cudaStream_t stream) {
-    k_householder_r<<<1, kSmallThreads, 0, stream>>>(A, lda, s, n, W, R, ldr);
+    RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_householder_r<<<1, kSmallThreads, 0, stream>>>(A, lda, s, n, W, R, ldr));
     return cudaGetLastError();
 }
 
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kSmallThreads)
 cudaError_t launch_cholesky(const double *G, int64_t ldg, int n, double *W, double *RP,
                             double *rinv, double *R, int64_t ldr, DevStatus *st, int step_id,
                             cudaStream_t stream) {
-    k_cholesky<<<1, kSmallThreads, 0, stream>>>(G, ldg, n, W, RP, rinv, R, ldr, st, step_id);
+    RQ_LAUNCH(KID_CHOLESKY, stream, k_cholesky<<<1, kSmallThreads, 0, stream>>>(G, ldg, n, W, RP, rinv, R, ldr, st, step_id));
     return cudaGetLastError();
 }
 
@@ -330,8 +330,8 @@ __global__ void k_trmm_upper(const double *__restrict__ A, int64_t lda,
 cudaError_t launch_trmm_upper(const double *A, int64_t lda, const double *B, int64_t ldb, int n,
                               double *C, int64_t ldc, cudaStream_t stream) {
     const int64_t ne = int64_t(n) * n;
-    k_trmm_upper<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(A, lda, B, ldb, n, C,
-                                                                              ldc);
+    RQ_LAUNCH(KID_TRMM, stream, k_trmm_upper<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(A, lda, B, ldb, n, C,
+                                                                              ldc));
     return cudaGetLastError();
 }
 
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kSmallThreads)
 
 cudaError_t launch_lc2_r1(const double *Sc, int64_t lds, const double *LU, int64_t lda, int n,
                           double *RP, double *rinv, cudaStream_t stream) {
-    k_lc2_r1<<<1, kSmallThreads, 0, stream>>>(Sc, lds, LU, lda, n, RP, rinv);
+    RQ_LAUNCH(KID_TRMM, stream, k_lc2_r1<<<1, kSmallThreads, 0, stream>>>(Sc, lds, LU, lda, n, RP, rinv));
     return cudaGetLastError();
 }
 

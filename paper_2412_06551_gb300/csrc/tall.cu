@@ -351,31 +351,31 @@ cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit
     if (bm == 128) {
         auto k = k_gram<128, 5>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1));
-        k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
-                                              part_diag, nd, st);
+        RQ_LAUNCH(KID_GRAM, stream, k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
+                                              part_diag, nd, st));
     } else if (bm == 64) {
         auto k = k_gram<64, 5>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1));
-        k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
-                                              part_diag, nd, st);
+        RQ_LAUNCH(KID_GRAM, stream, k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
+                                              part_diag, nd, st));
     } else {
         auto k = k_gram<32, 5>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem1));
-        k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
-                                              part_diag, nd, st);
+        RQ_LAUNCH(KID_GRAM, stream, k<<<grid, kThreads, smem1, stream>>>(map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, 1,
+                                              part_diag, nd, st));
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n > 128) {
         auto k = k_gram<32, 8>;
         const size_t smem2 = size_t(2) * 32 * 128 * 8;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem2));
-        k<<<dim3(pl.grid_x, 1), kThreads, smem2, stream>>>(map, tma, A, lda, m, n, unit_lower,
-                                                            pl.chunk, 128, 0, part_off, 1, st);
+        RQ_LAUNCH(KID_GRAM, stream, k<<<dim3(pl.grid_x, 1), kThreads, smem2, stream>>>(map, tma, A, lda, m, n, unit_lower,
+                                                            pl.chunk, 128, 0, part_off, 1, st));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t ne = int64_t(n) * n;
-    k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-        part_diag, nd, part_off, pl.grid_x, n, G, ldg);
+    RQ_LAUNCH(KID_REDUCE, stream, k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+        part_diag, nd, part_off, pl.grid_x, n, G, ldg));
     return cudaGetLastError();
 }
 
@@ -471,8 +471,9 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
     do {                                                                                         \
         auto k = k_trsm<BMV, GV>;                                                                \
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));         \
-        k<<<pl.grid_x, kThreads, smem, stream>>>(map, tma, A, lda, m, n, n_pad, pl.chunk, RP,     \
-                                                  rinv, Q, ldq, part, st);                       \
+        RQ_LAUNCH(GV ? KID_TRSM_GRAM : KID_TRSM, stream,                                         \
+                  k<<<pl.grid_x, kThreads, smem, stream>>>(map, tma, A, lda, m, n, n_pad,        \
+                                                            pl.chunk, RP, rinv, Q, ldq, part, st)); \
     } while (0)
     if (bm == 128) {
         if (fuse) RQ_TRSM_LAUNCH(128, true); else RQ_TRSM_LAUNCH(128, false);
@@ -486,8 +487,8 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
     if (G == nullptr) return cudaSuccess;
     if (fuse) {
         const int64_t ne = int64_t(n) * n;
-        k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-            part, 1, part, pl.grid_x, n, G, ldg);
+        RQ_LAUNCH(KID_REDUCE, stream, k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+            part, 1, part, pl.grid_x, n, G, ldg));
         return cudaGetLastError();
     }
     // n > 128: Gram of the solved Q in a separate pass
@@ -717,9 +718,9 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
         const size_t smem = size_t(s_pad) * kSparseNT * 8 + size_t(kSparseBM) * (kSparseNT + 1) * 8 +
                             size_t(kSparseBM) * zeta * 4;
         cudaFuncSetAttribute(k_sketch_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        k_sketch_sparse<<<dim3(pl.grid_x, ny), kThreads, smem, stream>>>(
+        RQ_LAUNCH(KID_SKETCH_SPARSE, stream, k_sketch_sparse<<<dim3(pl.grid_x, ny), kThreads, smem, stream>>>(
             A, lda, m, n, unit_lower, pl.chunk, static_cast<int>(s), zeta, seed,
-            1.0 / sqrt(double(zeta)), part, s_pad, n_pad);
+            1.0 / sqrt(double(zeta)), part, s_pad, n_pad));
         nparts = pl.grid_x;
     } else {
         const int ncb = std::min(pad16(n), 128);
@@ -733,15 +734,15 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
         const size_t smem = size_t(bm) * ncb * 8 + size_t(bm) * 64 * 8;
         auto k = k_sketch_gauss<64>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        k<<<dim3(pl.grid_x, n_st * n_ct), kThreads, smem, stream>>>(
+        RQ_LAUNCH(KID_SKETCH_GAUSS, stream, k<<<dim3(pl.grid_x, n_st * n_ct), kThreads, smem, stream>>>(
             map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, n_st, s, seed,
-            1.0 / sqrt(double(s)), S, lds, part, s_pad, n_pad, st);
+            1.0 / sqrt(double(s)), S, lds, part, s_pad, n_pad, st));
         nparts = pl.grid_x;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t ne = s * int64_t(n);
-    k_reduce_sketch<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-        part, nparts, static_cast<int>(s), n, s_pad, n_pad, Y, ldy);
+    RQ_LAUNCH(KID_REDUCE, stream, k_reduce_sketch<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+        part, nparts, static_cast<int>(s), n, s_pad, n_pad, Y, ldy));
     return cudaGetLastError();
 }
 
@@ -760,8 +761,8 @@ cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, do
                              cudaStream_t stream) {
     const int n_pad = pad16(n);
     const int64_t ne = int64_t(n_pad) * n_pad;
-    k_pad_upper<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(R, ldr, n, n_pad, RP,
-                                                                             rinv);
+    RQ_LAUNCH(KID_PAD, stream, k_pad_upper<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(R, ldr, n, n_pad, RP,
+                                                                             rinv));
     return cudaGetLastError();
 }
 

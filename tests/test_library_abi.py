@@ -19,7 +19,7 @@ def _declared():
     for h in hdrs:
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for mt in re.finditer(r"\b(?:rclupp_status_t|const char \*)\s*\*?\s*(\w+)\s*\(", txt):
+        for mt in re.finditer(r"\b(?:rclupp_status_t|const char \*|void|int|unsigned long long)\s*\*?\s*(\w+)\s*\(", txt):
             names.add(mt.group(1))
     return names
 
