@@ -200,6 +200,29 @@ rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t
 rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t n,
                                      const double *A, int64_t lda, double *R, int64_t ldr);
 
+/* ---- allocation-free Gram (no counterpart in the paper) ------------------
+ * G = A^T A (n x n, ldg >= n, both triangles), the same kernels as
+ * rclupp_gram, for callers that cannot let a library allocate device memory:
+ * hosts that reserve nearly all GPU memory for their own pool up front,
+ * loops where cudaMalloc/cudaFree would add device-wide synchronization, and
+ * callers that account for every buffer themselves.  No handle is needed and
+ * nothing is allocated (no cudaMalloc, cudaFree or allocating library call):
+ * the split-K partial sums and a status word live in a fixed array of
+ * 8 MiB + 256 bytes inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   m, n, A, lda : DEVICE matrix A (m x n, lda >= m), 1 <= n <= 128,
+ *                  m < 2^31; larger n or m returns RCLUPP_ERR_UNSUPPORTED.
+ *   G, ldg       : DEVICE output (caller-owned).
+ *   stream       : cudaStream_t to run on (NULL = legacy default stream).
+ * The call returns after its GPU work has finished (status read back).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * array and overwrites it: calls that overlap on the GPU race, so do not run
+ * two of them concurrently on one device. */
+rclupp_status_t rclupp_gram_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, double *G,
+                                    int64_t ldg, void *stream);
+
 /* ---- instrumentation (no counterpart in the paper) ----------------------
  * Launch accounting and per-kernel timing for benchmarks.  Every kernel the
  * library launches increments a process-wide counter.  When profiling is

@@ -26,7 +26,7 @@ __all__ = [
     "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
     "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
-    "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r",
+    "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
 ]
 
@@ -94,6 +94,7 @@ _SIGNATURES = {
     "rclupp_tall_lupp": ([_P, _I64, _I64, _P, _I64, _P, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "rclupp_profile_enable": ([ctypes.c_int], None),
     "rclupp_profile_reset": ([], None),
     "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -341,6 +342,25 @@ def rclupp_gram(A, *, unit_lower=False, G=None):
     st = load().rclupp_gram(_handle(A).bind(), m, n, _ptr(A), lda, int(bool(unit_lower)), _ptr(G),
                             ldg)
     _raise("rclupp_gram", st)
+    return G
+
+
+def rclupp_gram_noalloc(A, *, G=None):
+    """G = A^T A through the allocation-free entry point (n <= 128).
+
+    For callers that must not let the library allocate device memory: the
+    scratch lives in a fixed array inside the library; no handle is used.
+    Calls on one device must not overlap on the GPU (they share that array).
+    """
+    torch = _torch()
+    A, lda = colmajor(A)
+    m, n = A.shape
+    G = empty_colmajor(n, n, A.device) if G is None else G
+    G, ldg = colmajor(G)
+    with torch.cuda.device(A.device):
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+        st = load().rclupp_gram_noalloc(m, n, _ptr(A), lda, _ptr(G), ldg, _P(stream))
+    _raise("rclupp_gram_noalloc", st)
     return G
 
 

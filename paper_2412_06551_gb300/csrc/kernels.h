@@ -42,6 +42,12 @@ size_t sketch_partials_doubles(int64_t m, int n, int64_t s, int kind);
 cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit_lower, double *G,
                         int64_t ldg, double *part, DevStatus *st, cudaStream_t stream);
 
+// G = A^T A for n <= 128 using at most max_parts CTAs; `part` holds
+// max_parts x 16384 doubles.
+cudaError_t launch_gram_bounded(const double *A, int64_t lda, int64_t m, int n, double *G,
+                                int64_t ldg, double *part, int max_parts, DevStatus *st,
+                                cudaStream_t stream);
+
 // Q = A R^{-1} with R given as a padded upper factor RP (n_pad x n_pad,
 // ld n_pad, zeros elsewhere) and rinv[n_pad] = 1 / diag; optionally G = Q^T Q.
 cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, const double *RP,

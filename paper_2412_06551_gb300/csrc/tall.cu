@@ -379,6 +379,45 @@ cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit
     return cudaGetLastError();
 }
 
+// G = A^T A for n <= 128 with at most max_parts CTAs, so that the partial
+// sums fit a caller-supplied buffer of max_parts x 16384 doubles.  Same
+// kernels as launch_gram; only the row partition differs.
+cudaError_t launch_gram_bounded(const double *A, int64_t lda, int64_t m, int n, double *G,
+                                int64_t ldg, double *part, int max_parts, DevStatus *st,
+                                cudaStream_t stream) {
+    if (n > 128 || max_parts < 1) return cudaErrorInvalidValue;
+    const int ncb = pad16(n);
+    const int bm = gram_bm(n);
+    CUtensorMap map;
+    const bool tma = make_tma_map(&map, A, m, n, lda, bm, ncb);
+    if (!tma) memset(&map, 0, sizeof map);
+    TallPlan pl = plan_rows(m, bm, 2, 1);
+    if (pl.grid_x > max_parts) {
+        pl.chunk = round_up(ceil_div(m, max_parts), bm);
+        pl.grid_x = static_cast<int>(ceil_div(m, pl.chunk));
+    }
+    const size_t smem = size_t(bm) * ncb * 8;
+    const dim3 grid(pl.grid_x, 1);
+    if (bm == 128) {
+        auto k = k_gram<128, 5>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        RQ_LAUNCH(KID_GRAM, stream, k<<<grid, kThreads, smem, stream>>>(map, tma, A, lda, m, n, 0,
+                                                                       pl.chunk, ncb, 1, part, 1, st));
+    } else {
+        auto k = k_gram<64, 5>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        RQ_LAUNCH(KID_GRAM, stream, k<<<grid, kThreads, smem, stream>>>(map, tma, A, lda, m, n, 0,
+                                                                       pl.chunk, ncb, 1, part, 1, st));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t ne = int64_t(n) * n;
+    RQ_LAUNCH(KID_REDUCE, stream,
+              k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+                  part, 1, part, pl.grid_x, n, G, ldg));
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- TRSM (+ Gram) ---
 
 // Q = A R^{-1} tile by tile: blocked substitution with 16-column blocks.
