@@ -279,15 +279,21 @@ void orc_householder_r(int64_t s, int64_t n, const double *A, int64_t lda, doubl
 void orc_sketch_dense(int64_t s, int64_t m, int64_t n, const double *S, int64_t lds,
                       const double *X, int64_t ldx, double *Y, int64_t ldy)
 {
-#pragma omp parallel for collapse(2) schedule(static)
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t r = 0; r < s; ++r) {
-            const double *xj = X + j * ldx;
-            double acc = 0.0;
-            for (int64_t i = 0; i < m; ++i)
-                acc += IDX(S, lds, r, i) * xj[i];
-            IDX(Y, ldy, r, j) = acc;
+    /* Column j of Y is owned by one thread; i runs outermost so that column i
+     * of S is read contiguously.  Each Y[r][j] still receives its terms in
+     * increasing i, one rounding per term, exactly as in the formula. */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+        const double *xj = X + j * ldx;
+        for (int64_t r = 0; r < s; ++r)
+            IDX(Y, ldy, r, j) = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            const double x = xj[i];
+            const double *si = S + i * lds;
+            for (int64_t r = 0; r < s; ++r)
+                IDX(Y, ldy, r, j) += si[r] * x;
         }
+    }
 }
 
 /* Y = S X for a sparse-sign sketch given column by column: column i of S has
