@@ -55,10 +55,19 @@ typedef enum {
     RCLUPP_SKETCH_SPARSE_SIGN = 1 /* zeta distinct rows per column, +-1/sqrt(zeta)   */
 } rclupp_sketch_kind_t;
 
+/* Precision of the sketch product (the sketch only has to be an embedding,
+ * Section 3).  The reduced tiers run the generated Gaussian sketch on the
+ * tensor cores (tcgen05, bf16 operands, fp32 accumulation in tensor memory):
+ * S's entries z(r, i) are rounded to bf16 and every x of X is either rounded
+ * to bf16 (BF16) or split into three bf16 terms x1 = bf16(x),
+ * x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums are
+ * combined in binary64.  All other steps stay in binary64.  The sparse-sign
+ * sketch only adds and always runs in binary64; an explicit S requires
+ * RCLUPP_PREC_FP64. */
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
-    RCLUPP_PREC_SKETCH_BF16 = 1, /* Gaussian sketch on tensor cores: bf16 S, bf16 X, fp32 sum */
-    RCLUPP_PREC_SKETCH_FP32 = 2  /* bf16 S, X split into three bf16 terms, fp32 sum          */
+    RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
+    RCLUPP_PREC_SKETCH_FP32 = 2  /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
 } rclupp_precision_t;
 
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
@@ -93,6 +102,11 @@ typedef struct {
     int32_t failed_step; /* 0 none; 1 sketch LU; 2 tall LU; 3 first Cholesky;
                             4 second Cholesky; 5 third Cholesky (LC2 / CholeskyQR2) */
     int64_t info;        /* failing column for breakdown / zero pivot, else -1 */
+    int32_t prec_used;   /* sketch tier that produced the result (rclupp_precision_t);
+                            RCLUPP/RCLUPPr escalate bf16 -> three-term bf16 -> FP64 when
+                            the first Cholesky breaks down or the spread of its diagonal
+                            exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2) */
+    int32_t reserved;
 } rclupp_info_t;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -228,11 +242,12 @@ rclupp_status_t rclupp_gram_noalloc(int64_t m, int64_t n, const double *A, int64
  * library launches increments a process-wide counter.  When profiling is
  * enabled, a CUDA event pair is recorded on the launching stream around each
  * kernel; rclupp_profile_get synchronizes on the recorded events and returns,
- * for one kernel class (0 <= kid < 13), the number of timed launches, their
+ * for one kernel class (0 <= kid < 14), the number of timed launches, their
  * summed duration in milliseconds and the class name (static string).
  * Classes: 0 sketch_gauss, 1 sketch_sparse, 2 gram, 3 trsm_gram (fused
  * TRSM + Gram), 4 trsm, 5 reduce, 6 lu_col, 7 lu_trailing, 8 lu_u12,
- * 9 small_precond, 10 cholesky, 11 trmm, 12 pad.  Returns ERR_ARG for an
+ * 9 small_precond, 10 cholesky, 11 trmm, 12 pad, 13 sketch_tc (tensor-core
+ * sketch).  Returns ERR_ARG for an
  * invalid class. */
 void rclupp_profile_enable(int enable);
 void rclupp_profile_reset(void);

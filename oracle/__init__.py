@@ -80,6 +80,8 @@ def _load():
                 "orc_gaussian_sketch_matrix": ([I64, I64, U64, P, I64], None),
                 "orc_sparse_sign_column": ([U64, I64, I64, I32, P, P], None),
                 "orc_sparse_sign_pattern": ([I64, I64, I32, U64, P, P], None),
+                "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
+                "orc_sketch_bf16": ([I64, I64, I64, U64, I32, P, I64, P, I64], I32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -329,6 +331,35 @@ def sparse_to_dense(s: int, m: int, zeta: int, rows, signs) -> np.ndarray:
     cols = np.repeat(np.arange(m), zeta)
     S[np.asarray(rows), cols] = np.where(np.asarray(signs) > 0, val, -val)
     return S
+
+
+def round_bf16(x: float) -> float:
+    """Nearest bf16 value (8 significant bits, ties to even) of a binary64 value."""
+    return float(_load().orc_round_bf16(float(x)))
+
+
+def sketch_bf16(s: int, seed: int, nterms: int, x) -> np.ndarray:
+    """Y = S_bf16 X_split / sqrt(s): the tensor-core tier's sketch definition
+    (S entries z(r, i) rounded to bf16; X in one or three bf16 terms)."""
+    x = _f(x)
+    m, n = x.shape
+    y = np.zeros((s, n), order="F")
+    st = _load().orc_sketch_bf16(s, m, n, seed, nterms, _p(x), m, _p(y), s)
+    if st != OK:
+        raise OracleError(st, -1)
+    return y
+
+
+def bf16_split(x, nterms: int = 3) -> np.ndarray:
+    """Sum of the nterms bf16 terms of each entry (elementwise, via round_bf16)."""
+    x = np.asarray(x, dtype=np.float64)
+    r = np.vectorize(round_bf16)
+    x1 = r(x)
+    if nterms == 1:
+        return x1
+    x2 = r(x - x1)
+    x3 = r(x - x1 - x2)
+    return x1 + x2 + x3
 
 
 # ---------------------------------------------------------------- metrics ---

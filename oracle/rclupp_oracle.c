@@ -790,6 +790,90 @@ void orc_sparse_sign_column(uint64_t seed, int64_t i, int64_t s, int zeta, int32
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision sketch definition (the library's tensor-core tier)      */
+/*                                                                          */
+/* The sketch only has to be an embedding, so its product may run in bf16   */
+/* with fp32 sums: S's entries are z(r, i) rounded to bf16, and each x of X */
+/* is either rounded to bf16 (one term) or split into three bf16 terms      */
+/* x ~ x1 + x2 + x3 with x1 = bf16(x), x2 = bf16(x - x1),                    */
+/* x3 = bf16(x - x1 - x2) (the differences are exact in binary64).  All      */
+/* roundings are to nearest, ties to even.  The result is then              */
+/* Y = (sum_i bf16(z) (x1 + x2 + x3)) / sqrt(s), evaluated here in binary64. */
+/* ------------------------------------------------------------------------ */
+
+/* Round a binary64 value to the nearest bf16 value (8 significant bits,
+ * ties to even), returned as a binary64 value.  Normal range only (the
+ * inputs here are far from bf16's under/overflow thresholds); zero stays
+ * zero. */
+double orc_round_bf16(double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    const uint64_t mag = b & 0x7fffffffffffffffull;
+    if (mag == 0)
+        return x;
+    const uint64_t lsb = (b >> 45) & 1u;
+    const uint64_t rnd = (b >> 44) & 1u;
+    const uint64_t sticky = (b & ((1ull << 44) - 1u)) != 0;
+    if (rnd && (sticky || lsb))
+        b += 1ull << 45;
+    b &= ~((1ull << 45) - 1u);
+    double y;
+    memcpy(&y, &b, sizeof y);
+    return y;
+}
+
+/* bf16 rounding of a binary32 value (ties to even), as binary64. */
+double orc_round_bf16_f32(float z)
+{
+    return orc_round_bf16((double)z);
+}
+
+/* Y = (sum_i bf16(z(r, i)) * xs(i, j)) / sqrt(s) with xs the one- or
+ * three-term bf16 split of X, sums in increasing i (binary64).
+ * nterms is 1 or 3. */
+int orc_sketch_bf16(int64_t s, int64_t m, int64_t n, uint64_t seed, int nterms, const double *X,
+                    int64_t ldx, double *Y, int64_t ldy)
+{
+    double *Sb = (double *)malloc(sizeof(double) * (size_t)s * (size_t)m);
+    double *Xs = (double *)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    if (!Sb || !Xs) {
+        free(Sb);
+        free(Xs);
+        return ORC_ERR_NOMEM;
+    }
+    /* S entries rounded to bf16 */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t r = 0; r < s; ++r)
+            Sb[r + i * s] = orc_round_bf16_f32(orc_gauss_entry(seed, r, i));
+    /* X as the sum of its bf16 terms; x1 + x2 + x3 is exact in binary64
+     * (the three terms cover disjoint runs of at most 8 bits) */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) {
+            const double x = IDX(X, ldx, i, j);
+            const double x1 = orc_round_bf16(x);
+            double xs = x1;
+            if (nterms == 3) {
+                const double r1 = x - x1;
+                const double x2 = orc_round_bf16(r1);
+                const double x3 = orc_round_bf16(r1 - x2);
+                xs = x1 + x2 + x3;
+            }
+            Xs[i + j * m] = xs;
+        }
+    orc_sketch_dense(s, m, n, Sb, s, Xs, m, Y, ldy);
+    const double scale = 1.0 / sqrt((double)s);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t r = 0; r < s; ++r)
+            IDX(Y, ldy, r, j) *= scale;
+    free(Xs);
+    free(Sb);
+    return ORC_OK;
+}
+
 /* Patterns of all m columns: rows/signs of length m*zeta. */
 void orc_sparse_sign_pattern(int64_t s, int64_t m, int zeta, uint64_t seed, int32_t *rows,
                              int8_t *signs)

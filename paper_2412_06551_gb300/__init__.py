@@ -55,7 +55,8 @@ class Opts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     """rclupp_info_t: status, failed step, failing column."""
-    _fields_ = [("status", ctypes.c_int32), ("failed_step", ctypes.c_int32), ("info", ctypes.c_int64)]
+    _fields_ = [("status", ctypes.c_int32), ("failed_step", ctypes.c_int32), ("info", ctypes.c_int64),
+                ("prec_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RclupError(RuntimeError):
@@ -103,7 +104,7 @@ _SIGNATURES = {
 }
 
 KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
-                  "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad"]
+                  "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc"]
 
 
 def profile_enable(on: bool = True) -> None:

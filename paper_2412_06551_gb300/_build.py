@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librclupp.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["tall.cu", "lu.cu", "small.cu", "api.cu", "prof.cu", "noalloc.cu"]
+SOURCES = ["tall.cu", "lu.cu", "small.cu", "api.cu", "prof.cu", "noalloc.cu", "tc_sketch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-expt-relaxed-constexpr",
          "-I" + INCLUDE]

@@ -126,6 +126,8 @@ rclupp_status_t finish(rclupp_handle_t h, rclupp_status_t launch_status, rclupp_
         info->status = st;
         info->failed_step = step;
         info->info = inf;
+        info->prec_used = RCLUPP_PREC_FP64;
+        info->reserved = 0;
     }
     if (col) *col = inf;
     return st;
@@ -166,9 +168,58 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
         const size_t smem = size_t(round_up(o.s, 64)) * 32 * 8 + 64 * 33 * 8 + 64 * 16 * 4;
         if (smem > 220 * 1024) return RCLUPP_ERR_UNSUPPORTED;
     }
-    if (o.prec != RCLUPP_PREC_FP64) return RCLUPP_ERR_UNSUPPORTED;
+    if (o.prec != RCLUPP_PREC_FP64 && o.prec != RCLUPP_PREC_SKETCH_BF16 &&
+        o.prec != RCLUPP_PREC_SKETCH_FP32)
+        return RCLUPP_ERR_ARG;
+    if (o.prec != RCLUPP_PREC_FP64 && o.S) return RCLUPP_ERR_UNSUPPORTED;
     (void)m;
     return RCLUPP_OK;
+}
+
+// The sketch product at a precision tier: the tensor-core kernel for the
+// generated Gaussian sketch at the reduced tiers, the binary64 kernels
+// otherwise (the sparse-sign sketch only adds, so its tier is irrelevant).
+cudaError_t sketch_step(const Bufs &b, const double *A, int64_t lda, int64_t m, int n,
+                        int unit_lower, const rclupp_opts_t &o, int tier, DevStatus *ds,
+                        cudaStream_t s) {
+    if (tier != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
+        return launch_sketch_tc(A, lda, m, n, unit_lower, o.s, o.seed,
+                                tier == RCLUPP_PREC_SKETCH_BF16 ? 1 : 3, b.Y, o.s, b.part, ds, s);
+    return launch_sketch(A, lda, m, n, unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s,
+                         b.part, ds, s);
+}
+
+// A reduced-precision sketch leaves Q1 = X R1^{-1} less well conditioned
+// (its error acts like a perturbation of S of the sketch's relative size).
+// Accept the first Cholesky only if it succeeded and the spread of R2's
+// diagonal (a lower bound on kappa(Q1)) stays below this.
+constexpr double kEscalateRatio = 1.0e4;
+
+int next_tier(int tier) {
+    return tier == RCLUPP_PREC_SKETCH_BF16 ? RCLUPP_PREC_SKETCH_FP32 : RCLUPP_PREC_FP64;
+}
+
+enum class Verdict { Accept, Escalate, Fail };
+
+// Synchronizes the stream and judges the first Cholesky of a reduced tier.
+Verdict judge_first_pass(rclupp_handle_t h, const Bufs &b, int n) {
+    const int np = pad16(n);
+    double diag[256];
+    if (cudaMemcpyAsync(h->h_status, h->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpy2DAsync(diag, sizeof(double), b.RP[1], size_t(np + 1) * sizeof(double),
+                          sizeof(double), size_t(n), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return Verdict::Fail;
+    const DevStatus &ds = *h->h_status;
+    if (ds.code != 0) return (ds.code == RCLUPP_ERR_CHOL_BREAKDOWN && ds.step == 3) ? Verdict::Escalate
+                                                                                   : Verdict::Fail;
+    double lo = diag[0], hi = diag[0];
+    for (int i = 1; i < n; ++i) {
+        lo = std::min(lo, diag[i]);
+        hi = std::max(hi, diag[i]);
+    }
+    return (!(lo > 0.0) || hi / lo > kEscalateRatio) ? Verdict::Escalate : Verdict::Accept;
 }
 
 #define RQ_TRY(expr)                                     \
@@ -180,20 +231,66 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
 // Steps 5-7 of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
-rclupp_status_t precond_then_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
-                                     const double *X, int64_t ldx, double *Q, int64_t ldq,
-                                     double *R, int64_t ldr) {
+// First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
+rclupp_status_t first_cholqr_pass(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
+                                  const double *X, int64_t ldx, double *Q, int64_t ldq) {
+    cudaStream_t s = h->stream;
+    DevStatus *st = h->d_status;
+    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, st, 3, s));
+    return RCLUPP_OK;
+}
+
+// The rest of C3-C8 after R2 is known.
+rclupp_status_t rest_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n, double *Q,
+                             int64_t ldq, double *R, int64_t ldr) {
     cudaStream_t s = h->stream;
     DevStatus *st = h->d_status;
     const int np = pad16(n);
-    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
-    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, st, 3, s));
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
     RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[3], b.rinv[3], nullptr, 0, st, 4, s));
     RQ_TRY(launch_trmm_upper(b.RP[3], np, b.RP[2], np, n, R, ldr, s));  // R = R4 R3
     RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, nullptr, 0, b.part, st, s));
     return RCLUPP_OK;
+}
+
+// Randomized drivers after the sketch: R1 from the sketch (the preconditioner
+// `precond`, steps 2-4 of Algorithm 6 or 3-4 of Algorithm 7), then CholeskyQR2
+// of Q1 = X R1^{-1}.  At a reduced sketch tier the first Cholesky is judged
+// and, if it broke down or shows Q1 too ill-conditioned, the sketch is redone
+// at the next tier (bf16 -> three-term bf16 -> binary64).  *tier_used reports
+// the tier that produced the result.
+template <class Precond>
+rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_opts_t &o,
+                                int64_t m, int n, const double *SA, int64_t ldsa, int unit_lower,
+                                Precond precond, const double *X, int64_t ldx, double *Q,
+                                int64_t ldq, double *R, int64_t ldr, int *tier_used) {
+    int tier = o.prec;
+    for (;;) {
+        if (sketch_step(b, SA, ldsa, m, n, unit_lower, o, tier, h->d_status, h->stream) != cudaSuccess)
+            return RCLUPP_ERR_CUDA;
+        if (precond() != cudaSuccess) return RCLUPP_ERR_CUDA;
+        const rclupp_status_t st = first_cholqr_pass(h, b, m, n, X, ldx, Q, ldq);
+        if (st != RCLUPP_OK) return st;
+        if (tier == RCLUPP_PREC_FP64) break;
+        const Verdict v = judge_first_pass(h, b, n);
+        if (v == Verdict::Fail) break;  // the status is reported by finish()
+        if (v == Verdict::Accept) break;
+        tier = next_tier(tier);
+        if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
+            return RCLUPP_ERR_CUDA;
+    }
+    *tier_used = tier;
+    return rest_cholqr2(h, b, m, n, Q, ldq, R, ldr);
+}
+
+rclupp_status_t precond_then_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
+                                     const double *X, int64_t ldx, double *Q, int64_t ldq,
+                                     double *R, int64_t ldr) {
+    const rclupp_status_t st = first_cholqr_pass(h, b, m, n, X, ldx, Q, ldq);
+    if (st != RCLUPP_OK) return st;
+    return rest_cholqr2(h, b, m, n, Q, ldq, R, ldr);
 }
 
 // copy an m x n matrix (device to device, possibly different leading dims)
@@ -275,17 +372,17 @@ rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const dou
     cudaStream_t s = h->stream;
     DevStatus *ds = h->d_status;
     const int ni = int(n), si = int(o.s);
-    rclupp_status_t ls = RCLUPP_OK;
-    do {
-        // X_s = S X (step 1)
-        if (launch_sketch(X, ldx, m, ni, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
-                          ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        // [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M); R1 = R0 N (steps 2-4)
-        if (launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s) !=
-            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        ls = precond_then_cholqr2(h, b, m, ni, X, ldx, Q, ldq, R, ldr);
-    } while (0);
-    return finish(h, ls, info, nullptr);
+    int tier = o.prec;
+    // X_s = S X (step 1); [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M);
+    // R1 = R0 N (steps 2-4); then steps 5-7
+    auto precond = [&]() {
+        return launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s);
+    };
+    const rclupp_status_t ls =
+        randomized_tail(h, b, o, m, ni, X, ldx, 0, precond, X, ldx, Q, ldq, R, ldr, &tier);
+    const rclupp_status_t r = finish(h, ls, info, nullptr);
+    if (info) info->prec_used = tier;
+    return r;
 }
 
 rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
@@ -295,29 +392,33 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
     if (st != RCLUPP_OK) return st;
     const rclupp_opts_t o = resolve_opts(opts, n);
     if ((st = check_opts(o, m, n)) != RCLUPP_OK) return st;
-    const bool alias = (Q == X);
-    Bufs b = prepare(h, m, int(n), o.s, alias, &st);
+    // The LU factor lives in Q unless Q aliases X or a reduced sketch tier may
+    // need M again after Q1 has been written (escalation re-sketches M).
+    const bool own_lu = (Q == X) || o.prec != RCLUPP_PREC_FP64;
+    Bufs b = prepare(h, m, int(n), o.s, own_lu, &st);
     if (st != RCLUPP_OK) return st;
     cudaStream_t s = h->stream;
     DevStatus *ds = h->d_status;
     const int ni = int(n), si = int(o.s);
-    double *L = alias ? b.LUbuf : Q;
-    const int64_t ldl = alias ? m : ldq;
+    double *L = own_lu ? b.LUbuf : Q;
+    const int64_t ldl = own_lu ? m : ldq;
     rclupp_status_t ls = RCLUPP_OK;
+    int tier = o.prec;
     do {
         if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
         // [M, N, P] = LU(X) (step 1)
         if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
             ls = RCLUPP_ERR_CUDA; break; }
-        // M_s = S M (step 2)
-        if (launch_sketch(L, ldl, m, ni, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s,
-                          b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        // R0 = R of HouseholderQR(M_s); R1 = R0 N (steps 3-4)
-        if (launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        ls = precond_then_cholqr2(h, b, m, ni, X, ldx, Q, ldq, R, ldr);
+        // M_s = S M (step 2); R0 = R of HouseholderQR(M_s); R1 = R0 N (steps 3-4);
+        // then steps 5-7.  Q1 overwrites the LU only after M_s is formed.
+        auto precond = [&]() {
+            return launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s);
+        };
+        ls = randomized_tail(h, b, o, m, ni, L, ldl, 1, precond, X, ldx, Q, ldq, R, ldr, &tier);
     } while (0);
-    return finish(h, ls, info, nullptr);
+    const rclupp_status_t r = finish(h, ls, info, nullptr);
+    if (info) info->prec_used = tier;
+    return r;
 }
 
 rclupp_status_t cholqr2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
@@ -400,8 +501,14 @@ rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const dou
     if (bad_ld(ldy, o.s)) return RCLUPP_ERR_ARG;
     Bufs b = prepare(h, m, int(n), o.s, false, &st);
     if (st != RCLUPP_OK) return st;
-    const cudaError_t e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed,
-                                        o.S, o.lds, Y, ldy, b.part, h->d_status, h->stream);
+    cudaError_t e;
+    if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN)
+        e = launch_sketch_tc(A, lda, m, int(n), unit_lower, o.s, o.seed,
+                             o.prec == RCLUPP_PREC_SKETCH_BF16 ? 1 : 3, Y, ldy, b.part, h->d_status,
+                             h->stream);
+    else
+        e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, Y,
+                          ldy, b.part, h->d_status, h->stream);
     return finish(h, from_cuda(e), nullptr, nullptr);
 }
 

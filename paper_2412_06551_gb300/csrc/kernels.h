@@ -61,6 +61,18 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
                           double *Y, int64_t ldy, double *part, DevStatus *st,
                           cudaStream_t stream);
 
+// Fixed-order sum of sketch partials: Y[r][c] = sum_p part[p][c*s_pad + r].
+cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
+                                 double *Y, int64_t ldy, cudaStream_t stream);
+
+// ---- tensor-core sketch (tc_sketch.cu) ----
+// Y = S X with S's entries rounded to bf16 and X split into nterms (1 or 3)
+// bf16 terms, fp32 accumulation on tcgen05 (n <= 256).
+cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
+                             int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
+                             double *part, DevStatus *st, cudaStream_t stream);
+size_t tc_sketch_smem_bytes(int n, int nterms);
+
 // Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
 cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,
                              cudaStream_t stream);
@@ -125,6 +137,7 @@ enum KernelId : int {
     KID_CHOLESKY,
     KID_TRMM,
     KID_PAD,
+    KID_SKETCH_TC,
     KID_COUNT
 };
 

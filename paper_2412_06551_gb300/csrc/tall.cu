@@ -735,6 +735,15 @@ __global__ void k_reduce_sketch(const double *__restrict__ part, int nparts, int
     Y[r + int64_t(c) * ldy] = acc;
 }
 
+cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
+                                 double *Y, int64_t ldy, cudaStream_t stream) {
+    const int64_t ne = int64_t(s) * n;
+    RQ_LAUNCH(KID_REDUCE, stream,
+              k_reduce_sketch<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+                  part, nparts, s, n, s_pad, n_pad, Y, ldy));
+    return cudaGetLastError();
+}
+
 size_t sketch_partials_doubles(int64_t m, int n, int64_t s, int kind) {
     const size_t s_pad = size_t(round_up(s, 64)), n_pad = size_t(round_up(n, 32));
     const size_t p = size_t(2) * num_sms() + 8;

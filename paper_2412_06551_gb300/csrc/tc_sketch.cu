@@ -1,0 +1,340 @@
+// Reduced-precision Gaussian sketch on the 5th-generation tensor cores
+// (tcgen05, kind::f16 with bf16 operands, fp32 accumulation in TMEM).
+//
+// The sketch of Algorithm 6 step 1 (and of Algorithm 7 step 2) only has to
+// be a subspace embedding (Section 3), so its product may run at reduced
+// precision.  Y = S X with S generated on the fly: each CTA owns one tile of
+// 128 sketch rows x NT columns of Y (M = 128, N = NT <= 256) and a contiguous
+// chunk of rows of X (split-K).  For every 32 rows of X the 256 threads
+//   * draw the 128 x 32 block of z (the same Philox4x32-10 / Box-Muller
+//     definition as the FP64 sketch) and round it to bf16,
+//   * load the 32 x NT block of X (binary64) and split each value into one
+//     or three bf16 terms x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2),
+//   * store both as K-major operand tiles (8 x 8 bf16 core matrices) in
+//     shared memory,
+// and one thread issues tcgen05.mma for the 16-row k-steps (one MMA per bf16
+// term of X), committing to an mbarrier per stage.  Three stages let the
+// tensor core consume stage k while the threads fill k+1 and k+2.  At the
+// end the fp32 accumulator is read from TMEM (tcgen05.ld), scaled by
+// 1/sqrt(s) in binary64 and written as this CTA's partial; partials are
+// summed in a fixed order by the same reduction as the FP64 sketch.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rq {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcBK = 32;      // rows of X per stage
+constexpr int kTcStages = 3;
+constexpr int kTcM = 128;      // sketch rows per CTA tile
+
+// ---- tcgen05 / TMEM wrappers ------------------------------------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of
+// 8 rows x 16 bytes stored as 128 contiguous bytes; lbo = byte distance of
+// neighbouring core matrices along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;  // descriptor version of sm_100-class MMA
+    return d;                             // base offset 0, no swizzle
+}
+
+// Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 consecutive fp32 columns of the warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// ---- bf16 rounding (nearest, ties to even) ----------------------------------
+
+// binary64 -> nearest bf16 (8 significant bits), as raw bits; normal range.
+__device__ __forceinline__ uint16_t bf16_bits_from_f64(double x, double &rounded) {
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    if (mag == 0) {
+        rounded = x;
+        return static_cast<uint16_t>((b >> 48) & 0x8000u);
+    }
+    const unsigned long long lsb = (b >> 45) & 1ull, rnd = (b >> 44) & 1ull;
+    const unsigned long long sticky = (b & ((1ull << 44) - 1ull)) != 0ull;
+    if (rnd && (sticky || lsb)) b += 1ull << 45;
+    b &= ~((1ull << 45) - 1ull);
+    rounded = __longlong_as_double(static_cast<long long>(b));
+    // repack: sign | exponent rebased 1023 -> 127 | top 7 fraction bits
+    const unsigned sign = static_cast<unsigned>(b >> 63);
+    const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
+    const unsigned frac = static_cast<unsigned>((b >> 45) & 0x7f);
+    if (e <= 0) return static_cast<uint16_t>(sign << 15);  // below bf16's normal range: zero
+    return static_cast<uint16_t>((sign << 15) | (static_cast<unsigned>(e) << 7) | frac);
+}
+
+// binary32 -> nearest bf16, ties to even (finite inputs).
+__device__ __forceinline__ uint16_t bf16_bits_from_f32(float z) {
+    const uint32_t b = __float_as_uint(z);
+    return static_cast<uint16_t>((b + 0x7fffu + ((b >> 16) & 1u)) >> 16);
+}
+
+// Byte offset of element (row, k) inside a K-major operand tile of BK
+// columns laid out as [row/8][k/8][row%8][k%8] (bf16).
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
+    return static_cast<uint32_t>(((row >> 3) * (kTcBK / 8) + (k >> 3)) * 128 + (row & 7) * 16 +
+                                 (k & 7) * 2);
+}
+
+template <int NSL>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_sketch_tc(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int unit_lower,
+                int64_t chunk, int n_st, int nt, uint64_t seed, double scale,
+                double *__restrict__ part, int s_pad, int n_pad, DevStatus *st) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mma[kTcStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int a_bytes = kTcM * kTcBK * 2;       // 8 KB
+    const int b_bytes = nt * kTcBK * 2;         // per bf16 term of X
+    const int stage_bytes = a_bytes + NSL * b_bytes;
+    const int st_idx = blockIdx.x % n_st, ct_idx = blockIdx.x / n_st;
+    const int rt0 = kTcM * st_idx;              // first sketch row of the tile
+    const int c0 = 256 * ct_idx;                // first column of the tile
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t ncols = 32;
+    while (ncols < static_cast<uint32_t>(nt)) ncols <<= 1;
+
+    if (warp == 0) tmem_alloc(&tmem_slot, ncols);
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) mbar_init(&bar_mma[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_bf16_f32(kTcM, nt);
+    const uint32_t smem_base = smem_u32(smem_raw);
+
+    const int64_t rb = int64_t(blockIdx.y) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    const int nsteps = static_cast<int>(ceil_div(re - rb, kTcBK));
+    bool ok = true;
+    for (int ks = 0; ks < nsteps; ++ks) {
+        const int sidx = ks % kTcStages;
+        unsigned char *stage = smem_raw + sidx * stage_bytes;
+        const int64_t r0 = rb + int64_t(ks) * kTcBK;
+        if (ks >= kTcStages) {
+            // the MMAs issued kTcStages steps ago read this stage
+            ok = mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / kTcStages - 1) & 1));
+            if (!ok) abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        // (1) S block: entry (r, i) for 128 sketch rows x 32 rows of X
+        for (int task = tid; task < (kTcM / 4) * kTcBK; task += kTcThreads) {
+            const int i = task % kTcBK, q = task / kTcBK;
+            const int64_t row = r0 + i;
+            uint16_t h[4] = {0, 0, 0, 0};
+            if (row < re) {
+                const float4 z = sk_gauss4(seed, row, (rt0 >> 2) + q);
+                h[0] = bf16_bits_from_f32(z.x);
+                h[1] = bf16_bits_from_f32(z.y);
+                h[2] = bf16_bits_from_f32(z.z);
+                h[3] = bf16_bits_from_f32(z.w);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                *reinterpret_cast<uint16_t *>(stage + kmajor_off(4 * q + j, i)) = h[j];
+        }
+        // (2) X block split into NSL bf16 terms: 8 consecutive rows of one column per task
+        for (int task = tid; task < nt * (kTcBK / 8); task += kTcThreads) {
+            const int kb = task % (kTcBK / 8), c = task / (kTcBK / 8);
+            const int col = c0 + c;
+            uint16_t hv[NSL][8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int64_t row = r0 + kb * 8 + t;
+                double x = 0.0;
+                if (row < re && col < n) {
+                    x = X[row + int64_t(col) * ldx];
+                    if (unit_lower && row <= col) x = (row == col) ? 1.0 : 0.0;
+                }
+                double rnd;
+                hv[0][t] = bf16_bits_from_f64(x, rnd);
+                if (NSL == 3) {
+                    const double r1 = x - rnd;
+                    double rnd2;
+                    hv[NSL > 1 ? 1 : 0][t] = bf16_bits_from_f64(r1, rnd2);
+                    double rnd3;
+                    hv[NSL > 2 ? 2 : 0][t] = bf16_bits_from_f64(r1 - rnd2, rnd3);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NSL; ++p) {
+                uint4 v;
+                v.x = uint32_t(hv[p][0]) | (uint32_t(hv[p][1]) << 16);
+                v.y = uint32_t(hv[p][2]) | (uint32_t(hv[p][3]) << 16);
+                v.z = uint32_t(hv[p][4]) | (uint32_t(hv[p][5]) << 16);
+                v.w = uint32_t(hv[p][6]) | (uint32_t(hv[p][7]) << 16);
+                *reinterpret_cast<uint4 *>(stage + a_bytes + p * b_bytes + kmajor_off(c, kb * 8)) = v;
+            }
+        }
+        fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_base + sidx * stage_bytes;
+#pragma unroll
+            for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + kk * 256, 128, kTcBK * 16);
+#pragma unroll
+                for (int p = 0; p < NSL; ++p) {
+                    const uint64_t bd = smem_desc(a0 + a_bytes + p * b_bytes + kk * 256, 128, kTcBK * 16);
+                    mma_bf16(tmem, ad, bd, idesc, (ks > 0 || kk > 0 || p > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&bar_mma[sidx]);
+        }
+    }
+    // all MMAs done: wait for the last commit (it covers every earlier MMA)
+    if (!abort_flag && nsteps > 0) {
+        const int last = nsteps - 1;
+        const bool okw = mbar_wait_bounded(&bar_mma[last % kTcStages],
+                                           static_cast<uint32_t>((last / kTcStages) & 1));
+        if (!okw) abort_flag = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (abort_flag) {
+        if (tid == 0) report(st, kErrTimeout, 0, -1);
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (sketch rows) and
+        // half (w / 4) of the columns
+        const int lane_base = 32 * (warp & 3);
+        const int half = warp >> 2;
+        const int nchunks = (nt + 31) / 32;  // 32-column loads (TMEM holds >= 32 columns)
+        const int per_half = (nchunks + 1) / 2;
+        const int r = rt0 + lane_base + lane;
+        double *out = part + size_t(blockIdx.y) * s_pad * n_pad;
+        for (int ch = half * per_half; ch < std::min(nchunks, (half + 1) * per_half); ++ch) {
+            const int cb = 32 * ch;
+            float v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(lane_base) << 16) + static_cast<uint32_t>(cb), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + cb + j;
+                if (cb + j < nt && c < n_pad && r < s_pad)
+                    out[size_t(c) * s_pad + r] = double(v[j]) * scale;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace
+
+size_t tc_sketch_smem_bytes(int n, int nterms) {
+    const int nt = std::min(pad16(n), 256);
+    return size_t(kTcStages) * (size_t(kTcM) * kTcBK * 2 + size_t(nterms) * nt * kTcBK * 2);
+}
+
+cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
+                             int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
+                             double *part, DevStatus *st, cudaStream_t stream) {
+    if (n > 256 || (nterms != 1 && nterms != 3)) return cudaErrorInvalidValue;
+    const int nt = std::min(pad16(n), 256);
+    const int s_pad = static_cast<int>(round_up(s, kTcM));
+    const int n_pad = static_cast<int>(round_up(n, 32));
+    const int n_st = s_pad / kTcM;
+    const int tiles = n_st;  // n <= 256: one column tile
+    int p = std::max(1, num_sms() / tiles);
+    int64_t chunk = round_up(ceil_div(m, p), kTcBK);
+    p = static_cast<int>(ceil_div(m, chunk));
+    // at least 120 KB of shared memory so that one CTA (and one TMEM
+    // allocation) runs per SM
+    const size_t smem = std::max<size_t>(tc_sketch_smem_bytes(n, nterms), 120 * 1024);
+    const dim3 grid(tiles, p);
+    const double scale = 1.0 / sqrt(double(s));
+    if (nterms == 1) {
+        cudaFuncSetAttribute(k_sketch_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        RQ_LAUNCH(KID_SKETCH_TC, stream,
+                  k_sketch_tc<1><<<grid, kTcThreads, smem, stream>>>(X, ldx, m, n, unit_lower, chunk,
+                                                                   n_st, nt, seed, scale, part,
+                                                                   s_pad, n_pad, st));
+    } else {
+        cudaFuncSetAttribute(k_sketch_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        RQ_LAUNCH(KID_SKETCH_TC, stream,
+                  k_sketch_tc<3><<<grid, kTcThreads, smem, stream>>>(X, ldx, m, n, unit_lower, chunk,
+                                                                   n_st, nt, seed, scale, part,
+                                                                   s_pad, n_pad, st));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce_sketch(part, p, static_cast<int>(s), n, s_pad, n_pad, Y, ldy, stream);
+}
+
+}  // namespace rq

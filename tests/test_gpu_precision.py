@@ -1,0 +1,124 @@
+"""Reduced-precision sketch tier (tensor cores) against the oracle.
+
+The tensor-core sketch computes Y = S_bf16 X_split / sqrt(s) with fp32 sums
+inside each CTA and binary64 sums across CTAs.  The oracle evaluates the same
+definition (bf16 rounding of z, one- or three-term bf16 split of X) in
+binary64; every product is exact in fp32, so the two differ only by the fp32
+summation: |Y_gpu - Y_ref| <= gamma32_m (|S_bf16| |X_split|) / sqrt(s) with
+gamma32_k = k 2^-24 / (1 - k 2^-24).  |S_bf16| <= (1 + 2^-8) |z| and
+|X_split| <= (1 + 2^-7) |X| bound the right-hand side from the binary64 S.
+
+The drivers must meet the same gates as the binary64 path against the
+binary64 oracle, reporting the tier that produced the result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def gamma32(k):
+    u = 2.0 ** -24
+    return k * u / (1 - k * u)
+
+
+def dev(a):
+    a = np.asfortranarray(a)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda").t()
+
+
+def host(t):
+    return np.asfortranarray(t.detach().cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def rq():
+    import paper_2412_06551_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.mark.parametrize("prec,nterms", [(1, 1), (2, 3)])
+@pytest.mark.parametrize("m,n,s", [(1, 1, 1), (100, 7, 8), (4096, 64, 128), (5003, 128, 256),
+                                   (3001, 200, 300), (2048, 256, 512), (20001, 16, 32)])
+def test_tc_sketch_matches_definition(rq, prec, nterms, m, n, s):
+    x = synth.svd_matrix(m, n, 1e3, m + n) if m >= n else synth.integer_matrix(m, n, 1)
+    seed = 1234 + m
+    y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=prec))
+    ref = oracle.sketch_bf16(s, seed, nterms, x)
+    S = oracle.gaussian_sketch_matrix(s, m, seed)  # z / sqrt(s) in binary64
+    mag = (1 + 2.0 ** -8) * (1 + 2.0 ** -7) * (np.abs(S) @ np.abs(x))
+    assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
+    # and close to the binary64 sketch: S's bf16 rounding (2^-9 relative) plus
+    # X's (2^-9 for one term, 2^-23 for three) plus the fp32 sums
+    full = oracle.sketch_dense(S, x)
+    rel = np.max(np.abs(y - full) / (mag + 1e-300))
+    assert rel <= 2.0 ** -9 + (2.0 ** -9 if nterms == 1 else 2.0 ** -23) + gamma32(m)
+
+
+def test_tc_sketch_unit_lower(rq):
+    m, n, s = 3000, 24, 48
+    x = synth.svd_matrix(m, n, 1e4, 8)
+    lu, _, _, _ = oracle.gepp(x)
+    M = oracle.unit_lower(lu)
+    y = host(rq.rclupp_sketch(dev(lu), s=s, seed=4, prec=2, unit_lower=True))
+    ref = oracle.sketch_bf16(s, 4, 3, M)
+    S = oracle.gaussian_sketch_matrix(s, m, 4)
+    mag = 1.02 * (np.abs(S) @ np.abs(M))
+    assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
+
+
+def test_tc_sketch_deterministic(rq):
+    x = synth.svd_matrix(50000, 128, 1e2, 3)
+    X = dev(x)
+    y1 = rq.rclupp_sketch(X, s=256, seed=9, prec=2)
+    y2 = rq.rclupp_sketch(X, s=256, seed=9, prec=2)
+    assert torch.equal(y1, y2)
+
+
+def _gate(x, q, r, q_o, r_o, kappa):
+    orth, res = oracle.orthogonality(q), oracle.residual(x, q, r)
+    orth_o, res_o = oracle.orthogonality(q_o), oracle.residual(x, q_o, r_o)
+    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+    assert orth <= max(10 * orth_o, 1e-13), (orth, orth_o)
+    assert res <= max(10 * res_o, 1e-13), (res, res_o)
+    if kappa <= 1e6:
+        assert np.linalg.norm(r - r_o) / np.linalg.norm(r_o) <= 1e-10 * kappa
+
+
+@pytest.mark.parametrize("algo", ["rclupp", "rcluppr"])
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10, 1e12])
+def test_driver_at_reduced_tier(rq, algo, prec, kappa):
+    m, n, s = 8192, 64, 128
+    x = synth.svd_matrix(m, n, kappa, 71)
+    fn = rq.rclupp_factor if algo == "rclupp" else rq.rclupp_r_factor
+    Q, R, info = fn(dev(x), s=s, seed=5, prec=prec)
+    q_o, r_o, _ = getattr(oracle, algo)(x, S=oracle.gaussian_sketch_matrix(s, m, 5))
+    _gate(x, host(Q), host(R), q_o, r_o, kappa)
+    assert info.prec_used in (0, 1, 2)
+    if kappa <= 1e2:
+        assert info.prec_used == prec  # a well-conditioned X needs no escalation
+    if algo == "rcluppr" and kappa <= 1e10:
+        # RCLUPPr sketches the well-conditioned M: the reduced tier suffices
+        assert info.prec_used == prec
+
+
+def test_escalation_reaches_binary64_when_needed(rq):
+    # kappa 1e15: a bf16 sketch leaves Q1 far too ill-conditioned; the driver
+    # must escalate and still meet the binary64 result's accuracy
+    m, n, s = 8192, 32, 64
+    x = synth.svd_matrix(m, n, 1e15, 72)
+    Q, R, info = rq.rclupp_factor(dev(x), s=s, seed=6, prec=1, check=False)
+    q_o, r_o, st_o = oracle.rclupp(x, S=oracle.gaussian_sketch_matrix(s, m, 6), raise_on_error=False)
+    assert info.prec_used != 1
+    if st_o == 0 and info.status == 0:
+        assert oracle.orthogonality(host(Q)) <= max(1e3 * oracle.orthogonality(q_o), 1e-12)

@@ -428,3 +428,48 @@ def test_stacked_lower_section_5_1_2():
     for algo in ("rclupp", "rcluppr"):
         q, r, st = getattr(oracle, algo)(x, S=synth.gaussian_sketch(40, x.shape[0], 3))
         assert st == 0 and oracle.orthogonality(q) < 1e-12 and oracle.residual(x, q, r) < 1e-14
+
+
+# ------------------------------------------- reduced-precision sketch tier ---
+
+def _rne_bf16_reference(x):
+    # independent formula: x = f 2^e, f in [0.5, 1); keep 8 bits of f with
+    # Python's round() (ties to even on exactly representable halves)
+    if x == 0.0:
+        return 0.0
+    f, e = math.frexp(x)
+    return math.ldexp(round(f * 256.0), e - 8)
+
+
+def test_round_bf16_against_independent_formula():
+    g = np.random.default_rng(17)
+    vals = np.concatenate([g.standard_normal(2000) * 10.0 ** g.integers(-30, 30, 2000),
+                           [1.0, -1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -9, 255.5, 256.5, 1e-30]])
+    for v in vals:
+        assert oracle.round_bf16(float(v)) == _rne_bf16_reference(float(v)), v
+    # ties: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1.0)
+    assert oracle.round_bf16(1.0 + 2 ** -8) == 1.0
+    assert oracle.round_bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6
+
+
+def test_bf16_split_keeps_24_bits():
+    x = synth.rng(3).standard_normal(5000)
+    xs = oracle.bf16_split(x, 3)
+    assert np.all(np.abs(x - xs) <= 2.0 ** -23 * np.abs(x))
+    x1 = oracle.bf16_split(x, 1)
+    assert np.all(np.abs(x - x1) <= 2.0 ** -8 * np.abs(x))
+
+
+@pytest.mark.parametrize("nterms", [1, 3])
+def test_sketch_bf16_definition(nterms):
+    m, n, s, seed = 700, 9, 24, 5
+    x = synth.svd_matrix(m, n, 1e3, 2)
+    y = oracle.sketch_bf16(s, seed, nterms, x)
+    z = oracle.gaussian_sketch_matrix(s, m, seed) * math.sqrt(s)  # unscaled z, exact
+    Sb = np.vectorize(oracle.round_bf16)(np.float32(z).astype(np.float64))
+    ref = oracle.sketch_dense(Sb, oracle.bf16_split(x, nterms)) / math.sqrt(s)
+    assert np.allclose(y, ref, rtol=0, atol=1e-14 * np.max(np.abs(ref)))
+    # and the reduced-precision sketch is close to the binary64 one
+    full = oracle.sketch_dense(oracle.gaussian_sketch_matrix(s, m, seed), x)
+    tol = (2.0 ** -8 if nterms == 1 else 2.0 ** -7) * np.abs(Sb / math.sqrt(s)) @ np.abs(x) * 3
+    assert np.all(np.abs(y - full) <= tol + 1e-300)
