@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "sketch_gauss", "sketch_sparse",
                                       "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
+    p.add_argument("--workload", choices=["side_by_side", "precision"], default="side_by_side",
+                   help="precision: FP64 vs tensor-core sketch RCLUPP at m=2^22, n=256, s=512")
+    p.add_argument("--prec", type=int, default=0, help="sketch tier for --case runs")
     p.add_argument("--m", type=int, default=1 << 18)
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--reps", type=int, default=3)
@@ -86,6 +89,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(t_ms, device=None):
+    """Slowest rank's time (the job's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_ms)
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(per_rank_flops, steps, t_ms, world):
+    """Whole-job GFLOP/s: every rank factors its own matrix (weak scaling), so
+    the job does world x per-rank work in the slowest rank's time."""
+    return world * per_rank_flops * steps / (t_ms / 1e3) / 1e9
 
 
 # ------------------------------------------------------------ CPU oracle ---
@@ -212,6 +232,67 @@ def accuracy(torch, X, Q, R):
     return orth, res
 
 
+def time_call(torch, stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
+    """RCLUPP and RCLUPPr with the tensor-core sketch (starting at the bf16
+    tier, escalating as needed) on the same X, against the FP64 paths."""
+    m, n = X.shape
+    out = {}
+    for name, fn in (("rclupp", rq.rclupp_factor), ("rcluppr", rq.rclupp_r_factor)):
+        call = lambda: fn(X, s=S_SKETCH, seed=SEED_S, prec=rq.PREC_SKETCH_BF16)
+        call()
+        ms, (Q, R, info) = time_call(torch, stream, call, max(2, reps))
+        o, r = accuracy(torch, X, Q, R)
+        out[name] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "orth": o, "res": r,
+                     "prec_used": int(info.prec_used),
+                     "speedup_vs_fp64": fp64_paths[name]["ms"] / ms,
+                     "orth_fp64": fp64_paths[name]["orth"]}
+        del Q, R
+    return out
+
+
+def run_precision(args):
+    """FP64 vs tensor-core-sketch RCLUPP on m = 2^22, n = 256, s = 512 at
+    kappa 1e2, 1e8, 1e14 (one JSON line)."""
+    import torch
+    import paper_2412_06551_gb300 as rq
+    m, n, s = 1 << 22, 256, 512
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    rows = {}
+    for k_i, kap in enumerate((1e2, 1e8, 1e14)):
+        seed = synth.kappa_seed(2, k_i)
+        X = to_dev(synth.svd_matrix(m, n, kap, seed), torch, device)
+        row = {}
+        for label, prec in (("fp64", rq.PREC_FP64), ("mixed", rq.PREC_SKETCH_BF16)):
+            call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec, check=False)
+            call()
+            ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
+            entry = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9,
+                     "status": int(info.status), "prec_used": int(info.prec_used)}
+            if info.status == 0:
+                o, r = accuracy(torch, X, Q, R)
+                entry.update({"orth": o, "res": r})
+            row[label] = entry
+            del Q, R
+        row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        rows["%.0e" % kap] = row
+        del X
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "RCLUPP FP64 vs tensor-core sketch (bf16 start, escalating)",
+                      "m": m, "n": n, "s": s, "results": rows}), flush=True)
+
+
 def run_ours(args):
     import torch
 
@@ -271,14 +352,10 @@ def run_ours(args):
     rq.profile_enable(False)
     prof = rq.profile_read()
     clocks = sampler.stop() if sampler else None
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), device)
     ms_per_step = t_ms / args.steps
     model_flops = len(PATHS) * 2.0 * M * N * N
-    value = world * model_flops * args.steps / (t_ms / 1e3) / 1e9
+    value = job_throughput(model_flops, args.steps, t_ms, world)
 
     # ---- end to end: pinned host X in, Q and R of every path out ----
     xh = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T)).pin_memory()
@@ -297,11 +374,7 @@ def run_ours(args):
             rh[i].copy_(Rs[i].t(), non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, device)
     h2d = M * N * 8
     d2h = len(PATHS) * (M * N * 8 + N * N * 8)
 
@@ -370,6 +443,7 @@ def run_ours(args):
     }
     if sweep:
         line["accuracy_sweep"] = sweep
+    line["mixed"] = mixed_on_same_x(rq, torch, X, stream, paths, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -396,7 +470,7 @@ def run_case(args):
         elif args.case == "gram":
             rq.rclupp_gram(X)
         elif args.case == "sketch_gauss":
-            rq.rclupp_sketch(X, s=2 * n, seed=1)
+            rq.rclupp_sketch(X, s=2 * n, seed=1, prec=args.prec)
         elif args.case == "sketch_sparse":
             rq.rclupp_sketch(X, s=2 * n, kind=rq.SKETCH_SPARSE_SIGN, zeta=8, seed=1)
         elif args.case == "lu":
@@ -413,6 +487,8 @@ def main():
         args.warmup = 3
     if args.case:
         run_case(args)
+    elif args.workload == "precision":
+        run_precision(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -2,6 +2,7 @@
 // argument checks, and the drivers that sequence the tall passes and the
 // small factorizations in the order the algorithm boxes fix.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -199,6 +200,30 @@ int next_tier(int tier) {
     return tier == RCLUPP_PREC_SKETCH_BF16 ? RCLUPP_PREC_SKETCH_FP32 : RCLUPP_PREC_FP64;
 }
 
+// Before the first tall pass: R1's diagonal spread bounds kappa(R1) ~ kappa(X)
+// from below.  A tier whose sketch error times kappa(X) would leave Q1 far
+// beyond what CholeskyQR2 repairs is skipped at once (the limits are where the
+// bf16 and three-term tiers stopped meeting the binary64 accuracy).
+constexpr double kMaxSpreadBF16 = 1.0e11;
+constexpr double kMaxSpreadFP32 = 1.0e13;
+
+// Spread max/min of |diag| of a padded factor (synchronizes the stream).
+bool diag_spread(rclupp_handle_t h, const double *RP, int n, double *spread) {
+    const int np = pad16(n);
+    double diag[256];
+    if (cudaMemcpy2DAsync(diag, sizeof(double), RP, size_t(np + 1) * sizeof(double),
+                          sizeof(double), size_t(n), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return false;
+    double lo = std::abs(diag[0]), hi = lo;
+    for (int i = 1; i < n; ++i) {
+        lo = std::min(lo, std::abs(diag[i]));
+        hi = std::max(hi, std::abs(diag[i]));
+    }
+    *spread = (lo > 0.0) ? hi / lo : 1.0e300;
+    return true;
+}
+
 enum class Verdict { Accept, Escalate, Fail };
 
 // Synchronizes the stream and judges the first Cholesky of a reduced tier.
@@ -271,6 +296,19 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
         if (sketch_step(b, SA, ldsa, m, n, unit_lower, o, tier, h->d_status, h->stream) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
         if (precond() != cudaSuccess) return RCLUPP_ERR_CUDA;
+        // (RCLUPP only: RCLUPPr sketches the well-conditioned M, and R1's
+        // spread there comes from N, which the sketch does not touch)
+        if (tier != RCLUPP_PREC_FP64 && !unit_lower) {
+            double spread = 0.0;
+            if (!diag_spread(h, b.RP[0], n, &spread)) return RCLUPP_ERR_CUDA;
+            const double limit = tier == RCLUPP_PREC_SKETCH_BF16 ? kMaxSpreadBF16 : kMaxSpreadFP32;
+            if (!(spread <= limit)) {
+                tier = next_tier(tier);
+                if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
+                    return RCLUPP_ERR_CUDA;
+                continue;
+            }
+        }
         const rclupp_status_t st = first_cholqr_pass(h, b, m, n, X, ldx, Q, ldq);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
