@@ -162,6 +162,39 @@ rclupp_status_t lc2_factor(rclupp_handle_t handle, int64_t m, int64_t n, const d
                            int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
                            rclupp_info_t *info);
 
+/* ---- batched form ---------------------------------------------------------- */
+
+typedef enum {
+    RCLUPP_ALGO_RCLUPP = 0,  /* Algorithm 6 */
+    RCLUPP_ALGO_RCLUPPR = 1, /* Algorithm 7 */
+    RCLUPP_ALGO_CHOLQR2 = 2, /* Algorithm 2 */
+    RCLUPP_ALGO_LC2 = 3      /* Algorithm 4 */
+} rclupp_algo_t;
+
+/* Many independent factorizations of uneven sizes in one call: problem i is
+ * the m[i] x n[i] matrix X[i] (ldx[i]) with outputs Q[i] (ldq[i]) and R[i]
+ * (ldr[i]), every pointer a DEVICE pointer; the arrays themselves (m, n, X,
+ * ldx, opts, Q, ldq, R, ldr, status) are HOST arrays of length count.  opts
+ * holds one rclupp_opts_t per problem (NULL = defaults) and is used by the
+ * randomized algorithms, binary64 tier only (a reduced tier returns
+ * RCLUPP_ERR_UNSUPPORTED).  Each problem obeys the single-problem rules.
+ * The whole batch is enqueued as one CUDA graph: it forks into B parallel
+ * branches (streams; problem i runs on branch i mod B, B set by
+ * rclupp_set_batch_branches, default 16) so that small problems fill the GPU
+ * together, and joins.  The instantiated graph is cached in the handle and
+ * replayed while the batch (sizes, pointers, options) is unchanged.  The
+ * workspace holds B per-branch slices sized for the largest problem.
+ * status[i] (may be NULL) receives problem i's status; the return value is
+ * the first non-OK status, or RCLUPP_OK.  Synchronous like the other calls. */
+rclupp_status_t rclupp_factor_batched(rclupp_handle_t handle, int32_t algo, int32_t count,
+                                      const int64_t *m, const int64_t *n, const double *const *X,
+                                      const int64_t *ldx, const rclupp_opts_t *opts,
+                                      double *const *Q, const int64_t *ldq, double *const *R,
+                                      const int64_t *ldr, int32_t *status);
+
+/* Number of parallel branches of the batched graph (1 ..64). */
+rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t handle, int32_t branches);
+
 /* ---- individual steps of the tall path (each is one row of the path) ---- */
 
 /* Y = S A (s x n, ldy >= s): the sketch of Algorithm 6 step 1 (S X) and of

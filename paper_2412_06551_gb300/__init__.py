@@ -27,6 +27,8 @@ __all__ = [
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
     "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
+    "rclupp_factor_batched", "rclupp_set_batch_branches", "ALGO_RCLUPP", "ALGO_RCLUPPR",
+    "ALGO_CHOLQR2", "ALGO_LC2",
     "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
 ]
 
@@ -96,6 +98,8 @@ _SIGNATURES = {
     "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
+    "rclupp_factor_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "rclupp_set_batch_branches": ([_P, _I32], _I32),
     "rclupp_profile_enable": ([ctypes.c_int], None),
     "rclupp_profile_reset": ([], None),
     "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -344,6 +348,58 @@ def rclupp_gram(A, *, unit_lower=False, G=None):
                             ldg)
     _raise("rclupp_gram", st)
     return G
+
+
+ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2 = 0, 1, 2, 3
+
+
+def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
+                          Qs=None, Rs=None, check=True):
+    """Factor a list of column-major matrices in one batched call (one CUDA
+    graph).  s is a per-problem list (or None for 2 n); seed is a list or an
+    int (then seed + i for problem i).  Returns (Qs, Rs, statuses)."""
+    import numpy as np
+    count = len(Xs)
+    Xs = [colmajor(x) for x in Xs]
+    dev = Xs[0][0].device
+    Qs = [empty_colmajor(x.shape[0], x.shape[1], dev) for x, _ in Xs] if Qs is None else list(Qs)
+    Rs = [empty_colmajor(x.shape[1], x.shape[1], dev) for x, _ in Xs] if Rs is None else list(Rs)
+    qc = [colmajor(q) for q in Qs]
+    rc = [colmajor(r) for r in Rs]
+    m = np.array([x.shape[0] for x, _ in Xs], dtype=np.int64)
+    n = np.array([x.shape[1] for x, _ in Xs], dtype=np.int64)
+    ldx = np.array([ld for _, ld in Xs], dtype=np.int64)
+    ldq = np.array([ld for _, ld in qc], dtype=np.int64)
+    ldr = np.array([ld for _, ld in rc], dtype=np.int64)
+    xp = np.array([x.data_ptr() for x, _ in Xs], dtype=np.uint64)
+    qp = np.array([q.data_ptr() for q, _ in qc], dtype=np.uint64)
+    rp = np.array([r.data_ptr() for r, _ in rc], dtype=np.uint64)
+    opts = (Opts * count)()
+    for i in range(count):
+        opts[i].kind = int(kind)
+        opts[i].zeta = int(zeta)
+        opts[i].s = int(s[i] if s is not None else 2 * n[i])
+        opts[i].seed = int(seed[i] if isinstance(seed, (list, tuple)) else seed + i)
+        opts[i].prec = PREC_FP64
+        opts[i].S = None
+        opts[i].lds = 0
+    status = np.zeros(count, dtype=np.int32)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    h = _handle(Xs[0][0])
+    st = load().rclupp_factor_batched(h.bind(), int(algo), count, p(m), p(n), p(xp), p(ldx),
+                                      ctypes.cast(opts, _P), p(qp), p(ldq), p(rp), p(ldr), p(status))
+    _raise("rclupp_factor_batched", st, None, check)
+    return [q for q, _ in qc], [r for r, _ in rc], status
+
+
+def rclupp_set_batch_branches(branches: int, device=None):
+    """Parallel branches of the batched graph on the current handle."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    h = _handles.get(dev.index) or Handle(dev)
+    _handles[dev.index] = h
+    st = load().rclupp_set_batch_branches(h._h, int(branches))
+    _raise("rclupp_set_batch_branches", st)
 
 
 def rclupp_gram_noalloc(A, *, G=None):

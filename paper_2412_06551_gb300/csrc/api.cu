@@ -6,12 +6,17 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/rclupp.h"
 #include "common.cuh"
 #include "kernels.h"
 
 using namespace rq;
+
+namespace {
+constexpr int kMaxBranches = 64;
+}
 
 struct rclupp_handle_s {
     cudaStream_t stream = nullptr;
@@ -20,9 +25,68 @@ struct rclupp_handle_s {
     size_t ws_bytes = 0;
     DevStatus *d_status = nullptr;
     DevStatus *h_status = nullptr;  // pinned
+    // batched form: parallel branches of the batch graph and the cached graph
+    int batch_branches = 16;
+    int nstreams = 0;
+    cudaStream_t bstreams[kMaxBranches] = {};
+    cudaEvent_t join[kMaxBranches] = {};
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;  // origin stream of the batch graph's capture
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_sig = 0;
+    unsigned long long graph_kernels = 0;
 };
 
 namespace {
+
+rclupp_status_t ensure_streams(rclupp_handle_t h, int k) {
+    if (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
+        return RCLUPP_ERR_CUDA;
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return RCLUPP_ERR_CUDA;
+    while (h->nstreams < k) {
+        const int i = h->nstreams;
+        if (cudaStreamCreateWithFlags(&h->bstreams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming) != cudaSuccess)
+            return RCLUPP_ERR_CUDA;
+        ++h->nstreams;
+    }
+    return RCLUPP_OK;
+}
+
+// FNV-1a over the batch description (graph cache key).
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    template <class T>
+    void add(const T *p, size_t count) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < count * sizeof(T); ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+uint64_t batch_signature(int algo, int count, const int64_t *m, const int64_t *n,
+                         const double *const *X, const int64_t *ldx, double *const *Q,
+                         const int64_t *ldq, double *const *R, const int64_t *ldr,
+                         const rclupp_opts_t *o, int branches, const void *ws) {
+    Fnv f;
+    f.add(&algo, 1);
+    f.add(&count, 1);
+    f.add(m, count);
+    f.add(n, count);
+    f.add(X, count);
+    f.add(ldx, count);
+    f.add(Q, count);
+    f.add(ldq, count);
+    f.add(R, count);
+    f.add(ldr, count);
+    f.add(o, count);
+    f.add(&branches, 1);
+    f.add(&ws, 1);
+    return f.h;
+}
 
 constexpr int kMaxN = 256;
 constexpr int64_t kMaxS = 4096;
@@ -80,6 +144,10 @@ rclupp_status_t ensure_ws(rclupp_handle_t h, size_t bytes) {
     if (h->ws_bytes >= bytes) return RCLUPP_OK;
     if (h->ws) {
         cudaStreamSynchronize(h->stream);
+        if (h->graph_exec) {  // a cached batch graph points into the old workspace
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
         cudaFree(h->ws);
         h->ws = nullptr;
         h->ws_bytes = 0;
@@ -253,24 +321,32 @@ Verdict judge_first_pass(rclupp_handle_t h, const Bufs &b, int n) {
         if (_e != cudaSuccess) return RCLUPP_ERR_CUDA;   \
     } while (0)
 
+// Where a factorization's work is enqueued: its stream and its status word.
+struct Ctx {
+    cudaStream_t s;
+    DevStatus *st;
+};
+
+Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
+
 // Steps 5-7 of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
 // First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
-rclupp_status_t first_cholqr_pass(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
-                                  const double *X, int64_t ldx, double *Q, int64_t ldq) {
-    cudaStream_t s = h->stream;
-    DevStatus *st = h->d_status;
+rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
+                                  int64_t ldx, double *Q, int64_t ldq) {
+    cudaStream_t s = c.s;
+    DevStatus *st = c.st;
     RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, st, 3, s));
     return RCLUPP_OK;
 }
 
 // The rest of C3-C8 after R2 is known.
-rclupp_status_t rest_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n, double *Q,
-                             int64_t ldq, double *R, int64_t ldr) {
-    cudaStream_t s = h->stream;
-    DevStatus *st = h->d_status;
+rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, int64_t ldq,
+                             double *R, int64_t ldr) {
+    cudaStream_t s = c.s;
+    DevStatus *st = c.st;
     const int np = pad16(n);
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
     RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
@@ -309,7 +385,7 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
                 continue;
             }
         }
-        const rclupp_status_t st = first_cholqr_pass(h, b, m, n, X, ldx, Q, ldq);
+        const rclupp_status_t st = first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
         const Verdict v = judge_first_pass(h, b, n);
@@ -320,15 +396,78 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
             return RCLUPP_ERR_CUDA;
     }
     *tier_used = tier;
-    return rest_cholqr2(h, b, m, n, Q, ldq, R, ldr);
+    return rest_cholqr2(ctx_of(h), b, m, n, Q, ldq, R, ldr);
 }
 
-rclupp_status_t precond_then_cholqr2(rclupp_handle_t h, const Bufs &b, int64_t m, int n,
-                                     const double *X, int64_t ldx, double *Q, int64_t ldq,
-                                     double *R, int64_t ldr) {
-    const rclupp_status_t st = first_cholqr_pass(h, b, m, n, X, ldx, Q, ldq);
+// copy an m x n matrix (device to device, possibly different leading dims)
+cudaError_t copy_matrix(double *dst, int64_t ldd, const double *src, int64_t lds, int64_t m,
+                        int64_t n, cudaStream_t s);
+
+// ---- binary64 drivers as pure enqueues (no host synchronization) -------------
+// They put the whole factorization on c.s with its status in c.st, so they
+// can run several at once on different streams and be captured in a graph.
+
+// RCLUPP, Algorithm 6, binary64 sketch.
+rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int64_t m, int n,
+                               const double *X, int64_t ldx, double *Q, int64_t ldq, double *R,
+                               int64_t ldr) {
+    RQ_TRY(launch_sketch(X, ldx, m, n, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
+                         c.st, c.s));
+    RQ_TRY(launch_sketch_precond(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 1,
+                                 c.s));
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
     if (st != RCLUPP_OK) return st;
-    return rest_cholqr2(h, b, m, n, Q, ldq, R, ldr);
+    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr);
+}
+
+// RCLUPPr, Algorithm 7, binary64 sketch; the LU runs in L (ldl).
+rclupp_status_t enqueue_rcluppr(Ctx c, const Bufs &b, const rclupp_opts_t &o, int64_t m, int n,
+                                const double *X, int64_t ldx, double *L, int64_t ldl, double *Q,
+                                int64_t ldq, double *R, int64_t ldr) {
+    RQ_TRY(copy_matrix(L, ldl, X, ldx, m, n, c.s));
+    RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
+    RQ_TRY(launch_sketch(L, ldl, m, n, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
+                         c.st, c.s));
+    RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s));
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    if (st != RCLUPP_OK) return st;
+    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr);
+}
+
+// CholeskyQR2, Algorithm 2.
+rclupp_status_t enqueue_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
+                                int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr) {
+    const int np = pad16(n);
+    // [Q1, R1] = CholeskyQR(X)
+    RQ_TRY(launch_gram(X, ldx, m, n, 0, b.G, n, b.part, c.st, c.s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 3, c.s));
+    // [Q, Z] = CholeskyQR(Q1)
+    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, c.st, c.s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, c.st, 4, c.s));
+    // R = Z R1
+    RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
+    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st, c.s));
+    return RCLUPP_OK;
+}
+
+// LC2, Algorithm 4; the LU runs in L (ldl).
+rclupp_status_t enqueue_lc2(Ctx c, const Bufs &b, int64_t m, int n, const double *X, int64_t ldx,
+                            double *L, int64_t ldl, double *Q, int64_t ldq, double *R,
+                            int64_t ldr) {
+    const int np = pad16(n);
+    RQ_TRY(copy_matrix(L, ldl, X, ldx, m, n, c.s));
+    // [M, N, P] = LU(X)
+    RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
+    // G = M^T M; S = chol(G); R1 = S N
+    RQ_TRY(launch_gram(L, ldl, m, n, 1, b.G, n, b.part, c.st, c.s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[4], b.rinv[4], nullptr, 0, c.st, 3, c.s));
+    RQ_TRY(launch_lc2_r1(b.RP[4], np, L, ldl, n, b.RP[0], b.rinv[0], c.s));
+    // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
+    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, c.st, c.s));
+    RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, c.st, 4, c.s));
+    RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
+    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st, c.s));
+    return RCLUPP_OK;
 }
 
 // copy an m x n matrix (device to device, possibly different leading dims)
@@ -364,6 +503,14 @@ rclupp_status_t rclupp_create(rclupp_handle_t *handle, void *stream) {
 rclupp_status_t rclupp_destroy(rclupp_handle_t h) {
     if (!h) return RCLUPP_ERR_ARG;
     cudaStreamSynchronize(h->stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    for (int i = 0; i < h->nstreams; ++i) {
+        cudaStreamSynchronize(h->bstreams[i]);
+        cudaStreamDestroy(h->bstreams[i]);
+        cudaEventDestroy(h->join[i]);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ws) cudaFree(h->ws);
     if (h->d_status) cudaFree(h->d_status);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -466,27 +613,8 @@ rclupp_status_t cholqr2_factor(rclupp_handle_t h, int64_t m, int64_t n, const do
     if (st != RCLUPP_OK) return st;
     Bufs b = prepare(h, m, int(n), n, false, &st);
     if (st != RCLUPP_OK) return st;
-    cudaStream_t s = h->stream;
-    DevStatus *ds = h->d_status;
-    const int ni = int(n), np = pad16(ni);
-    rclupp_status_t ls = RCLUPP_OK;
-    do {
-        // [Q1, R1] = CholeskyQR(X)
-        if (launch_gram(X, ldx, m, ni, 0, b.G, n, b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_cholesky(b.G, n, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 3, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        // [Q, Z] = CholeskyQR(Q1)
-        if (launch_trsm_gram(X, ldx, m, ni, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, ds, s) !=
-            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_cholesky(b.G, n, ni, b.W, b.RP[1], b.rinv[1], nullptr, 0, ds, 4, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        // R = Z R1
-        if (launch_trmm_upper(b.RP[1], np, b.RP[0], np, ni, R, ldr, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_trsm_gram(Q, ldq, m, ni, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, ds, s) !=
-            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-    } while (0);
-    return finish(h, ls, info, nullptr);
+    return finish(h, enqueue_cholqr2(ctx_of(h), b, m, int(n), X, ldx, Q, ldq, R, ldr), info,
+                  nullptr);
 }
 
 rclupp_status_t lc2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X, int64_t ldx,
@@ -496,34 +624,142 @@ rclupp_status_t lc2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double
     const bool alias = (Q == X);
     Bufs b = prepare(h, m, int(n), n, alias, &st);
     if (st != RCLUPP_OK) return st;
-    cudaStream_t s = h->stream;
-    DevStatus *ds = h->d_status;
-    const int ni = int(n), np = pad16(ni);
     double *L = alias ? b.LUbuf : Q;
     const int64_t ldl = alias ? m : ldq;
-    rclupp_status_t ls = RCLUPP_OK;
-    do {
-        if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        // [M, N, P] = LU(X)
-        if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        // G = M^T M; S = chol(G); R1 = S N
-        if (launch_gram(L, ldl, m, ni, 1, b.G, n, b.part, ds, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_cholesky(b.G, n, ni, b.W, b.RP[4], b.rinv[4], nullptr, 0, ds, 3, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_lc2_r1(b.RP[4], np, L, ldl, ni, b.RP[0], b.rinv[0], s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
-        if (launch_trsm_gram(X, ldx, m, ni, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, ds, s) !=
-            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_cholesky(b.G, n, ni, b.W, b.RP[1], b.rinv[1], nullptr, 0, ds, 4, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_trmm_upper(b.RP[1], np, b.RP[0], np, ni, R, ldr, s) != cudaSuccess) {
-            ls = RCLUPP_ERR_CUDA; break; }
-        if (launch_trsm_gram(Q, ldq, m, ni, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, ds, s) !=
-            cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-    } while (0);
-    return finish(h, ls, info, nullptr);
+    return finish(h, enqueue_lc2(ctx_of(h), b, m, int(n), X, ldx, L, ldl, Q, ldq, R, ldr), info,
+                  nullptr);
+}
+
+// ---- batched form ------------------------------------------------------------
+
+rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t count,
+                                      const int64_t *m, const int64_t *n, const double *const *X,
+                                      const int64_t *ldx, const rclupp_opts_t *opts,
+                                      double *const *Q, const int64_t *ldq, double *const *R,
+                                      const int64_t *ldr, int32_t *status) {
+    if (!h || count < 0 || (count > 0 && (!m || !n || !X || !ldx || !Q || !ldq || !R || !ldr)))
+        return RCLUPP_ERR_ARG;
+    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_LC2) return RCLUPP_ERR_ARG;
+    if (count == 0) return RCLUPP_OK;
+    // validate every problem and size one branch's workspace for the largest
+    std::vector<rclupp_opts_t> o(count);
+    size_t per_branch = 0;
+    for (int i = 0; i < count; ++i) {
+        rclupp_status_t st = check_common(h, m[i], n[i], X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+        if (st != RCLUPP_OK) return st;
+        o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
+        if (algo <= RCLUPP_ALGO_RCLUPPR) {
+            if ((st = check_opts(o[i], m[i], n[i])) != RCLUPP_OK) return st;
+            if (o[i].prec != RCLUPP_PREC_FP64) return RCLUPP_ERR_UNSUPPORTED;
+        }
+        const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
+        const int64_t s = algo <= RCLUPP_ALGO_RCLUPPR ? o[i].s : n[i];
+        size_t total = 0;
+        carve(nullptr, m[i], int(n[i]), s, own_lu, &total);
+        per_branch = std::max(per_branch, total);
+    }
+    per_branch = (per_branch + 255) & ~size_t(255);
+    const int branches = std::max(1, std::min<int>(count, h->batch_branches));
+    const size_t status_bytes = (size_t(count) * sizeof(DevStatus) + 255) & ~size_t(255);
+    rclupp_status_t st = ensure_ws(h, per_branch * branches + status_bytes);
+    if (st != RCLUPP_OK) return st;
+    if (ensure_streams(h, branches) != RCLUPP_OK) return RCLUPP_ERR_CUDA;
+    char *base = static_cast<char *>(h->ws);
+    DevStatus *d_st = reinterpret_cast<DevStatus *>(base + per_branch * branches);
+
+    // Graph of the whole batch: fork into `branches` streams, matrix i on
+    // branch i mod branches, join.  Reused while the batch is unchanged.
+    const uint64_t sig = batch_signature(algo, count, m, n, X, ldx, Q, ldq, R, ldr, o.data(),
+                                         branches, h->ws);
+    if (!(h->graph_exec && h->graph_sig == sig)) {
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        // capture on the handle's own origin stream (the caller's stream may be the
+        // legacy default stream, which cannot be captured); launch on the caller's
+        if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return RCLUPP_ERR_CUDA;
+        rclupp_status_t ls = RCLUPP_OK;
+        if (cudaMemsetAsync(d_st, 0, size_t(count) * sizeof(DevStatus), h->cap) != cudaSuccess ||
+            cudaEventRecord(h->fork, h->cap) != cudaSuccess)
+            ls = RCLUPP_ERR_CUDA;
+        for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
+            if (cudaStreamWaitEvent(h->bstreams[k], h->fork, 0) != cudaSuccess) ls = RCLUPP_ERR_CUDA;
+        for (int i = 0; i < count && ls == RCLUPP_OK; ++i) {
+            const int k = i % branches;
+            const Ctx c{h->bstreams[k], d_st + i};
+            const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
+            const int64_t s = algo <= RCLUPP_ALGO_RCLUPPR ? o[i].s : n[i];
+            size_t total = 0;
+            const Bufs b = carve(base + per_branch * k, m[i], int(n[i]), s, own_lu, &total);
+            double *L = own_lu ? b.LUbuf : Q[i];
+            const int64_t ldl = own_lu ? m[i] : ldq[i];
+            const int ni = int(n[i]);
+            switch (algo) {
+                case RCLUPP_ALGO_RCLUPP:
+                    ls = enqueue_rclupp(c, b, o[i], m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                    break;
+                case RCLUPP_ALGO_RCLUPPR:
+                    ls = enqueue_rcluppr(c, b, o[i], m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i],
+                                         ldr[i]);
+                    break;
+                case RCLUPP_ALGO_CHOLQR2:
+                    ls = enqueue_cholqr2(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                    break;
+                default:
+                    ls = enqueue_lc2(c, b, m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i], ldr[i]);
+                    break;
+            }
+        }
+        for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
+            if (cudaEventRecord(h->join[k], h->bstreams[k]) != cudaSuccess ||
+                cudaStreamWaitEvent(h->cap, h->join[k], 0) != cudaSuccess)
+                ls = RCLUPP_ERR_CUDA;
+        const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+        if (ls != RCLUPP_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return ls != RCLUPP_OK ? ls : RCLUPP_ERR_CUDA;
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(graph, nodes.data(), &nn);
+        h->graph_kernels = 0;
+        for (size_t j = 0; j < nn; ++j) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[j], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                ++h->graph_kernels;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            h->graph_exec = nullptr;
+            return RCLUPP_ERR_CUDA;
+        }
+        h->graph_sig = sig;
+    }
+    if (cudaGraphLaunch(h->graph_exec, h->stream) != cudaSuccess) return RCLUPP_ERR_CUDA;
+    prof_add_launches(h->graph_kernels);
+    std::vector<DevStatus> hs(count);
+    if (cudaMemcpyAsync(hs.data(), d_st, size_t(count) * sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return RCLUPP_ERR_CUDA;
+    rclupp_status_t first = RCLUPP_OK;
+    for (int i = 0; i < count; ++i) {
+        if (status) status[i] = hs[i].code;
+        if (first == RCLUPP_OK && hs[i].code != 0) first = static_cast<rclupp_status_t>(hs[i].code);
+    }
+    return first;
+}
+
+rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t h, int32_t branches) {
+    if (!h || branches < 1 || branches > kMaxBranches) return RCLUPP_ERR_ARG;
+    h->batch_branches = branches;
+    return RCLUPP_OK;
 }
 
 // ---- individual steps ----

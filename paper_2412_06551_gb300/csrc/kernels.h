@@ -146,6 +146,7 @@ enum KernelId : int {
 // brackets the launch on its stream.
 void prof_begin(int kid, cudaStream_t stream);
 void prof_end(int kid, cudaStream_t stream);
+void prof_add_launches(unsigned long long k);
 
 #define RQ_LAUNCH(KID, STREAM, ...)       \
     do {                                  \

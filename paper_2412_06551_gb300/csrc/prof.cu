@@ -48,7 +48,20 @@ const char *kNames[KID_COUNT] = {"sketch_gauss", "sketch_sparse", "gram",       
 
 }  // namespace
 
+static bool capturing(cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Kernels inside a captured graph are counted when the graph is launched.
+void prof_add_launches(unsigned long long k) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.launches += k;
+}
+
 void prof_begin(int kid, cudaStream_t stream) {
+    if (capturing(stream)) return;
     Profiler &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     ++p.launches;
@@ -59,6 +72,7 @@ void prof_begin(int kid, cudaStream_t stream) {
 }
 
 void prof_end(int kid, cudaStream_t stream) {
+    if (capturing(stream)) return;
     Profiler &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     if (!p.enabled || p.open_a[kid] == nullptr) return;

@@ -1,0 +1,107 @@
+"""Batched form: many uneven factorizations in one graph launch.
+
+The batch runs the same kernels as single calls with the same launch
+shapes, so every problem's Q and R must equal the single call's bit for bit;
+against the oracle they meet the usual gates.  Each problem reports its own
+status.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    a = np.asfortranarray(a)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda").t()
+
+
+def host(t):
+    return np.asfortranarray(t.detach().cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def rq():
+    import paper_2412_06551_gb300 as m
+    m.load()
+    return m
+
+
+def _batch(count, seed, nmax=128):
+    g = np.random.default_rng(seed)
+    ns = g.choice([1, 3, 16, 33, 64, 96, nmax], size=count)
+    ms = np.maximum(ns, np.exp(g.uniform(np.log(64), np.log(6000), size=count)).astype(int))
+    kap = 10.0 ** g.uniform(1, 8, size=count)
+    xs = [synth.svd_matrix(int(m), int(n), float(k), 1000 + i) for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
+    return xs, kap
+
+
+ALGOS = [(0, "rclupp"), (1, "rcluppr"), (2, "cholqr2"), (3, "lc2")]
+
+
+@pytest.mark.parametrize("algo,name", ALGOS)
+def test_batched_equals_single_calls(rq, algo, name):
+    xs, kap = _batch(20, algo + 5)
+    Xs = [dev(x) for x in xs]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=algo, seed=77)
+    assert np.all(st == 0)
+    for i, X in enumerate(Xs):
+        if algo == 0:
+            Q, R, _ = rq.rclupp_factor(X, seed=77 + i)
+        elif algo == 1:
+            Q, R, _ = rq.rclupp_r_factor(X, seed=77 + i)
+        elif algo == 2:
+            Q, R, _ = rq.cholqr2_factor(X)
+        else:
+            Q, R, _ = rq.lc2_factor(X)
+        assert torch.equal(Q, Qb[i]) and torch.equal(R, Rb[i]), i
+
+
+@pytest.mark.parametrize("algo,name", ALGOS)
+def test_batched_against_oracle(rq, algo, name):
+    xs, kap = _batch(8, algo + 50, nmax=64)
+    Xs = [dev(x) for x in xs]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=algo, seed=5)
+    for i, x in enumerate(xs):
+        m, n = x.shape
+        if name == "rclupp":
+            q_o, r_o, _ = oracle.rclupp(x, S=oracle.gaussian_sketch_matrix(2 * n, m, 5 + i))
+        elif name == "rcluppr":
+            q_o, r_o, _ = oracle.rcluppr(x, S=oracle.gaussian_sketch_matrix(2 * n, m, 5 + i))
+        else:
+            q_o, r_o, _ = getattr(oracle, name)(x)
+        q, r = host(Qb[i]), host(Rb[i])
+        assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+        assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
+        if kap[i] <= 1e6:
+            assert np.linalg.norm(r - r_o) / np.linalg.norm(r_o) <= 1e-10 * kap[i]
+
+
+def test_graph_is_reused_and_rebuilt(rq):
+    xs, _ = _batch(10, 9)
+    Xs = [dev(x) for x in xs]
+    Q1, R1, _ = rq.rclupp_factor_batched(Xs, seed=3)
+    Q2, R2, _ = rq.rclupp_factor_batched(Xs, Qs=Q1 and None, seed=3)  # new outputs: new graph
+    for a, b in zip(R1, R2):
+        assert torch.equal(a, b)
+    Q3, R3, _ = rq.rclupp_factor_batched(Xs, Qs=Q2, Rs=R2, seed=3)   # same pointers: cached graph
+    for a, b in zip(R1, R3):
+        assert torch.equal(a, b)
+    rq.rclupp_set_batch_branches(3)
+    Q4, R4, _ = rq.rclupp_factor_batched(Xs, seed=3)                  # other branch count
+    for a, b in zip(R1, R4):
+        assert torch.equal(a, b)
+    rq.rclupp_set_batch_branches(16)
+
+
+def test_per_problem_status(rq):
+    good = synth.svd_matrix(500, 8, 1e2, 1)
+    bad = np.zeros((400, 8))
+    bad[:, 0] = 1.0  # rank 1: Cholesky breaks down
+    Qb, Rb, st = rq.rclupp_factor_batched([dev(good), dev(bad), dev(good)], algo=2, check=False)
+    assert st[0] == 0 and st[2] == 0
+    assert st[1] == rq.Status.ERR_CHOL_BREAKDOWN
