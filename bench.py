@@ -75,8 +75,10 @@ def parse():
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "sketch_gauss", "sketch_sparse",
                                       "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
-    p.add_argument("--workload", choices=["side_by_side", "precision"], default="side_by_side",
-                   help="precision: FP64 vs tensor-core sketch RCLUPP at m=2^22, n=256, s=512")
+    p.add_argument("--workload", choices=["side_by_side", "precision", "batched"],
+                   default="side_by_side",
+                   help="precision: FP64 vs tensor-core sketch RCLUPP at m=2^22, n=256, s=512; "
+                        "batched: 512 uneven RCLUPP problems in one batched call")
     p.add_argument("--prec", type=int, default=0, help="sketch tier for --case runs")
     p.add_argument("--m", type=int, default=1 << 18)
     p.add_argument("--n", type=int, default=N)
@@ -293,6 +295,60 @@ def run_precision(args):
                       "m": m, "n": n, "s": s, "results": rows}), flush=True)
 
 
+def batched_problems(count=512):
+    """The batched workload: m = floor(2^U(12,17)), n uniform in
+    {16, 32, 48, 64, 96, 128}, kappa = 10^U(2,12), Gaussian s = 2n."""
+    g = synth.rng(synth.kappa_seed(3, 0))
+    ms = np.floor(2.0 ** g.uniform(12, 17, count)).astype(np.int64)
+    ns = g.choice(np.array([16, 32, 48, 64, 96, 128]), count)
+    kap = 10.0 ** g.uniform(2, 12, count)
+    return ms, ns, kap
+
+
+def run_batched(args):
+    """512 uneven RCLUPP factorizations: one batched call (cached CUDA graph,
+    autotuned branch count) against the same problems as single calls."""
+    import torch
+    import paper_2412_06551_gb300 as rq
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    ms, ns, kap = batched_problems()
+    base = synth.kappa_seed(3, 0)
+    Xs = [to_dev(synth.svd_matrix(int(m), int(n), float(k), base + 1 + i), torch, device)
+          for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
+    model = float(np.sum(2.0 * ms * ns * ns))
+    branches, tune_ms = rq.rclupp_autotune_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base)
+    Qs = [rq.empty_colmajor(int(m), int(n), device) for m, n in zip(ms, ns)]
+    Rs = [rq.empty_colmajor(int(n), int(n), device) for n in ns]
+    call = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs)
+    for _ in range(max(3, args.warmup)):
+        call()
+    l0 = rq.kernel_launches()
+    batch_ms, (_, _, status) = time_call(torch, stream, call, args.steps)
+    launches = (rq.kernel_launches() - l0) // args.steps
+    # the same problems as sequential single calls
+    def seq():
+        for i, X in enumerate(Xs):
+            rq.rclupp_factor(X, seed=base + i, Q=Qs[i], R=Rs[i], check=False)
+    seq()
+    seq_ms, _ = time_call(torch, stream, seq, 1)
+    worst_orth, worst_res = 0.0, 0.0
+    for i in range(len(Xs)):
+        o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
+        worst_orth, worst_res = max(worst_orth, o), max(worst_res, r)
+    line = {
+        "workload": "batched RCLUPP: 512 FP64 problems, m=floor(2^U(12,17)), n in {16..128}, "
+                    "kappa=10^U(2,12), Gaussian s=2n",
+        "problems": len(Xs), "rows_total": int(ms.sum()), "model_flops": model,
+        "branches_autotuned": branches, "ms_per_batch": batch_ms,
+        "gflops_2mn2": model / (batch_ms / 1e3) / 1e9,
+        "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
+        "gpu_launches_per_batch": int(launches), "statuses_nonzero": int(np.count_nonzero(status)),
+        "worst_orth": worst_orth, "worst_res": worst_res,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
 
@@ -489,6 +545,8 @@ def main():
         run_case(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "batched":
+        run_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -195,6 +195,19 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t handle, int32_t algo, int3
 /* Number of parallel branches of the batched graph (1 ..64). */
 rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t handle, int32_t branches);
 
+/* Autotuner of the batched form: runs the batch (same arguments as
+ * rclupp_factor_batched; outputs are overwritten) with 4, 8, 16, 32 and 64
+ * branches (up to the batch size), times one replay of each cached graph
+ * with CUDA events on the handle's stream, keeps the fastest in the handle
+ * and returns it in *best_branches and its time in *best_ms (either may be
+ * NULL).  A numerical breakdown of a problem does not stop the tuning. */
+rclupp_status_t rclupp_autotune_batched(rclupp_handle_t handle, int32_t algo, int32_t count,
+                                        const int64_t *m, const int64_t *n,
+                                        const double *const *X, const int64_t *ldx,
+                                        const rclupp_opts_t *opts, double *const *Q,
+                                        const int64_t *ldq, double *const *R, const int64_t *ldr,
+                                        int32_t *best_branches, float *best_ms);
+
 /* ---- individual steps of the tall path (each is one row of the path) ---- */
 
 /* Y = S A (s x n, ldy >= s): the sketch of Algorithm 6 step 1 (S X) and of

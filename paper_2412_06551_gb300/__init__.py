@@ -27,7 +27,8 @@ __all__ = [
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
     "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
-    "rclupp_factor_batched", "rclupp_set_batch_branches", "ALGO_RCLUPP", "ALGO_RCLUPPR",
+    "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
+    "ALGO_RCLUPP", "ALGO_RCLUPPR",
     "ALGO_CHOLQR2", "ALGO_LC2",
     "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
 ]
@@ -100,6 +101,8 @@ _SIGNATURES = {
     "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "rclupp_factor_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "rclupp_set_batch_branches": ([_P, _I32], _I32),
+    "rclupp_autotune_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)], _I32),
     "rclupp_profile_enable": ([ctypes.c_int], None),
     "rclupp_profile_reset": ([], None),
     "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -358,6 +361,26 @@ def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN,
     """Factor a list of column-major matrices in one batched call (one CUDA
     graph).  s is a per-problem list (or None for 2 n); seed is a list or an
     int (then seed + i for problem i).  Returns (Qs, Rs, statuses)."""
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed)
+    st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
+    _raise("rclupp_factor_batched", st, None, check)
+    return a["Qs"], a["Rs"], a["status"]
+
+
+def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
+                            Qs=None, Rs=None):
+    """Time the batch over candidate branch counts and keep the fastest in
+    the handle.  Returns (branches, ms of one batched call)."""
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed)
+    best = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    st = load().rclupp_autotune_batched(a["h"], int(algo), a["count"], *a["args"], ctypes.byref(best),
+                                        ctypes.byref(ms))
+    _raise("rclupp_autotune_batched", st)
+    return int(best.value), float(ms.value)
+
+
+def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed):
     import numpy as np
     count = len(Xs)
     Xs = [colmajor(x) for x in Xs]
@@ -386,10 +409,10 @@ def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN,
     status = np.zeros(count, dtype=np.int32)
     p = lambda a: ctypes.c_void_p(a.ctypes.data)
     h = _handle(Xs[0][0])
-    st = load().rclupp_factor_batched(h.bind(), int(algo), count, p(m), p(n), p(xp), p(ldx),
-                                      ctypes.cast(opts, _P), p(qp), p(ldq), p(rp), p(ldr), p(status))
-    _raise("rclupp_factor_batched", st, None, check)
-    return [q for q, _ in qc], [r for r, _ in rc], status
+    keep = (m, n, xp, ldx, opts, qp, ldq, rp, ldr, status)
+    return {"h": h.bind(), "count": count, "keep": keep, "status": status, "pst": p(status),
+            "args": (p(m), p(n), p(xp), p(ldx), ctypes.cast(opts, _P), p(qp), p(ldq), p(rp), p(ldr)),
+            "Qs": [q for q, _ in qc], "Rs": [r for r, _ in rc]}
 
 
 def rclupp_set_batch_branches(branches: int, device=None):

@@ -268,30 +268,6 @@ int next_tier(int tier) {
     return tier == RCLUPP_PREC_SKETCH_BF16 ? RCLUPP_PREC_SKETCH_FP32 : RCLUPP_PREC_FP64;
 }
 
-// Before the first tall pass: R1's diagonal spread bounds kappa(R1) ~ kappa(X)
-// from below.  A tier whose sketch error times kappa(X) would leave Q1 far
-// beyond what CholeskyQR2 repairs is skipped at once (the limits are where the
-// bf16 and three-term tiers stopped meeting the binary64 accuracy).
-constexpr double kMaxSpreadBF16 = 1.0e11;
-constexpr double kMaxSpreadFP32 = 1.0e13;
-
-// Spread max/min of |diag| of a padded factor (synchronizes the stream).
-bool diag_spread(rclupp_handle_t h, const double *RP, int n, double *spread) {
-    const int np = pad16(n);
-    double diag[256];
-    if (cudaMemcpy2DAsync(diag, sizeof(double), RP, size_t(np + 1) * sizeof(double),
-                          sizeof(double), size_t(n), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess)
-        return false;
-    double lo = std::abs(diag[0]), hi = lo;
-    for (int i = 1; i < n; ++i) {
-        lo = std::min(lo, std::abs(diag[i]));
-        hi = std::max(hi, std::abs(diag[i]));
-    }
-    *spread = (lo > 0.0) ? hi / lo : 1.0e300;
-    return true;
-}
-
 enum class Verdict { Accept, Escalate, Fail };
 
 // Synchronizes the stream and judges the first Cholesky of a reduced tier.
@@ -372,19 +348,9 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
         if (sketch_step(b, SA, ldsa, m, n, unit_lower, o, tier, h->d_status, h->stream) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
         if (precond() != cudaSuccess) return RCLUPP_ERR_CUDA;
-        // (RCLUPP only: RCLUPPr sketches the well-conditioned M, and R1's
-        // spread there comes from N, which the sketch does not touch)
-        if (tier != RCLUPP_PREC_FP64 && !unit_lower) {
-            double spread = 0.0;
-            if (!diag_spread(h, b.RP[0], n, &spread)) return RCLUPP_ERR_CUDA;
-            const double limit = tier == RCLUPP_PREC_SKETCH_BF16 ? kMaxSpreadBF16 : kMaxSpreadFP32;
-            if (!(spread <= limit)) {
-                tier = next_tier(tier);
-                if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
-                    return RCLUPP_ERR_CUDA;
-                continue;
-            }
-        }
+        // No a-priori test on R1 is made: a reduced-tier R1 only sees the
+        // rounded X, whose condition number saturates near 1/u of the tier,
+        // so R1 cannot tell an X the tier handles from one it does not.
         const rclupp_status_t st = first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
@@ -760,6 +726,45 @@ rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t h, int32_t branches) {
     if (!h || branches < 1 || branches > kMaxBranches) return RCLUPP_ERR_ARG;
     h->batch_branches = branches;
     return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t count,
+                                        const int64_t *m, const int64_t *n,
+                                        const double *const *X, const int64_t *ldx,
+                                        const rclupp_opts_t *opts, double *const *Q,
+                                        const int64_t *ldq, double *const *R, const int64_t *ldr,
+                                        int32_t *best_branches, float *best_ms) {
+    if (!h) return RCLUPP_ERR_ARG;
+    static const int kCandidates[] = {4, 8, 16, 32, 64};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return RCLUPP_ERR_CUDA;
+    int best = h->batch_branches;
+    float best_t = 0.f;
+    rclupp_status_t st = RCLUPP_OK;
+    for (int b : kCandidates) {
+        if (b > std::max<int>(count, 1) && b != kCandidates[0]) break;
+        h->batch_branches = b;
+        // first call builds and caches the graph; the second one is timed
+        st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
+        if (st != RCLUPP_OK && st != RCLUPP_ERR_CHOL_BREAKDOWN && st != RCLUPP_ERR_LU_ZERO_PIVOT) break;
+        cudaEventRecord(e0, h->stream);
+        st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (best_t == 0.f || t < best_t) {
+            best_t = t;
+            best = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->batch_branches = best;
+    if (best_branches) *best_branches = best;
+    if (best_ms) *best_ms = best_t;
+    return (st == RCLUPP_ERR_CHOL_BREAKDOWN || st == RCLUPP_ERR_LU_ZERO_PIVOT) ? RCLUPP_OK : st;
 }
 
 // ---- individual steps ----
