@@ -80,6 +80,9 @@ def _load():
                 "orc_gaussian_sketch_matrix": ([I64, I64, U64, P, I64], None),
                 "orc_sparse_sign_column": ([U64, I64, I64, I32, P, P], None),
                 "orc_sparse_sign_pattern": ([I64, I64, I32, U64, P, P], None),
+                "orc_rcholqr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P], I32),
+                "orc_scholqr3": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
+                "orc_scholqr3_shift": ([I64, I64, P, I64], ctypes.c_double),
                 "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
                 "orc_sketch_bf16": ([I64, I64, I64, U64, I32, P, I64, P, I64], I32),
             }
@@ -283,6 +286,28 @@ def rclupp(x, S=None, sparse=None, raise_on_error: bool = True):
 def rcluppr(x, S=None, sparse=None, raise_on_error: bool = True):
     """[Q, R] = RCLUPPr(X) (Algorithm 7) with dense S or sparse=(s, zeta, rows, signs)."""
     return _rand_driver("orc_rcluppr", x, S, sparse, raise_on_error)
+
+
+def rcholqr(x, S=None, sparse=None, raise_on_error: bool = True):
+    """[Q, R] = RCholeskyQR(X) (Algorithm 5, one sketch, one CholeskyQR)."""
+    return _rand_driver("orc_rcholqr", x, S, sparse, raise_on_error)
+
+
+def scholqr3(x, raise_on_error: bool = True):
+    """[Q, R] = SCholeskyQR3(X) (Algorithm 3, shift 11(mnu + n(n+1)u)||X||_g^2)."""
+    x = _f(x)
+    m, n = x.shape
+    q, r, info = _qr_out(m, n)
+    st = _load().orc_scholqr3(m, n, _p(x), m, _p(q), m, _p(r), n, _p(info))
+    _check(st, info, raise_on_error)
+    return q, r, st
+
+
+def scholqr3_shift(m: int, g) -> float:
+    """The shift s of SCholeskyQR3 from the Gram matrix G of an m-row X."""
+    g = _f(g)
+    n = g.shape[0]
+    return float(_load().orc_scholqr3_shift(m, n, _p(g), n))
 
 
 # ------------------------------------------------------------ generators ---

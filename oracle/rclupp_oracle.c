@@ -597,6 +597,91 @@ int orc_lc2(int64_t m, int64_t n, const double *X, int64_t ldx, double *Q, int64
     return st;
 }
 
+/* [Q, R] = RCholeskyQR(X) (Algorithm 5, single sketch):
+ *   K = S X; R1 = R-factor of HouseholderQR(K) (diagonal signs normalised);
+ *   Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1. */
+int orc_rcholqr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int64_t s, int zeta,
+                const double *S, int64_t lds, const int32_t *rows, const int8_t *signs, double *Q,
+                int64_t ldq, double *R, int64_t ldr, int64_t *info)
+{
+    if (m < n || n < 1 || s < n)
+        return ORC_ERR_ARG;
+    size_t mn = (size_t)m * (size_t)n, nn = (size_t)n * (size_t)n;
+    double *K = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
+    double *R1 = (double *)malloc(sizeof(double) * nn);
+    double *Q1 = (double *)malloc(sizeof(double) * mn);
+    double *G = (double *)malloc(sizeof(double) * nn);
+    double *Z = (double *)malloc(sizeof(double) * nn);
+    int st = ORC_ERR_NOMEM;
+    int64_t col = -1;
+    if (K && R1 && Q1 && G && Z) {
+        orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, X, ldx, K, s);
+        orc_householder_r(s, n, K, s, R1, n);
+        orc_sign_fix_rows(n, R1, n);
+        orc_trsm_right_upper(m, n, X, ldx, R1, n, Q1, m);
+        orc_gram(m, n, Q1, m, G, n);
+        st = orc_cholesky(n, G, n, Z, n, &col);
+        if (st != ORC_OK) {
+            if (info)
+                *info = 100000 + col;
+        } else {
+            orc_trsm_right_upper(m, n, Q1, m, Z, n, Q, ldq);
+            orc_trmm_upper(n, Z, n, R1, n, R, ldr);
+            if (info)
+                *info = -1;
+        }
+    }
+    free(Z);
+    free(G);
+    free(Q1);
+    free(R1);
+    free(K);
+    return st;
+}
+
+/* Shift of SCholeskyQR3 (Section 2.2): s = 11 (m n u + n (n+1) u) ||X||_g^2
+ * with ||X||_g = max_j ||X_j||_2 (Definition 2.1), ||X_j||_2^2 = G_jj. */
+double orc_scholqr3_shift(int64_t m, int64_t n, const double *G, int64_t ldg)
+{
+    const double u = 0x1p-53;
+    double g = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        if (IDX(G, ldg, j, j) > g)
+            g = IDX(G, ldg, j, j);
+    return 11.0 * ((double)m * (double)n * u + (double)n * (double)(n + 1) * u) * g;
+}
+
+/* [Q, R] = SCholeskyQR3(X) (Algorithm 3): G = X^T X; R1 = chol(G + s I);
+ * Q1 = X R1^{-1}; [Q, Z] = CholeskyQR2(Q1); R = Z R1, evaluated like the
+ * randomized drivers (R3 = R2 R1, R = R4 R3). */
+int orc_scholqr3(int64_t m, int64_t n, const double *X, int64_t ldx, double *Q, int64_t ldq,
+                 double *R, int64_t ldr, int64_t *info)
+{
+    if (m < n || n < 1)
+        return ORC_ERR_ARG;
+    size_t nn = (size_t)n * (size_t)n;
+    double *G = (double *)malloc(sizeof(double) * nn);
+    double *R1 = (double *)malloc(sizeof(double) * nn);
+    int st = ORC_ERR_NOMEM;
+    int64_t col = -1;
+    if (G && R1) {
+        orc_gram(m, n, X, ldx, G, n);
+        const double shift = orc_scholqr3_shift(m, n, G, n);
+        for (int64_t j = 0; j < n; ++j)
+            IDX(G, n, j, j) += shift;
+        st = orc_cholesky(n, G, n, R1, n, &col);
+        if (st != ORC_OK) {
+            if (info)
+                *info = col;
+        } else {
+            st = orc_precond_then_cholqr2(m, n, X, ldx, R1, Q, ldq, R, ldr, info);
+        }
+    }
+    free(R1);
+    free(G);
+    return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based sketch generators                                           */
 /*                                                                          */

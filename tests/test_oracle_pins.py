@@ -473,3 +473,61 @@ def test_sketch_bf16_definition(nterms):
     full = oracle.sketch_dense(oracle.gaussian_sketch_matrix(s, m, seed), x)
     tol = (2.0 ** -8 if nterms == 1 else 2.0 ** -7) * np.abs(Sb / math.sqrt(s)) @ np.abs(x) * 3
     assert np.all(np.abs(y - full) <= tol + 1e-300)
+
+
+# ------------------------------------- comparison paths (Algorithms 3, 5) ---
+
+def test_scholqr3_shift_closed_form():
+    m, n = 1000, 7
+    x = synth.integer_matrix(m, n, 4)
+    g = oracle.gram(x)
+    s = oracle.scholqr3_shift(m, g)
+    col_norm2 = np.max(np.sum(x * x, axis=0))       # ||X||_g^2 (Definition 2.1)
+    assert s == 11.0 * (m * n * U + n * (n + 1) * U) * col_norm2
+
+
+@pytest.mark.parametrize("name", ["rcholqr", "scholqr3"])
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_comparison_paths_brute_force(name, n):
+    x = synth.svd_matrix(40, n, 1e3, 200 + n)
+    q_ref, r_ref = _mp_qr(x)
+    if name == "rcholqr":
+        q, r, st = oracle.rcholqr(x, S=synth.gaussian_sketch(max(2 * n, 4), 40, 4))
+    else:
+        q, r, st = oracle.scholqr3(x)
+    assert np.max(np.abs(r - r_ref)) <= 1e-12 * np.max(np.abs(r_ref))
+    assert np.max(np.abs(q - q_ref)) <= 1e-11
+
+
+def test_scholqr3_lemma_3_2():
+    # orthogonality 6(mnu + n(n+1)u) and residual 6.57 n^2 u ||X||_g + 4.81 n^2 u ||X||_2
+    m, n = 4096, 32
+    x = synth.svd_matrix(m, n, 1e6, 81)
+    q, r, st = oracle.scholqr3(x)
+    assert oracle.orthogonality(q) <= 6 * (m * n * U + n * (n + 1) * U)
+    xg = np.max(np.linalg.norm(x, axis=0))
+    assert np.linalg.norm(q @ r - x, "fro") <= 6.57 * n * n * U * xg + 4.81 * n * n * U * 1.0
+
+
+def test_rcholqr_orthogonality_worse_than_rclupp_when_ill_conditioned():
+    # Section 5.1: RCholeskyQR's single CholeskyQR leaves worse orthogonality
+    # than RCLUPP on ill-conditioned X (qualitative claim)
+    m, n = 4096, 32
+    x = synth.svd_matrix(m, n, 1e12, 82)
+    S = synth.gaussian_sketch(64, m, 83)
+    q1, r1, st1 = oracle.rcholqr(x, S=S, raise_on_error=False)
+    q2, r2, st2 = oracle.rclupp(x, S=S)
+    assert st2 == 0
+    if st1 == 0:
+        assert oracle.orthogonality(q1) > oracle.orthogonality(q2)
+
+
+def test_scholqr3_breaks_down_where_rclupp_does_not():
+    # Section 2.2 / 5.1: SCholeskyQR3 fails as kappa approaches 1/u
+    m, n = 2000, 20
+    x = synth.svd_matrix(m, n, 1e15, 84)
+    q, r, st = oracle.scholqr3(x, raise_on_error=False)
+    ok = st == 0 and oracle.orthogonality(q) < 1e-10
+    q2, r2, st2 = oracle.rcluppr(x, S=synth.gaussian_sketch(40, m, 85))
+    assert st2 == 0 and oracle.orthogonality(q2) < 1e-12
+    assert not ok or oracle.orthogonality(q) > oracle.orthogonality(q2)
