@@ -99,8 +99,9 @@ typedef struct {
 /* Diagnostic output of a factorization (may be NULL). */
 typedef struct {
     int32_t status;      /* same as the return value */
-    int32_t failed_step; /* 0 none; 1 sketch LU; 2 tall LU; 3 first Cholesky;
-                            4 second Cholesky; 5 third Cholesky (LC2 / CholeskyQR2) */
+    int32_t failed_step; /* 0 none; 1 sketch LU; 2 tall LU; 3 first Cholesky of the
+                            CholeskyQR passes; 4 second one; 6 shifted Cholesky
+                            (SCholeskyQR3) */
     int64_t info;        /* failing column for breakdown / zero pivot, else -1 */
     int32_t prec_used;   /* sketch tier that produced the result (rclupp_precision_t);
                             RCLUPP/RCLUPPr escalate bf16 -> three-term bf16 -> FP64 when
@@ -162,13 +163,34 @@ rclupp_status_t lc2_factor(rclupp_handle_t handle, int64_t m, int64_t n, const d
                            int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
                            rclupp_info_t *info);
 
+/* [Q, R] = RCholeskyQR(X) -- Algorithm 5 (single sketch): K = S X;
+ * R1 = R of HouseholderQR(K) (signs normalised); Q1 = X R1^{-1};
+ * [Q, Z] = CholeskyQR(Q1); R = Z R1.  A comparison path: one CholeskyQR
+ * after the preconditioner, so its orthogonality is worse than RCLUPP's on
+ * ill-conditioned X (Section 5.1).  Arguments as rclupp_factor; the sketch
+ * tier is used as given (no escalation). */
+rclupp_status_t rcholqr_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                               int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                               double *R, int64_t ldr, rclupp_info_t *info);
+
+/* [Q, R] = SCholeskyQR3(X) -- Algorithm 3 with the shift of Section 2.2,
+ * s = 11 (m n u + n (n+1) u) ||X||_g^2, ||X||_g = max_j ||X_j||_2
+ * (Definition 2.1): G = X^T X; R1 = chol(G + s I); Q1 = X R1^{-1};
+ * [Q, Z] = CholeskyQR2(Q1); R = Z R1.  failed_step 6 marks a breakdown of
+ * the shifted Cholesky. */
+rclupp_status_t scholqr3_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
+                                int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
+                                rclupp_info_t *info);
+
 /* ---- batched form ---------------------------------------------------------- */
 
 typedef enum {
     RCLUPP_ALGO_RCLUPP = 0,  /* Algorithm 6 */
     RCLUPP_ALGO_RCLUPPR = 1, /* Algorithm 7 */
     RCLUPP_ALGO_CHOLQR2 = 2, /* Algorithm 2 */
-    RCLUPP_ALGO_LC2 = 3      /* Algorithm 4 */
+    RCLUPP_ALGO_LC2 = 3,     /* Algorithm 4 */
+    RCLUPP_ALGO_RCHOLQR = 4, /* Algorithm 5 */
+    RCLUPP_ALGO_SCHOLQR3 = 5 /* Algorithm 3 */
 } rclupp_algo_t;
 
 /* Many independent factorizations of uneven sizes in one call: problem i is

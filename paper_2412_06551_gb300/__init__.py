@@ -24,7 +24,8 @@ __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
     "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32",
     "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
-    "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor",
+    "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
+    "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
     "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
@@ -90,6 +91,9 @@ _SIGNATURES = {
                          ctypes.POINTER(Info)], _I32),
     "cholqr2_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
     "lc2_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
+    "rcholqr_factor": ([_P, _I64, _I64, _P, _I64, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
+                        ctypes.POINTER(Info)], _I32),
+    "scholqr3_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
     "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
     "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
@@ -325,6 +329,18 @@ def lc2_factor(X, *, Q=None, R=None, check=True):
     return _factor("lc2_factor", X, False, Q, R, check)
 
 
+def rcholqr_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
+                   Q=None, R=None, check=True):
+    """[Q, R] = RCholeskyQR(X) (Algorithm 5, one sketch, one CholeskyQR)."""
+    return _factor("rcholqr_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
+                   prec=prec, S=S)
+
+
+def scholqr3_factor(X, *, Q=None, R=None, check=True):
+    """[Q, R] = SCholeskyQR3(X) (Algorithm 3)."""
+    return _factor("scholqr3_factor", X, False, Q, R, check)
+
+
 # ---------------------------------------------------------------- steps
 
 def rclupp_sketch(A, *, s, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
@@ -353,7 +369,7 @@ def rclupp_gram(A, *, unit_lower=False, G=None):
     return G
 
 
-ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2 = 0, 1, 2, 3
+ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2, ALGO_RCHOLQR, ALGO_SCHOLQR3 = 0, 1, 2, 3, 4, 5
 
 
 def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,

@@ -416,6 +416,34 @@ rclupp_status_t enqueue_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, const do
     return RCLUPP_OK;
 }
 
+// RCholeskyQR, Algorithm 5 (one sketch, one CholeskyQR), sketch at `tier`.
+rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, int tier, int64_t m,
+                                int n, const double *X, int64_t ldx, double *Q, int64_t ldq,
+                                double *R, int64_t ldr) {
+    const int np = pad16(n);
+    // K = S X; R1 = R of HouseholderQR(K)
+    RQ_TRY(sketch_step(b, X, ldx, m, n, 0, o, tier, c.st, c.s));
+    RQ_TRY(launch_rcholqr_r1(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], c.s));
+    // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    if (st != RCLUPP_OK) return st;
+    RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
+    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st, c.s));
+    return RCLUPP_OK;
+}
+
+// SCholeskyQR3, Algorithm 3: G = X^T X; R1 = chol(G + s I); Q1 = X R1^{-1};
+// [Q, Z] = CholeskyQR2(Q1); R = Z R1.
+rclupp_status_t enqueue_scholqr3(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
+                                 int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr) {
+    RQ_TRY(launch_gram(X, ldx, m, n, 0, b.G, n, b.part, c.st, c.s));
+    RQ_TRY(launch_shifted_gram(b.G, n, n, m, b.Y, c.s));
+    RQ_TRY(launch_cholesky(b.Y, n, n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 6, c.s));
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    if (st != RCLUPP_OK) return st;
+    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr);
+}
+
 // LC2, Algorithm 4; the LU runs in L (ldl).
 rclupp_status_t enqueue_lc2(Ctx c, const Bufs &b, int64_t m, int n, const double *X, int64_t ldx,
                             double *L, int64_t ldl, double *Q, int64_t ldq, double *R,
@@ -596,6 +624,32 @@ rclupp_status_t lc2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double
                   nullptr);
 }
 
+rclupp_status_t rcholqr_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
+                               int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
+                               double *R, int64_t ldr, rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    const rclupp_opts_t o = resolve_opts(opts, n);
+    if ((st = check_opts(o, m, n)) != RCLUPP_OK) return st;
+    Bufs b = prepare(h, m, int(n), o.s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const rclupp_status_t r = finish(
+        h, enqueue_rcholqr(ctx_of(h), b, o, o.prec, m, int(n), X, ldx, Q, ldq, R, ldr), info, nullptr);
+    if (info) info->prec_used = o.prec;
+    return r;
+}
+
+rclupp_status_t scholqr3_factor(rclupp_handle_t h, int64_t m, int64_t n, const double *X,
+                                int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
+                                rclupp_info_t *info) {
+    rclupp_status_t st = check_common(h, m, n, X, ldx, Q, ldq, R, ldr);
+    if (st != RCLUPP_OK) return st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    return finish(h, enqueue_scholqr3(ctx_of(h), b, m, int(n), X, ldx, Q, ldq, R, ldr), info,
+                  nullptr);
+}
+
 // ---- batched form ------------------------------------------------------------
 
 rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t count,
@@ -605,7 +659,9 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
                                       const int64_t *ldr, int32_t *status) {
     if (!h || count < 0 || (count > 0 && (!m || !n || !X || !ldx || !Q || !ldq || !R || !ldr)))
         return RCLUPP_ERR_ARG;
-    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_LC2) return RCLUPP_ERR_ARG;
+    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_SCHOLQR3) return RCLUPP_ERR_ARG;
+    const bool randomized =
+        algo == RCLUPP_ALGO_RCLUPP || algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_RCHOLQR;
     if (count == 0) return RCLUPP_OK;
     // validate every problem and size one branch's workspace for the largest
     std::vector<rclupp_opts_t> o(count);
@@ -614,12 +670,12 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         rclupp_status_t st = check_common(h, m[i], n[i], X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
         if (st != RCLUPP_OK) return st;
         o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
-        if (algo <= RCLUPP_ALGO_RCLUPPR) {
+        if (randomized) {
             if ((st = check_opts(o[i], m[i], n[i])) != RCLUPP_OK) return st;
             if (o[i].prec != RCLUPP_PREC_FP64) return RCLUPP_ERR_UNSUPPORTED;
         }
         const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
-        const int64_t s = algo <= RCLUPP_ALGO_RCLUPPR ? o[i].s : n[i];
+        const int64_t s = randomized ? o[i].s : n[i];
         size_t total = 0;
         carve(nullptr, m[i], int(n[i]), s, own_lu, &total);
         per_branch = std::max(per_branch, total);
@@ -657,7 +713,7 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
             const int k = i % branches;
             const Ctx c{h->bstreams[k], d_st + i};
             const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
-            const int64_t s = algo <= RCLUPP_ALGO_RCLUPPR ? o[i].s : n[i];
+            const int64_t s = randomized ? o[i].s : n[i];
             size_t total = 0;
             const Bufs b = carve(base + per_branch * k, m[i], int(n[i]), s, own_lu, &total);
             double *L = own_lu ? b.LUbuf : Q[i];
@@ -673,6 +729,13 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
                     break;
                 case RCLUPP_ALGO_CHOLQR2:
                     ls = enqueue_cholqr2(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                    break;
+                case RCLUPP_ALGO_RCHOLQR:
+                    ls = enqueue_rcholqr(c, b, o[i], RCLUPP_PREC_FP64, m[i], ni, X[i], ldx[i], Q[i],
+                                         ldq[i], R[i], ldr[i]);
+                    break;
+                case RCLUPP_ALGO_SCHOLQR3:
+                    ls = enqueue_scholqr3(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
                     break;
                 default:
                     ls = enqueue_lc2(c, b, m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i], ldr[i]);

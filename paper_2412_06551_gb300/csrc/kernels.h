@@ -98,6 +98,14 @@ cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const
                               int64_t lda, double *W, double *RP, double *rinv,
                               cudaStream_t stream);
 
+// RCholeskyQR's R1: Householder R of the sketch K (s x n), signs normalised.
+cudaError_t launch_rcholqr_r1(const double *K, int64_t ldk, int s, int n, double *W, double *RP,
+                              double *rinv, cudaStream_t stream);
+
+// Gs = G + s I with SCholeskyQR3's shift s = 11 (mnu + n(n+1)u) max_j G_jj.
+cudaError_t launch_shifted_gram(const double *G, int64_t ldg, int n, int64_t m, double *Gs,
+                                cudaStream_t stream);
+
 // R-factor of the Householder QR of A (s x n) into R (ldr); W: s*n scratch.
 cudaError_t launch_householder_r(const double *A, int64_t lda, int s, int n, double *W, double *R,
                                  int64_t ldr, cudaStream_t stream);

@@ -154,8 +154,13 @@ __device__ void small_trmm_to_padded(const double *A, int64_t lda, const double 
     for (int idx = threadIdx.x; idx < n_pad * n_pad; idx += blockDim.x) {
         const int i = idx % n_pad, j = idx / n_pad;
         double acc = 0.0;
-        if (i <= j && j < n)
-            for (int t = i; t <= j; ++t) acc = fma(A[i + int64_t(t) * lda], B[t + int64_t(j) * ldb], acc);
+        if (i <= j && j < n) {
+            if (B == nullptr)  // B = I
+                acc = A[i + int64_t(j) * lda];
+            else
+                for (int t = i; t <= j; ++t)
+                    acc = fma(A[i + int64_t(t) * lda], B[t + int64_t(j) * ldb], acc);
+        }
         RP[idx] = acc;
     }
     __syncthreads();
@@ -224,6 +229,45 @@ cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, do
                                   DevStatus *st, int step_id, cudaStream_t stream) {
     RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_small_precond<<<1, kSmallThreads, 0, stream>>>(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1,
                                                      ldr, st, step_id));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rcholqr_r1(const double *K, int64_t ldk, int s, int n, double *W, double *RP,
+                              double *rinv, cudaStream_t stream) {
+    // mode 1 with N = I: R1 = R-factor of HouseholderQR(K), signs normalised
+    RQ_LAUNCH(KID_SMALL_PRECOND, stream,
+              k_small_precond<<<1, kSmallThreads, 0, stream>>>(K, ldk, s, n, 1, nullptr, 0, W, RP,
+                                                               rinv, nullptr, 0, nullptr, 0));
+    return cudaGetLastError();
+}
+
+// G + s I with the SCholeskyQR3 shift s = 11 (m n u + n (n+1) u) max_j G_jj
+// (||X||_g^2 = max_j ||X_j||^2 = max_j G_jj), written to Gs (ld n).
+__global__ void __launch_bounds__(256)
+    k_shifted_gram(const double *__restrict__ G, int64_t ldg, int n, int64_t m, double *Gs) {
+    __shared__ double red[33];
+    double g = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) g = fmax(g, G[j + int64_t(j) * ldg]);
+    for (int off = 16; off > 0; off >>= 1) g = fmax(g, __shfl_down_sync(0xffffffffu, g, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        const double u = 0x1p-53;
+        red[32] = 11.0 * (double(m) * double(n) * u + double(n) * double(n + 1) * u) * mx;
+    }
+    __syncthreads();
+    const double shift = red[32];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx % n, j = idx / n;
+        Gs[idx] = G[i + int64_t(j) * ldg] + (i == j ? shift : 0.0);
+    }
+}
+
+cudaError_t launch_shifted_gram(const double *G, int64_t ldg, int n, int64_t m, double *Gs,
+                                cudaStream_t stream) {
+    RQ_LAUNCH(KID_CHOLESKY, stream, k_shifted_gram<<<1, 256, 0, stream>>>(G, ldg, n, m, Gs));
     return cudaGetLastError();
 }
 
