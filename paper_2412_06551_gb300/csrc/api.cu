@@ -127,7 +127,7 @@ Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *t
     b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
     b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
     for (int i = 0; i < 5; ++i) {
-        b.RP[i] = c.take<double>(size_t(n_pad) * n_pad);
+        b.RP[i] = c.take<double>(size_t(2) * n_pad * n_pad);  // column- then row-major
         b.rinv[i] = c.take<double>(n_pad);
     }
     b.G = c.take<double>(size_t(n) * n);

@@ -249,4 +249,34 @@ __host__ __device__ __forceinline__ int pad16(int n) { return (n + 15) / 16 * 16
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
+// sum_p base[p * stride] for p = 0..np-1, added in increasing p (the same
+// rounding as a plain loop); loads are issued eight at a time so that the
+// reduction is not one memory latency per term.
+__device__ __forceinline__ double ordered_sum(const double *__restrict__ base, size_t stride,
+                                              int np) {
+    double s = 0.0;
+    int p = 0;
+    for (; p + 8 <= np; p += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(base + size_t(p + u) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; p < np; ++p) s += __ldg(base + size_t(p) * stride);
+    return s;
+}
+
+// A padded upper factor is stored as RP (n_pad x n_pad, column-major) followed
+// by the same matrix row-major (RT[i * n_pad + j] = r_ij), so that the
+// substitution kernel reads a row of R with contiguous loads.  Called by one
+// CTA after a barrier that completes its writes of RP.
+__device__ __forceinline__ void store_r_rows(double *RP, int n_pad) {
+    double *RT = RP + int64_t(n_pad) * n_pad;
+    for (int idx = threadIdx.x; idx < n_pad * n_pad; idx += blockDim.x) {
+        const int i = idx % n_pad, j = idx / n_pad;
+        RT[int64_t(i) * n_pad + j] = RP[idx];
+    }
+}
+
 }  // namespace rq

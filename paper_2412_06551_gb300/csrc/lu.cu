@@ -78,12 +78,20 @@ __device__ __forceinline__ void finish_pivot(ArgCand mine, ArgCand *cands, unsig
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        ArgCand best{-1.0, 0x7fffffffffffffffll};
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            const ArgCand c = cands[b];
-            if (cand_better(c.v, c.i, best.v, best.i)) best = c;
+    // all threads of the last CTA combine the candidates (L2 reads: other
+    // CTAs wrote them in this launch)
+    double cv = -1.0;
+    long long ci = 0x7fffffffffffffffll;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        const double v = __ldcg(&cands[b].v);
+        const long long i = __ldcg(&cands[b].i);
+        if (cand_better(v, i, cv, ci)) {
+            cv = v;
+            ci = i;
         }
+    }
+    const ArgCand best = block_argmax(cv, ci);
+    if (threadIdx.x == 0) {
         long long p = best.i;
         if (!(best.v > 0.0)) {  // zero (or non-finite) column: rank < n
             report(st, best.v == 0.0 ? kErrLuZeroPivot : kErrNonfinite, step, col);
@@ -96,9 +104,11 @@ __device__ __forceinline__ void finish_pivot(ArgCand mine, ArgCand *cands, unsig
     __syncthreads();
     const long long p = piv_row;
     if (p != col) {
+        // L2 reads: the panel entries of both rows were written by other
+        // CTAs in this launch
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double t = A[col + int64_t(j) * lda];
-            A[col + int64_t(j) * lda] = A[p + int64_t(j) * lda];
+            const double t = __ldcg(A + col + int64_t(j) * lda);
+            A[col + int64_t(j) * lda] = __ldcg(A + p + int64_t(j) * lda);
             A[p + int64_t(j) * lda] = t;
         }
     }
@@ -106,30 +116,53 @@ __device__ __forceinline__ void finish_pivot(ArgCand mine, ArgCand *cands, unsig
 
 // Column step k of the panel [.., pe): scale column k below the diagonal,
 // update panel columns k+1 .. pe-1, and search the pivot of column k+1.
-__global__ void __launch_bounds__(kLuThreads)
+// Each thread takes kColRows rows at a time and loads all their panel
+// entries before its first store, so that the loads of a row are in flight
+// together instead of one memory round trip per column.
+constexpr int kColRows = 4;
+
+__global__ void __launch_bounds__(kLuThreads, 2)
     k_lu_col(double *A, int64_t lda, int64_t m, int n, int k, int pe, int64_t chunk,
              ArgCand *cands, unsigned *ticket, int32_t *ipiv, DevStatus *st, int step) {
+    constexpr int NC = kLuNB - 1;
     __shared__ double urow[kLuNB];
     const int ncol = pe - k - 1;  // panel columns right of k
     if (threadIdx.x < ncol) urow[threadIdx.x] = A[k + int64_t(k + 1 + threadIdx.x) * lda];
     __syncthreads();
     const double rcp = 1.0 / A[k + int64_t(k) * lda];
+    double u[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) u[c] = (c < ncol) ? urow[c] : 0.0;
     const bool search = (k + 1 < pe);
     double bv = -1.0;
     long long bi = 0x7fffffffffffffffll;
     const int64_t rb = k + 1 + int64_t(blockIdx.x) * chunk;
     const int64_t re = std::min<int64_t>(m, rb + chunk);
-    for (int64_t i = rb + threadIdx.x; i < re; i += kLuThreads) {
-        const double l = A[i + int64_t(k) * lda] * rcp;
-        A[i + int64_t(k) * lda] = l;
-        for (int c = 0; c < ncol; ++c) {
-            double *p = A + i + int64_t(k + 1 + c) * lda;
-            const double a = fma(-l, urow[c], *p);
-            *p = a;
-            if (c == 0) {
-                const double v = fabs(a);
-                if (cand_better(v, i, bv, bi)) {
-                    bv = v;
+    double *colk = A + int64_t(k) * lda;
+    double *col1 = A + int64_t(k + 1) * lda;
+    for (int64_t i0 = rb + threadIdx.x; i0 < re; i0 += int64_t(kLuThreads) * kColRows) {
+        double l[kColRows], a[kColRows][NC];
+#pragma unroll
+        for (int r = 0; r < kColRows; ++r) {
+            const int64_t i = i0 + int64_t(r) * kLuThreads;
+            const bool in = i < re;
+            l[r] = in ? colk[i] : 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) a[r][c] = (in && c < ncol) ? col1[i + int64_t(c) * lda] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < kColRows; ++r) {
+            const int64_t i = i0 + int64_t(r) * kLuThreads;
+            if (i >= re) break;
+            const double li = l[r] * rcp;
+            colk[i] = li;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (c >= ncol) break;
+                const double v = fma(-li, u[c], a[r][c]);
+                col1[i + int64_t(c) * lda] = v;
+                if (c == 0 && cand_better(fabs(v), i, bv, bi)) {
+                    bv = fabs(v);
                     bi = i;
                 }
             }
@@ -196,14 +229,23 @@ __global__ void __launch_bounds__(kLuThreads)
     finish_pivot(mine, cands, ticket, A, lda, n, pe, ipiv, st, step);
 }
 
+// CTAs per SM: the column step holds kColRows x kLuNB values per thread
+// (two CTAs fit); the trailing update is latency-bound on its
+// load-update-store chain per column and takes as many CTAs as fit.
+constexpr int kColCtasPerSm = 2;
+constexpr int kTrailCtasPerSm = 6;
+constexpr int kMaxCtasPerSm = 6;
+
+static size_t cand_slots() { return size_t(kMaxCtasPerSm) * num_sms() + 8; }
+
 size_t lu_scratch_bytes(int64_t m, int n) {
     (void)m;
     (void)n;
-    return (size_t(2) * num_sms() + 8) * sizeof(ArgCand) + 256;
+    return cand_slots() * sizeof(ArgCand) + 256;
 }
 
-static int lu_grid(int64_t rows, int64_t &chunk) {
-    const int64_t maxg = int64_t(2) * num_sms();
+static int lu_grid(int64_t rows, int64_t &chunk, int per_sm) {
+    const int64_t maxg = int64_t(per_sm) * num_sms();
     int64_t g = std::max<int64_t>(1, std::min<int64_t>(maxg, ceil_div(rows, 2 * kLuThreads)));
     chunk = std::max<int64_t>(1, ceil_div(rows, g));
     g = std::max<int64_t>(1, ceil_div(rows, chunk));
@@ -214,14 +256,13 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
                              void *scratch, DevStatus *st, int step_id, cudaStream_t stream) {
     ArgCand *cands = reinterpret_cast<ArgCand *>(scratch);
     unsigned *ticket =
-        reinterpret_cast<unsigned *>(static_cast<char *>(scratch) +
-                                     (size_t(2) * num_sms() + 8) * sizeof(ArgCand));
+        reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + cand_slots() * sizeof(ArgCand));
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     const size_t smax = size_t(kLuNB) * n * sizeof(double);
     cudaFuncSetAttribute(k_lu_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax));
     int64_t chunk;
-    int g = lu_grid(m, chunk);
+    int g = lu_grid(m, chunk, kTrailCtasPerSm);
     RQ_LAUNCH(KID_LU_TRAILING, stream, k_lu_trailing<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, 0, 0, chunk, cands, ticket, ipiv, st,
                                                 step_id));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -230,7 +271,7 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
         for (int k = k0; k < pe; ++k) {
             const int64_t rows = m - k - 1;
             if (rows <= 0) break;
-            g = lu_grid(rows, chunk);
+            g = lu_grid(rows, chunk, kColCtasPerSm);
             RQ_LAUNCH(KID_LU_COL, stream, k_lu_col<<<g, kLuThreads, 0, stream>>>(A, lda, m, n, k, pe, chunk, cands, ticket, ipiv,
                                                    st, step_id));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -239,7 +280,7 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
             RQ_LAUNCH(KID_LU_U12, stream, k_lu_u12<<<1, kLuThreads, 0, stream>>>(A, lda, n, k0, pe));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             const int64_t rows = m - pe;
-            g = lu_grid(rows, chunk);
+            g = lu_grid(rows, chunk, kTrailCtasPerSm);
             const size_t sm = size_t(pe - k0) * (n - pe) * sizeof(double);
             RQ_LAUNCH(KID_LU_TRAILING, stream, k_lu_trailing<<<g, kLuThreads, sm, stream>>>(A, lda, m, n, k0, pe, chunk, cands, ticket,
                                                          ipiv, st, step_id));

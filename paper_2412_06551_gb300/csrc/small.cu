@@ -173,6 +173,7 @@ __device__ void small_trmm_to_padded(const double *A, int64_t lda, const double 
         }
         __syncthreads();
     }
+    store_r_rows(RP, n_pad);
     for (int i = threadIdx.x; i < n_pad; i += blockDim.x)
         rinv[i] = (i < n) ? 1.0 / RP[i + int64_t(i) * n_pad] : 0.0;
     __syncthreads();
@@ -343,7 +344,9 @@ __global__ void __launch_bounds__(kSmallThreads)
     // padded output (NaN-free even after a breakdown: entries are only copied)
     for (int idx = threadIdx.x; idx < n_pad * n_pad; idx += blockDim.x) {
         const int i = idx % n_pad, j = idx / n_pad;
-        RP[idx] = (i <= j && j < n) ? W[i + int64_t(j) * n] : 0.0;
+        const double v = (i <= j && j < n) ? W[i + int64_t(j) * n] : 0.0;
+        RP[idx] = v;
+        RP[int64_t(n_pad) * n_pad + int64_t(i) * n_pad + j] = v;  // row-major copy
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_pad; i += blockDim.x)

@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(kThreads, (MAXW > 5 ? 1 : 2))
 
 // G[j][k] = G[k][j] = sum over CTAs (in CTA order) of the slot partials.
 __global__ void k_reduce_gram(const double *__restrict__ part_diag, int nslots_diag,
-                              const double *__restrict__ part_off, int nparts, int n,
-                              double *__restrict__ G, int64_t ldg) {
+                              int nparts_diag, const double *__restrict__ part_off,
+                              int nparts_off, int n, double *__restrict__ G, int64_t ldg) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= int64_t(n) * n) return;
     const int j = static_cast<int>(e % n), k = static_cast<int>(e / n);
@@ -310,16 +310,18 @@ __global__ void k_reduce_gram(const double *__restrict__ part_diag, int nslots_d
     const int bj = j / 128, bk = k / 128;
     const double *base;
     size_t stride;
+    int nparts;
     if (bj == bk) {
         base = part_diag + size_t(bj) * 16384;
         stride = size_t(nslots_diag) * 16384;
+        nparts = nparts_diag;
     } else {
         base = part_off;
         stride = 16384;
+        nparts = nparts_off;
     }
     const int off = (k % 128) * 128 + (j % 128);
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += base[size_t(p) * stride + off];
+    const double s = ordered_sum(base + off, stride, nparts);
     G[j + int64_t(k) * ldg] = s;
     G[k + int64_t(j) * ldg] = s;
 }
@@ -342,7 +344,11 @@ cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit
     if (n > 128) bm = 32;  // off-diagonal launches stage two 128-column slices
     const bool tma = make_tma_map(&map, A, m, n, lda, bm, ncb);
     if (!tma) memset(&map, 0, sizeof map);
-    const TallPlan pl = plan_rows(m, bm, 2, nd + (n > 128 ? 1 : 0));
+    // diagonal blocks: two CTAs per SM over nd slots; the off-diagonal block
+    // (n > 128, 8 warp tiles per warp) runs alone per SM: each launch gets its
+    // own row partition so that both fill every SM
+    const TallPlan pl = plan_rows(m, bm, 2, nd);
+    const TallPlan po = plan_rows(m, bm, 1, 1);
     double *part_diag = part;
     double *part_off = part + size_t(pl.grid_x) * nd * 16384;
     const size_t smem1 = size_t(bm) * ncb * 8;
@@ -369,13 +375,13 @@ cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit
         auto k = k_gram<32, 8>;
         const size_t smem2 = size_t(2) * 32 * 128 * 8;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem2));
-        RQ_LAUNCH(KID_GRAM, stream, k<<<dim3(pl.grid_x, 1), kThreads, smem2, stream>>>(map, tma, A, lda, m, n, unit_lower,
-                                                            pl.chunk, 128, 0, part_off, 1, st));
+        RQ_LAUNCH(KID_GRAM, stream, k<<<dim3(po.grid_x, 1), kThreads, smem2, stream>>>(map, tma, A, lda, m, n, unit_lower,
+                                                            po.chunk, 128, 0, part_off, 1, st));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t ne = int64_t(n) * n;
     RQ_LAUNCH(KID_REDUCE, stream, k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-        part_diag, nd, part_off, pl.grid_x, n, G, ldg));
+        part_diag, nd, pl.grid_x, part_off, po.grid_x, n, G, ldg));
     return cudaGetLastError();
 }
 
@@ -414,28 +420,37 @@ cudaError_t launch_gram_bounded(const double *A, int64_t lda, int64_t m, int n, 
     const int64_t ne = int64_t(n) * n;
     RQ_LAUNCH(KID_REDUCE, stream,
               k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-                  part, 1, part, pl.grid_x, n, G, ldg));
+                  part, 1, pl.grid_x, part, pl.grid_x, n, G, ldg));
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------- TRSM (+ Gram) ---
 
 // Q = A R^{-1} tile by tile: blocked substitution with 16-column blocks.
-// Update phase (all threads): a_ij -= sum_{k < j0} q_ik r_kj for the 16
-// columns of block J, in increasing k; diagonal phase (one thread per row):
-// q_ij = (a_ij - sum_{j0 <= k < j} q_ik r_kj) * (1 / r_jj).  Optional fused
-// Gram of the solved tile (n_pad <= 128).
+// Each row of the tile belongs to P = 256 / BM adjacent lanes of one warp;
+// lane p holds columns j0 + p + cP (c < CPT = 16 / P) of the current block
+// in registers.  Update: a_ij -= sum_{k < j0} q_ik r_kj in increasing k (q_ik
+// from shared memory, row k of R from its row-major copy).  Diagonal block,
+// column t = 0..15 in turn: its owner scales it by 1 / r_jj, a shuffle
+// broadcasts it and the row's later columns subtract q_ij r_jc.  Every
+// column thus sees the same subtractions in the same order as the column
+// formula q_ij = (a_ij - sum_{k<j} q_ik r_kj) / r_jj, and no barrier is
+// needed inside the tile: a row's values only move within its warp.
+// Interleaved columns retire early from the diagonal steps, so few of the
+// predicated updates issue for nothing.  Optional fused Gram of the solved
+// tile (n_pad <= 128).
 template <int BM, bool kGram>
 __global__ void __launch_bounds__(kThreads, 2)
     k_trsm(const __grid_constant__ CUtensorMap map, int use_tma, const double *__restrict__ A,
-           int64_t lda, int64_t m, int n, int n_pad, int64_t chunk, const double *__restrict__ RP,
+           int64_t lda, int64_t m, int n, int n_pad, int64_t chunk, const double *__restrict__ RT,
            const double *__restrict__ rinv, double *Q, int64_t ldq, double *__restrict__ part,
            DevStatus *st) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     double *T = reinterpret_cast<double *>(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
-    constexpr int CPT = 16 * BM / kThreads;  // update columns per thread
+    constexpr int P = kThreads / BM;  // lanes per row
+    constexpr int CPT = 16 / P;       // block columns per lane
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -447,7 +462,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (kGram) g.init(n_pad / 16, n_pad / 16, true);
     uint32_t phase = 0;
     const int tid = threadIdx.x;
-    const int ti = tid % BM, tg = tid / BM;
+    const int p = tid % P, ti = tid / P;
+    const int src0 = (tid & 31) - p;  // lane of this row's p = 0
     const int64_t rb = int64_t(blockIdx.x) * chunk;
     const int64_t re = std::min<int64_t>(m, rb + chunk);
     const int nblk = n_pad / 16;
@@ -455,32 +471,34 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool ok = stage_tile<BM>(T, &map, use_tma, &bar, phase, A, lda, m, n, r0, 0, n_pad);
         if (check_abort(&abort_flag, ok, st, 0)) return;
         for (int J = 0; J < nblk; ++J) {
-            const int j0 = 16 * J;
-            if (J > 0) {
-                const int cb = j0 + tg * CPT;
-                double acc[CPT];
+            const int cb = 16 * J + p;  // column of c = 0
+            double acc[CPT];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) acc[c] = T[(cb + c) * BM + ti];
-                const double *rcol = RP + int64_t(cb) * n_pad;
-                for (int k = 0; k < j0; ++k) {
-                    const double q = T[k * BM + ti];
+            for (int c = 0; c < CPT; ++c) acc[c] = T[(cb + c * P) * BM + ti];
+            const double *rrow = RT + cb;
+            for (int k = 0; k < 16 * J; ++k) {
+                const double q = T[k * BM + ti];
+                const double *rk = rrow + int64_t(k) * n_pad;
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) acc[c] = fma(-q, __ldg(rcol + c * n_pad + k), acc[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) T[(cb + c) * BM + ti] = acc[c];
-                __syncthreads();
+                for (int c = 0; c < CPT; ++c) acc[c] = fma(-q, __ldg(rk + c * P), acc[c]);
             }
-            if (tid < BM) {
-                for (int j = j0; j < j0 + 16; ++j) {
-                    double x = T[j * BM + tid];
-                    const double *rcol = RP + int64_t(j) * n_pad;
-                    for (int k = j0; k < j; ++k) x = fma(-T[k * BM + tid], __ldg(rcol + k), x);
-                    T[j * BM + tid] = x * __ldg(rinv + j);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int owner = t % P, lc = t / P;
+                if (p == owner) acc[lc] *= __ldg(rinv + 16 * J + t);
+                const double q = __shfl_sync(0xffffffffu, acc[lc], src0 + owner);
+                const double *rk = RT + int64_t(16 * J + t) * n_pad + cb;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    if ((P - 1) + c * P <= t) continue;  // no lane has a column past t
+                    if (p + c * P > t) acc[c] = fma(-q, __ldg(rk + c * P), acc[c]);
                 }
             }
-            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) T[(cb + c * P) * BM + ti] = acc[c];
+            __syncwarp();
         }
+        __syncthreads();
         const int rows = static_cast<int>(std::min<int64_t>(BM, re - r0));
         for (int idx = tid; idx < BM * n; idx += kThreads) {
             const int i = idx % BM, c = idx / BM;
@@ -500,6 +518,7 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
     const int n_pad = pad16(n);
     const int bm = trsm_bm(n_pad);
     const bool fuse = (G != nullptr) && n_pad <= 128;
+    const double *RT = RP + size_t(n_pad) * n_pad;
     CUtensorMap map;
     const bool tma = make_tma_map(&map, A, m, n, lda, bm, n_pad);
     if (!tma) memset(&map, 0, sizeof map);
@@ -512,7 +531,7 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));         \
         RQ_LAUNCH(GV ? KID_TRSM_GRAM : KID_TRSM, stream,                                         \
                   k<<<pl.grid_x, kThreads, smem, stream>>>(map, tma, A, lda, m, n, n_pad,        \
-                                                            pl.chunk, RP, rinv, Q, ldq, part, st)); \
+                                                            pl.chunk, RT, rinv, Q, ldq, part, st)); \
     } while (0)
     if (bm == 128) {
         if (fuse) RQ_TRSM_LAUNCH(128, true); else RQ_TRSM_LAUNCH(128, false);
@@ -527,7 +546,7 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
     if (fuse) {
         const int64_t ne = int64_t(n) * n;
         RQ_LAUNCH(KID_REDUCE, stream, k_reduce_gram<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
-            part, 1, part, pl.grid_x, n, G, ldg));
+            part, 1, pl.grid_x, part, pl.grid_x, n, G, ldg));
         return cudaGetLastError();
     }
     // n > 128: Gram of the solved Q in a separate pass
@@ -730,9 +749,7 @@ __global__ void k_reduce_sketch(const double *__restrict__ part, int nparts, int
     const int r = static_cast<int>(e % s), c = static_cast<int>(e / s);
     const size_t off = size_t(c) * s_pad + r;
     const size_t stride = size_t(s_pad) * n_pad;
-    double acc = 0.0;
-    for (int p = 0; p < nparts; ++p) acc += part[size_t(p) * stride + off];
-    Y[r + int64_t(c) * ldy] = acc;
+    Y[r + int64_t(c) * ldy] = ordered_sum(part + off, stride, nparts);
 }
 
 cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
@@ -794,7 +811,8 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
     return cudaGetLastError();
 }
 
-// RP = triu(R) zero-padded to n_pad x n_pad (ld n_pad); rinv = 1/diag (0 in padding).
+// RP = triu(R) zero-padded to n_pad x n_pad (ld n_pad), followed by its
+// row-major copy; rinv = 1/diag (0 in padding).
 __global__ void k_pad_upper(const double *__restrict__ R, int64_t ldr, int n, int n_pad,
                             double *__restrict__ RP, double *__restrict__ rinv) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -802,6 +820,7 @@ __global__ void k_pad_upper(const double *__restrict__ R, int64_t ldr, int n, in
     const int i = static_cast<int>(e % n_pad), j = static_cast<int>(e / n_pad);
     const double v = (i <= j && j < n) ? R[i + int64_t(j) * ldr] : 0.0;
     RP[e] = v;
+    RP[int64_t(n_pad) * n_pad + int64_t(i) * n_pad + j] = v;
     if (i == j) rinv[i] = (i < n) ? 1.0 / v : 0.0;
 }
 
