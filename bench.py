@@ -72,8 +72,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--accuracy-sweep", action="store_true",
                    help="also report orthogonality/residual at kappa 1e10 and 1e15")
-    p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "sketch_gauss", "sketch_sparse",
-                                      "lu", "rclupp"],
+    p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "sketch_gauss",
+                                      "sketch_sparse", "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
     p.add_argument("--workload", choices=["side_by_side", "precision", "batched"],
                    default="side_by_side",
@@ -250,16 +250,18 @@ def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
     tier, escalating as needed) on the same X, against the FP64 paths."""
     m, n = X.shape
     out = {}
-    for name, fn in (("rclupp", rq.rclupp_factor), ("rcluppr", rq.rclupp_r_factor)):
-        call = lambda: fn(X, s=S_SKETCH, seed=SEED_S, prec=rq.PREC_SKETCH_BF16)
-        call()
-        ms, (Q, R, info) = time_call(torch, stream, call, max(2, reps))
-        o, r = accuracy(torch, X, Q, R)
-        out[name] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "orth": o, "res": r,
-                     "prec_used": int(info.prec_used),
-                     "speedup_vs_fp64": fp64_paths[name]["ms"] / ms,
-                     "orth_fp64": fp64_paths[name]["orth"]}
-        del Q, R
+    for tier, prec in (("", rq.PREC_SKETCH_BF16), ("_emulated", rq.PREC_EMULATED)):
+        for name, fn in (("rclupp", rq.rclupp_factor), ("rcluppr", rq.rclupp_r_factor)):
+            call = lambda: fn(X, s=S_SKETCH, seed=SEED_S, prec=prec)
+            call()
+            ms, (Q, R, info) = time_call(torch, stream, call, max(2, reps))
+            o, r = accuracy(torch, X, Q, R)
+            out[name + tier] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9,
+                                "orth": o, "res": r, "prec_used": int(info.prec_used),
+                                "emulated_gram": int(info.emulated),
+                                "speedup_vs_fp64": fp64_paths[name]["ms"] / ms,
+                                "orth_fp64": fp64_paths[name]["orth"]}
+            del Q, R
     return out
 
 
@@ -276,7 +278,8 @@ def run_precision(args):
         seed = synth.kappa_seed(2, k_i)
         X = to_dev(synth.svd_matrix(m, n, kap, seed), torch, device)
         row = {}
-        for label, prec in (("fp64", rq.PREC_FP64), ("mixed", rq.PREC_SKETCH_BF16)):
+        for label, prec in (("fp64", rq.PREC_FP64), ("mixed", rq.PREC_SKETCH_BF16),
+                            ("emulated", rq.PREC_EMULATED)):
             call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec, check=False)
             call()
             ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
@@ -288,10 +291,12 @@ def run_precision(args):
             row[label] = entry
             del Q, R
         row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        row["speedup_emulated"] = row["fp64"]["ms"] / row["emulated"]["ms"]
         rows["%.0e" % kap] = row
         del X
         torch.cuda.empty_cache()
-    print(json.dumps({"workload": "RCLUPP FP64 vs tensor-core sketch (bf16 start, escalating)",
+    print(json.dumps({"workload": "RCLUPP FP64 vs tensor-core sketch (bf16 start, escalating) "
+                                  "vs that sketch plus the binary64-emulating tensor-core Gram",
                       "m": m, "n": n, "s": s, "results": rows}), flush=True)
 
 
@@ -525,6 +530,8 @@ def run_case(args):
             rq.rclupp_trsm_gram(X, R, gram=False)
         elif args.case == "gram":
             rq.rclupp_gram(X)
+        elif args.case == "gram_emu":
+            rq.rclupp_gram_emulated(X)
         elif args.case == "sketch_gauss":
             rq.rclupp_sketch(X, s=2 * n, seed=1, prec=args.prec)
         elif args.case == "sketch_sparse":
@@ -547,6 +554,7 @@ def run_case(args):
     # (n(n+1)/2 dot products of length m), 2 s m n per sketch, m n^2 - n^3/3
     # per tall LU
     flops = {"trsm_gram": 2.0 * m * n * n, "trsm": 1.0 * m * n * n, "gram": 1.0 * m * n * n,
+             "gram_emu": 1.0 * m * n * n,
              "sketch_gauss": 4.0 * m * n * n, "lu": m * n * n - n ** 3 / 3.0}.get(args.case)
     total = sum(v[1] for v in prof.values()) / args.reps
     line = {"case": args.case, "m": m, "n": n, "reps": args.reps, "ms_per_call": total,

@@ -67,7 +67,13 @@ typedef enum {
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
     RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
-    RCLUPP_PREC_SKETCH_FP32 = 2  /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
+    RCLUPP_PREC_SKETCH_FP32 = 2, /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
+    RCLUPP_PREC_EMULATED = 3     /* the BF16 sketch tier, and the Gram of the first CholeskyQR
+                                    pass (Q1^T Q1) as binary64-emulating split-bf16 products on
+                                    the tensor cores (rclupp_gram_emulated); the final-pass Gram,
+                                    the triangular solves and the n x n factorizations stay in
+                                    binary64.  An explicit S or the sparse-sign sketch keeps a
+                                    binary64 sketch. */
 } rclupp_precision_t;
 
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
@@ -107,7 +113,8 @@ typedef struct {
                             RCLUPP/RCLUPPr escalate bf16 -> three-term bf16 -> FP64 when
                             the first Cholesky breaks down or the spread of its diagonal
                             exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2) */
-    int32_t reserved;
+    int32_t emulated;    /* 1 when the first pass's Gram ran on the binary64-emulating
+                            tensor-core path (RCLUPP_PREC_EMULATED) */
 } rclupp_info_t;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -245,6 +252,19 @@ rclupp_status_t rclupp_sketch(rclupp_handle_t handle, int64_t m, int64_t n, cons
  * C1/C5 of Theorem 4.1; unit_lower as in rclupp_sketch (LC2's M^T M). */
 rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                             int64_t lda, int32_t unit_lower, double *G, int64_t ldg);
+
+/* G = A^T A (n x n, both triangles) as binary64-emulating products on the
+ * tensor cores: the Gram product of the CholeskyQR pass (Algorithm 1 step 1,
+ * C1) in the precision form RCLUPP_PREC_EMULATED.  Each element is written as
+ * a_ij = 2^(E_j - 7) sum_{s=0..6} d_s 2^(-8s) with integer digits |d_s| <= 128
+ * (E_j: 2^E_j exceeds every |a_ij| of column j; round to nearest, half away
+ * from zero, at 2^(E_j - 55)); G sums the digit products of levels
+ * s + t <= 6 exactly in fp32 over 128-row windows, then in int64 and binary64.
+ * Error: at most about (m + 1) 2^-53 2^(E_j + E_k) beyond the rounding of the
+ * digits, i.e. binary64-like relative to the columns' largest entries.
+ * NaN in G(j, k) when column j or k holds a non-finite value.  n <= 256. */
+rclupp_status_t rclupp_gram_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                                     int64_t lda, double *G, int64_t ldg);
 
 /* Q = A R^{-1} by substitution (eq. (ewy), C3, C7) and, when G != NULL,
  * G = Q^T Q (C1, C5) in the same pass.  R: n x n upper, nonzero diagonal.

@@ -22,11 +22,11 @@ from . import _build
 
 __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
-    "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32",
+    "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED",
     "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
-    "rclupp_sketch", "rclupp_gram", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
+    "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
     "ALGO_RCLUPP", "ALGO_RCLUPPR",
@@ -35,7 +35,7 @@ __all__ = [
 ]
 
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN = 0, 1
-PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32 = 0, 1, 2
+PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED = 0, 1, 2, 3
 
 
 class Status:
@@ -58,9 +58,10 @@ class Opts(ctypes.Structure):
 
 
 class Info(ctypes.Structure):
-    """rclupp_info_t: status, failed step, failing column."""
+    """rclupp_info_t: status, failed step, failing column, sketch tier used,
+    whether the first pass's Gram ran on the emulated path."""
     _fields_ = [("status", ctypes.c_int32), ("failed_step", ctypes.c_int32), ("info", ctypes.c_int64),
-                ("prec_used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("prec_used", ctypes.c_int32), ("emulated", ctypes.c_int32)]
 
 
 class RclupError(RuntimeError):
@@ -96,6 +97,7 @@ _SIGNATURES = {
     "scholqr3_factor": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(Info)], _I32),
     "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
     "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
+    "rclupp_gram_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_cholesky": ([_P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_trmm_upper": ([_P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
@@ -115,7 +117,8 @@ _SIGNATURES = {
 }
 
 KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
-                  "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc"]
+                  "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc",
+                  "gram_emu", "emu_aux"]
 
 
 def profile_enable(on: bool = True) -> None:
@@ -366,6 +369,17 @@ def rclupp_gram(A, *, unit_lower=False, G=None):
     st = load().rclupp_gram(_handle(A).bind(), m, n, _ptr(A), lda, int(bool(unit_lower)), _ptr(G),
                             ldg)
     _raise("rclupp_gram", st)
+    return G
+
+
+def rclupp_gram_emulated(A, *, G=None):
+    """G = A^T A as binary64-emulating split-bf16 products on the tensor cores."""
+    A, lda = colmajor(A)
+    m, n = A.shape
+    G = empty_colmajor(n, n, A.device) if G is None else G
+    G, ldg = colmajor(G)
+    st = load().rclupp_gram_emulated(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(G), ldg)
+    _raise("rclupp_gram_emulated", st)
     return G
 
 

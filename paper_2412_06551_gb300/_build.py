@@ -19,7 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "librclupp.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["tall.cu", "lu.cu", "small.cu", "api.cu", "prof.cu", "noalloc.cu", "tc_sketch.cu"]
+SOURCES = ["tall.cu", "lu.cu", "small.cu", "api.cu", "prof.cu", "noalloc.cu", "tc_sketch.cu",
+           "emu_gram.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-expt-relaxed-constexpr",
          "-I" + INCLUDE]

@@ -122,7 +122,8 @@ Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *t
     Carver c(base);
     Bufs b;
     const int n_pad = pad16(n);
-    const size_t part = std::max(gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0));
+    const size_t part = std::max({gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0),
+                                  gram_emu_partials_doubles(n)});
     b.part = c.take<double>(part);
     b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
     b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
@@ -196,7 +197,7 @@ rclupp_status_t finish(rclupp_handle_t h, rclupp_status_t launch_status, rclupp_
         info->failed_step = step;
         info->info = inf;
         info->prec_used = RCLUPP_PREC_FP64;
-        info->reserved = 0;
+        info->emulated = 0;
     }
     if (col) *col = inf;
     return st;
@@ -238,9 +239,10 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
         if (smem > 220 * 1024) return RCLUPP_ERR_UNSUPPORTED;
     }
     if (o.prec != RCLUPP_PREC_FP64 && o.prec != RCLUPP_PREC_SKETCH_BF16 &&
-        o.prec != RCLUPP_PREC_SKETCH_FP32)
+        o.prec != RCLUPP_PREC_SKETCH_FP32 && o.prec != RCLUPP_PREC_EMULATED)
         return RCLUPP_ERR_ARG;
-    if (o.prec != RCLUPP_PREC_FP64 && o.S) return RCLUPP_ERR_UNSUPPORTED;
+    if ((o.prec == RCLUPP_PREC_SKETCH_BF16 || o.prec == RCLUPP_PREC_SKETCH_FP32) && o.S)
+        return RCLUPP_ERR_UNSUPPORTED;
     (void)m;
     return RCLUPP_OK;
 }
@@ -253,7 +255,7 @@ cudaError_t sketch_step(const Bufs &b, const double *A, int64_t lda, int64_t m, 
                         cudaStream_t s) {
     if (tier != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
         return launch_sketch_tc(A, lda, m, n, unit_lower, o.s, o.seed,
-                                tier == RCLUPP_PREC_SKETCH_BF16 ? 1 : 3, b.Y, o.s, b.part, ds, s);
+                                tier == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, b.Y, o.s, b.part, ds, s);
     return launch_sketch(A, lda, m, n, unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s,
                          b.part, ds, s);
 }
@@ -309,11 +311,18 @@ Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
 // First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
+// With `emulated` the Gram runs on the tensor cores emulating binary64 (the
+// final-pass Gram of rest_cholqr2 always stays binary64).
 rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
-                                  int64_t ldx, double *Q, int64_t ldq) {
+                                  int64_t ldx, double *Q, int64_t ldq, bool emulated = false) {
     cudaStream_t s = c.s;
     DevStatus *st = c.st;
-    RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
+    if (emulated) {
+        RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, nullptr, 0, b.part, st, s));
+        RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
+    } else {
+        RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
+    }
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[1], b.rinv[1], nullptr, 0, st, 3, s));
     return RCLUPP_OK;
 }
@@ -343,7 +352,12 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
                                 int64_t m, int n, const double *SA, int64_t ldsa, int unit_lower,
                                 Precond precond, const double *X, int64_t ldx, double *Q,
                                 int64_t ldq, double *R, int64_t ldr, int *tier_used) {
+    // the emulated tier sketches like the bf16 one (on the tensor cores when
+    // the Gaussian sketch is generated, else in binary64)
+    const bool emulated = o.prec == RCLUPP_PREC_EMULATED;
     int tier = o.prec;
+    if (emulated)
+        tier = (o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S) ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64;
     for (;;) {
         if (sketch_step(b, SA, ldsa, m, n, unit_lower, o, tier, h->d_status, h->stream) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
@@ -351,7 +365,7 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
         // No a-priori test on R1 is made: a reduced-tier R1 only sees the
         // rounded X, whose condition number saturates near 1/u of the tier,
         // so R1 cannot tell an X the tier handles from one it does not.
-        const rclupp_status_t st = first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq);
+        const rclupp_status_t st = first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq, emulated);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
         const Verdict v = judge_first_pass(h, b, n);
@@ -425,7 +439,8 @@ rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     RQ_TRY(sketch_step(b, X, ldx, m, n, 0, o, tier, c.st, c.s));
     RQ_TRY(launch_rcholqr_r1(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], c.s));
     // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
-    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    const rclupp_status_t st =
+        first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, tier == RCLUPP_PREC_EMULATED);
     if (st != RCLUPP_OK) return st;
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
     RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st, c.s));
@@ -560,7 +575,10 @@ rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const dou
     const rclupp_status_t ls =
         randomized_tail(h, b, o, m, ni, X, ldx, 0, precond, X, ldx, Q, ldq, R, ldr, &tier);
     const rclupp_status_t r = finish(h, ls, info, nullptr);
-    if (info) info->prec_used = tier;
+    if (info) {
+        info->prec_used = tier;
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+    }
     return r;
 }
 
@@ -596,7 +614,10 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
         ls = randomized_tail(h, b, o, m, ni, L, ldl, 1, precond, X, ldx, Q, ldq, R, ldr, &tier);
     } while (0);
     const rclupp_status_t r = finish(h, ls, info, nullptr);
-    if (info) info->prec_used = tier;
+    if (info) {
+        info->prec_used = tier;
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+    }
     return r;
 }
 
@@ -635,7 +656,13 @@ rclupp_status_t rcholqr_factor(rclupp_handle_t h, int64_t m, int64_t n, const do
     if (st != RCLUPP_OK) return st;
     const rclupp_status_t r = finish(
         h, enqueue_rcholqr(ctx_of(h), b, o, o.prec, m, int(n), X, ldx, Q, ldq, R, ldr), info, nullptr);
-    if (info) info->prec_used = o.prec;
+    if (info) {
+        const bool tc_sketch = o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S;
+        info->prec_used = o.prec != RCLUPP_PREC_EMULATED
+                              ? o.prec
+                              : (tc_sketch ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64);
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+    }
     return r;
 }
 
@@ -844,9 +871,9 @@ rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const dou
     Bufs b = prepare(h, m, int(n), o.s, false, &st);
     if (st != RCLUPP_OK) return st;
     cudaError_t e;
-    if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN)
+    if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
         e = launch_sketch_tc(A, lda, m, int(n), unit_lower, o.s, o.seed,
-                             o.prec == RCLUPP_PREC_SKETCH_BF16 ? 1 : 3, Y, ldy, b.part, h->d_status,
+                             o.prec == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, Y, ldy, b.part, h->d_status,
                              h->stream);
     else
         e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, Y,
@@ -863,6 +890,17 @@ rclupp_status_t rclupp_gram(rclupp_handle_t h, int64_t m, int64_t n, const doubl
     if (st != RCLUPP_OK) return st;
     const cudaError_t e =
         launch_gram(A, lda, m, int(n), unit_lower, G, ldg, b.part, h->d_status, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_gram_emulated(rclupp_handle_t h, int64_t m, int64_t n, const double *A,
+                                     int64_t lda, double *G, int64_t ldg) {
+    if (!h || !A || !G || n < 1 || m < 1 || bad_ld(lda, m) || bad_ld(ldg, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_gram_emu(A, lda, m, int(n), G, ldg, b.part, h->d_status, h->stream);
     return finish(h, from_cuda(e), nullptr, nullptr);
 }
 

@@ -1,0 +1,391 @@
+// Gram product G = A^T A emulating binary64 on the tensor cores (the
+// precision form of the CholeskyQR pass: Gram as split-bf16 products with
+// fp32 accumulation, Algorithm 1 step 1 / C1).
+//
+// Splitting (per column j of A, exponent E_j with |a_ij| < 2^E_j over all
+// rows): F_ij = round(a_ij 2^(55 - E_j)) (half away from zero), an integer
+// with |F| < 2^55, written in seven balanced base-256 digits
+//   F = sum_{s=0..6} d_s 256^(6-s),  |d_s| <= 128,
+// so a_ij = 2^(E_j - 7) sum_s d_s 2^(-8s) up to 2^(E_j - 56).  Every digit is
+// an exact bf16 and every digit product an integer of magnitude <= 2^14.
+// Level L = s + t collects the products d_s(i, j) d_t(i, k); levels 0..6 are
+// kept (28 products), deeper ones are below 2^-53 of the column scales.
+//
+// Exactness: over a window of 128 rows a level's sum has at most 7 x 128
+// products of magnitude <= 2^14, so it stays below 2^24 and the tensor
+// core's fp32 accumulation of these integers is exact.  After each window
+// the seven fp32 accumulators are drained into one int64 per element, in
+// units of 2^-32 of level 0: C0 2^32 + C1 2^24 + C2 2^16 + C3 2^8 exactly,
+// plus C4 + 2^-8 C5 + 2^-16 C6 formed in fp32 and rounded to an integer
+// (an error of at most 1.5 units, 2^-46 of a window's level-0 scale).  Every
+// 512 windows, and at the end, the int64 (|sum| < 2^62) is added to the
+// CTA's binary64 partial in global memory.  The partials are reduced in a
+// fixed order and scaled by 2^(E_j + E_k - 46).
+//
+// Tiles: a CTA owns 128 rows (columns j of A) x 64 columns (k of A) of G and
+// a contiguous chunk of rows of A (split-K).  Its seven 128 x 64 fp32
+// accumulators take 448 of the 512 TMEM columns.  Per 32 rows of A the 256
+// threads split the block into digits (K-major 8 x 8 bf16 core matrices in
+// shared memory), one thread issues the 28 x 2 MMAs (kind::f16, M=128, N=64,
+// K=16) and commits to the stage's mbarrier; two stages alternate.
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int kEmuThreads = 512;
+constexpr int kEmuBK = 32;      // rows of A per stage
+constexpr int kEmuWinSteps = 4; // stages per exact window (128 rows)
+constexpr int kEmuDigits = 7;
+constexpr int kEmuM = 128;      // rows of G per tile (columns j of A)
+constexpr int kEmuN = 64;       // columns of G per tile (columns k of A)
+constexpr int kEmuStages = 2;
+constexpr int kTileA = kEmuM * kEmuBK * 2;  // bytes of one digit tile of the j columns
+constexpr int kTileB = kEmuN * kEmuBK * 2;  // ... of the k columns
+constexpr int kEmuStageBytes = kEmuDigits * (kTileA + kTileB);
+constexpr int kEmuTmemCols = 512;
+constexpr int kEmuSlot = kEmuM * kEmuN;  // elements of one per-CTA partial
+constexpr int kEmuFlushWindows = 512;    // int64 drains between binary64 flushes
+constexpr int kEmuTaskSlots = 2;         // digit tasks per thread and stage (A: 1, B: 1 more)
+
+// Byte offset of element (row, k) of a K-major operand tile of kEmuBK
+// columns laid out as [row/8][k/8][row%8][k%8] (bf16).
+__device__ __forceinline__ uint32_t emu_off(int row, int k) {
+    return static_cast<uint32_t>(((row >> 3) * (kEmuBK / 8) + (k >> 3)) * 128 + (row & 7) * 16 +
+                                 (k & 7) * 2);
+}
+
+// Balanced base-256 digits of F = round(x 2^(55 - E)), for |x| < 2^E: the
+// digits of |F| (bytes with a carry into the next one when a byte is >= 128),
+// negated for negative x.  Every digit lies in [-128, 128].
+__device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int e = static_cast<int>((b >> 52) & 0x7ff);
+    unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+    if (e != 0) M |= 1ull << 52;
+    // |F| = M 2^sh; sh <= 2 for normal x as |x| < 2^E, 3 for subnormals of a
+    // column whose largest exponent is subnormal
+    const int sh = (e != 0 ? e : 1) - 1020 - E;
+    unsigned long long F;
+    if (sh >= 0)
+        F = M << (sh & 3);
+    else if (sh > -55)
+        F = (M + (1ull << (-sh - 1))) >> (-sh);
+    else
+        F = 0ull;
+    const uint32_t lo = static_cast<uint32_t>(F), hi = static_cast<uint32_t>(F >> 32);
+    const int neg = static_cast<int>(b >> 63);
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const uint32_t byte = ((q < 4 ? lo : hi) >> (8 * (q & 3))) & 0xffu;
+        const uint32_t u = byte + c + 128u;
+        const int dq = static_cast<int>(u & 0xffu) - 128;
+        c = u >> 8;
+        d[kEmuDigits - 1 - q] = neg ? -dq : dq;
+    }
+    const int top = static_cast<int>((hi >> 16) + c);
+    d[0] = neg ? -top : top;
+}
+
+// bf16 bits of an integer |d| <= 256 (exact): 1.5 * 2^23 + d in binary32,
+// minus 1.5 * 2^23, keeps the top 16 bits.
+__device__ __forceinline__ uint32_t small_int_bf16(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// Tile t of the upper triangle of G: rows [128 jb, +128), columns [64 kb, +64),
+// kb >= 2 jb, enumerated jb-major.
+__host__ __device__ __forceinline__ void emu_tile(int t, int n, int &j0, int &k0) {
+    const int nJ = (n + kEmuM - 1) / kEmuM, nK = (n + kEmuN - 1) / kEmuN;
+    int jb = 0;
+    for (; jb < nJ; ++jb) {
+        const int cnt = nK - 2 * jb;
+        if (t < cnt) break;
+        t -= cnt;
+    }
+    j0 = kEmuM * jb;
+    k0 = kEmuN * (2 * jb + t);
+}
+
+int emu_tiles(int n) {
+    const int nJ = (n + kEmuM - 1) / kEmuM, nK = (n + kEmuN - 1) / kEmuN;
+    int c = 0;
+    for (int jb = 0; jb < nJ; ++jb) c += nK - 2 * jb;
+    return c;
+}
+
+// Largest biased binary64 exponent of each column (atomic max; colbits zeroed first).
+__global__ void k_col_exponent(const double *__restrict__ A, int64_t lda, int64_t m, int64_t chunk,
+                               int *__restrict__ colbits) {
+    const int j = blockIdx.x;
+    const int64_t rb = int64_t(blockIdx.y) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    int e = 0;
+    for (int64_t i = rb + threadIdx.x; i < re; i += blockDim.x) {
+        const unsigned long long b =
+            static_cast<unsigned long long>(__double_as_longlong(A[i + int64_t(j) * lda]));
+        e = max(e, static_cast<int>((b >> 52) & 0x7ff));
+    }
+    for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_down_sync(0xffffffffu, e, off));
+    if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(colbits + j, e);
+}
+
+// Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
+__device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
+
+__global__ void __launch_bounds__(kEmuThreads, 1)
+    k_gram_emu(const double *__restrict__ A, int64_t lda, int64_t m, int n,
+               const int *__restrict__ colbits, int64_t chunk, double *__restrict__ part,
+               DevStatus *st) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mma[kEmuStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int expA[kEmuM], expB[kEmuN];
+
+    int j0, k0;
+    emu_tile(blockIdx.x, n, j0, k0);
+    const bool b_in_a = (k0 >= j0) && (k0 + kEmuN <= j0 + kEmuM);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) tmem_alloc(&tmem_slot, kEmuTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kEmuStages; ++s) mbar_init(&bar_mma[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    for (int c = tid; c < kEmuM; c += kEmuThreads)
+        expA[c] = (j0 + c < n) ? emu_exponent(colbits[j0 + c]) : 0;
+    for (int c = tid; c < kEmuN; c += kEmuThreads)
+        expB[c] = (k0 + c < n) ? emu_exponent(colbits[k0 + c]) : 0;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
+    const uint32_t smem_base = smem_u32(smem_raw);
+
+    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows j of the tile),
+    // columns 16 (warp / 4) .. +15
+    const int lane_base = 32 * (warp & 3);
+    const int cgrp = warp >> 2;
+    long long acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0;
+    // this thread's elements of the CTA's binary64 partial, [col][row]
+    double *mine = part + (size_t(blockIdx.x) * gridDim.y + blockIdx.y) * kEmuSlot +
+                   size_t(16 * cgrp) * kEmuM + lane_base + lane;
+    int windows = 0;
+    bool flushed = false;
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const double v = static_cast<double>(acc[q]);
+            mine[q * kEmuM] = flushed ? mine[q * kEmuM] + v : v;
+            acc[q] = 0;
+        }
+        flushed = true;
+    };
+
+    const int64_t rb = int64_t(blockIdx.y) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    const int nsteps = re > rb ? static_cast<int>(ceil_div(re - rb, kEmuBK)) : 0;
+    const int ncolsB = b_in_a ? 0 : kEmuN;
+    const int ntasks = (kEmuM + ncolsB) * (kEmuBK / 8);
+    for (int ks = 0; ks < nsteps; ++ks) {
+        const int sidx = ks % kEmuStages;
+        unsigned char *stage = smem_raw + sidx * kEmuStageBytes;
+        const int64_t r0 = rb + int64_t(ks) * kEmuBK;
+        // (1) load this thread's blocks of 8 rows x 1 column (the loads are in
+        // flight while the stage's previous MMAs finish)
+        double xv[kEmuTaskSlots][8];
+#pragma unroll
+        for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
+            const int task = tid + ts * kEmuThreads;
+            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
+            const int col = c < kEmuM ? j0 + c : k0 + (c - kEmuM);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int64_t row = r0 + kb * 8 + t;
+                xv[ts][t] = (task < ntasks && row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
+            }
+        }
+        if (ks >= kEmuStages &&
+            !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / kEmuStages - 1) & 1)))
+            abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        // (2) digits, stored as K-major operand tiles
+#pragma unroll
+        for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
+            const int task = tid + ts * kEmuThreads;
+            if (task >= ntasks) break;
+            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
+            const bool isA = c < kEmuM;
+            const int cc = isA ? c : c - kEmuM;
+            const int E = isA ? expA[cc] : expB[cc];
+            uint32_t h[kEmuDigits][4];
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                int d0[kEmuDigits], d1[kEmuDigits];
+                emu_digits(xv[ts][t], E, d0);
+                emu_digits(xv[ts][t + 1], E, d1);
+#pragma unroll
+                for (int s = 0; s < kEmuDigits; ++s)
+                    h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+            }
+            unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
+            const int tbytes = isA ? kTileA : kTileB;
+#pragma unroll
+            for (int s = 0; s < kEmuDigits; ++s)
+                *reinterpret_cast<uint4 *>(base + s * tbytes + emu_off(cc, kb * 8)) =
+                    make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        __syncthreads();
+        // (3) one thread issues the level products of this block
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t sa = smem_base + sidx * kEmuStageBytes;
+            const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128
+                                       : sa + kEmuDigits * kTileA;
+            const uint32_t tb = b_in_a ? kTileA : kTileB;
+            const bool fresh = (ks % kEmuWinSteps) == 0;
+#pragma unroll 1
+            for (int L = 0; L < kEmuDigits; ++L) {
+#pragma unroll 1
+                for (int s = 0; s <= L; ++s) {
+                    const int t = L - s;
+#pragma unroll
+                    for (int kk = 0; kk < kEmuBK / 16; ++kk) {
+                        const uint64_t ad = smem_desc(sa + s * kTileA + kk * 256, 128, (kEmuBK / 8) * 128);
+                        const uint64_t bd = smem_desc(sb + t * tb + kk * 256, 128, (kEmuBK / 8) * 128);
+                        const uint32_t accum = (fresh && s == 0 && kk == 0) ? 0u : 1u;
+                        mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN), ad, bd, idesc, accum);
+                    }
+                }
+            }
+            mma_commit(&bar_mma[sidx]);
+        }
+        // (4) end of a window: drain the seven level accumulators
+        if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) {
+            if (!mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / kEmuStages) & 1)))
+                abort_flag = 1;
+            __syncthreads();
+            if (abort_flag) break;
+            tc_fence_after();
+            const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
+                                static_cast<uint32_t>(16 * cgrp);
+            float v[16], w[16];
+            tmem_ld16(tl + static_cast<uint32_t>(6 * kEmuN), w);
+            tmem_ld16(tl + static_cast<uint32_t>(5 * kEmuN), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
+            tmem_ld16(tl + static_cast<uint32_t>(4 * kEmuN), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
+#pragma unroll
+            for (int L = 0; L < 4; ++L) {
+                tmem_ld16(tl + static_cast<uint32_t>(L * kEmuN), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    acc[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << (32 - 8 * L));
+            }
+            if (++windows == kEmuFlushWindows) {
+                flush();
+                windows = 0;
+            }
+            tc_fence_before();
+            __syncthreads();  // TMEM read before the next window's first MMAs overwrite it
+        }
+    }
+    if (abort_flag) {
+        if (tid == 0) report(st, kErrTimeout, 0, -1);
+    } else {
+        flush();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kEmuTmemCols);
+}
+
+// G[j][k] = G[k][j] = 2^(E_j + E_k - 46) times the sum over the tile's CTAs
+// (in order) of their binary64 partials; NaN where a column holds a
+// non-finite value.
+__global__ void k_reduce_gram_emu(const double *__restrict__ part, int nsplit, int n,
+                                  const int *__restrict__ colbits, double *__restrict__ G,
+                                  int64_t ldg) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(n) * n) return;
+    const int j = static_cast<int>(e % n), k = static_cast<int>(e / n);
+    if (j > k) return;
+    const int jb = j / kEmuM, kb = k / kEmuN;
+    const int nK = (n + kEmuN - 1) / kEmuN;
+    int t = 0;
+    for (int q = 0; q < jb; ++q) t += nK - 2 * q;
+    t += kb - 2 * jb;
+    const size_t off = size_t(k - kEmuN * kb) * kEmuM + (j - kEmuM * jb);
+    const double s = ordered_sum(part + size_t(t) * nsplit * kEmuSlot + off, kEmuSlot, nsplit);
+    const int bj = __ldg(colbits + j), bk = __ldg(colbits + k);
+    double g;
+    if (bj == 0x7ff || bk == 0x7ff)
+        g = __longlong_as_double(0x7ff8000000000000ll);
+    else
+        g = ldexp(s, emu_exponent(bj) + emu_exponent(bk) - 46);
+    G[j + int64_t(k) * ldg] = g;
+    G[k + int64_t(j) * ldg] = g;
+}
+
+int emu_split(int n, int64_t m) {
+    const int tiles = emu_tiles(n);
+    int p = std::max(1, num_sms() / tiles);
+    const int64_t windows = ceil_div(m, int64_t(kEmuBK) * kEmuWinSteps);
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p, windows)));
+}
+
+}  // namespace
+
+size_t gram_emu_partials_doubles(int n) {
+    const size_t slots = size_t(num_sms()) + 8;
+    (void)n;
+    // one binary64 partial per CTA slot, plus the column exponents
+    return slots * kEmuSlot + 64;
+}
+
+cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, double *G, int64_t ldg,
+                            double *part, DevStatus *st, cudaStream_t stream) {
+    if (n < 1 || n > 256 || m < 1) return cudaErrorInvalidValue;
+    const int tiles = emu_tiles(n);
+    const int p = emu_split(n, m);
+    // chunks of whole windows, so that every window but the last is full
+    const int64_t win = int64_t(kEmuBK) * kEmuWinSteps;
+    int64_t chunk = round_up(ceil_div(m, p), win);
+    const int nsplit = static_cast<int>(ceil_div(m, chunk));
+    int *colbits = reinterpret_cast<int *>(part + size_t(tiles) * nsplit * kEmuSlot);
+    cudaError_t e = cudaMemsetAsync(colbits, 0, sizeof(int) * size_t(n), stream);
+    if (e != cudaSuccess) return e;
+    const int64_t cchunk = std::max<int64_t>(4096, ceil_div(m, 64));
+    const dim3 gx(n, static_cast<unsigned>(ceil_div(m, cchunk)));
+    RQ_LAUNCH(KID_EMU_AUX, stream, k_col_exponent<<<gx, 256, 0, stream>>>(A, lda, m, cchunk, colbits));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = size_t(kEmuStages) * kEmuStageBytes;
+    cudaFuncSetAttribute(k_gram_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    RQ_LAUNCH(KID_GRAM_EMU, stream,
+              k_gram_emu<<<dim3(tiles, nsplit), kEmuThreads, smem, stream>>>(
+                  A, lda, m, n, colbits, chunk, part, st));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t ne = int64_t(n) * n;
+    RQ_LAUNCH(KID_EMU_AUX, stream,
+              k_reduce_gram_emu<<<static_cast<unsigned>(ceil_div(ne, 256)), 256, 0, stream>>>(
+                  part, nsplit, n, colbits, G, ldg));
+    return cudaGetLastError();
+}
+
+}  // namespace rq

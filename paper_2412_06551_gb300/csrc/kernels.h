@@ -73,6 +73,15 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
                              double *part, DevStatus *st, cudaStream_t stream);
 size_t tc_sketch_smem_bytes(int n, int nterms);
 
+// ---- binary64-emulating Gram on the tensor cores (emu_gram.cu) ----
+// G = A^T A (n <= 256) from seven balanced base-256 digits of every element
+// (per-column exponents), exact fp32 level sums over 128-row windows,
+// int64/fp32 drains and a fixed-order binary64 reduction.  part holds the
+// per-CTA partials and the column exponents (gram_emu_partials_doubles).
+cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, double *G, int64_t ldg,
+                            double *part, DevStatus *st, cudaStream_t stream);
+size_t gram_emu_partials_doubles(int n);
+
 // Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
 cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,
                              cudaStream_t stream);
@@ -146,6 +155,8 @@ enum KernelId : int {
     KID_TRMM,
     KID_PAD,
     KID_SKETCH_TC,
+    KID_GRAM_EMU,
+    KID_EMU_AUX,
     KID_COUNT
 };
 

@@ -1,0 +1,170 @@
+"""Binary64-emulating tensor-core Gram (split-bf16 digits, exact fp32 level
+sums) and the RCLUPP_PREC_EMULATED tier of the drivers, against the oracle.
+
+Error model of the emulated Gram G = A^T A.  With E_j the column exponent
+(2^E_j > max_i |a_ij|), the digit split rounds a_ij at 2^(E_j - 56) and the
+product keeps the levels s + t <= 6 of the 7 x 7 digit products; both
+perturb G(j, k) by at most about (m + 1) 2^-53 2^(E_j + E_k).  The fp32
+window sums are exact and the binary64 combination adds at most
+(m / 128 + 2) u |A|^T |A|.  The tests bound the distance to the exact Gram
+(Python integers on integer-scaled inputs) or to the binary64 oracle (whose
+own error is gamma_m |A|^T |A|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def gamma(k):
+    return k * U / (1 - k * U)
+
+
+def dev(a):
+    a = np.asfortranarray(a)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda").t()
+
+
+def host(t):
+    return np.asfortranarray(t.detach().cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def rq():
+    import paper_2412_06551_gb300 as m
+    m.load()
+    return m
+
+
+def col_scale(x):
+    """2^E_j with 2^E_j > max_i |x_ij| (the smallest such power of two)."""
+    mx = np.max(np.abs(x), axis=0)
+    e = np.where(mx > 0, np.floor(np.log2(np.where(mx > 0, mx, 1.0))) + 1, -1022)
+    return np.ldexp(1.0, e.astype(int))
+
+
+def emu_bound(x):
+    m = x.shape[0]
+    sc = col_scale(x)
+    a = np.abs(x)
+    return 4 * (m + 128) * U * np.outer(sc, sc) + (m / 128 + 2) * U * (a.T @ a)
+
+
+def test_exact_on_small_integers(rq):
+    # |x| <= 100: one digit per entry, every level sum exact -> G exact
+    g = np.random.default_rng(1)
+    for m, n in [(1, 1), (300, 7), (5000, 64), (2049, 128), (1500, 200), (777, 256)]:
+        x = g.integers(-100, 101, size=(m, n)).astype(np.float64)
+        G = host(rq.rclupp_gram_emulated(dev(x)))
+        xi = x.astype(np.int64)
+        assert np.array_equal(G, (xi.T @ xi).astype(np.float64)), (m, n)
+
+
+def test_all_digits_against_exact_integers(rq):
+    # x = k 2^-40 with |k| < 2^47: the 56-bit scaled value k 2^8 is exact, so
+    # all seven digits are used and the only error is the dropped levels and
+    # the binary64 combination; the exact Gram comes from Python integers
+    g = np.random.default_rng(2)
+    for m, n in [(129, 5), (1000, 48), (3001, 130)]:
+        k = g.integers(-(2 ** 46), 2 ** 46, size=(m, n), dtype=np.int64)
+        x = np.ldexp(k.astype(np.float64), -40)
+        assert np.array_equal(np.ldexp(x, 40).astype(np.int64), k)  # exact
+        G = host(rq.rclupp_gram_emulated(dev(x)))
+        ko = k.astype(object)
+        exact = ko.T.dot(ko)
+        ref = np.array([[math.ldexp(float(v), -80) for v in row] for row in exact])
+        err = np.abs(G - ref)
+        assert np.all(err <= emu_bound(x)), float(np.max(err / emu_bound(x)))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (127, 3), (128, 64), (129, 65), (1000, 100), (5000, 128),
+                                 (3001, 129), (2100, 256), (70001, 200), (262144, 128)])
+def test_against_oracle(rq, m, n):
+    g = np.random.default_rng(m + n)
+    x = g.standard_normal((m, n)) * np.logspace(-3, 3, n)  # columns of very different scales
+    G = host(rq.rclupp_gram_emulated(dev(x)))
+    ref = oracle.gram(x)
+    a = np.abs(x)
+    tol = emu_bound(x) + gamma(m) * (a.T @ a)
+    assert np.all(np.abs(G - ref) <= tol), float(np.max(np.abs(G - ref) / tol))
+    assert np.array_equal(G, G.T)
+
+
+def test_special_columns(rq):
+    m, n = 3000, 6
+    g = np.random.default_rng(3)
+    x = g.standard_normal((m, n))
+    x[:, 1] = 0.0                      # zero column
+    x[:, 2] *= 1e-310                  # subnormal entries
+    x[:, 3] *= 1e150                   # large scale (x^2 ~ 1e300 is finite)
+    G = host(rq.rclupp_gram_emulated(dev(x)))
+    ref = oracle.gram(x)
+    assert np.all(G[1, :] == 0) and np.all(G[:, 1] == 0)
+    ok = np.ones((n, n), bool)
+    ok[1, :] = ok[:, 1] = False
+    a = np.abs(x)
+    tol = emu_bound(x) + gamma(m) * (a.T @ a)
+    assert np.all(np.abs(G - ref)[ok] <= tol[ok])
+    x[5, 4] = np.nan                   # a non-finite column poisons its row/column only
+    G = host(rq.rclupp_gram_emulated(dev(x)))
+    assert np.all(np.isnan(G[4, :])) and np.all(np.isnan(G[:, 4]))
+    assert np.all(np.isfinite(np.delete(np.delete(G, 4, 0), 4, 1)))
+
+
+def test_deterministic_and_ld(rq):
+    m, n = 40000, 96
+    x = synth.svd_matrix(m, n, 1e6, 5)
+    X = dev(x)
+    assert torch.equal(rq.rclupp_gram_emulated(X), rq.rclupp_gram_emulated(X))
+    buf = torch.zeros((n, m + 3), dtype=torch.float64, device="cuda")
+    Xp = buf.t()[:m]
+    Xp.copy_(X)
+    assert torch.equal(rq.rclupp_gram_emulated(Xp), rq.rclupp_gram_emulated(X))
+
+
+def _gate(x, q, r, q_o, r_o, kappa):
+    orth, res = oracle.orthogonality(q), oracle.residual(x, q, r)
+    orth_o, res_o = oracle.orthogonality(q_o), oracle.residual(x, q_o, r_o)
+    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+    assert orth <= max(10 * orth_o, 1e-13), (orth, orth_o)
+    assert res <= max(10 * res_o, 1e-13), (res, res_o)
+    if kappa <= 1e6:
+        assert np.linalg.norm(r - r_o) / np.linalg.norm(r_o) <= 1e-10 * kappa
+
+
+@pytest.mark.parametrize("algo", ["rclupp", "rcluppr"])
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10, 1e12])
+def test_driver_emulated_tier(rq, algo, kappa):
+    m, n, s = 8192, 64, 128
+    x = synth.svd_matrix(m, n, kappa, 81)
+    fn = rq.rclupp_factor if algo == "rclupp" else rq.rclupp_r_factor
+    Q, R, info = fn(dev(x), s=s, seed=7, prec=rq.PREC_EMULATED)
+    q_o, r_o, _ = getattr(oracle, algo)(x, S=oracle.gaussian_sketch_matrix(s, m, 7))
+    _gate(x, host(Q), host(R), q_o, r_o, kappa)
+    assert info.emulated == 1
+    assert info.prec_used in (0, 1, 2)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(4096, 64, 1e8), (5003, 128, 1e4), (3000, 256, 1e3),
+                                       (1000, 17, 1e10)])
+def test_emulated_with_explicit_sketch(rq, m, n, kappa):
+    # explicit S: binary64 sketch, emulated first-pass Gram; same S as the oracle
+    x = synth.svd_matrix(m, n, kappa, 82 + n)
+    S = synth.gaussian_sketch(2 * n, m, 13)
+    Q, R, info = rq.rclupp_factor(dev(x), s=2 * n, S=dev(S), prec=rq.PREC_EMULATED)
+    q_o, r_o, _ = oracle.rclupp(x, S=S)
+    _gate(x, host(Q), host(R), q_o, r_o, kappa)
+    assert info.emulated == 1 and info.prec_used == 0
+    Q2, R2, info2 = rq.rcholqr_factor(dev(x), s=2 * n, S=dev(S), prec=rq.PREC_EMULATED)
+    q2, r2, _ = oracle.rcholqr(x, S=S)
+    if kappa <= 1e8:
+        _gate(x, host(Q2), host(R2), q2, r2, kappa)
+    assert info2.emulated == 1
