@@ -55,25 +55,27 @@ typedef enum {
     RCLUPP_SKETCH_SPARSE_SIGN = 1 /* zeta distinct rows per column, +-1/sqrt(zeta)   */
 } rclupp_sketch_kind_t;
 
-/* Precision of the sketch product (the sketch only has to be an embedding,
- * Section 3).  The reduced tiers run the generated Gaussian sketch on the
- * tensor cores (tcgen05, bf16 operands, fp32 accumulation in tensor memory):
- * S's entries z(r, i) are rounded to bf16 and every x of X is either rounded
- * to bf16 (BF16) or split into three bf16 terms x1 = bf16(x),
- * x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums are
- * combined in binary64.  All other steps stay in binary64.  The sparse-sign
+/* Precision form.  The sketch only has to be an embedding (Section 3): the
+ * reduced tiers run the generated Gaussian sketch on the tensor cores
+ * (tcgen05, bf16 operands, fp32 accumulation in tensor memory): S's entries
+ * z(r, i) are rounded to bf16 and every x of X is either rounded to bf16
+ * (BF16) or split into three bf16 terms x1 = bf16(x), x2 = bf16(x - x1),
+ * x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums are combined in
+ * binary64.  EMULATED adds binary64-emulating tensor-core products for the
+ * solves and the first Gram.  Other steps stay in binary64.  The sparse-sign
  * sketch only adds and always runs in binary64; an explicit S requires
- * RCLUPP_PREC_FP64. */
+ * RCLUPP_PREC_FP64 or RCLUPP_PREC_EMULATED (whose sketch is then binary64). */
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
     RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
     RCLUPP_PREC_SKETCH_FP32 = 2, /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
-    RCLUPP_PREC_EMULATED = 3     /* the BF16 sketch tier, and the Gram of the first CholeskyQR
-                                    pass (Q1^T Q1) as binary64-emulating split-bf16 products on
-                                    the tensor cores (rclupp_gram_emulated); the final-pass Gram,
-                                    the triangular solves and the n x n factorizations stay in
-                                    binary64.  An explicit S or the sparse-sign sketch keeps a
-                                    binary64 sketch. */
+    RCLUPP_PREC_EMULATED = 3     /* the BF16 sketch tier; the triangular solves' block products
+                                    (rclupp_trsm_emulated) and the Gram of the first CholeskyQR
+                                    pass (Q1^T Q1, rclupp_gram_emulated) as binary64-emulating
+                                    split-bf16 products on the tensor cores; the final-pass Gram,
+                                    the diagonal blocks of the solves and the n x n
+                                    factorizations stay in binary64.  An explicit S or the
+                                    sparse-sign sketch keeps a binary64 sketch. */
 } rclupp_precision_t;
 
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
@@ -113,8 +115,8 @@ typedef struct {
                             RCLUPP/RCLUPPr escalate bf16 -> three-term bf16 -> FP64 when
                             the first Cholesky breaks down or the spread of its diagonal
                             exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2) */
-    int32_t emulated;    /* 1 when the first pass's Gram ran on the binary64-emulating
-                            tensor-core path (RCLUPP_PREC_EMULATED) */
+    int32_t emulated;    /* 1 when the solves and the first pass's Gram ran on the
+                            binary64-emulating tensor-core path (RCLUPP_PREC_EMULATED) */
 } rclupp_info_t;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -265,6 +267,19 @@ rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const 
  * NaN in G(j, k) when column j or k holds a non-finite value.  n <= 256. */
 rclupp_status_t rclupp_gram_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                                      int64_t lda, double *G, int64_t ldg);
+
+/* Q = A R^{-1} with the block products emulating binary64 on the tensor
+ * cores: the triangular solve of eq. (ewy) (C3, C7) in the precision form
+ * RCLUPP_PREC_EMULATED.  Substitution by 32-column blocks: the update
+ * A_J - Q_{<J} R_{<J,J} uses the digits of rclupp_gram_emulated (one exponent
+ * per row of Q over its first 32J columns, one per column of R over rows
+ * < 32J; levels <= 6 summed exactly in fp32 over at most 128 K-columns, then
+ * in int64), the 32 x 32 diagonal blocks are solved in binary64.  Error of
+ * an update entry: about (j0 + 128) 2^-53 2^(E_i + E'_c).  R: n x n upper,
+ * nonzero diagonal.  Q may alias A.  n <= 256. */
+rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                                     int64_t lda, const double *R, int64_t ldr, double *Q,
+                                     int64_t ldq);
 
 /* Q = A R^{-1} by substitution (eq. (ewy), C3, C7) and, when G != NULL,
  * G = Q^T Q (C1, C5) in the same pass.  R: n x n upper, nonzero diagonal.

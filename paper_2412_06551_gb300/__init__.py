@@ -26,7 +26,7 @@ __all__ = [
     "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
-    "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
+    "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
     "ALGO_RCLUPP", "ALGO_RCLUPPR",
@@ -98,6 +98,7 @@ _SIGNATURES = {
     "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
     "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_trsm_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_cholesky": ([_P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_trmm_upper": ([_P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
@@ -118,7 +119,7 @@ _SIGNATURES = {
 
 KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
                   "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc",
-                  "gram_emu", "emu_aux"]
+                  "gram_emu", "emu_aux", "trsm_emu"]
 
 
 def profile_enable(on: bool = True) -> None:
@@ -381,6 +382,18 @@ def rclupp_gram_emulated(A, *, G=None):
     st = load().rclupp_gram_emulated(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(G), ldg)
     _raise("rclupp_gram_emulated", st)
     return G
+
+
+def rclupp_trsm_emulated(A, R, *, Q=None):
+    """Q = A R^{-1} with binary64-emulating tensor-core block products."""
+    A, lda = colmajor(A)
+    m, n = A.shape
+    R, ldr = colmajor(R)
+    Q = empty_colmajor(m, n, A.device) if Q is None else Q
+    Q, ldq = colmajor(Q)
+    st = load().rclupp_trsm_emulated(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(R), ldr, _ptr(Q), ldq)
+    _raise("rclupp_trsm_emulated", st)
+    return Q
 
 
 ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2, ALGO_RCHOLQR, ALGO_SCHOLQR3 = 0, 1, 2, 3, 4, 5

@@ -123,7 +123,7 @@ Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *t
     Bufs b;
     const int n_pad = pad16(n);
     const size_t part = std::max({gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0),
-                                  gram_emu_partials_doubles(n)});
+                                  gram_emu_partials_doubles(n), trsm_emu_scratch_bytes(n) / 8 + 1});
     b.part = c.take<double>(part);
     b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
     b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
@@ -311,14 +311,15 @@ Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
 // First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
-// With `emulated` the Gram runs on the tensor cores emulating binary64 (the
-// final-pass Gram of rest_cholqr2 always stays binary64).
+// With `emulated` the triangular solve's block products and the Gram run on
+// the tensor cores emulating binary64 (the final-pass Gram of rest_cholqr2
+// always stays binary64).
 rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
                                   int64_t ldx, double *Q, int64_t ldq, bool emulated = false) {
     cudaStream_t s = c.s;
     DevStatus *st = c.st;
     if (emulated) {
-        RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, nullptr, 0, b.part, st, s));
+        RQ_TRY(launch_trsm_emu(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.part, st, s));
         RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
     } else {
         RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
@@ -327,17 +328,27 @@ rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const 
     return RCLUPP_OK;
 }
 
-// The rest of C3-C8 after R2 is known.
+// The rest of C3-C8 after R2 is known.  With `emulated` both triangular
+// solves use the emulated block products; the Gram of this final pass (C5)
+// stays binary64.
 rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, int64_t ldq,
-                             double *R, int64_t ldr) {
+                             double *R, int64_t ldr, bool emulated = false) {
     cudaStream_t s = c.s;
     DevStatus *st = c.st;
     const int np = pad16(n);
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
-    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
+    if (emulated) {
+        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, st, s));
+        RQ_TRY(launch_gram(Q, ldq, m, n, 0, b.G, n, b.part, st, s));
+    } else {
+        RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
+    }
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[3], b.rinv[3], nullptr, 0, st, 4, s));
     RQ_TRY(launch_trmm_upper(b.RP[3], np, b.RP[2], np, n, R, ldr, s));  // R = R4 R3
-    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, nullptr, 0, b.part, st, s));
+    if (emulated)
+        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, b.part, st, s));
+    else
+        RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, nullptr, 0, b.part, st, s));
     return RCLUPP_OK;
 }
 
@@ -376,7 +387,7 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
             return RCLUPP_ERR_CUDA;
     }
     *tier_used = tier;
-    return rest_cholqr2(ctx_of(h), b, m, n, Q, ldq, R, ldr);
+    return rest_cholqr2(ctx_of(h), b, m, n, Q, ldq, R, ldr, emulated);
 }
 
 // copy an m x n matrix (device to device, possibly different leading dims)
@@ -443,7 +454,11 @@ rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
         first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, tier == RCLUPP_PREC_EMULATED);
     if (st != RCLUPP_OK) return st;
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
-    RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st, c.s));
+    if (tier == RCLUPP_PREC_EMULATED)
+        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, c.st, c.s));
+    else
+        RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st,
+                                c.s));
     return RCLUPP_OK;
 }
 
@@ -918,6 +933,22 @@ rclupp_status_t rclupp_trsm_gram(rclupp_handle_t h, int64_t m, int64_t n, const 
     if (e == cudaSuccess)
         e = launch_trsm_gram(A, lda, m, int(n), b.RP[0], b.rinv[0], Q, ldq, G, ldg, b.part,
                              h->d_status, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t h, int64_t m, int64_t n, const double *A,
+                                     int64_t lda, const double *R, int64_t ldr, double *Q,
+                                     int64_t ldq) {
+    if (!h || !A || !R || !Q || n < 1 || m < 1 || bad_ld(lda, m) || bad_ld(ldr, n) || bad_ld(ldq, m))
+        return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaError_t e = launch_pad_upper(R, ldr, int(n), b.RP[0], b.rinv[0], h->stream);
+    if (e == cudaSuccess)
+        e = launch_trsm_emu(A, lda, m, int(n), b.RP[0], b.rinv[0], Q, ldq, b.part, h->d_status,
+                            h->stream);
     return finish(h, from_cuda(e), nullptr, nullptr);
 }
 

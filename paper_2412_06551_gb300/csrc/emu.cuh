@@ -1,0 +1,70 @@
+// Digits of the binary64-emulating tensor-core products (split-bf16 with
+// exact fp32 sums): an element x of a row or column with exponent E
+// (2^E > every |x| of it) becomes F = round(x 2^(55 - E)) (half away from
+// zero), written in seven balanced base-256 digits d_0..d_6, |d_s| <= 128,
+// so that x = 2^(E - 7) sum_s d_s 2^(-8s) up to 2^(E - 56).  Every digit is
+// an exact bf16 and every product of two digits an integer of magnitude
+// <= 2^14.  Operand tiles are K-major 8 x 8 bf16 core matrices of 32 K-columns.
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace rq {
+
+constexpr int kEmuDigits = 7;
+constexpr int kEmuBK = 32;  // K-columns of one operand tile
+
+// Byte offset of element (row, k) of a K-major operand tile of kEmuBK
+// columns laid out as [row/8][k/8][row%8][k%8] (bf16).
+__device__ __forceinline__ uint32_t emu_off(int row, int k) {
+    return static_cast<uint32_t>(((row >> 3) * (kEmuBK / 8) + (k >> 3)) * 128 + (row & 7) * 16 +
+                                 (k & 7) * 2);
+}
+
+// Balanced base-256 digits of F = round(x 2^(55 - E)), for |x| < 2^E: the
+// digits of |F| (bytes with a carry into the next one when a byte is >= 128),
+// negated for negative x.  Every digit lies in [-128, 128].
+__device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int e = static_cast<int>((b >> 52) & 0x7ff);
+    unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+    if (e != 0) M |= 1ull << 52;
+    // |F| = M 2^sh; sh <= 2 for normal x as |x| < 2^E, 3 for subnormals of a
+    // column whose largest exponent is subnormal
+    const int sh = (e != 0 ? e : 1) - 1020 - E;
+    unsigned long long F;
+    if (sh >= 0)
+        F = M << (sh & 3);
+    else if (sh > -55)
+        F = (M + (1ull << (-sh - 1))) >> (-sh);
+    else
+        F = 0ull;
+    const uint32_t lo = static_cast<uint32_t>(F), hi = static_cast<uint32_t>(F >> 32);
+    const int neg = static_cast<int>(b >> 63);
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const uint32_t byte = ((q < 4 ? lo : hi) >> (8 * (q & 3))) & 0xffu;
+        const uint32_t u = byte + c + 128u;
+        const int dq = static_cast<int>(u & 0xffu) - 128;
+        c = u >> 8;
+        d[kEmuDigits - 1 - q] = neg ? -dq : dq;
+    }
+    const int top = static_cast<int>((hi >> 16) + c);
+    d[0] = neg ? -top : top;
+}
+
+// bf16 bits of an integer |d| <= 256 (exact): 1.5 * 2^23 + d in binary32,
+// minus 1.5 * 2^23, keeps the top 16 bits.
+__device__ __forceinline__ uint32_t small_int_bf16(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
+__device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
+
+
+}  // namespace rq

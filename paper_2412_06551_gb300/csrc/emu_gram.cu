@@ -33,18 +33,17 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "emu.cuh"
 #include "tcgen05.cuh"
 
 namespace rq {
 namespace {
 
 constexpr int kEmuThreads = 512;
-constexpr int kEmuBK = 32;      // rows of A per stage
 constexpr int kEmuWinSteps = 4; // stages per exact window (128 rows)
-constexpr int kEmuDigits = 7;
 constexpr int kEmuM = 128;      // rows of G per tile (columns j of A)
 constexpr int kEmuN = 64;       // columns of G per tile (columns k of A)
-constexpr int kEmuStages = 2;
+constexpr int kEmuMaxStages = 3;  // 3 stages of j digits only, or 2 with k digits
 constexpr int kTileA = kEmuM * kEmuBK * 2;  // bytes of one digit tile of the j columns
 constexpr int kTileB = kEmuN * kEmuBK * 2;  // ... of the k columns
 constexpr int kEmuStageBytes = kEmuDigits * (kTileA + kTileB);
@@ -52,53 +51,6 @@ constexpr int kEmuTmemCols = 512;
 constexpr int kEmuSlot = kEmuM * kEmuN;  // elements of one per-CTA partial
 constexpr int kEmuFlushWindows = 512;    // int64 drains between binary64 flushes
 constexpr int kEmuTaskSlots = 2;         // digit tasks per thread and stage (A: 1, B: 1 more)
-
-// Byte offset of element (row, k) of a K-major operand tile of kEmuBK
-// columns laid out as [row/8][k/8][row%8][k%8] (bf16).
-__device__ __forceinline__ uint32_t emu_off(int row, int k) {
-    return static_cast<uint32_t>(((row >> 3) * (kEmuBK / 8) + (k >> 3)) * 128 + (row & 7) * 16 +
-                                 (k & 7) * 2);
-}
-
-// Balanced base-256 digits of F = round(x 2^(55 - E)), for |x| < 2^E: the
-// digits of |F| (bytes with a carry into the next one when a byte is >= 128),
-// negated for negative x.  Every digit lies in [-128, 128].
-__device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int e = static_cast<int>((b >> 52) & 0x7ff);
-    unsigned long long M = b & 0xFFFFFFFFFFFFFull;
-    if (e != 0) M |= 1ull << 52;
-    // |F| = M 2^sh; sh <= 2 for normal x as |x| < 2^E, 3 for subnormals of a
-    // column whose largest exponent is subnormal
-    const int sh = (e != 0 ? e : 1) - 1020 - E;
-    unsigned long long F;
-    if (sh >= 0)
-        F = M << (sh & 3);
-    else if (sh > -55)
-        F = (M + (1ull << (-sh - 1))) >> (-sh);
-    else
-        F = 0ull;
-    const uint32_t lo = static_cast<uint32_t>(F), hi = static_cast<uint32_t>(F >> 32);
-    const int neg = static_cast<int>(b >> 63);
-    uint32_t c = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const uint32_t byte = ((q < 4 ? lo : hi) >> (8 * (q & 3))) & 0xffu;
-        const uint32_t u = byte + c + 128u;
-        const int dq = static_cast<int>(u & 0xffu) - 128;
-        c = u >> 8;
-        d[kEmuDigits - 1 - q] = neg ? -dq : dq;
-    }
-    const int top = static_cast<int>((hi >> 16) + c);
-    d[0] = neg ? -top : top;
-}
-
-// bf16 bits of an integer |d| <= 256 (exact): 1.5 * 2^23 + d in binary32,
-// minus 1.5 * 2^23, keeps the top 16 bits.
-__device__ __forceinline__ uint32_t small_int_bf16(int d) {
-    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
-}
 
 // Tile t of the upper triangle of G: rows [128 jb, +128), columns [64 kb, +64),
 // kb >= 2 jb, enumerated jb-major.
@@ -137,15 +89,12 @@ __global__ void k_col_exponent(const double *__restrict__ A, int64_t lda, int64_
     if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(colbits + j, e);
 }
 
-// Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
-__device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
-
 __global__ void __launch_bounds__(kEmuThreads, 1)
     k_gram_emu(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                const int *__restrict__ colbits, int64_t chunk, double *__restrict__ part,
                DevStatus *st) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mma[kEmuStages];
+    __shared__ __align__(8) uint64_t bar_mma[kEmuMaxStages];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int expA[kEmuM], expB[kEmuN];
@@ -153,11 +102,15 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     int j0, k0;
     emu_tile(blockIdx.x, n, j0, k0);
     const bool b_in_a = (k0 >= j0) && (k0 + kEmuN <= j0 + kEmuM);
+    // the k columns inside the j columns need no digits of their own, which
+    // leaves room for a third stage
+    const int nst = b_in_a ? 3 : 2;
+    const int stage_bytes = b_in_a ? kEmuDigits * kTileA : kEmuStageBytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) tmem_alloc(&tmem_slot, kEmuTmemCols);
     if (tid == 0) {
-        for (int s = 0; s < kEmuStages; ++s) mbar_init(&bar_mma[s], 1);
+        for (int s = 0; s < kEmuMaxStages; ++s) mbar_init(&bar_mma[s], 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -200,8 +153,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     const int ncolsB = b_in_a ? 0 : kEmuN;
     const int ntasks = (kEmuM + ncolsB) * (kEmuBK / 8);
     for (int ks = 0; ks < nsteps; ++ks) {
-        const int sidx = ks % kEmuStages;
-        unsigned char *stage = smem_raw + sidx * kEmuStageBytes;
+        const int sidx = ks % nst;
+        unsigned char *stage = smem_raw + sidx * stage_bytes;
         const int64_t r0 = rb + int64_t(ks) * kEmuBK;
         // (1) load this thread's blocks of 8 rows x 1 column (the loads are in
         // flight while the stage's previous MMAs finish)
@@ -217,8 +170,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
                 xv[ts][t] = (task < ntasks && row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
             }
         }
-        if (ks >= kEmuStages &&
-            !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / kEmuStages - 1) & 1)))
+        if (ks >= nst &&
+            !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst - 1) & 1)))
             abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
@@ -253,7 +206,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         // (3) one thread issues the level products of this block
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t sa = smem_base + sidx * kEmuStageBytes;
+            const uint32_t sa = smem_base + sidx * stage_bytes;
             const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128
                                        : sa + kEmuDigits * kTileA;
             const uint32_t tb = b_in_a ? kTileA : kTileB;
@@ -276,7 +229,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         }
         // (4) end of a window: drain the seven level accumulators
         if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) {
-            if (!mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / kEmuStages) & 1)))
+            if (!mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst) & 1)))
                 abort_flag = 1;
             __syncthreads();
             if (abort_flag) break;
@@ -375,7 +328,7 @@ cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, doub
     const dim3 gx(n, static_cast<unsigned>(ceil_div(m, cchunk)));
     RQ_LAUNCH(KID_EMU_AUX, stream, k_col_exponent<<<gx, 256, 0, stream>>>(A, lda, m, cchunk, colbits));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t smem = size_t(kEmuStages) * kEmuStageBytes;
+    const size_t smem = std::max(size_t(2) * kEmuStageBytes, size_t(3) * kEmuDigits * kTileA);
     cudaFuncSetAttribute(k_gram_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     RQ_LAUNCH(KID_GRAM_EMU, stream,
               k_gram_emu<<<dim3(tiles, nsplit), kEmuThreads, smem, stream>>>(

@@ -1,0 +1,339 @@
+// Triangular solve Q = A R^{-1} with its block products emulating binary64 on
+// the tensor cores (the precision form of eq. (ewy) / C3, C7: substitution by
+// 32-column blocks, the off-diagonal block products as split-bf16 products
+// with exact fp32 sums, the diagonal blocks solved in binary64).
+//
+// For column block J (columns [32J, 32J + 32)):
+//   C_J = A_J - Q_{<J} R_{<J,J}      (emulated: digits of Q's rows, R's columns)
+//   Q_J = C_J R_JJ^{-1}              (binary64 substitution, as the FP64 kernel)
+// Q_{<J}'s digits use one exponent per row over its first 32J columns (from a
+// running maximum of the row's solved exponents), R's one per column over
+// rows < 32J (precomputed by k_trsm_emu_prep).  Digits are those of the
+// emulated Gram (emu.cuh); levels s + t <= 6 are kept; a level's fp32 sum over
+// at most 128 K-columns (7 x 128 products <= 2^14) is exact, so the TMEM
+// accumulators are drained into one int64 per element after every 4 K-chunks
+// of 32.  The update is then 2^(E_i + E'_c - 46) times that integer.
+//
+// A CTA walks its chunk of rows in tiles of 128 (M = 128, one row per TMEM
+// lane).  Per K-chunk the 512 threads load 128 x 32 solved values of Q (L2,
+// written by the CTA itself), split them into digits (K-major operand tiles),
+// copy R's precomputed digit tiles, and one thread issues 28 x 2 MMAs
+// (kind::f16, M=128, N=32, K=16) into seven 32-column accumulators; two stages
+// alternate.  The diagonal-block solve gives each row 4 adjacent lanes of a
+// warp (8 interleaved columns each) and broadcasts solved values by shuffles.
+#include <algorithm>
+
+#include "common.cuh"
+#include "emu.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int kTeThreads = 512;
+constexpr int kTeM = 128;         // rows per tile
+constexpr int kTeB = 32;          // columns per block (= K per chunk = N of the MMA)
+constexpr int kTeWinChunks = 4;   // K-chunks per exact window (128 K-columns)
+constexpr int kTeStages = 2;
+constexpr int kTeTileA = kTeM * kEmuBK * 2;   // one digit tile of Q: 8 KB
+constexpr int kTeTileB = kTeB * kEmuBK * 2;   // one digit tile of R: 2 KB
+constexpr int kTeStageA = kEmuDigits * kTeTileA;
+constexpr int kTeStageB = kEmuDigits * kTeTileB;
+constexpr int kTeStageBytes = kTeStageA + kTeStageB;
+constexpr int kTeCBytes = kTeM * kTeB * 8;    // binary64 block C_J
+constexpr int kTeTmemCols = 256;
+constexpr int kTeP = kTeThreads / kTeM;       // lanes per row in the diagonal solve
+constexpr int kTeCPT = kTeB / kTeP;           // columns per lane
+
+// R's digit tiles of (target block J, K-chunk kc), kc < J, stored densely.
+__host__ __device__ __forceinline__ size_t te_rtile(int J, int kc) {
+    return (size_t(J) * (J - 1) / 2 + kc) * kTeStageB;
+}
+
+// Column exponents of R over rows < 32J for each target block J >= 1, and the
+// digit tiles of R[32 kc .. 32 kc + 31][32J .. 32J + 31].  One CTA per J.
+__global__ void k_trsm_emu_prep(const double *__restrict__ RP, int ldr, int n,
+                                unsigned char *__restrict__ rdig, int *__restrict__ rbits) {
+    const int J = blockIdx.x + 1;
+    const int j0 = kTeB * J;
+    __shared__ int cb[kTeB];
+    if (threadIdx.x < kTeB) {
+        const int col = j0 + threadIdx.x;
+        int e = 0;
+        if (col < n)
+            for (int k = 0; k < j0; ++k) {
+                const unsigned long long b =
+                    static_cast<unsigned long long>(__double_as_longlong(RP[k + int64_t(col) * ldr]));
+                e = max(e, static_cast<int>((b >> 52) & 0x7ff));
+            }
+        cb[threadIdx.x] = e;
+        rbits[J * kTeB + threadIdx.x] = e;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < j0 * kTeB; idx += blockDim.x) {
+        const int k = idx % j0, c = idx / j0;
+        const int col = j0 + c;
+        const double r = col < n ? RP[k + int64_t(col) * ldr] : 0.0;
+        int d[kEmuDigits];
+        emu_digits(r, emu_exponent(cb[c]), d);
+        unsigned char *tile = rdig + te_rtile(J, k / kEmuBK);
+#pragma unroll
+        for (int s = 0; s < kEmuDigits; ++s)
+            *reinterpret_cast<uint16_t *>(tile + s * kTeTileB + emu_off(c, k % kEmuBK)) =
+                static_cast<uint16_t>(small_int_bf16(d[s]));
+    }
+}
+
+__global__ void __launch_bounds__(kTeThreads, 1)
+    k_trsm_emu(const double *A, int64_t lda, int64_t m, int n, int n_pad, int64_t chunk,
+               const double *__restrict__ RT, const double *__restrict__ rinv,
+               const unsigned char *__restrict__ rdig, const int *__restrict__ rbits, double *Q,
+               int64_t ldq, DevStatus *st) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mma[kTeStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int rowbits[kTeM];
+    double *Cb = reinterpret_cast<double *>(smem_raw + kTeStages * kTeStageBytes);  // [col][row]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(&tmem_slot, kTeTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kTeStages; ++s) mbar_init(&bar_mma[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_bf16_f32(kTeM, kTeB);
+    const uint32_t smem_base = smem_u32(smem_raw);
+    const int nblk = (n + kTeB - 1) / kTeB;
+
+    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows), columns 8 (warp / 4) .. +7
+    const int lane_base = 32 * (warp & 3);
+    const int cgrp = warp >> 2;
+    const int drow = lane_base + lane;
+    // digit task: row tid % 128, K-columns 8 (tid / 128) .. +7 of the chunk
+    const int srow = tid % kTeM, skg = tid / kTeM;
+    // diagonal solve: row ti, lane p of 4, columns p + 4c
+    const int p = tid % kTeP, ti = tid / kTeP;
+    const int src0 = (tid & 31) - p;
+
+    const int64_t rb = int64_t(blockIdx.x) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    unsigned kcount = 0;  // K-chunks issued by this CTA (ring position and phase)
+    for (int64_t r0 = rb; r0 < re; r0 += kTeM) {
+        if (tid < kTeM) rowbits[tid] = 0;
+        __syncthreads();
+        for (int J = 0; J < nblk; ++J) {
+            const int j0 = kTeB * J;
+            long long acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0;
+            // ---- C_J update: emulated Q_{<J} R_{<J,J} over K-chunks kc < J
+            for (int kc = 0; kc < J; ++kc, ++kcount) {
+                const int sidx = kcount % kTeStages;
+                unsigned char *stage = smem_raw + sidx * kTeStageBytes;
+                // loads first: in flight while the ring slot's MMAs finish
+                double xv[8];
+                const int64_t row = r0 + srow;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int col = kEmuBK * kc + 8 * skg + t;
+                    xv[t] = row < re ? __ldcg(Q + row + int64_t(col) * ldq) : 0.0;
+                }
+                const uint4 *rsrc = reinterpret_cast<const uint4 *>(rdig + te_rtile(J, kc));
+                uint4 rv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = tid + u * kTeThreads;
+                    rv[u] = idx < kTeStageB / 16 ? __ldg(rsrc + idx) : make_uint4(0, 0, 0, 0);
+                }
+                if (kcount >= kTeStages &&
+                    !mbar_wait_bounded(&bar_mma[sidx],
+                                       static_cast<uint32_t>((kcount / kTeStages - 1) & 1)))
+                    abort_flag = 1;
+                __syncthreads();
+                if (abort_flag) break;
+                const int E = emu_exponent(rowbits[srow]);
+                uint32_t h[kEmuDigits][4];
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    int d0[kEmuDigits], d1[kEmuDigits];
+                    emu_digits(xv[t], E, d0);
+                    emu_digits(xv[t + 1], E, d1);
+#pragma unroll
+                    for (int s = 0; s < kEmuDigits; ++s)
+                        h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                }
+#pragma unroll
+                for (int s = 0; s < kEmuDigits; ++s)
+                    *reinterpret_cast<uint4 *>(stage + s * kTeTileA + emu_off(srow, 8 * skg)) =
+                        make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = tid + u * kTeThreads;
+                    if (idx < kTeStageB / 16)
+                        reinterpret_cast<uint4 *>(stage + kTeStageA)[idx] = rv[u];
+                }
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t sa = smem_base + sidx * kTeStageBytes;
+                    const uint32_t sb = sa + kTeStageA;
+                    const bool fresh = (kc % kTeWinChunks) == 0;
+#pragma unroll 1
+                    for (int L = 0; L < kEmuDigits; ++L) {
+#pragma unroll 1
+                        for (int s = 0; s <= L; ++s) {
+                            const int t = L - s;
+#pragma unroll
+                            for (int kk = 0; kk < kEmuBK / 16; ++kk) {
+                                const uint64_t ad =
+                                    smem_desc(sa + s * kTeTileA + kk * 256, 128, (kEmuBK / 8) * 128);
+                                const uint64_t bd =
+                                    smem_desc(sb + t * kTeTileB + kk * 256, 128, (kEmuBK / 8) * 128);
+                                mma_bf16(tmem + static_cast<uint32_t>(L * kTeB), ad, bd, idesc,
+                                         (fresh && s == 0 && kk == 0) ? 0u : 1u);
+                            }
+                        }
+                    }
+                    mma_commit(&bar_mma[sidx]);
+                }
+                if ((kc % kTeWinChunks) == kTeWinChunks - 1 || kc == J - 1) {
+                    if (!mbar_wait_bounded(&bar_mma[sidx],
+                                           static_cast<uint32_t>((kcount / kTeStages) & 1)))
+                        abort_flag = 1;
+                    __syncthreads();
+                    if (abort_flag) break;
+                    tc_fence_after();
+                    const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
+                                        static_cast<uint32_t>(8 * cgrp);
+                    float v[8], w[8];
+                    tmem_ld8(tl + static_cast<uint32_t>(6 * kTeB), w);
+                    tmem_ld8(tl + static_cast<uint32_t>(5 * kTeB), v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
+                    tmem_ld8(tl + static_cast<uint32_t>(4 * kTeB), v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
+#pragma unroll
+                    for (int L = 0; L < 4; ++L) {
+                        tmem_ld8(tl + static_cast<uint32_t>(L * kTeB), v);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            acc[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << (32 - 8 * L));
+                    }
+                    tc_fence_before();
+                    __syncthreads();
+                }
+            }
+            if (abort_flag) break;
+            // ---- C_J = A_J - update, in shared memory [col][row]
+            {
+                const int64_t row = r0 + drow;
+                const int rbit = rowbits[drow];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int c = 8 * cgrp + q, col = j0 + c;
+                    double a = (row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
+                    if (J > 0 && col < n) {
+                        const int cbit = __ldg(rbits + J * kTeB + c);
+                        const double u = (rbit == 0x7ff || cbit == 0x7ff)
+                                             ? __longlong_as_double(0x7ff8000000000000ll)
+                                             : ldexp(static_cast<double>(acc[q]),
+                                                     emu_exponent(rbit) + emu_exponent(cbit) - 46);
+                        a -= u;
+                    }
+                    Cb[c * kTeM + drow] = a;
+                }
+            }
+            __syncthreads();
+            // ---- Q_J = C_J R_JJ^{-1} (binary64): column j0 + t in turn
+            {
+                double x[kTeCPT];
+#pragma unroll
+                for (int c = 0; c < kTeCPT; ++c) x[c] = Cb[(p + kTeP * c) * kTeM + ti];
+#pragma unroll
+                for (int t = 0; t < kTeB; ++t) {
+                    const int owner = t % kTeP, lc = t / kTeP;
+                    const int jt = j0 + t;
+                    if (p == owner) x[lc] *= (jt < n) ? __ldg(rinv + jt) : 0.0;
+                    const double q = __shfl_sync(0xffffffffu, x[lc], src0 + owner);
+                    if (jt < n) {
+                        const double *rk = RT + int64_t(jt) * n_pad + j0 + p;
+#pragma unroll
+                        for (int c = 0; c < kTeCPT; ++c) {
+                            if ((kTeP - 1) + kTeP * c <= t) continue;  // no lane has a column past t
+                            if (p + kTeP * c > t && j0 + p + kTeP * c < n)
+                                x[c] = fma(-q, __ldg(rk + kTeP * c), x[c]);
+                        }
+                    }
+                }
+                // store Q_J and fold the row's exponents into its running maximum
+                const int64_t row = r0 + ti;
+                int eb = 0;
+#pragma unroll
+                for (int c = 0; c < kTeCPT; ++c) {
+                    const int col = j0 + p + kTeP * c;
+                    if (col < n) {
+                        if (row < re) Q[row + int64_t(col) * ldq] = x[c];
+                        const unsigned long long b =
+                            static_cast<unsigned long long>(__double_as_longlong(x[c]));
+                        eb = max(eb, static_cast<int>((b >> 52) & 0x7ff));
+                    }
+                }
+#pragma unroll
+                for (int off = 1; off < kTeP; off <<= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
+                __syncthreads();  // every thread has read rowbits for this block
+                if (p == 0) rowbits[ti] = max(rowbits[ti], eb);
+                __syncthreads();  // Q_J stored and rowbits updated before the next block reads them
+            }
+        }
+        if (abort_flag) break;
+    }
+    if (abort_flag && tid == 0) report(st, kErrTimeout, 0, -1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTeTmemCols);
+}
+
+}  // namespace
+
+size_t trsm_emu_scratch_bytes(int n) {
+    const int nblk = (n + kTeB - 1) / kTeB;
+    return te_rtile(nblk, 0) + size_t(nblk) * kTeB * sizeof(int) + 256;
+}
+
+cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                            const double *rinv, double *Q, int64_t ldq, void *scratch,
+                            DevStatus *st, cudaStream_t stream) {
+    if (n < 1 || n > 256 || m < 1) return cudaErrorInvalidValue;
+    const int n_pad = pad16(n);
+    const int nblk = (n + kTeB - 1) / kTeB;
+    unsigned char *rdig = static_cast<unsigned char *>(scratch);
+    int *rbits = reinterpret_cast<int *>(rdig + te_rtile(nblk, 0));
+    cudaError_t e;
+    if (nblk > 1) {
+        RQ_LAUNCH(KID_EMU_AUX, stream,
+                  k_trsm_emu_prep<<<nblk - 1, 256, 0, stream>>>(RP, n_pad, n, rdig, rbits));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t tiles = ceil_div(m, kTeM);
+    const int64_t grid = std::min<int64_t>(tiles, num_sms());
+    const int64_t chunk = ceil_div(tiles, grid) * kTeM;
+    const int g = static_cast<int>(ceil_div(m, chunk));
+    const size_t smem = size_t(kTeStages) * kTeStageBytes + kTeCBytes;
+    cudaFuncSetAttribute(k_trsm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    RQ_LAUNCH(KID_TRSM_EMU, stream,
+              k_trsm_emu<<<g, kTeThreads, smem, stream>>>(A, lda, m, n, n_pad, chunk,
+                                                          RP + size_t(n_pad) * n_pad, rinv, rdig,
+                                                          rbits, Q, ldq, st));
+    return cudaGetLastError();
+}
+
+}  // namespace rq

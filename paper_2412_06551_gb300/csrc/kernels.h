@@ -82,6 +82,17 @@ cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, doub
                             double *part, DevStatus *st, cudaStream_t stream);
 size_t gram_emu_partials_doubles(int n);
 
+// ---- triangular solve with binary64-emulating block products (emu_trsm.cu) ----
+// Q = A R^{-1} by 32-column blocks: the off-diagonal block products on the
+// tensor cores (digits of Q's rows and R's columns, exact fp32 level sums,
+// int64 drains), the diagonal blocks in binary64.  RP/rinv as for
+// launch_trsm_gram (padded factor followed by its row-major copy); scratch
+// holds R's digit tiles (trsm_emu_scratch_bytes).  Q may alias A.
+cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                            const double *rinv, double *Q, int64_t ldq, void *scratch,
+                            DevStatus *st, cudaStream_t stream);
+size_t trsm_emu_scratch_bytes(int n);
+
 // Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
 cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,
                              cudaStream_t stream);
@@ -157,6 +168,7 @@ enum KernelId : int {
     KID_SKETCH_TC,
     KID_GRAM_EMU,
     KID_EMU_AUX,
+    KID_TRSM_EMU,
     KID_COUNT
 };
 

@@ -44,7 +44,8 @@ Profiler &prof() {
 const char *kNames[KID_COUNT] = {"sketch_gauss", "sketch_sparse", "gram",       "trsm_gram",
                                  "trsm",         "reduce",        "lu_col",     "lu_trailing",
                                  "lu_u12",       "small_precond", "cholesky",   "trmm",
-                                 "pad",          "sketch_tc",     "gram_emu",   "emu_aux"};
+                                 "pad",          "sketch_tc",     "gram_emu",   "emu_aux",
+                                 "trsm_emu"};
 
 }  // namespace
 

@@ -168,3 +168,61 @@ def test_emulated_with_explicit_sketch(rq, m, n, kappa):
     if kappa <= 1e8:
         _gate(x, host(Q2), host(R2), q2, r2, kappa)
     assert info2.emulated == 1
+
+
+# ---------------------------------------------------------------- triangular solve ---
+
+def trsm_bound(x, r, q_ref):
+    """|Q_emu - Q_ref| bound: the emulated updates perturb C_J by about
+    (n + 128) 2^-53 2^(E_i + E'_c) per entry; substitution turns a
+    perturbation of A into one of Q through R^{-1}; plus both sides' binary64
+    rounding (n u kappa-like growth, taken from |Q| |R| |R^{-1}|)."""
+    m, n = x.shape
+    qs = col_scale(np.abs(q_ref).T).reshape(-1, 1)  # per-row scale of Q
+    rs = col_scale(r)                               # per-column scale of R
+    rinv = np.abs(np.linalg.inv(r))
+    pert = (n + 128) * 4 * U * (qs * (np.ones((1, n)) * rs.max())) * n
+    return pert @ rinv + 20 * n * U * (np.abs(q_ref) @ np.abs(r)) @ rinv
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (300, 31), (1000, 32), (3001, 33), (5000, 64), (4097, 100),
+                                 (2048, 128), (3000, 129), (2100, 256), (70001, 200)])
+def test_trsm_emulated_against_oracle(rq, m, n):
+    g = np.random.default_rng(m * n + 1)
+    r = np.triu(g.standard_normal((n, n))) / math.sqrt(n) + 2 * np.eye(n)
+    x = g.standard_normal((m, n)) * np.logspace(-2, 2, n)
+    q = host(rq.rclupp_trsm_emulated(dev(x), dev(r)))
+    q_ref = oracle.trsm(x, r)
+    err = np.abs(q - q_ref)
+    tol = trsm_bound(x, r, q_ref)
+    assert np.all(err <= tol), float(np.max(err / tol))
+    # residual of the solve at binary64 level
+    assert np.linalg.norm(q @ r - x) <= 50 * n * U * np.linalg.norm(np.abs(q) @ np.abs(r))
+
+
+def test_trsm_emulated_exact_on_integers(rq):
+    # unit upper R with small integers and Q0 with small integers: every update
+    # is an exact integer of few digits, so Q comes back exactly
+    g = np.random.default_rng(4)
+    for n, m in [(48, 3000), (130, 1000), (256, 700)]:
+        r = np.triu(g.integers(-3, 4, size=(n, n)), 1).astype(np.float64) + np.diag(g.choice([-1.0, 1.0], n))
+        q0 = g.integers(-5, 6, size=(m, n)).astype(np.float64)
+        x = (q0.astype(np.int64) @ r.astype(np.int64)).astype(np.float64)
+        assert np.max(np.abs(x)) < 2 ** 50
+        q = host(rq.rclupp_trsm_emulated(dev(x), dev(r)))
+        assert np.array_equal(q, q0), (n, m)
+
+
+def test_trsm_emulated_in_place_and_ld(rq):
+    m, n = 3001, 97
+    g = np.random.default_rng(5)
+    r = np.triu(g.standard_normal((n, n))) + 3 * np.eye(n)
+    x = g.standard_normal((m, n))
+    ref = host(rq.rclupp_trsm_emulated(dev(x), dev(r)))
+    for ld in (3005, 3008):
+        buf = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+        X = buf.t()[:m]
+        X.copy_(dev(x))
+        rq.rclupp_trsm_emulated(X, dev(r), Q=X)
+        assert np.array_equal(host(X), ref)
+        assert float(buf.t()[m:].abs().max()) == 0.0
