@@ -15,12 +15,14 @@
 // of 32.  The update is then 2^(E_i + E'_c - 46) times that integer.
 //
 // A CTA walks its chunk of rows in tiles of 128 (M = 128, one row per TMEM
-// lane).  Per K-chunk the 512 threads load 128 x 32 solved values of Q (L2,
+// lane).  Per K-chunk the 256 threads load 128 x 32 solved values of Q (L2,
 // written by the CTA itself), split them into digits (K-major operand tiles),
 // copy R's precomputed digit tiles, and one thread issues 28 x 2 MMAs
-// (kind::f16, M=128, N=32, K=16) into seven 32-column accumulators; two stages
-// alternate.  The diagonal-block solve gives each row 4 adjacent lanes of a
-// warp (8 interleaved columns each) and broadcasts solved values by shuffles.
+// (kind::f16, M=128, N=32, K=16) into seven 32-column accumulators.  Two CTAs
+// share an SM (104 KB of shared memory and 256 TMEM columns each), so one's
+// binary64 diagonal solve overlaps the other's digit split and tensor-core
+// work.  The diagonal-block solve gives each row 2 adjacent lanes of a warp
+// (16 interleaved columns each) and broadcasts solved values by shuffles.
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,11 +33,11 @@
 namespace rq {
 namespace {
 
-constexpr int kTeThreads = 512;
+constexpr int kTeThreads = 256;
 constexpr int kTeM = 128;         // rows per tile
 constexpr int kTeB = 32;          // columns per block (= K per chunk = N of the MMA)
 constexpr int kTeWinChunks = 4;   // K-chunks per exact window (128 K-columns)
-constexpr int kTeStages = 2;
+constexpr int kTeStages = 1;      // one stage: the second CTA on the SM covers the waits
 constexpr int kTeTileA = kTeM * kEmuBK * 2;   // one digit tile of Q: 8 KB
 constexpr int kTeTileB = kTeB * kEmuBK * 2;   // one digit tile of R: 2 KB
 constexpr int kTeStageA = kEmuDigits * kTeTileA;
@@ -43,7 +45,7 @@ constexpr int kTeStageB = kEmuDigits * kTeTileB;
 constexpr int kTeStageBytes = kTeStageA + kTeStageB;
 constexpr int kTeCBytes = kTeM * kTeB * 8;    // binary64 block C_J
 constexpr int kTeTmemCols = 256;
-constexpr int kTeP = kTeThreads / kTeM;       // lanes per row in the diagonal solve
+constexpr int kTeP = kTeThreads / kTeM;       // lanes per row in the diagonal solve (2)
 constexpr int kTeCPT = kTeB / kTeP;           // columns per lane
 
 // R's digit tiles of (target block J, K-chunk kc), kc < J, stored densely.
@@ -85,7 +87,7 @@ __global__ void k_trsm_emu_prep(const double *__restrict__ RP, int ldr, int n,
     }
 }
 
-__global__ void __launch_bounds__(kTeThreads, 1)
+__global__ void __launch_bounds__(kTeThreads, 2)
     k_trsm_emu(const double *A, int64_t lda, int64_t m, int n, int n_pad, int64_t chunk,
                const double *__restrict__ RT, const double *__restrict__ rinv,
                const unsigned char *__restrict__ rdig, const int *__restrict__ rbits, double *Q,
@@ -112,13 +114,14 @@ __global__ void __launch_bounds__(kTeThreads, 1)
     const uint32_t smem_base = smem_u32(smem_raw);
     const int nblk = (n + kTeB - 1) / kTeB;
 
-    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows), columns 8 (warp / 4) .. +7
+    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows), columns 16 (warp / 4) .. +15
     const int lane_base = 32 * (warp & 3);
     const int cgrp = warp >> 2;
     const int drow = lane_base + lane;
-    // digit task: row tid % 128, K-columns 8 (tid / 128) .. +7 of the chunk
-    const int srow = tid % kTeM, skg = tid / kTeM;
-    // diagonal solve: row ti, lane p of 4, columns p + 4c
+    constexpr int kDrainCols = kTeB / (kTeThreads / kTeM);  // 16
+    // digit tasks: row task % 128, K-columns 8 (task / 128) .. +7 of the chunk
+    constexpr int kTasks = kTeM * (kEmuBK / 8) / kTeThreads;  // 2 per thread
+    // diagonal solve: row ti, lane p of 2, columns p + 2c
     const int p = tid % kTeP, ti = tid / kTeP;
     const int src0 = (tid & 31) - p;
 
@@ -130,25 +133,30 @@ __global__ void __launch_bounds__(kTeThreads, 1)
         __syncthreads();
         for (int J = 0; J < nblk; ++J) {
             const int j0 = kTeB * J;
-            long long acc[8];
+            long long acc[kDrainCols];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = 0;
+            for (int q = 0; q < kDrainCols; ++q) acc[q] = 0;
             // ---- C_J update: emulated Q_{<J} R_{<J,J} over K-chunks kc < J
             for (int kc = 0; kc < J; ++kc, ++kcount) {
                 const int sidx = kcount % kTeStages;
                 unsigned char *stage = smem_raw + sidx * kTeStageBytes;
-                // loads first: in flight while the ring slot's MMAs finish
-                double xv[8];
-                const int64_t row = r0 + srow;
+                // loads first: in flight while the stage's previous MMAs finish
+                double xv[kTasks][8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int col = kEmuBK * kc + 8 * skg + t;
-                    xv[t] = row < re ? __ldcg(Q + row + int64_t(col) * ldq) : 0.0;
+                for (int u = 0; u < kTasks; ++u) {
+                    const int task = tid + u * kTeThreads;
+                    const int64_t row = r0 + task % kTeM;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int col = kEmuBK * kc + 8 * (task / kTeM) + t;
+                        xv[u][t] = row < re ? __ldcg(Q + row + int64_t(col) * ldq) : 0.0;
+                    }
                 }
                 const uint4 *rsrc = reinterpret_cast<const uint4 *>(rdig + te_rtile(J, kc));
-                uint4 rv[2];
+                constexpr int kRv = (kTeStageB / 16 + kTeThreads - 1) / kTeThreads;  // 4
+                uint4 rv[kRv];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < kRv; ++u) {
                     const int idx = tid + u * kTeThreads;
                     rv[u] = idx < kTeStageB / 16 ? __ldg(rsrc + idx) : make_uint4(0, 0, 0, 0);
                 }
@@ -158,23 +166,28 @@ __global__ void __launch_bounds__(kTeThreads, 1)
                     abort_flag = 1;
                 __syncthreads();
                 if (abort_flag) break;
-                const int E = emu_exponent(rowbits[srow]);
-                uint32_t h[kEmuDigits][4];
 #pragma unroll
-                for (int t = 0; t < 8; t += 2) {
-                    int d0[kEmuDigits], d1[kEmuDigits];
-                    emu_digits(xv[t], E, d0);
-                    emu_digits(xv[t + 1], E, d1);
+                for (int u = 0; u < kTasks; ++u) {
+                    const int task = tid + u * kTeThreads;
+                    const int srow = task % kTeM, skg = task / kTeM;
+                    const int E = emu_exponent(rowbits[srow]);
+                    uint32_t h[kEmuDigits][4];
+#pragma unroll
+                    for (int t = 0; t < 8; t += 2) {
+                        int d0[kEmuDigits], d1[kEmuDigits];
+                        emu_digits(xv[u][t], E, d0);
+                        emu_digits(xv[u][t + 1], E, d1);
+#pragma unroll
+                        for (int s = 0; s < kEmuDigits; ++s)
+                            h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                    }
 #pragma unroll
                     for (int s = 0; s < kEmuDigits; ++s)
-                        h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                        *reinterpret_cast<uint4 *>(stage + s * kTeTileA + emu_off(srow, 8 * skg)) =
+                            make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
                 }
 #pragma unroll
-                for (int s = 0; s < kEmuDigits; ++s)
-                    *reinterpret_cast<uint4 *>(stage + s * kTeTileA + emu_off(srow, 8 * skg)) =
-                        make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < kRv; ++u) {
                     const int idx = tid + u * kTeThreads;
                     if (idx < kTeStageB / 16)
                         reinterpret_cast<uint4 *>(stage + kTeStageA)[idx] = rv[u];
@@ -212,20 +225,21 @@ __global__ void __launch_bounds__(kTeThreads, 1)
                     if (abort_flag) break;
                     tc_fence_after();
                     const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
-                                        static_cast<uint32_t>(8 * cgrp);
-                    float v[8], w[8];
-                    tmem_ld8(tl + static_cast<uint32_t>(6 * kTeB), w);
-                    tmem_ld8(tl + static_cast<uint32_t>(5 * kTeB), v);
+                                        static_cast<uint32_t>(kDrainCols * cgrp);
+                    float v[kDrainCols], w[kDrainCols];
+                    tmem_ld16(tl + static_cast<uint32_t>(6 * kTeB), w);
+                    tmem_ld16(tl + static_cast<uint32_t>(5 * kTeB), v);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
-                    tmem_ld8(tl + static_cast<uint32_t>(4 * kTeB), v);
+                    for (int q = 0; q < kDrainCols; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
+                    tmem_ld16(tl + static_cast<uint32_t>(4 * kTeB), v);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
+                    for (int q = 0; q < kDrainCols; ++q)
+                        acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
 #pragma unroll
                     for (int L = 0; L < 4; ++L) {
-                        tmem_ld8(tl + static_cast<uint32_t>(L * kTeB), v);
+                        tmem_ld16(tl + static_cast<uint32_t>(L * kTeB), v);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
+                        for (int q = 0; q < kDrainCols; ++q)
                             acc[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << (32 - 8 * L));
                     }
                     tc_fence_before();
@@ -238,8 +252,8 @@ __global__ void __launch_bounds__(kTeThreads, 1)
                 const int64_t row = r0 + drow;
                 const int rbit = rowbits[drow];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int c = 8 * cgrp + q, col = j0 + c;
+                for (int q = 0; q < kDrainCols; ++q) {
+                    const int c = kDrainCols * cgrp + q, col = j0 + c;
                     double a = (row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
                     if (J > 0 && col < n) {
                         const int cbit = __ldg(rbits + J * kTeB + c);
@@ -324,7 +338,7 @@ cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, cons
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = ceil_div(m, kTeM);
-    const int64_t grid = std::min<int64_t>(tiles, num_sms());
+    const int64_t grid = std::min<int64_t>(tiles, int64_t(2) * num_sms());
     const int64_t chunk = ceil_div(tiles, grid) * kTeM;
     const int g = static_cast<int>(ceil_div(m, chunk));
     const size_t smem = size_t(kTeStages) * kTeStageBytes + kTeCBytes;
