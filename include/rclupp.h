@@ -258,12 +258,12 @@ rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const 
 /* G = A^T A (n x n, both triangles) as binary64-emulating products on the
  * tensor cores: the Gram product of the CholeskyQR pass (Algorithm 1 step 1,
  * C1) in the precision form RCLUPP_PREC_EMULATED.  Each element is written as
- * a_ij = 2^(E_j - 7) sum_{s=0..6} d_s 2^(-8s) with integer digits |d_s| <= 128
+ * a_ij = 2^(E_j - 7) sum_{s=0..7} d_s 2^(-8s) with integer digits |d_s| <= 128
  * (E_j: 2^E_j exceeds every |a_ij| of column j; round to nearest, half away
- * from zero, at 2^(E_j - 55)); G sums the digit products of levels
- * s + t <= 6 exactly in fp32 over 128-row windows, then in int64 and binary64.
- * Error: at most about (m + 1) 2^-53 2^(E_j + E_k) beyond the rounding of the
- * digits, i.e. binary64-like relative to the columns' largest entries.
+ * from zero, at 2^(E_j - 63)); G sums the digit products of levels
+ * s + t <= 7 exactly in fp32 over 128-row windows, then in int64 and binary64.
+ * Error: about m 2^-60 2^(E_j + E_k) from the split plus binary64 sums, i.e.
+ * at or below binary64's, relative to the columns' largest entries.
  * NaN in G(j, k) when column j or k holds a non-finite value.  n <= 256. */
 rclupp_status_t rclupp_gram_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                                      int64_t lda, double *G, int64_t ldg);
@@ -273,9 +273,9 @@ rclupp_status_t rclupp_gram_emulated(rclupp_handle_t handle, int64_t m, int64_t 
  * RCLUPP_PREC_EMULATED.  Substitution by 32-column blocks: the update
  * A_J - Q_{<J} R_{<J,J} uses the digits of rclupp_gram_emulated (one exponent
  * per row of Q over its first 32J columns, one per column of R over rows
- * < 32J; levels <= 6 summed exactly in fp32 over at most 128 K-columns, then
+ * < 32J; levels <= 7 summed exactly in fp32 over at most 128 K-columns, then
  * in int64), the 32 x 32 diagonal blocks are solved in binary64.  Error of
- * an update entry: about (j0 + 128) 2^-53 2^(E_i + E'_c).  R: n x n upper,
+ * an update entry: about (j0 + 128) 2^-60 2^(E_i + E'_c).  R: n x n upper,
  * nonzero diagonal.  Q may alias A.  n <= 256. */
 rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                                      int64_t lda, const double *R, int64_t ldr, double *Q,

@@ -94,6 +94,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // 2-D tiled TMA load global -> shared, completion signalled on `bar`.
 // c0 = innermost (row) coordinate, c1 = column coordinate.
+// Plain bulk copy global -> shared (both 16-byte aligned, bytes a multiple of
+// 16), completing on an mbarrier that expects the bytes.
+__device__ __forceinline__ void bulk_load(void *smem_dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, uint64_t *bar,
                                             int32_t c0, int32_t c1) {
     asm volatile(

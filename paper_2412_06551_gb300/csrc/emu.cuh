@@ -1,10 +1,12 @@
 // Digits of the binary64-emulating tensor-core products (split-bf16 with
 // exact fp32 sums): an element x of a row or column with exponent E
-// (2^E > every |x| of it) becomes F = round(x 2^(55 - E)) (half away from
-// zero), written in seven balanced base-256 digits d_0..d_6, |d_s| <= 128,
-// so that x = 2^(E - 7) sum_s d_s 2^(-8s) up to 2^(E - 56).  Every digit is
-// an exact bf16 and every product of two digits an integer of magnitude
-// <= 2^14.  Operand tiles are K-major 8 x 8 bf16 core matrices of 32 K-columns.
+// (2^E above every |x| of it) becomes F = round(x 2^(63 - E)) (half away
+// from zero), written in eight balanced base-256 digits d_0..d_7,
+// |d_s| <= 128, so that x = 2^(E - 7) sum_s d_s 2^(-8s) up to 2^(E - 64).
+// Every digit is an exact bf16 and every product of two digits an integer of
+// magnitude <= 2^14.  Operand tiles are K-major 8 x 8 bf16 core matrices of
+// 32 K-columns.  Products keep the levels s + t <= 7 (36 digit pairs); the
+// dropped ones are below 2^-61 of the scale.
 #pragma once
 
 #include <cstdint>
@@ -13,7 +15,7 @@
 
 namespace rq {
 
-constexpr int kEmuDigits = 7;
+constexpr int kEmuDigits = 8;
 constexpr int kEmuBK = 32;  // K-columns of one operand tile
 
 // Byte offset of element (row, k) of a K-major operand tile of kEmuBK
@@ -23,7 +25,7 @@ __device__ __forceinline__ uint32_t emu_off(int row, int k) {
                                  (k & 7) * 2);
 }
 
-// Balanced base-256 digits of F = round(x 2^(55 - E)), for |x| < 2^E: the
+// Balanced base-256 digits of F = round(x 2^(63 - E)), for |x| < 2^E: the
 // digits of |F| (bytes with a carry into the next one when a byte is >= 128),
 // negated for negative x.  Every digit lies in [-128, 128].
 __device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
@@ -31,13 +33,13 @@ __device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]
     const int e = static_cast<int>((b >> 52) & 0x7ff);
     unsigned long long M = b & 0xFFFFFFFFFFFFFull;
     if (e != 0) M |= 1ull << 52;
-    // |F| = M 2^sh; sh <= 2 for normal x as |x| < 2^E, 3 for subnormals of a
-    // column whose largest exponent is subnormal
-    const int sh = (e != 0 ? e : 1) - 1020 - E;
+    // |F| = M 2^sh; sh <= 10 for normal x as |x| < 2^E, 11 for subnormals of a
+    // column whose largest exponent is subnormal; |F| < 2^63
+    const int sh = (e != 0 ? e : 1) - 1012 - E;
     unsigned long long F;
     if (sh >= 0)
-        F = M << (sh & 3);
-    else if (sh > -55)
+        F = M << (sh & 15);
+    else if (sh > -64)
         F = (M + (1ull << (-sh - 1))) >> (-sh);
     else
         F = 0ull;
@@ -45,14 +47,14 @@ __device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]
     const int neg = static_cast<int>(b >> 63);
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < kEmuDigits - 1; ++q) {
         const uint32_t byte = ((q < 4 ? lo : hi) >> (8 * (q & 3))) & 0xffu;
         const uint32_t u = byte + c + 128u;
         const int dq = static_cast<int>(u & 0xffu) - 128;
         c = u >> 8;
         d[kEmuDigits - 1 - q] = neg ? -dq : dq;
     }
-    const int top = static_cast<int>((hi >> 16) + c);
+    const int top = static_cast<int>((hi >> 24) + c);
     d[0] = neg ? -top : top;
 }
 
@@ -66,5 +68,17 @@ __device__ __forceinline__ uint32_t small_int_bf16(int d) {
 // Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
 __device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
 
+// A level sum C (an exact integer in fp32, |C| <= 2^24) times 2^k as an
+// integer: exact for k >= 0, rounded (half up) for k < 0.  A window's levels
+// L = 0..7 enter one int64 accumulator with k = 24 - 8L + u, i.e. in units of
+// 2^-(24 + u) of level 0.
+template <int k>
+__device__ __forceinline__ long long emu_level(float c) {
+    const long long v = __float2int_rn(c);
+    if constexpr (k >= 0)
+        return v * (1ll << k);
+    else
+        return (v + (1ll << (-k - 1))) >> (-k);
+}
 
 }  // namespace rq

@@ -2,32 +2,27 @@
 // precision form of the CholeskyQR pass: Gram as split-bf16 products with
 // fp32 accumulation, Algorithm 1 step 1 / C1).
 //
-// Splitting (per column j of A, exponent E_j with |a_ij| < 2^E_j over all
-// rows): F_ij = round(a_ij 2^(55 - E_j)) (half away from zero), an integer
-// with |F| < 2^55, written in seven balanced base-256 digits
-//   F = sum_{s=0..6} d_s 256^(6-s),  |d_s| <= 128,
-// so a_ij = 2^(E_j - 7) sum_s d_s 2^(-8s) up to 2^(E_j - 56).  Every digit is
-// an exact bf16 and every digit product an integer of magnitude <= 2^14.
-// Level L = s + t collects the products d_s(i, j) d_t(i, k); levels 0..6 are
-// kept (28 products), deeper ones are below 2^-53 of the column scales.
+// Splitting (emu.cuh): per column j of A, with 2^E_j above every |a_ij|,
+// a_ij = 2^(E_j - 7) sum_{s=0..7} d_s 2^(-8s) up to 2^(E_j - 64), |d_s| <= 128.
+// Level L = s + t collects the products d_s(i, j) d_t(i, k); levels 0..7 are
+// kept (36 digit pairs).
 //
-// Exactness: over a window of 128 rows a level's sum has at most 7 x 128
-// products of magnitude <= 2^14, so it stays below 2^24 and the tensor
+// Exactness: over a window of 128 rows a level's sum has at most 8 x 128
+// products of magnitude <= 2^14, so it stays within 2^24 and the tensor
 // core's fp32 accumulation of these integers is exact.  After each window
-// the seven fp32 accumulators are drained into one int64 per element, in
-// units of 2^-32 of level 0: C0 2^32 + C1 2^24 + C2 2^16 + C3 2^8 exactly,
-// plus C4 + 2^-8 C5 + 2^-16 C6 formed in fp32 and rounded to an integer
-// (an error of at most 1.5 units, 2^-46 of a window's level-0 scale).  Every
-// 512 windows, and at the end, the int64 (|sum| < 2^62) is added to the
-// CTA's binary64 partial in global memory.  The partials are reduced in a
-// fixed order and scaled by 2^(E_j + E_k - 46).
+// the eight fp32 accumulators are drained into one int64 per element in
+// units of 2^-36 of level 0 (levels 0..4 exactly, 5..7 rounded: at most 1.5
+// units, 2^-50 of a window's scale).  Every 16 windows, and at the end, the
+// int64 (|sum| < 2^62) is added to the CTA's binary64 partial in global
+// memory.  The partials are reduced in a fixed order and scaled by
+// 2^(E_j + E_k - 50).
 //
 // Tiles: a CTA owns 128 rows (columns j of A) x 64 columns (k of A) of G and
-// a contiguous chunk of rows of A (split-K).  Its seven 128 x 64 fp32
-// accumulators take 448 of the 512 TMEM columns.  Per 32 rows of A the 256
-// threads split the block into digits (K-major 8 x 8 bf16 core matrices in
-// shared memory), one thread issues the 28 x 2 MMAs (kind::f16, M=128, N=64,
-// K=16) and commits to the stage's mbarrier; two stages alternate.
+// a contiguous chunk of rows of A (split-K).  Its eight 128 x 64 fp32
+// accumulators take the 512 TMEM columns.  Per 32 rows of A the 512 threads
+// split the block into digits (K-major 8 x 8 bf16 core matrices in shared
+// memory), one thread issues the 36 x 2 MMAs (kind::f16, M=128, N=64, K=16)
+// and commits to the stage's mbarrier; stages rotate.
 #include <algorithm>
 #include <climits>
 
@@ -49,7 +44,8 @@ constexpr int kTileB = kEmuN * kEmuBK * 2;  // ... of the k columns
 constexpr int kEmuStageBytes = kEmuDigits * (kTileA + kTileB);
 constexpr int kEmuTmemCols = 512;
 constexpr int kEmuSlot = kEmuM * kEmuN;  // elements of one per-CTA partial
-constexpr int kEmuFlushWindows = 512;    // int64 drains between binary64 flushes
+constexpr int kEmuFlushWindows = 16;     // int64 drains between binary64 flushes
+constexpr int kEmuUnit = 12;             // drain units: 2^-(24 + 12) of level 0
 constexpr int kEmuTaskSlots = 2;         // digit tasks per thread and stage (A: 1, B: 1 more)
 
 // Tile t of the upper triangle of G: rows [128 jb, +128), columns [64 kb, +64),
@@ -184,7 +180,9 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             const bool isA = c < kEmuM;
             const int cc = isA ? c : c - kEmuM;
             const int E = isA ? expA[cc] : expB[cc];
-            uint32_t h[kEmuDigits][4];
+            unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
+            const int tbytes = isA ? kTileA : kTileB;
+            // two rows at a time: one 32-bit word (two bf16) per digit
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
                 int d0[kEmuDigits], d1[kEmuDigits];
@@ -192,14 +190,9 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
                 emu_digits(xv[ts][t + 1], E, d1);
 #pragma unroll
                 for (int s = 0; s < kEmuDigits; ++s)
-                    h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                    *reinterpret_cast<uint32_t *>(base + s * tbytes + emu_off(cc, kb * 8 + t)) =
+                        small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
             }
-            unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
-            const int tbytes = isA ? kTileA : kTileB;
-#pragma unroll
-            for (int s = 0; s < kEmuDigits; ++s)
-                *reinterpret_cast<uint4 *>(base + s * tbytes + emu_off(cc, kb * 8)) =
-                    make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
         }
         fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
         __syncthreads();
@@ -236,20 +229,23 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             tc_fence_after();
             const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
                                 static_cast<uint32_t>(16 * cgrp);
-            float v[16], w[16];
-            tmem_ld16(tl + static_cast<uint32_t>(6 * kEmuN), w);
-            tmem_ld16(tl + static_cast<uint32_t>(5 * kEmuN), v);
+            float v[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
-            tmem_ld16(tl + static_cast<uint32_t>(4 * kEmuN), v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
-#pragma unroll
-            for (int L = 0; L < 4; ++L) {
+            for (int L = 0; L < kEmuDigits; ++L) {
                 tmem_ld16(tl + static_cast<uint32_t>(L * kEmuN), v);
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    acc[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << (32 - 8 * L));
+                for (int q = 0; q < 16; ++q) {
+                    switch (L) {  // compile-time after unrolling
+                        case 0: acc[q] += emu_level<24 + kEmuUnit>(v[q]); break;
+                        case 1: acc[q] += emu_level<16 + kEmuUnit>(v[q]); break;
+                        case 2: acc[q] += emu_level<8 + kEmuUnit>(v[q]); break;
+                        case 3: acc[q] += emu_level<0 + kEmuUnit>(v[q]); break;
+                        case 4: acc[q] += emu_level<-8 + kEmuUnit>(v[q]); break;
+                        case 5: acc[q] += emu_level<-16 + kEmuUnit>(v[q]); break;
+                        case 6: acc[q] += emu_level<-24 + kEmuUnit>(v[q]); break;
+                        default: acc[q] += emu_level<-32 + kEmuUnit>(v[q]); break;
+                    }
+                }
             }
             if (++windows == kEmuFlushWindows) {
                 flush();
@@ -269,7 +265,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     if (warp == 0) tmem_dealloc(tmem, kEmuTmemCols);
 }
 
-// G[j][k] = G[k][j] = 2^(E_j + E_k - 46) times the sum over the tile's CTAs
+// G[j][k] = G[k][j] = 2^(E_j + E_k - 50) times the sum over the tile's CTAs
 // (in order) of their binary64 partials; NaN where a column holds a
 // non-finite value.
 __global__ void k_reduce_gram_emu(const double *__restrict__ part, int nsplit, int n,
@@ -291,7 +287,7 @@ __global__ void k_reduce_gram_emu(const double *__restrict__ part, int nsplit, i
     if (bj == 0x7ff || bk == 0x7ff)
         g = __longlong_as_double(0x7ff8000000000000ll);
     else
-        g = ldexp(s, emu_exponent(bj) + emu_exponent(bk) - 46);
+        g = ldexp(s, emu_exponent(bj) + emu_exponent(bk) - 14 - 24 - kEmuUnit);
     G[j + int64_t(k) * ldg] = g;
     G[k + int64_t(j) * ldg] = g;
 }

@@ -9,17 +9,18 @@
 // Q_{<J}'s digits use one exponent per row over its first 32J columns (from a
 // running maximum of the row's solved exponents), R's one per column over
 // rows < 32J (precomputed by k_trsm_emu_prep).  Digits are those of the
-// emulated Gram (emu.cuh); levels s + t <= 6 are kept; a level's fp32 sum over
-// at most 128 K-columns (7 x 128 products <= 2^14) is exact, so the TMEM
-// accumulators are drained into one int64 per element after every 4 K-chunks
-// of 32.  The update is then 2^(E_i + E'_c - 46) times that integer.
+// emulated Gram (emu.cuh); levels s + t <= 7 are kept; a level's fp32 sum over
+// at most 128 K-columns (8 x 128 products <= 2^14) is exact, so the TMEM
+// accumulators are drained into one int64 per element (units of 2^-40 of
+// level 0, levels 6 and 7 rounded to that unit) after every 4 K-chunks of 32.
+// The update is then 2^(E_i + E'_c - 54) times that integer.
 //
 // A CTA walks its chunk of rows in tiles of 128 (M = 128, one row per TMEM
 // lane).  Per K-chunk the 256 threads load 128 x 32 solved values of Q (L2,
 // written by the CTA itself), split them into digits (K-major operand tiles),
-// copy R's precomputed digit tiles, and one thread issues 28 x 2 MMAs
-// (kind::f16, M=128, N=32, K=16) into seven 32-column accumulators.  Two CTAs
-// share an SM (104 KB of shared memory and 256 TMEM columns each), so one's
+// copy R's precomputed digit tiles, and one thread issues 36 x 2 MMAs
+// (kind::f16, M=128, N=32, K=16) into eight 32-column accumulators.  Two CTAs
+// share an SM (80 KB of shared memory and 256 TMEM columns each), so one's
 // binary64 diagonal solve overlaps the other's digit split and tensor-core
 // work.  The diagonal-block solve gives each row 2 adjacent lanes of a warp
 // (16 interleaved columns each) and broadcasts solved values by shuffles.
@@ -43,7 +44,9 @@ constexpr int kTeTileB = kTeB * kEmuBK * 2;   // one digit tile of R: 2 KB
 constexpr int kTeStageA = kEmuDigits * kTeTileA;
 constexpr int kTeStageB = kEmuDigits * kTeTileB;
 constexpr int kTeStageBytes = kTeStageA + kTeStageB;
-constexpr int kTeCBytes = kTeM * kTeB * 8;    // binary64 block C_J
+constexpr int kTeCBytes = kTeM * kTeB * 8;    // binary64 block C_J (in the stage's Q digits)
+constexpr int kTeUnit = 16;                   // drain units: 2^-(24 + 16) of level 0
+static_assert(kTeCBytes <= kTeStageA, "C_J reuses the digit tiles of Q");
 constexpr int kTeTmemCols = 256;
 constexpr int kTeP = kTeThreads / kTeM;       // lanes per row in the diagonal solve (2)
 constexpr int kTeCPT = kTeB / kTeP;           // columns per lane
@@ -94,15 +97,19 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                int64_t ldq, DevStatus *st) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_mma[kTeStages];
+    __shared__ __align__(8) uint64_t bar_r;  // bulk copy of R's digit tiles
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int rowbits[kTeM];
-    double *Cb = reinterpret_cast<double *>(smem_raw + kTeStages * kTeStageBytes);  // [col][row]
+    // C_J [col][row] reuses the Q digit tiles: it is written only after the
+    // block's last MMAs completed and read before the next block's split
+    double *Cb = reinterpret_cast<double *>(smem_raw);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tmem_alloc(&tmem_slot, kTeTmemCols);
     if (tid == 0) {
         for (int s = 0; s < kTeStages; ++s) mbar_init(&bar_mma[s], 1);
+        mbar_init(&bar_r, 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -152,26 +159,23 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                         xv[u][t] = row < re ? __ldcg(Q + row + int64_t(col) * ldq) : 0.0;
                     }
                 }
-                const uint4 *rsrc = reinterpret_cast<const uint4 *>(rdig + te_rtile(J, kc));
-                constexpr int kRv = (kTeStageB / 16 + kTeThreads - 1) / kTeThreads;  // 4
-                uint4 rv[kRv];
-#pragma unroll
-                for (int u = 0; u < kRv; ++u) {
-                    const int idx = tid + u * kTeThreads;
-                    rv[u] = idx < kTeStageB / 16 ? __ldg(rsrc + idx) : make_uint4(0, 0, 0, 0);
-                }
                 if (kcount >= kTeStages &&
                     !mbar_wait_bounded(&bar_mma[sidx],
                                        static_cast<uint32_t>((kcount / kTeStages - 1) & 1)))
                     abort_flag = 1;
                 __syncthreads();
                 if (abort_flag) break;
+                if (tid == 0) {  // R's digit tiles of (J, kc), one bulk copy
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bar_r, kTeStageB);
+                    bulk_load(stage + kTeStageA, rdig + te_rtile(J, kc), kTeStageB, &bar_r);
+                }
 #pragma unroll
                 for (int u = 0; u < kTasks; ++u) {
                     const int task = tid + u * kTeThreads;
                     const int srow = task % kTeM, skg = task / kTeM;
                     const int E = emu_exponent(rowbits[srow]);
-                    uint32_t h[kEmuDigits][4];
+                    // two rows at a time: one 32-bit word (two bf16) per digit
 #pragma unroll
                     for (int t = 0; t < 8; t += 2) {
                         int d0[kEmuDigits], d1[kEmuDigits];
@@ -179,28 +183,22 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                         emu_digits(xv[u][t + 1], E, d1);
 #pragma unroll
                         for (int s = 0; s < kEmuDigits; ++s)
-                            h[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                            *reinterpret_cast<uint32_t *>(stage + s * kTeTileA +
+                                                          emu_off(srow, 8 * skg + t)) =
+                                small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
                     }
-#pragma unroll
-                    for (int s = 0; s < kEmuDigits; ++s)
-                        *reinterpret_cast<uint4 *>(stage + s * kTeTileA + emu_off(srow, 8 * skg)) =
-                            make_uint4(h[s][0], h[s][1], h[s][2], h[s][3]);
-                }
-#pragma unroll
-                for (int u = 0; u < kRv; ++u) {
-                    const int idx = tid + u * kTeThreads;
-                    if (idx < kTeStageB / 16)
-                        reinterpret_cast<uint4 *>(stage + kTeStageA)[idx] = rv[u];
                 }
                 fence_proxy_async_smem();
                 __syncthreads();
                 if (tid == 0) {
+                    const bool have_r = mbar_wait_bounded(&bar_r, kcount & 1u);
+                    if (!have_r) abort_flag = 1;
                     tc_fence_after();
                     const uint32_t sa = smem_base + sidx * kTeStageBytes;
                     const uint32_t sb = sa + kTeStageA;
                     const bool fresh = (kc % kTeWinChunks) == 0;
 #pragma unroll 1
-                    for (int L = 0; L < kEmuDigits; ++L) {
+                    for (int L = 0; L < (have_r ? kEmuDigits : 0); ++L) {
 #pragma unroll 1
                         for (int s = 0; s <= L; ++s) {
                             const int t = L - s;
@@ -226,21 +224,23 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                     tc_fence_after();
                     const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
                                         static_cast<uint32_t>(kDrainCols * cgrp);
-                    float v[kDrainCols], w[kDrainCols];
-                    tmem_ld16(tl + static_cast<uint32_t>(6 * kTeB), w);
-                    tmem_ld16(tl + static_cast<uint32_t>(5 * kTeB), v);
+                    float v[kDrainCols];
 #pragma unroll
-                    for (int q = 0; q < kDrainCols; ++q) w[q] = fmaf(w[q], 0x1p-8f, v[q]);
-                    tmem_ld16(tl + static_cast<uint32_t>(4 * kTeB), v);
-#pragma unroll
-                    for (int q = 0; q < kDrainCols; ++q)
-                        acc[q] += __float2int_rn(fmaf(w[q], 0x1p-8f, v[q]));
-#pragma unroll
-                    for (int L = 0; L < 4; ++L) {
+                    for (int L = 0; L < kEmuDigits; ++L) {
                         tmem_ld16(tl + static_cast<uint32_t>(L * kTeB), v);
 #pragma unroll
-                        for (int q = 0; q < kDrainCols; ++q)
-                            acc[q] += static_cast<long long>(__float2int_rn(v[q])) * (1ll << (32 - 8 * L));
+                        for (int q = 0; q < kDrainCols; ++q) {
+                            switch (L) {  // compile-time after unrolling
+                                case 0: acc[q] += emu_level<24 + kTeUnit>(v[q]); break;
+                                case 1: acc[q] += emu_level<16 + kTeUnit>(v[q]); break;
+                                case 2: acc[q] += emu_level<8 + kTeUnit>(v[q]); break;
+                                case 3: acc[q] += emu_level<0 + kTeUnit>(v[q]); break;
+                                case 4: acc[q] += emu_level<-8 + kTeUnit>(v[q]); break;
+                                case 5: acc[q] += emu_level<-16 + kTeUnit>(v[q]); break;
+                                case 6: acc[q] += emu_level<-24 + kTeUnit>(v[q]); break;
+                                default: acc[q] += emu_level<-32 + kTeUnit>(v[q]); break;
+                            }
+                        }
                     }
                     tc_fence_before();
                     __syncthreads();
@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                         const double u = (rbit == 0x7ff || cbit == 0x7ff)
                                              ? __longlong_as_double(0x7ff8000000000000ll)
                                              : ldexp(static_cast<double>(acc[q]),
-                                                     emu_exponent(rbit) + emu_exponent(cbit) - 46);
+                                                     emu_exponent(rbit) + emu_exponent(cbit) - 14 -
+                                                         24 - kTeUnit);
                         a -= u;
                     }
                     Cb[c * kTeM + drow] = a;
@@ -341,7 +342,7 @@ cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, cons
     const int64_t grid = std::min<int64_t>(tiles, int64_t(2) * num_sms());
     const int64_t chunk = ceil_div(tiles, grid) * kTeM;
     const int g = static_cast<int>(ceil_div(m, chunk));
-    const size_t smem = size_t(kTeStages) * kTeStageBytes + kTeCBytes;
+    const size_t smem = size_t(kTeStages) * kTeStageBytes;
     cudaFuncSetAttribute(k_trsm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     RQ_LAUNCH(KID_TRSM_EMU, stream,
               k_trsm_emu<<<g, kTeThreads, smem, stream>>>(A, lda, m, n, n_pad, chunk,

@@ -2,13 +2,14 @@
 sums) and the RCLUPP_PREC_EMULATED tier of the drivers, against the oracle.
 
 Error model of the emulated Gram G = A^T A.  With E_j the column exponent
-(2^E_j > max_i |a_ij|), the digit split rounds a_ij at 2^(E_j - 56) and the
-product keeps the levels s + t <= 6 of the 7 x 7 digit products; both
-perturb G(j, k) by at most about (m + 1) 2^-53 2^(E_j + E_k).  The fp32
-window sums are exact and the binary64 combination adds at most
-(m / 128 + 2) u |A|^T |A|.  The tests bound the distance to the exact Gram
-(Python integers on integer-scaled inputs) or to the binary64 oracle (whose
-own error is gamma_m |A|^T |A|).
+(2^E_j > max_i |a_ij|), the digit split rounds a_ij at 2^(E_j - 64) and the
+product keeps the levels s + t <= 7 of the 8 x 8 digit products; both
+perturb G(j, k) by far less than m 2^-53 2^(E_j + E_k).  The fp32 window
+sums are exact, the int64 drain rounds levels 5..7 (2^-50 of a window's
+scale) and the binary64 combination adds at most (m / 128 + 2) u |A|^T |A|.
+The tests bound the distance to the exact Gram (Python integers on
+integer-scaled inputs) or to the binary64 oracle (whose own error is
+gamma_m |A|^T |A|) with the binary64-like bound 4 (m + 128) u 2^(E_j + E_k).
 """
 import math
 
@@ -69,9 +70,10 @@ def test_exact_on_small_integers(rq):
 
 
 def test_all_digits_against_exact_integers(rq):
-    # x = k 2^-40 with |k| < 2^47: the 56-bit scaled value k 2^8 is exact, so
-    # all seven digits are used and the only error is the dropped levels and
-    # the binary64 combination; the exact Gram comes from Python integers
+    # x = k 2^-40 with |k| < 2^47: the scaled value k 2^(63 - E - 40) is an
+    # exact integer, so all digits are used and the only errors are the
+    # dropped levels and the drain and binary64 combination; the exact Gram
+    # comes from Python integers
     g = np.random.default_rng(2)
     for m, n in [(129, 5), (1000, 48), (3001, 130)]:
         k = g.integers(-(2 ** 46), 2 ** 46, size=(m, n), dtype=np.int64)
