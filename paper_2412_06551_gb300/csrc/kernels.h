@@ -65,6 +65,21 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
 cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
                                  double *Y, int64_t ldy, cudaStream_t stream);
 
+// ---- small factorizations in one thread block cluster (small_cluster.cu) ----
+// The s x n (n x n) matrix split by rows over 1..8 CTAs' shared memory.
+// mode 0: R1 = R(HouseholderQR(M)) N from the LU P Y = M N (Nbuf: n x n
+// scratch); mode 1: R1 = R(HouseholderQR(Y)) triu(Nsrc) (identity when
+// Nsrc == nullptr).  Outputs as launch_sketch_precond / launch_cholesky.
+bool precond_cluster_fits(int s, int n);
+cudaError_t launch_precond_cluster(const double *Y, int64_t ldy, int s, int n, int mode,
+                                   const double *Nsrc, int64_t ldn, double *Nbuf, double *RP,
+                                   double *rinv, double *R1, int64_t ldr, DevStatus *st, int step,
+                                   cudaStream_t stream);
+bool cholesky_cluster_fits(int n);
+cudaError_t launch_cholesky_cluster(const double *G, int64_t ldg, int n, double *RP, double *rinv,
+                                    double *R, int64_t ldr, DevStatus *st, int step,
+                                    cudaStream_t stream);
+
 // ---- tensor-core sketch (tc_sketch.cu) ----
 // Y = S X with S's entries rounded to bf16 and X split into nterms (1 or 3)
 // bf16 terms, fp32 accumulation on tcgen05 (n <= 256).

@@ -3,11 +3,14 @@
 // eq. (elu)), the R-factor of a thin Householder QR (step 3, eq. (eh)), the
 // triangular products R1 = R0 N, R3 = R2 R1, R = R4 R3 (eq. (ey), C4, C8),
 // and the Cholesky factorizations of the Gram matrices (C2, C6) with a
-// breakdown status instead of NaNs.  One CTA each: these steps are O(s n^2)
-// against the O(m n^2) tall passes.  Working arrays live in the (L2-resident)
-// workspace.  Triangular factors are handed to the tall kernels in padded
-// form: n_pad x n_pad (n_pad = 16-multiple), ld n_pad, zeros outside the
-// upper triangle, plus the reciprocals of the diagonal.
+// breakdown status instead of NaNs.  This file holds the general one-CTA
+// form with the working arrays in the (L2-resident) workspace; when the
+// matrix fits the shared memory of a thread block cluster the launchers use
+// the cluster form of small_cluster.cu instead.  These steps are O(s n^2)
+// against the O(m n^2) tall passes.  Triangular factors are handed to the
+// tall kernels in padded form: n_pad x n_pad (n_pad = 16-multiple), ld
+// n_pad, zeros outside the upper triangle, followed by the row-major copy,
+// plus the reciprocals of the diagonal.
 #include <algorithm>
 
 #include "common.cuh"
@@ -115,11 +118,18 @@ __device__ void small_householder(double *H, int rows, int n, double *wv, double
         }
         const double sigma = block_sum(part, red);
         if (sigma == 0.0) continue;  // uniform: every thread read the same sum
-        const double alpha = H[k + int64_t(k) * rows];
-        const double norm = sqrt(alpha * alpha + sigma);
-        const double beta = alpha >= 0.0 ? -norm : norm;
-        const double tau = (beta - alpha) / beta;
-        const double scal = 1.0 / (alpha - beta);
+        // one thread forms the scalars (a square root and two divisions per
+        // thread would load the slow FP64 pipe 1024-fold)
+        if (threadIdx.x == 0) {
+            const double alpha = H[k + int64_t(k) * rows];
+            const double norm = sqrt(alpha * alpha + sigma);
+            const double beta = alpha >= 0.0 ? -norm : norm;
+            red[33] = beta;
+            red[34] = (beta - alpha) / beta;
+            red[35] = 1.0 / (alpha - beta);
+        }
+        __syncthreads();
+        const double beta = red[33], tau = red[34], scal = red[35];
         for (int i = k + 1 + threadIdx.x; i < rows; i += blockDim.x)
             H[i + int64_t(k) * rows] *= scal;
         __syncthreads();
@@ -193,7 +203,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     k_small_precond(const double *__restrict__ Y, int64_t ldy, int s, int n, int mode,
                     const double *__restrict__ Nsrc, int64_t ldn, double *W, double *RP,
                     double *rinv, double *R1, int64_t ldr, DevStatus *st, int step) {
-    __shared__ double red[33];
+    __shared__ double red[36];
     __shared__ long long redi[33];
     __shared__ double wv[256];
     __shared__ int sgn[256];
@@ -228,6 +238,9 @@ __global__ void __launch_bounds__(kSmallThreads)
 cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, double *W,
                                   double *RP, double *rinv, double *R1, int64_t ldr,
                                   DevStatus *st, int step_id, cudaStream_t stream) {
+    if (precond_cluster_fits(s, n))  // the matrix fits a cluster's shared memory
+        return launch_precond_cluster(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1, ldr, st, step_id,
+                                      stream);
     RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_small_precond<<<1, kSmallThreads, 0, stream>>>(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1,
                                                      ldr, st, step_id));
     return cudaGetLastError();
@@ -236,6 +249,9 @@ cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, do
 cudaError_t launch_rcholqr_r1(const double *K, int64_t ldk, int s, int n, double *W, double *RP,
                               double *rinv, cudaStream_t stream) {
     // mode 1 with N = I: R1 = R-factor of HouseholderQR(K), signs normalised
+    if (precond_cluster_fits(s, n))
+        return launch_precond_cluster(K, ldk, s, n, 1, nullptr, 0, W, RP, rinv, nullptr, 0, nullptr, 0,
+                                      stream);
     RQ_LAUNCH(KID_SMALL_PRECOND, stream,
               k_small_precond<<<1, kSmallThreads, 0, stream>>>(K, ldk, s, n, 1, nullptr, 0, W, RP,
                                                                rinv, nullptr, 0, nullptr, 0));
@@ -275,6 +291,9 @@ cudaError_t launch_shifted_gram(const double *G, int64_t ldg, int n, int64_t m, 
 cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const double *LU,
                               int64_t lda, double *W, double *RP, double *rinv,
                               cudaStream_t stream) {
+    if (precond_cluster_fits(s, n))
+        return launch_precond_cluster(Ms, ldm, s, n, 1, LU, lda, W, RP, rinv, nullptr, 0, nullptr, 0,
+                                      stream);
     RQ_LAUNCH(KID_SMALL_PRECOND, stream, k_small_precond<<<1, kSmallThreads, 0, stream>>>(Ms, ldm, s, n, 1, LU, lda, W, RP, rinv,
                                                      nullptr, 0, nullptr, 0));
     return cudaGetLastError();
@@ -283,7 +302,7 @@ cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const
 __global__ void __launch_bounds__(kSmallThreads)
     k_householder_r(const double *__restrict__ A, int64_t lda, int s, int n, double *W, double *R,
                     int64_t ldr) {
-    __shared__ double red[33];
+    __shared__ double red[36];
     __shared__ double wv[256];
     for (int idx = threadIdx.x; idx < s * n; idx += blockDim.x) {
         const int i = idx % s, j = idx / s;
@@ -311,6 +330,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     k_cholesky(const double *__restrict__ G, int64_t ldg, int n, double *W, double *RP,
                double *rinv, double *R, int64_t ldr, DevStatus *st, int step) {
     __shared__ int fail;
+    __shared__ double rkk_sh;
     const int n_pad = pad16(n);
     if (threadIdx.x == 0) fail = 0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -325,8 +345,9 @@ __global__ void __launch_bounds__(kSmallThreads)
             fail = 1;
             break;
         }
-        const double rkk = sqrt(d);
+        if (threadIdx.x == 0) rkk_sh = sqrt(d);
         __syncthreads();
+        const double rkk = rkk_sh;
         for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
             W[k + int64_t(j) * n] = W[k + int64_t(j) * n] / rkk;
         if (threadIdx.x == 0) W[k + int64_t(k) * n] = rkk;
@@ -357,6 +378,8 @@ __global__ void __launch_bounds__(kSmallThreads)
 cudaError_t launch_cholesky(const double *G, int64_t ldg, int n, double *W, double *RP,
                             double *rinv, double *R, int64_t ldr, DevStatus *st, int step_id,
                             cudaStream_t stream) {
+    if (cholesky_cluster_fits(n))
+        return launch_cholesky_cluster(G, ldg, n, RP, rinv, R, ldr, st, step_id, stream);
     RQ_LAUNCH(KID_CHOLESKY, stream, k_cholesky<<<1, kSmallThreads, 0, stream>>>(G, ldg, n, W, RP, rinv, R, ldr, st, step_id));
     return cudaGetLastError();
 }
