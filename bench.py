@@ -75,11 +75,12 @@ def parse():
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "trsm_emu", "sketch_gauss",
                                       "sketch_sparse", "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
-    p.add_argument("--workload", choices=["side_by_side", "precision", "batched"],
+    p.add_argument("--workload", choices=["side_by_side", "precision", "batched", "small",
+                                          "large_sparse"],
                    default="side_by_side",
                    help="precision: FP64 vs tensor-core sketch RCLUPP at m=2^22, n=256, s=512; "
                         "batched: 512 uneven RCLUPP problems in one batched call")
-    p.add_argument("--prec", type=int, default=0, help="sketch tier for --case runs")
+    p.add_argument("--prec", type=int, default=0, help="precision tier for --case runs")
     p.add_argument("--m", type=int, default=1 << 18)
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--reps", type=int, default=3)
@@ -298,6 +299,79 @@ def run_precision(args):
     print(json.dumps({"workload": "RCLUPP FP64 vs tensor-core sketch (bf16 start, escalating) "
                                   "vs that sketch plus the binary64-emulating tensor-core Gram",
                       "m": m, "n": n, "s": s, "results": rows}), flush=True)
+
+
+def run_small(args):
+    """RCLUPP on the small single-matrix case m = 4096, n = 64, kappa = 1e8,
+    Gaussian s = 128: binary64 and the emulated tier against the oracle on
+    the same X and S (the oracle runs this size in full)."""
+    import torch
+    import oracle
+    import paper_2412_06551_gb300 as rq
+    m, n, s, kap = 4096, 64, 128, 1e8
+    seed = synth.kappa_seed(0, 0)
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    x = synth.svd_matrix(m, n, kap, seed)
+    X = to_dev(x, torch, device)
+    S = oracle.gaussian_sketch_matrix(s, m, seed + 7)
+    t0 = time.perf_counter()
+    q_o, r_o, _ = oracle.rclupp(x, S=S)
+    t_oracle = time.perf_counter() - t0
+    rows = {"oracle": {"ms": t_oracle * 1e3, "cores": oracle.num_threads(),
+                       "orth": oracle.orthogonality(q_o), "res": oracle.residual(x, q_o, r_o)}}
+    reps = max(20, 10 * args.steps)
+    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED)):
+        call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec)
+        for _ in range(3):
+            call()
+        ms, (Q, R, info) = time_call(torch, stream, call, reps)
+        o, r = accuracy(torch, X, Q, R)
+        rows[label] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "orth": o, "res": r,
+                       "prec_used": int(info.prec_used), "emulated": int(info.emulated)}
+    print(json.dumps({"workload": "RCLUPP, one matrix m=4096, n=64, kappa=1e8, Gaussian s=128 "
+                                  "(latency-bound: X is 2 MB, L2-resident)",
+                      "m": m, "n": n, "s": s, "kappa": kap, "seed_x": seed, "results": rows}), flush=True)
+
+
+def run_large_sparse(args):
+    """RCLUPPr with the sparse-sign sketch on m = 2^24, n = 64 (8.6 GB),
+    kappa = 1e15, s = 256, zeta = 8: binary64 and the emulated tier.  X is
+    built on the GPU by the same recipe as synth.svd_matrix (torch's QR of
+    seeded normal matrices), so the host needs no 8.6 GB copy."""
+    import torch
+    import paper_2412_06551_gb300 as rq
+    m, n, s, zeta, kap = 1 << 24, 64, 256, 8, 1e15
+    seed = synth.kappa_seed(4, 0)
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    gen = torch.Generator(device=device).manual_seed(seed)
+    U, _ = torch.linalg.qr(torch.randn(m, n, generator=gen, dtype=torch.float64, device=device))
+    V, _ = torch.linalg.qr(torch.randn(n, n, generator=gen, dtype=torch.float64, device=device))
+    sig = kap ** (-torch.arange(n, dtype=torch.float64, device=device) / (n - 1))
+    Xr = (U * sig) @ V.t()
+    del U
+    X = torch.empty((n, m), dtype=torch.float64, device=device).t()  # column-major
+    X.copy_(Xr)
+    del Xr
+    torch.cuda.empty_cache()
+    rows = {}
+    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED)):
+        call = lambda: rq.rclupp_r_factor(X, s=s, kind=rq.SKETCH_SPARSE_SIGN, zeta=zeta, seed=seed + 7,
+                                          prec=prec, check=False)
+        call()
+        ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
+        entry = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "status": int(info.status),
+                 "emulated": int(info.emulated)}
+        if info.status == 0:
+            o, r = accuracy(torch, X, Q, R)
+            entry.update({"orth": o, "res": r})
+        rows[label] = entry
+        del Q, R
+        torch.cuda.empty_cache()
+    rows["speedup_emulated"] = rows["fp64"]["ms"] / rows["emulated"]["ms"]
+    print(json.dumps({"workload": "RCLUPPr, sparse-sign sketch s=256 zeta=8, m=2^24, n=64, kappa=1e15 "
+                                  "(X generated on the GPU)", "m": m, "n": n, "results": rows}), flush=True)
 
 
 def batched_problems(count=512):
@@ -541,7 +615,7 @@ def run_case(args):
         elif args.case == "lu":
             rq.rclupp_tall_lupp(X)
         elif args.case == "rclupp":
-            rq.rclupp_factor(X, s=2 * n, seed=1)
+            rq.rclupp_factor(X, s=2 * n, seed=1, prec=args.prec)
 
     one()  # first call: workspace, tensor maps, module load
     torch.cuda.synchronize()
@@ -577,6 +651,10 @@ def main():
         run_precision(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "small":
+        run_small(args)
+    elif args.workload == "large_sparse":
+        run_large_sparse(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

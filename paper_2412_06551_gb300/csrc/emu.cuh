@@ -68,6 +68,13 @@ __device__ __forceinline__ uint32_t small_int_bf16(int d) {
 // Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
 __device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
 
+// v 2^e: one exact multiplication by a power of two built from its bits when
+// 2^e is a normal number, ldexp otherwise.
+__device__ __forceinline__ double emu_scale(double v, int e) {
+    if (e >= -1022 && e <= 1023) return v * __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+    return ldexp(v, e);
+}
+
 // A level sum C (an exact integer in fp32, |C| <= 2^24) times 2^k as an
 // integer: exact for k >= 0, rounded (half up) for k < 0.  A window's levels
 // L = 0..7 enter one int64 accumulator with k = 24 - 8L + u, i.e. in units of

@@ -197,3 +197,17 @@ def test_rcluppr_sparse_full_size(rq, big5):
     assert orth <= 1e-12 and res <= 1e-14
     r = host(R)
     assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+
+
+def test_rcluppr_sparse_full_size_emulated(rq, big5):
+    # the precision form on the same problem: binary64-emulating tensor-core
+    # solves and first Gram, binary64 sparse sketch
+    seed, x = big5
+    X = dev(x)
+    Q, R, info = rq.rclupp_r_factor(X, s=S5, kind=rq.SKETCH_SPARSE_SIGN, zeta=ZETA, seed=seed + 7,
+                                    prec=rq.PREC_EMULATED)
+    assert info.status == 0 and info.emulated == 1
+    orth, res = gpu_metrics(X, Q, R)
+    assert orth <= 6 * (M5 * N5 * U + N5 * (N5 + 1) * U)
+    assert orth <= 1e-12 and res <= 1e-14
+
