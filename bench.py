@@ -251,7 +251,8 @@ def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
     tier, escalating as needed) on the same X, against the FP64 paths."""
     m, n = X.shape
     out = {}
-    for tier, prec in (("", rq.PREC_SKETCH_BF16), ("_emulated", rq.PREC_EMULATED)):
+    for tier, prec in (("", rq.PREC_SKETCH_BF16), ("_emulated", rq.PREC_EMULATED),
+                       ("_emulated_all", rq.PREC_EMULATED_ALL)):
         for name, fn in (("rclupp", rq.rclupp_factor), ("rcluppr", rq.rclupp_r_factor)):
             call = lambda: fn(X, s=S_SKETCH, seed=SEED_S, prec=prec)
             call()
@@ -280,7 +281,7 @@ def run_precision(args):
         X = to_dev(synth.svd_matrix(m, n, kap, seed), torch, device)
         row = {}
         for label, prec in (("fp64", rq.PREC_FP64), ("mixed", rq.PREC_SKETCH_BF16),
-                            ("emulated", rq.PREC_EMULATED)):
+                            ("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
             call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec, check=False)
             call()
             ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
@@ -293,6 +294,7 @@ def run_precision(args):
             del Q, R
         row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
         row["speedup_emulated"] = row["fp64"]["ms"] / row["emulated"]["ms"]
+        row["speedup_emulated_all"] = row["fp64"]["ms"] / row["emulated_all"]["ms"]
         rows["%.0e" % kap] = row
         del X
         torch.cuda.empty_cache()
@@ -321,7 +323,8 @@ def run_small(args):
     rows = {"oracle": {"ms": t_oracle * 1e3, "cores": oracle.num_threads(),
                        "orth": oracle.orthogonality(q_o), "res": oracle.residual(x, q_o, r_o)}}
     reps = max(20, 10 * args.steps)
-    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED)):
+    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED),
+                        ("emulated_all", rq.PREC_EMULATED_ALL)):
         call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec)
         for _ in range(3):
             call()
@@ -356,7 +359,8 @@ def run_large_sparse(args):
     del Xr
     torch.cuda.empty_cache()
     rows = {}
-    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED)):
+    for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED),
+                        ("emulated_all", rq.PREC_EMULATED_ALL)):
         call = lambda: rq.rclupp_r_factor(X, s=s, kind=rq.SKETCH_SPARSE_SIGN, zeta=zeta, seed=seed + 7,
                                           prec=prec, check=False)
         call()
@@ -370,6 +374,7 @@ def run_large_sparse(args):
         del Q, R
         torch.cuda.empty_cache()
     rows["speedup_emulated"] = rows["fp64"]["ms"] / rows["emulated"]["ms"]
+    rows["speedup_emulated_all"] = rows["fp64"]["ms"] / rows["emulated_all"]["ms"]
     print(json.dumps({"workload": "RCLUPPr, sparse-sign sketch s=256 zeta=8, m=2^24, n=64, kappa=1e15 "
                                   "(X generated on the GPU)", "m": m, "n": n, "results": rows}), flush=True)
 
@@ -415,6 +420,21 @@ def run_batched(args):
     for i in range(len(Xs)):
         o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
         worst_orth, worst_res = max(worst_orth, o), max(worst_res, r)
+    # the same batch with the emulated tiers (binary64 sketch in a graph)
+    emu = {}
+    for label, prec in (("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
+        callp = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs,
+                                                 prec=prec)
+        for _ in range(max(3, args.warmup)):
+            callp()
+        e_ms, (_, _, e_st) = time_call(torch, stream, callp, args.steps)
+        wo, wr = 0.0, 0.0
+        for i in range(len(Xs)):
+            o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
+            wo, wr = max(wo, o), max(wr, r)
+        emu[label] = {"ms_per_batch": e_ms, "gflops_2mn2": model / (e_ms / 1e3) / 1e9,
+                      "speedup_vs_fp64_batch": batch_ms / e_ms,
+                      "statuses_nonzero": int(np.count_nonzero(e_st)), "worst_orth": wo, "worst_res": wr}
     line = {
         "workload": "batched RCLUPP: 512 FP64 problems, m=floor(2^U(12,17)), n in {16..128}, "
                     "kappa=10^U(2,12), Gaussian s=2n",
@@ -423,7 +443,7 @@ def run_batched(args):
         "gflops_2mn2": model / (batch_ms / 1e3) / 1e9,
         "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
         "gpu_launches_per_batch": int(launches), "statuses_nonzero": int(np.count_nonzero(status)),
-        "worst_orth": worst_orth, "worst_res": worst_res,
+        "worst_orth": worst_orth, "worst_res": worst_res, "precision_form": emu,
     }
     print(json.dumps(line), flush=True)
 

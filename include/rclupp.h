@@ -64,18 +64,22 @@ typedef enum {
  * binary64.  EMULATED adds binary64-emulating tensor-core products for the
  * solves and the first Gram.  Other steps stay in binary64.  The sparse-sign
  * sketch only adds and always runs in binary64; an explicit S requires
- * RCLUPP_PREC_FP64 or RCLUPP_PREC_EMULATED (whose sketch is then binary64). */
+ * RCLUPP_PREC_FP64 or one of the emulated tiers (whose sketch is then binary64). */
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
     RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
     RCLUPP_PREC_SKETCH_FP32 = 2, /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
-    RCLUPP_PREC_EMULATED = 3     /* the BF16 sketch tier; the triangular solves' block products
+    RCLUPP_PREC_EMULATED = 3,    /* the BF16 sketch tier; the triangular solves' block products
                                     (rclupp_trsm_emulated) and the Gram of the first CholeskyQR
                                     pass (Q1^T Q1, rclupp_gram_emulated) as binary64-emulating
                                     split-bf16 products on the tensor cores; the final-pass Gram,
                                     the diagonal blocks of the solves and the n x n
                                     factorizations stay in binary64.  An explicit S or the
                                     sparse-sign sketch keeps a binary64 sketch. */
+    RCLUPP_PREC_EMULATED_ALL = 4 /* EMULATED, and the final-pass Gram (C5; for RCholeskyQR its
+                                    one Gram) emulated as well: its digit products are exact and
+                                    are summed exactly in fp32 windows, then in int64 and
+                                    binary64, so the accumulation stays binary64 or better */
 } rclupp_precision_t;
 
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
@@ -116,7 +120,8 @@ typedef struct {
                             the first Cholesky breaks down or the spread of its diagonal
                             exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2) */
     int32_t emulated;    /* 1 when the solves and the first pass's Gram ran on the
-                            binary64-emulating tensor-core path (RCLUPP_PREC_EMULATED) */
+                            binary64-emulating tensor-core path (RCLUPP_PREC_EMULATED), 2 when
+                            every Gram did too (RCLUPP_PREC_EMULATED_ALL), else 0 */
 } rclupp_info_t;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -207,7 +212,9 @@ typedef enum {
  * (ldr[i]), every pointer a DEVICE pointer; the arrays themselves (m, n, X,
  * ldx, opts, Q, ldq, R, ldr, status) are HOST arrays of length count.  opts
  * holds one rclupp_opts_t per problem (NULL = defaults) and is used by the
- * randomized algorithms, binary64 tier only (a reduced tier returns
+ * randomized algorithms: the sketch is always binary64 here (a graph cannot
+ * escalate), prec may be RCLUPP_PREC_FP64 or one of the emulated tiers, whose
+ * emulated solves and Gram products are kept (the reduced sketch tiers return
  * RCLUPP_ERR_UNSUPPORTED).  Each problem obeys the single-problem rules.
  * The whole batch is enqueued as one CUDA graph: it forks into B parallel
  * branches (streams; problem i runs on branch i mod B, B set by

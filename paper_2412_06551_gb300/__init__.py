@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
-    "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED",
+    "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED", "PREC_EMULATED_ALL",
     "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
@@ -35,7 +35,7 @@ __all__ = [
 ]
 
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN = 0, 1
-PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED = 0, 1, 2, 3
+PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED, PREC_EMULATED_ALL = 0, 1, 2, 3, 4
 
 
 class Status:
@@ -400,21 +400,22 @@ ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2, ALGO_RCHOLQR, ALGO_SCHOLQR3 =
 
 
 def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
-                          Qs=None, Rs=None, check=True):
+                          Qs=None, Rs=None, check=True, prec=PREC_FP64):
     """Factor a list of column-major matrices in one batched call (one CUDA
     graph).  s is a per-problem list (or None for 2 n); seed is a list or an
-    int (then seed + i for problem i).  Returns (Qs, Rs, statuses)."""
-    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed)
+    int (then seed + i for problem i); prec is PREC_FP64 or an emulated tier
+    (binary64 sketch).  Returns (Qs, Rs, statuses)."""
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec)
     st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
     _raise("rclupp_factor_batched", st, None, check)
     return a["Qs"], a["Rs"], a["status"]
 
 
 def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
-                            Qs=None, Rs=None):
+                            Qs=None, Rs=None, prec=PREC_FP64):
     """Time the batch over candidate branch counts and keep the fastest in
     the handle.  Returns (branches, ms of one batched call)."""
-    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed)
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec)
     best = ctypes.c_int32(0)
     ms = ctypes.c_float(0.0)
     st = load().rclupp_autotune_batched(a["h"], int(algo), a["count"], *a["args"], ctypes.byref(best),
@@ -423,7 +424,7 @@ def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIA
     return int(best.value), float(ms.value)
 
 
-def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed):
+def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0):
     import numpy as np
     count = len(Xs)
     Xs = [colmajor(x) for x in Xs]
@@ -446,7 +447,7 @@ def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed):
         opts[i].zeta = int(zeta)
         opts[i].s = int(s[i] if s is not None else 2 * n[i])
         opts[i].seed = int(seed[i] if isinstance(seed, (list, tuple)) else seed + i)
-        opts[i].prec = PREC_FP64
+        opts[i].prec = int(prec)
         opts[i].S = None
         opts[i].lds = 0
     status = np.zeros(count, dtype=np.int32)

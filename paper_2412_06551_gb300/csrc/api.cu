@@ -239,7 +239,8 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
         if (smem > 220 * 1024) return RCLUPP_ERR_UNSUPPORTED;
     }
     if (o.prec != RCLUPP_PREC_FP64 && o.prec != RCLUPP_PREC_SKETCH_BF16 &&
-        o.prec != RCLUPP_PREC_SKETCH_FP32 && o.prec != RCLUPP_PREC_EMULATED)
+        o.prec != RCLUPP_PREC_SKETCH_FP32 && o.prec != RCLUPP_PREC_EMULATED &&
+        o.prec != RCLUPP_PREC_EMULATED_ALL)
         return RCLUPP_ERR_ARG;
     if ((o.prec == RCLUPP_PREC_SKETCH_BF16 || o.prec == RCLUPP_PREC_SKETCH_FP32) && o.S)
         return RCLUPP_ERR_UNSUPPORTED;
@@ -311,16 +312,22 @@ Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
 // First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
-// With `emulated` the triangular solve's block products and the Gram run on
-// the tensor cores emulating binary64 (the final-pass Gram of rest_cholqr2
-// always stays binary64).
+// With `emu_solve` the triangular solve's block products run on the tensor
+// cores emulating binary64, with `emu_gram` the Gram.
 rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const double *X,
-                                  int64_t ldx, double *Q, int64_t ldq, bool emulated = false) {
+                                  int64_t ldx, double *Q, int64_t ldq, bool emu_solve = false,
+                                  bool emu_gram = false) {
     cudaStream_t s = c.s;
     DevStatus *st = c.st;
-    if (emulated) {
-        RQ_TRY(launch_trsm_emu(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.part, st, s));
-        RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
+    if (emu_solve || emu_gram) {
+        if (emu_solve)
+            RQ_TRY(launch_trsm_emu(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.part, st, s));
+        else
+            RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, nullptr, 0, b.part, st, s));
+        if (emu_gram)
+            RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
+        else
+            RQ_TRY(launch_gram(Q, ldq, m, n, 0, b.G, n, b.part, st, s));
     } else {
         RQ_TRY(launch_trsm_gram(X, ldx, m, n, b.RP[0], b.rinv[0], Q, ldq, b.G, n, b.part, st, s));
     }
@@ -330,16 +337,20 @@ rclupp_status_t first_cholqr_pass(Ctx c, const Bufs &b, int64_t m, int n, const 
 
 // The rest of C3-C8 after R2 is known.  With `emulated` both triangular
 // solves use the emulated block products; the Gram of this final pass (C5)
-// stays binary64.
+// stays binary64 unless `emu_final_gram`.
 rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, int64_t ldq,
-                             double *R, int64_t ldr, bool emulated = false) {
+                             double *R, int64_t ldr, bool emulated = false,
+                             bool emu_final_gram = false) {
     cudaStream_t s = c.s;
     DevStatus *st = c.st;
     const int np = pad16(n);
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
     if (emulated) {
         RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, st, s));
-        RQ_TRY(launch_gram(Q, ldq, m, n, 0, b.G, n, b.part, st, s));
+        if (emu_final_gram)
+            RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
+        else
+            RQ_TRY(launch_gram(Q, ldq, m, n, 0, b.G, n, b.part, st, s));
     } else {
         RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.G, n, b.part, st, s));
     }
@@ -365,7 +376,7 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
                                 int64_t ldq, double *R, int64_t ldr, int *tier_used) {
     // the emulated tier sketches like the bf16 one (on the tensor cores when
     // the Gaussian sketch is generated, else in binary64)
-    const bool emulated = o.prec == RCLUPP_PREC_EMULATED;
+    const bool emulated = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     int tier = o.prec;
     if (emulated)
         tier = (o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S) ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64;
@@ -376,7 +387,8 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
         // No a-priori test on R1 is made: a reduced-tier R1 only sees the
         // rounded X, whose condition number saturates near 1/u of the tier,
         // so R1 cannot tell an X the tier handles from one it does not.
-        const rclupp_status_t st = first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq, emulated);
+        const rclupp_status_t st =
+            first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq, emulated, emulated);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
         const Verdict v = judge_first_pass(h, b, n);
@@ -387,7 +399,8 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
             return RCLUPP_ERR_CUDA;
     }
     *tier_used = tier;
-    return rest_cholqr2(ctx_of(h), b, m, n, Q, ldq, R, ldr, emulated);
+    return rest_cholqr2(ctx_of(h), b, m, n, Q, ldq, R, ldr, emulated,
+                        o.prec == RCLUPP_PREC_EMULATED_ALL);
 }
 
 // copy an m x n matrix (device to device, possibly different leading dims)
@@ -406,9 +419,10 @@ rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int
                          c.st, c.s));
     RQ_TRY(launch_sketch_precond(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 1,
                                  c.s));
-    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
     if (st != RCLUPP_OK) return st;
-    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr);
+    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr, emu, o.prec == RCLUPP_PREC_EMULATED_ALL);
 }
 
 // RCLUPPr, Algorithm 7, binary64 sketch; the LU runs in L (ldl).
@@ -420,9 +434,10 @@ rclupp_status_t enqueue_rcluppr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     RQ_TRY(launch_sketch(L, ldl, m, n, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
                          c.st, c.s));
     RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s));
-    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq);
+    const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
+    const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
     if (st != RCLUPP_OK) return st;
-    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr);
+    return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr, emu, o.prec == RCLUPP_PREC_EMULATED_ALL);
 }
 
 // CholeskyQR2, Algorithm 2.
@@ -441,7 +456,8 @@ rclupp_status_t enqueue_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, const do
     return RCLUPP_OK;
 }
 
-// RCholeskyQR, Algorithm 5 (one sketch, one CholeskyQR), sketch at `tier`.
+// RCholeskyQR, Algorithm 5 (one sketch, one CholeskyQR), sketch at `tier`,
+// emulated products as o.prec asks.
 rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, int tier, int64_t m,
                                 int n, const double *X, int64_t ldx, double *Q, int64_t ldq,
                                 double *R, int64_t ldr) {
@@ -450,11 +466,14 @@ rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     RQ_TRY(sketch_step(b, X, ldx, m, n, 0, o, tier, c.st, c.s));
     RQ_TRY(launch_rcholqr_r1(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], c.s));
     // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
+    // the one CholeskyQR's Gram is the final-pass Gram: emulated only when
+    // the caller asked for every Gram emulated (o.prec; `tier` is the sketch's)
+    const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     const rclupp_status_t st =
-        first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, tier == RCLUPP_PREC_EMULATED);
+        first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, o.prec == RCLUPP_PREC_EMULATED_ALL);
     if (st != RCLUPP_OK) return st;
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
-    if (tier == RCLUPP_PREC_EMULATED)
+    if (emu)
         RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, c.st, c.s));
     else
         RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st,
@@ -592,7 +611,7 @@ rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const dou
     const rclupp_status_t r = finish(h, ls, info, nullptr);
     if (info) {
         info->prec_used = tier;
-        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED ? 1 : (o.prec == RCLUPP_PREC_EMULATED_ALL ? 2 : 0);
     }
     return r;
 }
@@ -631,7 +650,7 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
     const rclupp_status_t r = finish(h, ls, info, nullptr);
     if (info) {
         info->prec_used = tier;
-        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED ? 1 : (o.prec == RCLUPP_PREC_EMULATED_ALL ? 2 : 0);
     }
     return r;
 }
@@ -673,10 +692,9 @@ rclupp_status_t rcholqr_factor(rclupp_handle_t h, int64_t m, int64_t n, const do
         h, enqueue_rcholqr(ctx_of(h), b, o, o.prec, m, int(n), X, ldx, Q, ldq, R, ldr), info, nullptr);
     if (info) {
         const bool tc_sketch = o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S;
-        info->prec_used = o.prec != RCLUPP_PREC_EMULATED
-                              ? o.prec
-                              : (tc_sketch ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64);
-        info->emulated = o.prec == RCLUPP_PREC_EMULATED;
+        const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
+        info->prec_used = !emu ? o.prec : (tc_sketch ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64);
+        info->emulated = o.prec == RCLUPP_PREC_EMULATED ? 1 : (o.prec == RCLUPP_PREC_EMULATED_ALL ? 2 : 0);
     }
     return r;
 }
@@ -714,7 +732,11 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
         if (randomized) {
             if ((st = check_opts(o[i], m[i], n[i])) != RCLUPP_OK) return st;
-            if (o[i].prec != RCLUPP_PREC_FP64) return RCLUPP_ERR_UNSUPPORTED;
+            // binary64 sketch always (no escalation inside a graph); the
+            // emulated tiers keep their emulated products
+            if (o[i].prec != RCLUPP_PREC_FP64 && o[i].prec != RCLUPP_PREC_EMULATED &&
+                o[i].prec != RCLUPP_PREC_EMULATED_ALL)
+                return RCLUPP_ERR_UNSUPPORTED;
         }
         const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
         const int64_t s = randomized ? o[i].s : n[i];

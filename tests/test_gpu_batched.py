@@ -105,3 +105,41 @@ def test_per_problem_status(rq):
     Qb, Rb, st = rq.rclupp_factor_batched([dev(good), dev(bad), dev(good)], algo=2, check=False)
     assert st[0] == 0 and st[2] == 0
     assert st[1] == rq.Status.ERR_CHOL_BREAKDOWN
+
+
+@pytest.mark.parametrize("prec", [3, 4])
+def test_batched_emulated_matches_single_calls(rq, prec):
+    # the batched form keeps a binary64 sketch; with the sparse-sign sketch
+    # (binary64 at every tier) each problem must equal the single call with
+    # the same emulated products bit for bit
+    g = np.random.default_rng(prec)
+    xs = [synth.svd_matrix(int(m), int(n), 1e6, 700 + i)
+          for i, (m, n) in enumerate(zip(g.integers(300, 6000, 10), g.choice([8, 33, 64, 100, 128], 10)))]
+    Xs = [dev(x) for x in xs]
+    fns = {rq.ALGO_RCLUPP: rq.rclupp_factor, rq.ALGO_RCLUPPR: rq.rclupp_r_factor,
+           rq.ALGO_RCHOLQR: rq.rcholqr_factor}
+    for algo, fn in fns.items():
+        Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=algo, seed=31, prec=prec,
+                                              kind=rq.SKETCH_SPARSE_SIGN, zeta=4)
+        assert np.all(st == 0)
+        for i, X in enumerate(Xs):
+            n = X.shape[1]
+            q, r, info = fn(X, s=2 * n, seed=31 + i, prec=prec, kind=rq.SKETCH_SPARSE_SIGN, zeta=4)
+            assert torch.equal(Qb[i], q) and torch.equal(Rb[i], r), (algo, i)
+            assert info.emulated == prec - 2
+
+
+@pytest.mark.parametrize("prec", [3, 4])
+def test_batched_emulated_gaussian_gates(rq, prec):
+    g = np.random.default_rng(10 + prec)
+    xs = [synth.svd_matrix(int(m), int(n), 10.0 ** g.uniform(2, 10), 800 + i)
+          for i, (m, n) in enumerate(zip(g.integers(300, 6000, 12), g.choice([16, 48, 96, 128], 12)))]
+    Xs = [dev(x) for x in xs]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=41, prec=prec)
+    assert np.all(st == 0)
+    for i, x in enumerate(xs):
+        m, n = x.shape
+        q_o, r_o, _ = oracle.rclupp(x, S=oracle.gaussian_sketch_matrix(2 * n, m, 41 + i))
+        q, r = host(Qb[i]), host(Rb[i])
+        assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+        assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)

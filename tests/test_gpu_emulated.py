@@ -144,15 +144,29 @@ def _gate(x, q, r, q_o, r_o, kappa):
 
 @pytest.mark.parametrize("algo", ["rclupp", "rcluppr"])
 @pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10, 1e12])
-def test_driver_emulated_tier(rq, algo, kappa):
+@pytest.mark.parametrize("tier", [3, 4])
+def test_driver_emulated_tier(rq, algo, kappa, tier):
     m, n, s = 8192, 64, 128
     x = synth.svd_matrix(m, n, kappa, 81)
     fn = rq.rclupp_factor if algo == "rclupp" else rq.rclupp_r_factor
-    Q, R, info = fn(dev(x), s=s, seed=7, prec=rq.PREC_EMULATED)
+    Q, R, info = fn(dev(x), s=s, seed=7, prec=tier)
     q_o, r_o, _ = getattr(oracle, algo)(x, S=oracle.gaussian_sketch_matrix(s, m, 7))
     _gate(x, host(Q), host(R), q_o, r_o, kappa)
-    assert info.emulated == 1
+    assert info.emulated == tier - 2
     assert info.prec_used in (0, 1, 2)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(20000, 128, 1e4), (9000, 256, 1e8)])
+def test_all_emulated_explicit_sketch(rq, m, n, kappa):
+    x = synth.svd_matrix(m, n, kappa, 90 + n)
+    S = synth.gaussian_sketch(2 * n, m, 17)
+    Q, R, info = rq.rclupp_factor(dev(x), s=2 * n, S=dev(S), prec=rq.PREC_EMULATED_ALL)
+    q_o, r_o, _ = oracle.rclupp(x, S=S)
+    _gate(x, host(Q), host(R), q_o, r_o, kappa)
+    assert info.emulated == 2 and info.prec_used == 0
+    Q2, R2, info2 = rq.rcholqr_factor(dev(x), s=2 * n, S=dev(S), prec=rq.PREC_EMULATED_ALL)
+    q2, r2, _ = oracle.rcholqr(x, S=S)
+    _gate(x, host(Q2), host(R2), q2, r2, kappa)
 
 
 @pytest.mark.parametrize("m,n,kappa", [(4096, 64, 1e8), (5003, 128, 1e4), (3000, 256, 1e3),
