@@ -98,7 +98,7 @@ cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, doub
 size_t gram_emu_partials_doubles(int n);
 
 // ---- triangular solve with binary64-emulating block products (emu_trsm.cu) ----
-// Q = A R^{-1} by 32-column blocks: the off-diagonal block products on the
+// Q = A R^{-1} by 16-column (n <= 128) or 32-column blocks: the off-diagonal block products on the
 // tensor cores (digits of Q's rows and R's columns, exact fp32 level sums,
 // int64 drains), the diagonal blocks in binary64.  RP/rinv as for
 // launch_trsm_gram (padded factor followed by its row-major copy); scratch
@@ -107,6 +107,11 @@ cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, cons
                             const double *rinv, double *Q, int64_t ldq, void *scratch,
                             DevStatus *st, cudaStream_t stream);
 size_t trsm_emu_scratch_bytes(int n);
+// The 32-column-block form (emu_trsm32.cu) that launch_trsm_emu uses for n > 128.
+cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                              const double *rinv, double *Q, int64_t ldq, void *scratch,
+                              DevStatus *st, cudaStream_t stream);
+size_t trsm_emu32_scratch_bytes(int n);
 
 // Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
 cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,
