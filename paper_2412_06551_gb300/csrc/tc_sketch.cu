@@ -71,7 +71,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
 }
 
 template <int NSL>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_sketch_tc(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int unit_lower,
                 int64_t chunk, int n_st, int nt, uint64_t seed, double scale,
                 double *__restrict__ part, int s_pad, int n_pad, DevStatus *st) {
@@ -237,12 +237,14 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
     const int n_pad = static_cast<int>(round_up(n, 32));
     const int n_st = s_pad / kTcM;
     const int tiles = n_st;  // n <= 256: one column tile
-    int p = std::max(1, num_sms() / tiles);
+    // CTAs per SM: two when their TMEM columns (<= 256 each) and shared
+    // memory both fit, so that one CTA's generation of S covers the other's
+    // load latency; each CTA's stages stay below half the SM's shared memory
+    const size_t smem = tc_sketch_smem_bytes(n, nterms);
+    const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+    int p = std::max(1, per_sm * num_sms() / tiles);
     int64_t chunk = round_up(ceil_div(m, p), kTcBK);
     p = static_cast<int>(ceil_div(m, chunk));
-    // at least 120 KB of shared memory so that one CTA (and one TMEM
-    // allocation) runs per SM
-    const size_t smem = std::max<size_t>(tc_sketch_smem_bytes(n, nterms), 120 * 1024);
     const dim3 grid(tiles, p);
     const double scale = 1.0 / sqrt(double(s));
     if (nterms == 1) {
