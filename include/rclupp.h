@@ -137,6 +137,15 @@ rclupp_status_t rclupp_destroy(rclupp_handle_t handle);
 rclupp_status_t rclupp_set_stream(rclupp_handle_t handle, void *stream);
 /* Bytes of device workspace currently held by the handle. */
 rclupp_status_t rclupp_workspace_bytes(rclupp_handle_t handle, size_t *bytes);
+/* Bytes of device workspace one factorization of an m x n matrix by `algo`
+ * (rclupp_algo_t) needs on the current device with these options (NULL =
+ * defaults): partial sums, the sketch, small-factor scratch, the padded
+ * triangular factors, and for RCLUPPr / LC2 an m x n copy of the LU factor
+ * when q_aliases_x != 0 (or, for RCLUPPr, at a non-binary64 tier).  A handle
+ * grows its workspace to this size on the first such call.  No GPU work;
+ * errors as the drivers' argument checks. */
+rclupp_status_t rclupp_workspace_size(int32_t algo, int64_t m, int64_t n, const rclupp_opts_t *opts,
+                                      int32_t q_aliases_x, size_t *bytes);
 /* Human-readable name of a status code (static string). */
 const char *rclupp_status_string(int status);
 

@@ -23,7 +23,7 @@ from . import _build
 __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
     "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED", "PREC_EMULATED_ALL",
-    "load", "library_path", "exported_symbols", "colmajor", "empty_colmajor", "Handle",
+    "load", "library_path", "exported_symbols", "workspace_size", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
     "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
@@ -98,6 +98,7 @@ _SIGNATURES = {
     "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
     "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_workspace_size": ([_I32, _I64, _I64, _P, _I32, _P], _I32),
     "rclupp_trsm_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_cholesky": ([_P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_int64)], _I32),
@@ -147,6 +148,18 @@ def profile_read() -> dict:
 def kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().rclupp_kernel_launches())
+
+
+def workspace_size(algo, m, n, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, prec=PREC_FP64,
+                   q_aliases_x=False) -> int:
+    """Device workspace bytes one factorization needs (no GPU work)."""
+    o = Opts()
+    o.kind, o.zeta, o.s, o.seed, o.prec = int(kind), int(zeta), int(s if s is not None else 2 * n), 0, int(prec)
+    out = ctypes.c_size_t(0)
+    st = load().rclupp_workspace_size(int(algo), int(m), int(n), ctypes.byref(o), int(bool(q_aliases_x)),
+                                      ctypes.byref(out))
+    _raise("rclupp_workspace_size", st)
+    return int(out.value)
 
 
 def library_path() -> str:

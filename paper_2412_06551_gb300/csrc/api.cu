@@ -567,6 +567,28 @@ rclupp_status_t rclupp_set_stream(rclupp_handle_t h, void *stream) {
     return RCLUPP_OK;
 }
 
+rclupp_status_t rclupp_workspace_size(int32_t algo, int64_t m, int64_t n, const rclupp_opts_t *opts,
+                                      int32_t q_aliases_x, size_t *bytes) {
+    if (!bytes || n < 1 || m < n) return RCLUPP_ERR_ARG;
+    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_SCHOLQR3) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    const bool randomized =
+        algo == RCLUPP_ALGO_RCLUPP || algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_RCHOLQR;
+    const rclupp_opts_t o = resolve_opts(opts, n);
+    if (randomized) {
+        const rclupp_status_t st = check_opts(o, m, n);
+        if (st != RCLUPP_OK) return st;
+    }
+    // the same rule as the drivers: RCLUPPr keeps its own LU copy when Q
+    // aliases X or a non-binary64 tier may re-sketch M; LC2 when Q aliases X
+    const bool lu_copy = (algo == RCLUPP_ALGO_RCLUPPR && (q_aliases_x || o.prec != RCLUPP_PREC_FP64)) ||
+                         (algo == RCLUPP_ALGO_LC2 && q_aliases_x);
+    size_t total = 0;
+    carve(nullptr, m, int(n), randomized ? o.s : n, lu_copy, &total);
+    *bytes = total;
+    return RCLUPP_OK;
+}
+
 rclupp_status_t rclupp_workspace_bytes(rclupp_handle_t h, size_t *bytes) {
     if (!h || !bytes) return RCLUPP_ERR_ARG;
     *bytes = h->ws_bytes;

@@ -63,3 +63,21 @@ def test_no_cpu_fallback_in_the_binding():
     x = torch.zeros((8, 2), dtype=torch.float64)
     with pytest.raises(TypeError):
         rq.cholqr2_factor(x)
+
+
+def test_workspace_size_query_needs_no_gpu():
+    # a host-only query: grows with the sketch size and adds the m x n LU copy
+    # exactly when RCLUPPr / LC2 cannot factor in the Q buffer
+    m, n = 100000, 64
+    a = rq.workspace_size(rq.ALGO_RCLUPP, m, n)
+    b = rq.workspace_size(rq.ALGO_RCLUPP, m, n, s=4 * n)
+    assert 0 < a <= b
+    lu = rq.workspace_size(rq.ALGO_RCLUPPR, m, n)
+    lu_alias = rq.workspace_size(rq.ALGO_RCLUPPR, m, n, q_aliases_x=True)
+    assert lu_alias - lu >= m * n * 8
+    assert rq.workspace_size(rq.ALGO_LC2, m, n, q_aliases_x=True) - rq.workspace_size(rq.ALGO_LC2, m, n) >= m * n * 8
+    assert rq.workspace_size(rq.ALGO_RCLUPPR, m, n, prec=rq.PREC_EMULATED) >= lu_alias - 256
+    with pytest.raises(rq.RclupError):
+        rq.workspace_size(rq.ALGO_RCLUPP, 10, 20)        # m < n
+    with pytest.raises(rq.RclupError):
+        rq.workspace_size(rq.ALGO_RCLUPP, 1000, 300)     # n > 256
