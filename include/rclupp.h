@@ -266,6 +266,16 @@ rclupp_status_t rclupp_sketch(rclupp_handle_t handle, int64_t m, int64_t n, cons
                               int64_t lda, int32_t unit_lower, const rclupp_opts_t *opts,
                               double *Y, int64_t ldy);
 
+/* The sketch of a block of rows: A holds rows row0 .. row0 + m - 1 of a
+ * taller matrix and Y = S[:, row0 : row0 + m] A, with the generated S's entry
+ * (r, row0 + i) multiplying row i of A -- the partial that each rank of a
+ * row-sharded factorization adds into the full S X (Section 3's sketch is a
+ * sum over rows).  An explicit S (opts->S) is read from its column 0, i.e.
+ * the caller passes the slice.  row0 >= 0; otherwise as rclupp_sketch. */
+rclupp_status_t rclupp_sketch_rows(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
+                                   int64_t lda, int64_t row0, int32_t unit_lower,
+                                   const rclupp_opts_t *opts, double *Y, int64_t ldy);
+
 /* G = A^T A (n x n, ldg >= n, both triangles written): Algorithm 1 step 1,
  * C1/C5 of Theorem 4.1; unit_lower as in rclupp_sketch (LC2's M^T M). */
 rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,

@@ -98,6 +98,7 @@ _SIGNATURES = {
     "rclupp_sketch": ([_P, _I64, _I64, _P, _I64, _I32, ctypes.POINTER(Opts), _P, _I64], _I32),
     "rclupp_gram": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_sketch_rows": ([_P, _I64, _I64, _P, _I64, _I64, _I32, _P, _P, _I64], _I32),
     "rclupp_workspace_size": ([_I32, _I64, _I64, _P, _I32, _P], _I32),
     "rclupp_trsm_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
@@ -361,15 +362,16 @@ def scholqr3_factor(X, *, Q=None, R=None, check=True):
 # ---------------------------------------------------------------- steps
 
 def rclupp_sketch(A, *, s, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
-                  unit_lower=False, Y=None):
-    """Y = S A (s x n)."""
+                  unit_lower=False, Y=None, row0=0):
+    """Y = S A (s x n); with row0 > 0, A is the row block starting at global
+    row row0 of a taller matrix and Y its partial sketch."""
     A, lda = colmajor(A)
     m, n = A.shape
     Y = empty_colmajor(s, n, A.device) if Y is None else Y
     Y, ldy = colmajor(Y)
     o, S_keep = _opts(kind=kind, s=s, zeta=zeta, seed=seed, prec=prec, S=S, n=n)
-    st = load().rclupp_sketch(_handle(A).bind(), m, n, _ptr(A), lda, int(bool(unit_lower)),
-                              ctypes.byref(o), _ptr(Y), ldy)
+    st = load().rclupp_sketch_rows(_handle(A).bind(), m, n, _ptr(A), lda, int(row0),
+                                   int(bool(unit_lower)), ctypes.byref(o), _ptr(Y), ldy)
     _raise("rclupp_sketch", st)
     return Y
 

@@ -918,10 +918,10 @@ rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t
 
 // ---- individual steps ----
 
-rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const double *A, int64_t lda,
-                              int32_t unit_lower, const rclupp_opts_t *opts, double *Y,
-                              int64_t ldy) {
-    if (!h || !A || !Y || n < 1 || m < 1 || bad_ld(lda, m)) return RCLUPP_ERR_ARG;
+rclupp_status_t rclupp_sketch_rows(rclupp_handle_t h, int64_t m, int64_t n, const double *A,
+                                   int64_t lda, int64_t row0, int32_t unit_lower,
+                                   const rclupp_opts_t *opts, double *Y, int64_t ldy) {
+    if (!h || !A || !Y || n < 1 || m < 1 || row0 < 0 || bad_ld(lda, m)) return RCLUPP_ERR_ARG;
     if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
     const rclupp_opts_t o = resolve_opts(opts, n);
     rclupp_status_t st = check_opts(o, m, n);
@@ -933,11 +933,17 @@ rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const dou
     if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
         e = launch_sketch_tc(A, lda, m, int(n), unit_lower, o.s, o.seed,
                              o.prec == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, Y, ldy, b.part, h->d_status,
-                             h->stream);
+                             h->stream, row0);
     else
         e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, Y,
-                          ldy, b.part, h->d_status, h->stream);
+                          ldy, b.part, h->d_status, h->stream, row0);
     return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_sketch(rclupp_handle_t h, int64_t m, int64_t n, const double *A, int64_t lda,
+                              int32_t unit_lower, const rclupp_opts_t *opts, double *Y,
+                              int64_t ldy) {
+    return rclupp_sketch_rows(h, m, n, A, lda, 0, unit_lower, opts, Y, ldy);
 }
 
 rclupp_status_t rclupp_gram(rclupp_handle_t h, int64_t m, int64_t n, const double *A, int64_t lda,

@@ -56,10 +56,12 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
 
 // Y = S A (s x n, ldy); kind 0 Gaussian (generated from seed, or explicit S
 // when S != nullptr), kind 1 sparse-sign.
+// row0: global index of A's first row, for the generated sketches (entry
+// (r, row0 + i) of S multiplies row i of A); 0 for a whole matrix.
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int kind,
                           int64_t s, int zeta, uint64_t seed, const double *S, int64_t lds,
                           double *Y, int64_t ldy, double *part, DevStatus *st,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int64_t row0 = 0);
 
 // Fixed-order sum of sketch partials: Y[r][c] = sum_p part[p][c*s_pad + r].
 cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
@@ -85,7 +87,7 @@ cudaError_t launch_cholesky_cluster(const double *G, int64_t ldg, int n, double 
 // bf16 terms, fp32 accumulation on tcgen05 (n <= 256).
 cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
                              int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
-                             double *part, DevStatus *st, cudaStream_t stream);
+                             double *part, DevStatus *st, cudaStream_t stream, int64_t row0 = 0);
 size_t tc_sketch_smem_bytes(int n, int nterms);
 
 // ---- binary64-emulating Gram on the tensor cores (emu_gram.cu) ----

@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                    const double *__restrict__ A, int64_t lda, int64_t m, int n, int unit_lower,
                    int64_t chunk, int ncb, int n_st, int64_t s, uint64_t seed, double scale,
                    const double *__restrict__ S, int64_t lds, double *__restrict__ part, int s_pad,
-                   int n_pad, DevStatus *st) {
+                   int n_pad, DevStatus *st, int64_t row0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     double *T = reinterpret_cast<double *>(smem_raw);
     double *Sg = T + BM * ncb;  // [i][64]
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int64_t row = r0 + i;
                 double *dst = Sg + i * 64 + 4 * q;
                 if (row < m) {
-                    const float4 z = sk_gauss4(seed, row, (rt0 >> 2) + q);
+                    const float4 z = sk_gauss4(seed, row0 + row, (rt0 >> 2) + q);
                     dst[0] = double(z.x) * scale;
                     dst[1] = double(z.y) * scale;
                     dst[2] = double(z.z) * scale;
@@ -689,7 +689,7 @@ constexpr int kSparseNT = 32;
 __global__ void __launch_bounds__(kThreads, 2)
     k_sketch_sparse(const double *__restrict__ A, int64_t lda, int64_t m, int n, int unit_lower,
                     int64_t chunk, int s, int zeta, uint64_t seed, double scale,
-                    double *__restrict__ part, int s_pad, int n_pad) {
+                    double *__restrict__ part, int s_pad, int n_pad, int64_t row0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     double *acc = reinterpret_cast<double *>(smem_raw);                    // [s_pad][32]
     double *T2 = acc + size_t(s_pad) * kSparseNT;                          // [BM][33]
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int64_t row = r0 + threadIdx.x;
             int rows_[16], sg[16];
             if (row < m) {
-                sk_sparse_column(seed, row, s, zeta, rows_, sg);
+                sk_sparse_column(seed, row0 + row, s, zeta, rows_, sg);
                 for (int t = 0; t < zeta; ++t)
                     tgt[threadIdx.x * zeta + t] = rows_[t] | (sg[t] < 0 ? int(0x80000000u) : 0);
             } else {
@@ -772,7 +772,7 @@ size_t sketch_partials_doubles(int64_t m, int n, int64_t s, int kind) {
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int kind,
                           int64_t s, int zeta, uint64_t seed, const double *S, int64_t lds,
                           double *Y, int64_t ldy, double *part, DevStatus *st,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int64_t row0) {
     const int s_pad = static_cast<int>(round_up(s, 64));
     const int n_pad = static_cast<int>(round_up(n, 32));
     cudaError_t e;
@@ -785,7 +785,7 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
         cudaFuncSetAttribute(k_sketch_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         RQ_LAUNCH(KID_SKETCH_SPARSE, stream, k_sketch_sparse<<<dim3(pl.grid_x, ny), kThreads, smem, stream>>>(
             A, lda, m, n, unit_lower, pl.chunk, static_cast<int>(s), zeta, seed,
-            1.0 / sqrt(double(zeta)), part, s_pad, n_pad));
+            1.0 / sqrt(double(zeta)), part, s_pad, n_pad, row0));
         nparts = pl.grid_x;
     } else {
         const int ncb = std::min(pad16(n), 128);
@@ -801,7 +801,7 @@ cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int un
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         RQ_LAUNCH(KID_SKETCH_GAUSS, stream, k<<<dim3(pl.grid_x, n_st * n_ct), kThreads, smem, stream>>>(
             map, tma, A, lda, m, n, unit_lower, pl.chunk, ncb, n_st, s, seed,
-            1.0 / sqrt(double(s)), S, lds, part, s_pad, n_pad, st));
+            1.0 / sqrt(double(s)), S, lds, part, s_pad, n_pad, st, row0));
         nparts = pl.grid_x;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

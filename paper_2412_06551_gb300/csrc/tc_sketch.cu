@@ -74,7 +74,7 @@ template <int NSL>
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_sketch_tc(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int unit_lower,
                 int64_t chunk, int n_st, int nt, uint64_t seed, double scale,
-                double *__restrict__ part, int s_pad, int n_pad, DevStatus *st) {
+                double *__restrict__ part, int s_pad, int n_pad, DevStatus *st, int64_t row0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_mma[kTcStages];
     __shared__ uint32_t tmem_slot;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int64_t row = r0 + i;
             uint16_t h[4] = {0, 0, 0, 0};
             if (row < re) {
-                const float4 z = sk_gauss4(seed, row, (rt0 >> 2) + q);
+                const float4 z = sk_gauss4(seed, row0 + row, (rt0 >> 2) + q);
                 h[0] = bf16_bits_from_f32(z.x);
                 h[1] = bf16_bits_from_f32(z.y);
                 h[2] = bf16_bits_from_f32(z.z);
@@ -230,7 +230,7 @@ size_t tc_sketch_smem_bytes(int n, int nterms) {
 
 cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
                              int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
-                             double *part, DevStatus *st, cudaStream_t stream) {
+                             double *part, DevStatus *st, cudaStream_t stream, int64_t row0) {
     if (n > 256 || (nterms != 1 && nterms != 3)) return cudaErrorInvalidValue;
     const int nt = std::min(pad16(n), 256);
     const int s_pad = static_cast<int>(round_up(s, kTcM));
@@ -252,13 +252,13 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
         RQ_LAUNCH(KID_SKETCH_TC, stream,
                   k_sketch_tc<1><<<grid, kTcThreads, smem, stream>>>(X, ldx, m, n, unit_lower, chunk,
                                                                    n_st, nt, seed, scale, part,
-                                                                   s_pad, n_pad, st));
+                                                                   s_pad, n_pad, st, row0));
     } else {
         cudaFuncSetAttribute(k_sketch_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         RQ_LAUNCH(KID_SKETCH_TC, stream,
                   k_sketch_tc<3><<<grid, kTcThreads, smem, stream>>>(X, ldx, m, n, unit_lower, chunk,
                                                                    n_st, nt, seed, scale, part,
-                                                                   s_pad, n_pad, st));
+                                                                   s_pad, n_pad, st, row0));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -1,0 +1,117 @@
+"""Row-sharded RCLUPP and CholeskyQR2 over the ranks of torch.distributed.
+
+Each rank holds a contiguous block of rows of X: rows ``row0 .. row0 + m_r - 1``
+of the m x n matrix, on its own GPU.  Every tall pass runs on the rank's own
+rows; the only exchange is the sum of the partial s x n sketch and of the
+partial n x n Gram matrices (the communication-avoiding property of
+Section 1): RCLUPP needs three all-reduces (S X, Q1^T Q1, Q2^T Q2),
+CholeskyQR2 two.  The small factorizations (sketch LU, Householder R,
+Cholesky, triangular products) run replicated on every rank from identical
+inputs, so every rank ends with the same R and its own rows of Q.
+
+RCLUPPr and LC2 are not sharded: their tall LU with partial pivoting needs an
+argmax across all ranks for every column and the exchange of pivot rows.
+
+The per-rank operations are those of this package's C ABI (:class:`LibrarySteps`);
+the driver takes them, and the all-reduce, as parameters so that the
+communication structure can be exercised with any implementation of the same
+steps.
+"""
+from __future__ import annotations
+
+from typing import Callable, Optional
+
+from . import (SKETCH_GAUSSIAN, RclupError, Status, rclupp_cholesky, rclupp_gram,
+               rclupp_sketch, rclupp_sketch_precond, rclupp_trmm_upper, rclupp_trsm_gram)
+
+__all__ = ["LibrarySteps", "torch_allreduce", "rclupp_factor_sharded", "cholqr2_factor_sharded",
+           "row_block"]
+
+
+def row_block(m: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous row block of `rank` among `world` ranks: (row0, rows)."""
+    base, extra = divmod(m, world)
+    row0 = rank * base + min(rank, extra)
+    return row0, base + (1 if rank < extra else 0)
+
+
+class LibrarySteps:
+    """The per-rank steps on the rank's GPU through the C ABI."""
+
+    def sketch(self, A, *, s, kind, zeta, seed, row0):
+        return rclupp_sketch(A, s=s, kind=kind, zeta=zeta, seed=seed, row0=row0)
+
+    def precond(self, Y):
+        return rclupp_sketch_precond(Y)
+
+    def trsm_gram(self, A, R, *, gram):
+        return rclupp_trsm_gram(A, R, gram=gram)
+
+    def gram(self, A):
+        return rclupp_gram(A)
+
+    def cholesky(self, G):
+        R, st, col = rclupp_cholesky(G, check=False)
+        return R, st, col
+
+    def trmm(self, A, B):
+        return rclupp_trmm_upper(A, B)
+
+
+def torch_allreduce(group=None) -> Callable:
+    """In-place sum over the ranks of `group` (torch.distributed: NCCL for
+    CUDA tensors, gloo for CPU tensors)."""
+    import torch.distributed as dist
+
+    def reduce_(t):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t
+    return reduce_
+
+
+def _cholesky_or_raise(steps, G, pass_no):
+    R, st, col = steps.cholesky(G)
+    if st != Status.OK:
+        # every rank holds the same all-reduced G, so every rank raises here
+        err = RclupError("cholesky (pass %d, column %d)" % (pass_no, col), st)
+        err.column = col
+        raise err
+    return R
+
+
+def rclupp_factor_sharded(X_local, row0: int, *, s: Optional[int] = None, kind: int = SKETCH_GAUSSIAN,
+                          zeta: int = 8, seed: int = 0, steps=None, allreduce: Optional[Callable] = None,
+                          group=None):
+    """[Q_local, R] = RCLUPP(X) (Algorithm 6) with X split by rows over the
+    ranks.  X_local: this rank's rows (row0 .. row0 + m_r - 1), column-major
+    on the rank's GPU.  The generated sketch is the one the whole matrix
+    would get (entry (r, i) depends on the global row i), so the result
+    equals the single-GPU factorization up to the order of the sums."""
+    steps = steps or LibrarySteps()
+    allreduce = allreduce or torch_allreduce(group)
+    n = X_local.shape[1]
+    s = 2 * n if s is None else s
+    # step 1: X_s = S X as a sum of the ranks' partials (all-reduce 1)
+    Y = allreduce(steps.sketch(X_local, s=s, kind=kind, zeta=zeta, seed=seed, row0=row0))
+    # steps 2-4 on every rank: LU of X_s, Householder R of M, R1 = R0 N
+    R1 = steps.precond(Y)
+    # steps 5-7: CholeskyQR2 of Q1 = X R1^{-1} (all-reduces 2 and 3)
+    Q1, G1 = steps.trsm_gram(X_local, R1, gram=True)
+    R2 = _cholesky_or_raise(steps, allreduce(G1), 1)
+    Q2, G2 = steps.trsm_gram(Q1, R2, gram=True)
+    R4 = _cholesky_or_raise(steps, allreduce(G2), 2)
+    Q, _ = steps.trsm_gram(Q2, R4, gram=False)
+    R = steps.trmm(R4, steps.trmm(R2, R1))  # R3 = R2 R1 (C4), R = R4 R3 (C8)
+    return Q, R
+
+
+def cholqr2_factor_sharded(X_local, *, steps=None, allreduce: Optional[Callable] = None, group=None):
+    """[Q_local, R] = CholeskyQR2(X) (Algorithm 2) with X split by rows over
+    the ranks (two all-reduces of n x n Gram partials)."""
+    steps = steps or LibrarySteps()
+    allreduce = allreduce or torch_allreduce(group)
+    R1 = _cholesky_or_raise(steps, allreduce(steps.gram(X_local)), 1)
+    Q1, G1 = steps.trsm_gram(X_local, R1, gram=True)
+    R2 = _cholesky_or_raise(steps, allreduce(G1), 2)
+    Q, _ = steps.trsm_gram(Q1, R2, gram=False)
+    return Q, steps.trmm(R2, R1)

@@ -1,0 +1,149 @@
+"""Row-sharded RCLUPP and CholeskyQR2 (paper_2412_06551_gb300.distributed).
+
+CPU, gloo, world_size 2 and 3: each rank runs the per-rank steps through the
+oracle (plain binary64 C) on its own rows of X, with torch.distributed's
+all-reduce between them.  Checked: exactly three all-reduces for RCLUPP (of
+s x n, n x n, n x n) and two for CholeskyQR2; every rank ends with the same R;
+the stacked Q and R meet the same gates against the single-matrix oracle as
+the GPU path (orthogonality and residual within max(10x, 1e-13), R within
+1e-10 kappa).  The generated sketch is the whole matrix's: rank r uses the
+columns row0 .. row0 + m_r - 1 of the same S.  The GPU form (the library's
+steps on one GPU, ranks emulated by summing row blocks in one process) is in
+test_gpu_sharded.py.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+class OracleSteps:
+    """The per-rank steps on the CPU through the oracle (test scaffolding)."""
+
+    def __init__(self, S_full):
+        self.S_full = S_full
+
+    def sketch(self, A, *, s, kind, zeta, seed, row0):
+        import oracle
+        return oracle.sketch_dense(self.S_full[:, row0:row0 + A.shape[0]], A)
+
+    def precond(self, Y):
+        import oracle
+        return oracle.sketch_precond(Y)[0]
+
+    def trsm_gram(self, A, R, *, gram):
+        import oracle
+        Q = oracle.trsm(A, R)
+        return Q, (oracle.gram(Q) if gram else None)
+
+    def gram(self, A):
+        import oracle
+        return oracle.gram(A)
+
+    def cholesky(self, G):
+        import oracle
+        return oracle.cholesky(G, raise_on_error=False)
+
+    def trmm(self, A, B):
+        import oracle
+        return oracle.trmm_upper(A, B)
+
+
+def _problem(m, n, kappa):
+    import synth
+    import oracle
+    x = synth.svd_matrix(m, n, kappa, 4242)
+    S = oracle.gaussian_sketch_matrix(2 * n, m, 77)
+    return x, S
+
+
+def _worker(rank, world, port, algo, m, n, kappa, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2412_06551_gb300 import distributed as D
+    x, S = _problem(m, n, kappa)
+    row0, rows = D.row_block(m, world, rank)
+    sizes = []
+
+    def allreduce(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        sizes.append(tuple(a.shape))
+        return np.asfortranarray(t.numpy())
+
+    steps = OracleSteps(S)
+    xl = np.asfortranarray(x[row0:row0 + rows])
+    if algo == "rclupp":
+        Q, R = D.rclupp_factor_sharded(xl, row0, s=2 * n, seed=77, steps=steps, allreduce=allreduce)
+    else:
+        Q, R = D.cholqr2_factor_sharded(xl, steps=steps, allreduce=allreduce)
+    q.put((rank, row0, Q, R, sizes))
+    dist.destroy_process_group()
+
+
+def _run(world, port, algo, m, n, kappa):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, algo, m, n, kappa, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=240) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    return sorted(out, key=lambda t: t[0])
+
+
+@pytest.mark.parametrize("world,port", [(2, 29561), (3, 29562)])
+@pytest.mark.parametrize("kappa", [1e4, 1e12])
+def test_rclupp_sharded_matches_single_matrix_oracle(world, port, kappa):
+    import oracle
+    m, n = 3001, 24
+    out = _run(world, port + (0 if kappa < 1e6 else 10), "rclupp", m, n, kappa)
+    x, S = _problem(m, n, kappa)
+    Q = np.vstack([o[2] for o in out])
+    R = out[0][3]
+    for o in out:
+        assert np.array_equal(o[3], R)                       # the same R everywhere
+        assert o[4] == [(2 * n, n), (n, n), (n, n)]           # three all-reduces
+    q_o, r_o, _ = oracle.rclupp(x, S=S)
+    orth, res = oracle.orthogonality(Q), oracle.residual(x, Q, R)
+    assert orth <= max(10 * oracle.orthogonality(q_o), 1e-13)
+    assert res <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
+    if kappa <= 1e6:
+        assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * kappa
+
+
+def test_cholqr2_sharded_two_allreduces():
+    import oracle
+    m, n = 2000, 16
+    out = _run(2, 29581, "cholqr2", m, n, 1e3)
+    x, _ = _problem(m, n, 1e3)
+    Q = np.vstack([o[2] for o in out])
+    R = out[0][3]
+    assert all(o[4] == [(n, n), (n, n)] for o in out)
+    q_o, r_o, _ = oracle.cholqr2(x)
+    assert oracle.orthogonality(Q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+    assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * 1e3
+
+
+def test_row_block_partition():
+    from paper_2412_06551_gb300.distributed import row_block
+    for m in (1, 7, 100, 3001):
+        for world in (1, 2, 3, 8):
+            blocks = [row_block(m, world, r) for r in range(world)]
+            assert blocks[0][0] == 0
+            assert sum(b[1] for b in blocks) == m
+            for (a0, an), (b0, _) in zip(blocks, blocks[1:]):
+                assert a0 + an == b0
