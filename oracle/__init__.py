@@ -4,7 +4,9 @@ Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this package.  It wraps ``rclupp_oracle.c``: a plain,
 sequential-sum FP64 implementation of CholeskyQR, CholeskyQR2 (Algorithm 2),
 LC2 (Algorithm 4), RCLUPP (Algorithm 6) and RCLUPPr (Algorithm 7), plus the
-building blocks they are made of, compiled with gcc ``-ffp-contract=off``.
+building blocks they are made of and the generated sketches (Gaussian,
+sparse-sign, subsampled randomized Hadamard), compiled with gcc
+``-ffp-contract=off``.
 
 All matrix arguments are numpy float64 arrays; results are returned
 column-major (Fortran order).  Status codes: 0 ok, -1 bad argument,
@@ -13,7 +15,7 @@ column-major (Fortran order).  Status codes: 0 ok, -1 bad argument,
 Parity pins: every routine is checked against values the paper or plain
 mathematics fix (closed forms, uniqueness of the positive-diagonal QR,
 brute force in extended precision, the paper's error bounds), in
-``tests/test_oracle_pins.py``.
+``tests/test_oracle_pins.py`` and ``tests/test_oracle_srht.py``.
 """
 from __future__ import annotations
 
@@ -85,6 +87,10 @@ def _load():
                 "orc_scholqr3_shift": ([I64, I64, P, I64], ctypes.c_double),
                 "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
                 "orc_sketch_bf16": ([I64, I64, I64, U64, I32, P, I64, P, I64], I32),
+                "orc_srht_perm_one": ([I32, U64, I64], I64),
+                "orc_srht_perm": ([I32, I64, U64, P], None),
+                "orc_srht_signs": ([U64, I64, I64, P], None),
+                "orc_srht_dense": ([I64, I64, I64, P, P, P, I64], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -355,6 +361,39 @@ def sparse_to_dense(s: int, m: int, zeta: int, rows, signs) -> np.ndarray:
     val = 1.0 / np.sqrt(zeta)
     cols = np.repeat(np.arange(m), zeta)
     S[np.asarray(rows), cols] = np.where(np.asarray(signs) > 0, val, -val)
+    return S
+
+
+def srht_order_log2(m: int) -> int:
+    """b of the SRHT's padded order m' = 2^b: the smallest b with 2^b >= m."""
+    b = 0
+    while (1 << b) < m:
+        b += 1
+    return b
+
+
+def srht_perm(s: int, b: int, seed: int) -> np.ndarray:
+    """Sampled rows p_0 .. p_{s-1} of the order-2^b Hadamard matrix (s <= 2^b)."""
+    p = np.zeros(s, dtype=np.int64)
+    _load().orc_srht_perm(b, s, seed, _p(p))
+    return p
+
+
+def srht_signs(m: int, seed: int, row0: int = 0) -> np.ndarray:
+    """Signs d_{row0} .. d_{row0 + m - 1} (int8, +1 or -1)."""
+    d = np.zeros(m, dtype=np.int8)
+    _load().orc_srht_signs(seed, row0, m, _p(d))
+    return d
+
+
+def srht_dense(s: int, m: int, seed: int, b: int = None, row0: int = 0) -> np.ndarray:
+    """Columns row0 .. row0 + m - 1 of the SRHT sketch S = R H D / sqrt(s)
+    (s x m, Fortran order); b defaults to srht_order_log2(row0 + m)."""
+    b = srht_order_log2(row0 + m) if b is None else b
+    p = srht_perm(s, b, seed)
+    d = srht_signs(m, seed, row0)
+    S = np.zeros((s, m), order="F")
+    _load().orc_srht_dense(s, m, row0, _p(p), _p(d), _p(S), s)
     return S
 
 

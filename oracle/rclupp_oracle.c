@@ -1,6 +1,7 @@
 /*
  * Plain FP64 CPU oracle for randomized CholeskyQR with LU partial pivoting
- * (RCLUPP, RCLUPPr) and the side-by-side paths CholeskyQR2 and LC2.
+ * (RCLUPP, RCLUPPr) and the side-by-side paths CholeskyQR2 and LC2, with the
+ * generated sketches (Gaussian, sparse-sign, subsampled randomized Hadamard).
  *
  * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite, the
  * smoke check and the benchmark's CPU-baseline leg may load this library.
@@ -966,4 +967,88 @@ void orc_sparse_sign_pattern(int64_t s, int64_t m, int zeta, uint64_t seed, int3
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i)
         orc_sparse_sign_column(seed, i, s, zeta, rows + i * zeta, signs + i * zeta);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Subsampled randomized Hadamard transform (SRHT), the third of the        */
+/* common sketches Section 3 lists next to the Gaussian sketch and          */
+/* CountSketch.  The paper gives no formula; the reading is the usual one    */
+/* (Tropp 2011; Boutsidis and Gittens 2013):                                 */
+/*   S = sqrt(m'/s) R (H / sqrt(m')) D = (1/sqrt(s)) R H D,                  */
+/* m' = 2^b >= m the padded order (X extended by zero rows), D = diag(d_i)   */
+/* with random signs d_i, H the unnormalised Sylvester-Hadamard matrix of    */
+/* order m', H(p, i) = (-1)^popcount(p AND i), and R the restriction to s    */
+/* distinct rows p_0 .. p_{s-1} drawn uniformly without replacement.  So     */
+/*   S(r, i) = d_i (-1)^popcount(p_r AND i) / sqrt(s).                       */
+/* Random draws, from Philox4x32-10 with key = seed:                        */
+/*   d_i  : bit (i mod 128) of the 128 output bits for counter              */
+/*          (q mod 2^32, q div 2^32, 0, 0x53524844), q = floor(i / 128);     */
+/*          bit k is bit (k mod 32) of word floor(k / 32); set means -1.     */
+/*   p_r  : pi(r), pi a permutation of [0, 2^b): a 4-round Feistel network   */
+/*          on b bits.  x = L 2^wr + R with widths (wl, wr) = (ceil(b/2),    */
+/*          floor(b/2)); round k = 0..3 replaces (L, R) by                    */
+/*          (R, L XOR (w0 mod 2^wl)), w0 the first word for counter          */
+/*          (R, k, b, 0x53524850), and swaps the widths.  Every round is a    */
+/*          bijection of [0, 2^b), so pi is one and p_0 .. p_{s-1} are        */
+/*          distinct.                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* pi(x) on b bits (0 <= b <= 31, 0 <= x < 2^b). */
+int64_t orc_srht_perm_one(int b, uint64_t seed, int64_t x)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int wl = (b + 1) / 2, wr = b / 2;
+    uint32_t L = (uint32_t)((uint64_t)x >> wr);
+    uint32_t R = (uint32_t)((uint64_t)x & ((1u << wr) - 1u));
+    for (uint32_t k = 0; k < 4; ++k) {
+        uint32_t ctr[4] = {R, k, (uint32_t)b, 0x53524850u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint32_t f = w[0] & ((1u << wl) - 1u);
+        uint32_t newL = R, newR = L ^ f;
+        int t = wl;
+        wl = wr;
+        wr = t;
+        L = newL;
+        R = newR;
+    }
+    return (int64_t)(((uint64_t)L << wr) | (uint64_t)R);
+}
+
+/* p[r] = pi(r), r = 0 .. s-1 (s <= 2^b): the sampled rows of H. */
+void orc_srht_perm(int b, int64_t s, uint64_t seed, int64_t *p)
+{
+    for (int64_t r = 0; r < s; ++r)
+        p[r] = orc_srht_perm_one(b, seed, r);
+}
+
+/* d[i] = d_{row0 + i}, i = 0 .. m-1 (+1 or -1). */
+void orc_srht_signs(uint64_t seed, int64_t row0, int64_t m, int8_t *d)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < m; ++i) {
+        uint64_t g = (uint64_t)(row0 + i), q = g >> 7;
+        uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), 0u, 0x53524844u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint32_t k = (uint32_t)(g & 127u);
+        d[i] = ((w[k >> 5] >> (k & 31u)) & 1u) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+/* Columns row0 .. row0 + m - 1 of S (s x m, lds): S(r, i) as defined above,
+ * with p and d from orc_srht_perm and orc_srht_signs(seed, row0, m, d). */
+void orc_srht_dense(int64_t s, int64_t m, int64_t row0, const int64_t *p, const int8_t *d,
+                    double *S, int64_t lds)
+{
+    double scale = 1.0 / sqrt((double)s);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        uint64_t g = (uint64_t)(row0 + i);
+        for (int64_t r = 0; r < s; ++r) {
+            int odd = __builtin_popcountll((uint64_t)p[r] & g) & 1;
+            double h = odd ? -1.0 : 1.0;
+            IDX(S, lds, r, i) = (d[i] < 0 ? -h : h) * scale;
+        }
+    }
 }
