@@ -90,7 +90,7 @@ def _load():
                 "orc_srht_perm_one": ([I32, U64, I64], I64),
                 "orc_srht_perm": ([I32, I64, U64, P], None),
                 "orc_srht_signs": ([U64, I64, I64, P], None),
-                "orc_srht_dense": ([I64, I64, I64, P, P, P, I64], None),
+                "orc_srht_dense": ([I64, I64, I64, I64, P, P, P, I64], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -389,11 +389,18 @@ def srht_signs(m: int, seed: int, row0: int = 0) -> np.ndarray:
 def srht_dense(s: int, m: int, seed: int, b: int = None, row0: int = 0) -> np.ndarray:
     """Columns row0 .. row0 + m - 1 of the SRHT sketch S = R H D / sqrt(s)
     (s x m, Fortran order); b defaults to srht_order_log2(row0 + m)."""
+    return srht_dense_rows(np.arange(s), s, m, seed, b, row0)
+
+
+def srht_dense_rows(rows, s: int, m: int, seed: int, b: int = None, row0: int = 0) -> np.ndarray:
+    """Rows `rows` (indices into 0 .. s-1) of the s-row SRHT sketch, columns
+    row0 .. row0 + m - 1 (len(rows) x m, Fortran order)."""
     b = srht_order_log2(row0 + m) if b is None else b
-    p = srht_perm(s, b, seed)
+    p = np.ascontiguousarray(srht_perm(s, b, seed)[np.asarray(rows, dtype=np.int64)])
     d = srht_signs(m, seed, row0)
-    S = np.zeros((s, m), order="F")
-    _load().orc_srht_dense(s, m, row0, _p(p), _p(d), _p(S), s)
+    k = len(p)
+    S = np.zeros((k, m), order="F")
+    _load().orc_srht_dense(k, s, m, row0, _p(p), _p(d), _p(S), k)
     return S
 
 

@@ -1036,16 +1036,19 @@ void orc_srht_signs(uint64_t seed, int64_t row0, int64_t m, int8_t *d)
     }
 }
 
-/* Columns row0 .. row0 + m - 1 of S (s x m, lds): S(r, i) as defined above,
- * with p and d from orc_srht_perm and orc_srht_signs(seed, row0, m, d). */
-void orc_srht_dense(int64_t s, int64_t m, int64_t row0, const int64_t *p, const int8_t *d,
-                    double *S, int64_t lds)
+/* k rows and columns row0 .. row0 + m - 1 of S (k x m, lds) for a sketch of
+ * s rows: row t is S(r, .) for the sampled Hadamard row p[t] = p_r, so
+ * S(t, i) = d_i (-1)^popcount(p[t] AND (row0 + i)) / sqrt(s), with p from
+ * orc_srht_perm (all s rows, or a selection) and d from
+ * orc_srht_signs(seed, row0, m, d). */
+void orc_srht_dense(int64_t k, int64_t s, int64_t m, int64_t row0, const int64_t *p,
+                    const int8_t *d, double *S, int64_t lds)
 {
     double scale = 1.0 / sqrt((double)s);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         uint64_t g = (uint64_t)(row0 + i);
-        for (int64_t r = 0; r < s; ++r) {
+        for (int64_t r = 0; r < k; ++r) {
             int odd = __builtin_popcountll((uint64_t)p[r] & g) & 1;
             double h = odd ? -1.0 : 1.0;
             IDX(S, lds, r, i) = (d[i] < 0 ? -h : h) * scale;

@@ -126,3 +126,9 @@ def test_rclupp_with_srht_sketch():
     assert st == 0
     assert oracle.orthogonality(q) < 1e-14
     assert oracle.residual(x, q, r) < 1e-15
+
+
+def test_selected_rows_are_rows_of_whole():
+    full = oracle.srht_dense(40, 123, 8)
+    rows = [0, 7, 39, 12]
+    np.testing.assert_array_equal(oracle.srht_dense_rows(rows, 40, 123, 8), full[rows])
