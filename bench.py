@@ -52,6 +52,18 @@ METRIC = "TSQR GFLOP/s (2mn^2 model) & roofline fraction, mixed vs FP64 at equal
 FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9  # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 
 
+def _hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU type (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
+
+
 def workload_config():
     return {
         "workload": "FP64 RCLUPP + RCLUPPr + CholeskyQR2 + LC2 side by side, one tall-skinny X",
@@ -73,7 +85,7 @@ def parse():
     p.add_argument("--accuracy-sweep", action="store_true",
                    help="also report orthogonality/residual at kappa 1e10 and 1e15")
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "trsm_emu", "sketch_gauss",
-                                      "sketch_sparse", "lu", "rclupp"],
+                                      "sketch_sparse", "sketch_srht", "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
     p.add_argument("--workload", choices=["side_by_side", "precision", "batched", "small",
                                           "large_sparse"],
@@ -81,6 +93,8 @@ def parse():
                    help="precision: FP64 vs tensor-core sketch RCLUPP at m=2^22, n=256, s=512; "
                         "batched: 512 uneven RCLUPP problems in one batched call")
     p.add_argument("--prec", type=int, default=0, help="precision tier for --case runs")
+    p.add_argument("--kind", type=int, default=0, help="sketch kind for --case rclupp (0 Gaussian, "
+                   "1 sparse-sign, 2 SRHT)")
     p.add_argument("--m", type=int, default=1 << 18)
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--reps", type=int, default=3)
@@ -632,10 +646,12 @@ def run_case(args):
             rq.rclupp_sketch(X, s=2 * n, seed=1, prec=args.prec)
         elif args.case == "sketch_sparse":
             rq.rclupp_sketch(X, s=2 * n, kind=rq.SKETCH_SPARSE_SIGN, zeta=8, seed=1)
+        elif args.case == "sketch_srht":
+            rq.rclupp_sketch(X, s=2 * n, kind=rq.SKETCH_SRHT, seed=1)
         elif args.case == "lu":
             rq.rclupp_tall_lupp(X)
         elif args.case == "rclupp":
-            rq.rclupp_factor(X, s=2 * n, seed=1, prec=args.prec)
+            rq.rclupp_factor(X, s=2 * n, seed=1, prec=args.prec, kind=args.kind)
 
     one()  # first call: workspace, tensor maps, module load
     torch.cuda.synchronize()
@@ -658,6 +674,10 @@ def run_case(args):
     if flops:
         line["gflops"] = flops / (total * 1e-3) / 1e9
         line["frac_fp64_peak"] = line["gflops"] / FP64_PEAK_GFLOPS
+    if args.case.startswith("sketch"):
+        # the sketches read X once: 8 m n algorithmic bytes
+        line["gbs"] = 8.0 * m * n / (total * 1e-3) / 1e9
+        line["frac_hbm_peak"] = line["gbs"] / HBM_PEAK_GBS
     print(json.dumps(line))
 
 

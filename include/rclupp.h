@@ -51,8 +51,11 @@ typedef enum {
 } rclupp_status_t;
 
 typedef enum {
-    RCLUPP_SKETCH_GAUSSIAN = 0,   /* S = G / sqrt(s), G standard Gaussian (Section 3) */
-    RCLUPP_SKETCH_SPARSE_SIGN = 1 /* zeta distinct rows per column, +-1/sqrt(zeta)   */
+    RCLUPP_SKETCH_GAUSSIAN = 0,    /* S = G / sqrt(s), G standard Gaussian (Section 3) */
+    RCLUPP_SKETCH_SPARSE_SIGN = 1, /* zeta distinct rows per column, +-1/sqrt(zeta);
+                                      zeta = 1 is CountSketch (Section 3)          */
+    RCLUPP_SKETCH_SRHT = 2         /* subsampled randomized Hadamard transform
+                                      S = R H D / sqrt(s) (Section 3)              */
 } rclupp_sketch_kind_t;
 
 /* Precision form.  The sketch only has to be an embedding (Section 3): the
@@ -63,7 +66,8 @@ typedef enum {
  * x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums are combined in
  * binary64.  EMULATED adds binary64-emulating tensor-core products for the
  * solves and the first Gram.  Other steps stay in binary64.  The sparse-sign
- * sketch only adds and always runs in binary64; an explicit S requires
+ * and SRHT sketches only add and always run in binary64 (their results report
+ * RCLUPP_PREC_FP64 as the tier used); an explicit S requires
  * RCLUPP_PREC_FP64 or one of the emulated tiers (whose sketch is then binary64). */
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
@@ -75,7 +79,7 @@ typedef enum {
                                     split-bf16 products on the tensor cores; the final-pass Gram,
                                     the diagonal blocks of the solves and the n x n
                                     factorizations stay in binary64.  An explicit S or the
-                                    sparse-sign sketch keeps a binary64 sketch. */
+                                    sparse-sign or SRHT sketch keeps a binary64 sketch. */
     RCLUPP_PREC_EMULATED_ALL = 4 /* EMULATED, and the final-pass Gram (C5; for RCholeskyQR its
                                     one Gram) emulated as well: its digit products are exact and
                                     are summed exactly in fp32 windows, then in int64 and
@@ -83,11 +87,15 @@ typedef enum {
 } rclupp_precision_t;
 
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
- *   kind  : Gaussian or sparse-sign.
+ *   kind  : Gaussian, sparse-sign or SRHT.
  *   s     : sketch size, n <= s <= 4096 (the paper uses s = O(n), e.g. n+1 or 2n).
  *   zeta  : nonzeros per column for the sparse-sign sketch (1 <= zeta <= s, <= 16).
  *   seed  : key of the counter-based generator (Philox4x32-10) for S.
  *   prec  : precision of the sketch product (rclupp_precision_t).
+ *   order_log2 : SRHT only: b of the Hadamard order m' = 2^b (0 <= b <= 31);
+ *           0 takes the smallest power of two >= m (for rclupp_sketch_rows,
+ *           >= row0 + m).  A row-sharded sketch passes the whole matrix's b.
+ *           Requires m (row0 + m) <= 2^b and s <= 2^b.
  *   S/lds : optional explicit dense sketch (DEVICE, s x m, column-major); when
  *           non-NULL it replaces the generated one (kind and seed are ignored).
  * The generated S: entry (r, i) depends only on (seed, r, i), so S is never
@@ -96,14 +104,27 @@ typedef enum {
  * (w2, w3) rows 4b+2, 4b+3 by the Box-Muller transform, evaluated in binary32
  * with series for ln and sin/cos; S = z / sqrt(s).  Sparse-sign: Philox words
  * with counter (i mod 2^32, i div 2^32, block, 0x53535047) propose rows
- * floor(w s / 2^32), duplicates skipped, sign from the lowest bit. */
+ * floor(w s / 2^32), duplicates skipped, sign from the lowest bit.
+ * SRHT: S(r, i) = d_i (-1)^popcount(p_r AND i) / sqrt(s), i.e. rows p_r of
+ * the Sylvester-Hadamard matrix of order 2^b times random signs, A padded
+ * with zero rows.  d_i = -1 when bit (i mod 128) of the 128 output bits of
+ * Philox with counter (q mod 2^32, q div 2^32, 0, 0x53524844), q = i div 128,
+ * is set (bit k = bit k mod 32 of word k div 32).  p_r = pi(r) for a keyed
+ * permutation pi of [0, 2^b): four Feistel rounds on x = L 2^wr + R with
+ * widths (wl, wr) = (ceil(b/2), floor(b/2)), each mapping (L, R) to
+ * (R, L XOR (w0 mod 2^wl)), w0 the first Philox word for counter
+ * (R, round, b, 0x53524850), then swapping the widths; so the s rows are
+ * distinct.  The product runs in binary64 at every precision tier: the
+ * transform of each 256-row block is exact in integers (entries rounded to
+ * 53 bits relative to the block's largest), the sampled values are summed in
+ * binary64. */
 typedef struct {
     int32_t kind;
     int32_t zeta;
     int64_t s;
     uint64_t seed;
     int32_t prec;
-    int32_t reserved;
+    int32_t order_log2;
     const double *S;
     int64_t lds;
 } rclupp_opts_t;

@@ -21,7 +21,7 @@ import threading
 from . import _build
 
 __all__ = [
-    "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN",
+    "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN", "SKETCH_SRHT",
     "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED", "PREC_EMULATED_ALL",
     "load", "library_path", "exported_symbols", "workspace_size", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
@@ -34,7 +34,7 @@ __all__ = [
     "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
 ]
 
-SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN = 0, 1
+SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN, SKETCH_SRHT = 0, 1, 2
 PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED, PREC_EMULATED_ALL = 0, 1, 2, 3, 4
 
 
@@ -53,7 +53,7 @@ class Status:
 class Opts(ctypes.Structure):
     """rclupp_opts_t: sketch kind, zeta, s, seed, precision, optional explicit S."""
     _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_int32), ("s", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("order_log2", ctypes.c_int32),
                 ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
 
 
@@ -121,7 +121,7 @@ _SIGNATURES = {
 
 KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
                   "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc",
-                  "gram_emu", "emu_aux", "trsm_emu"]
+                  "gram_emu", "emu_aux", "trsm_emu", "sketch_srht"]
 
 
 def profile_enable(on: bool = True) -> None:
@@ -278,13 +278,14 @@ def _handle(t) -> Handle:
     return h
 
 
-def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None):
+def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None, order_log2=0):
     o = Opts()
     o.kind = int(kind)
     o.zeta = int(zeta)
     o.s = int(s if s is not None else 2 * n)
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     o.prec = int(prec)
+    o.order_log2 = int(order_log2)
     if S is not None:
         S, lds = colmajor(S)
         o.S = S.data_ptr()
@@ -362,14 +363,15 @@ def scholqr3_factor(X, *, Q=None, R=None, check=True):
 # ---------------------------------------------------------------- steps
 
 def rclupp_sketch(A, *, s, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
-                  unit_lower=False, Y=None, row0=0):
+                  unit_lower=False, Y=None, row0=0, order_log2=0):
     """Y = S A (s x n); with row0 > 0, A is the row block starting at global
-    row row0 of a taller matrix and Y its partial sketch."""
+    row row0 of a taller matrix and Y its partial sketch.  order_log2: the
+    SRHT's Hadamard order 2^b (0: the smallest power of two >= row0 + m)."""
     A, lda = colmajor(A)
     m, n = A.shape
     Y = empty_colmajor(s, n, A.device) if Y is None else Y
     Y, ldy = colmajor(Y)
-    o, S_keep = _opts(kind=kind, s=s, zeta=zeta, seed=seed, prec=prec, S=S, n=n)
+    o, S_keep = _opts(kind=kind, s=s, zeta=zeta, seed=seed, prec=prec, S=S, n=n, order_log2=order_log2)
     st = load().rclupp_sketch_rows(_handle(A).bind(), m, n, _ptr(A), lda, int(row0),
                                    int(bool(unit_lower)), ctypes.byref(o), _ptr(Y), ldy)
     _raise("rclupp_sketch", st)

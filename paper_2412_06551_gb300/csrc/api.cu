@@ -230,8 +230,17 @@ rclupp_opts_t resolve_opts(const rclupp_opts_t *opts, int64_t n) {
 
 rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
     if (o.s < n || o.s > kMaxS) return o.s < n ? RCLUPP_ERR_ARG : RCLUPP_ERR_UNSUPPORTED;
-    if (o.kind != RCLUPP_SKETCH_GAUSSIAN && o.kind != RCLUPP_SKETCH_SPARSE_SIGN) return RCLUPP_ERR_ARG;
+    if (o.kind != RCLUPP_SKETCH_GAUSSIAN && o.kind != RCLUPP_SKETCH_SPARSE_SIGN &&
+        o.kind != RCLUPP_SKETCH_SRHT)
+        return RCLUPP_ERR_ARG;
     if (o.S && o.lds < o.s) return RCLUPP_ERR_ARG;
+    if (o.kind == RCLUPP_SKETCH_SRHT && !o.S) {
+        // H of order 2^b must cover the rows and have s distinct rows to sample
+        if (o.order_log2 < 0 || o.order_log2 > 31) return RCLUPP_ERR_ARG;
+        const int b = o.order_log2 > 0 ? o.order_log2 : srht_order_log2(m);
+        if (b > 31) return RCLUPP_ERR_UNSUPPORTED;
+        if ((int64_t(1) << b) < m || (int64_t(1) << b) < o.s) return RCLUPP_ERR_ARG;
+    }
     if (o.kind == RCLUPP_SKETCH_SPARSE_SIGN && !o.S) {
         if (o.zeta < 1 || o.zeta > o.s) return RCLUPP_ERR_ARG;
         if (o.zeta > 16) return RCLUPP_ERR_UNSUPPORTED;
@@ -258,7 +267,7 @@ cudaError_t sketch_step(const Bufs &b, const double *A, int64_t lda, int64_t m, 
         return launch_sketch_tc(A, lda, m, n, unit_lower, o.s, o.seed,
                                 tier == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, b.Y, o.s, b.part, ds, s);
     return launch_sketch(A, lda, m, n, unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s,
-                         b.part, ds, s);
+                         b.part, ds, s, 0, o.order_log2);
 }
 
 // A reduced-precision sketch leaves Q1 = X R1^{-1} less well conditioned
@@ -378,8 +387,9 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
     // the Gaussian sketch is generated, else in binary64)
     const bool emulated = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     int tier = o.prec;
-    if (emulated)
-        tier = (o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S) ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64;
+    if (emulated) tier = RCLUPP_PREC_SKETCH_BF16;
+    // only the generated Gaussian sketch has reduced tiers; the others are binary64
+    if (o.kind != RCLUPP_SKETCH_GAUSSIAN || o.S) tier = RCLUPP_PREC_FP64;
     for (;;) {
         if (sketch_step(b, SA, ldsa, m, n, unit_lower, o, tier, h->d_status, h->stream) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
@@ -416,7 +426,7 @@ rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int
                                const double *X, int64_t ldx, double *Q, int64_t ldq, double *R,
                                int64_t ldr) {
     RQ_TRY(launch_sketch(X, ldx, m, n, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
-                         c.st, c.s));
+                         c.st, c.s, 0, o.order_log2));
     RQ_TRY(launch_sketch_precond(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 1,
                                  c.s));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
@@ -432,7 +442,7 @@ rclupp_status_t enqueue_rcluppr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     RQ_TRY(copy_matrix(L, ldl, X, ldx, m, n, c.s));
     RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
     RQ_TRY(launch_sketch(L, ldl, m, n, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
-                         c.st, c.s));
+                         c.st, c.s, 0, o.order_log2));
     RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
@@ -924,7 +934,7 @@ rclupp_status_t rclupp_sketch_rows(rclupp_handle_t h, int64_t m, int64_t n, cons
     if (!h || !A || !Y || n < 1 || m < 1 || row0 < 0 || bad_ld(lda, m)) return RCLUPP_ERR_ARG;
     if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
     const rclupp_opts_t o = resolve_opts(opts, n);
-    rclupp_status_t st = check_opts(o, m, n);
+    rclupp_status_t st = check_opts(o, row0 + m, n);
     if (st != RCLUPP_OK) return st;
     if (bad_ld(ldy, o.s)) return RCLUPP_ERR_ARG;
     Bufs b = prepare(h, m, int(n), o.s, false, &st);
@@ -936,7 +946,7 @@ rclupp_status_t rclupp_sketch_rows(rclupp_handle_t h, int64_t m, int64_t n, cons
                              h->stream, row0);
     else
         e = launch_sketch(A, lda, m, int(n), unit_lower, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, Y,
-                          ldy, b.part, h->d_status, h->stream, row0);
+                          ldy, b.part, h->d_status, h->stream, row0, o.order_log2);
     return finish(h, from_cuda(e), nullptr, nullptr);
 }
 

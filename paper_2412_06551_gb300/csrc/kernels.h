@@ -55,13 +55,22 @@ cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, con
                              double *part, DevStatus *st, cudaStream_t stream);
 
 // Y = S A (s x n, ldy); kind 0 Gaussian (generated from seed, or explicit S
-// when S != nullptr), kind 1 sparse-sign.
+// when S != nullptr), kind 1 sparse-sign, kind 2 subsampled randomized
+// Hadamard of order 2^srht_b (srht_b = 0: the smallest power of two >= row0 + m).
 // row0: global index of A's first row, for the generated sketches (entry
 // (r, row0 + i) of S multiplies row i of A); 0 for a whole matrix.
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int kind,
                           int64_t s, int zeta, uint64_t seed, const double *S, int64_t lds,
                           double *Y, int64_t ldy, double *part, DevStatus *st,
-                          cudaStream_t stream, int64_t row0 = 0);
+                          cudaStream_t stream, int64_t row0 = 0, int srht_b = 0);
+
+// The SRHT sketch (srht.cu): S = R H D / sqrt(s) with H of order 2^b,
+// b >= srht_order_log2(row0 + m), s <= 2^b; partials in `part` as for
+// launch_sketch, then the fixed-order reduction into Y.
+int srht_order_log2(int64_t rows);
+cudaError_t launch_sketch_srht(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int64_t s,
+                               uint64_t seed, int b, double *Y, int64_t ldy, double *part,
+                               cudaStream_t stream, int64_t row0);
 
 // Fixed-order sum of sketch partials: Y[r][c] = sum_p part[p][c*s_pad + r].
 cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, int s_pad, int n_pad,
@@ -191,6 +200,7 @@ enum KernelId : int {
     KID_GRAM_EMU,
     KID_EMU_AUX,
     KID_TRSM_EMU,
+    KID_SKETCH_SRHT,
     KID_COUNT
 };
 

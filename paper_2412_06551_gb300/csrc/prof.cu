@@ -45,7 +45,7 @@ const char *kNames[KID_COUNT] = {"sketch_gauss", "sketch_sparse", "gram",       
                                  "trsm",         "reduce",        "lu_col",     "lu_trailing",
                                  "lu_u12",       "small_precond", "cholesky",   "trmm",
                                  "pad",          "sketch_tc",     "gram_emu",   "emu_aux",
-                                 "trsm_emu"};
+                                 "trsm_emu",     "sketch_srht"};
 
 }  // namespace
 

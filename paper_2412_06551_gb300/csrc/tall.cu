@@ -772,7 +772,11 @@ size_t sketch_partials_doubles(int64_t m, int n, int64_t s, int kind) {
 cudaError_t launch_sketch(const double *A, int64_t lda, int64_t m, int n, int unit_lower, int kind,
                           int64_t s, int zeta, uint64_t seed, const double *S, int64_t lds,
                           double *Y, int64_t ldy, double *part, DevStatus *st,
-                          cudaStream_t stream, int64_t row0) {
+                          cudaStream_t stream, int64_t row0, int srht_b) {
+    if (kind == 2 && S == nullptr)
+        return launch_sketch_srht(A, lda, m, n, unit_lower, s, seed,
+                                  srht_b > 0 ? srht_b : srht_order_log2(row0 + m), Y, ldy, part, stream,
+                                  row0);
     const int s_pad = static_cast<int>(round_up(s, 64));
     const int n_pad = static_cast<int>(round_up(n, 32));
     cudaError_t e;
