@@ -21,7 +21,7 @@ from __future__ import annotations
 
 from typing import Callable, Optional
 
-from . import (SKETCH_GAUSSIAN, RclupError, Status, rclupp_cholesky, rclupp_gram,
+from . import (SKETCH_GAUSSIAN, SKETCH_SRHT, RclupError, Status, rclupp_cholesky, rclupp_gram,
                rclupp_sketch, rclupp_sketch_precond, rclupp_trmm_upper, rclupp_trsm_gram)
 
 __all__ = ["LibrarySteps", "torch_allreduce", "rclupp_factor_sharded", "cholqr2_factor_sharded",
@@ -38,8 +38,8 @@ def row_block(m: int, world: int, rank: int) -> tuple[int, int]:
 class LibrarySteps:
     """The per-rank steps on the rank's GPU through the C ABI."""
 
-    def sketch(self, A, *, s, kind, zeta, seed, row0):
-        return rclupp_sketch(A, s=s, kind=kind, zeta=zeta, seed=seed, row0=row0)
+    def sketch(self, A, *, s, kind, zeta, seed, row0, order_log2=0):
+        return rclupp_sketch(A, s=s, kind=kind, zeta=zeta, seed=seed, row0=row0, order_log2=order_log2)
 
     def precond(self, Y):
         return rclupp_sketch_precond(Y)
@@ -81,18 +81,26 @@ def _cholesky_or_raise(steps, G, pass_no):
 
 def rclupp_factor_sharded(X_local, row0: int, *, s: Optional[int] = None, kind: int = SKETCH_GAUSSIAN,
                           zeta: int = 8, seed: int = 0, steps=None, allreduce: Optional[Callable] = None,
-                          group=None):
+                          group=None, order_log2: int = 0):
     """[Q_local, R] = RCLUPP(X) (Algorithm 6) with X split by rows over the
     ranks.  X_local: this rank's rows (row0 .. row0 + m_r - 1), column-major
     on the rank's GPU.  The generated sketch is the one the whole matrix
     would get (entry (r, i) depends on the global row i), so the result
-    equals the single-GPU factorization up to the order of the sums."""
+    equals the single-GPU factorization up to the order of the sums.  The
+    SRHT needs the whole matrix's Hadamard order: order_log2 = b with
+    2^b >= m (every rank passes the same b)."""
     steps = steps or LibrarySteps()
     allreduce = allreduce or torch_allreduce(group)
     n = X_local.shape[1]
     s = 2 * n if s is None else s
+    sk = dict(s=s, kind=kind, zeta=zeta, seed=seed, row0=row0)
+    if kind == SKETCH_SRHT:
+        if order_log2 <= 0:
+            raise ValueError("the SRHT of a row-sharded matrix needs order_log2 = ceil(log2(m)) "
+                             "of the whole matrix")
+        sk["order_log2"] = order_log2
     # step 1: X_s = S X as a sum of the ranks' partials (all-reduce 1)
-    Y = allreduce(steps.sketch(X_local, s=s, kind=kind, zeta=zeta, seed=seed, row0=row0))
+    Y = allreduce(steps.sketch(X_local, **sk))
     # steps 2-4 on every rank: LU of X_s, Householder R of M, R1 = R0 N
     R1 = steps.precond(Y)
     # steps 5-7: CholeskyQR2 of Q1 = X R1^{-1} (all-reduces 2 and 3)

@@ -107,3 +107,16 @@ def test_two_blocks_summed_on_one_gpu(rq):
     q, r = host(Q), host(R)
     assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
     assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
+
+
+def test_single_rank_driver_srht_equals_single_call(rq):
+    import oracle as orc
+    from paper_2412_06551_gb300 import distributed as D
+    m, n = 7000, 40
+    x = synth.svd_matrix(m, n, 1e6, 77)
+    X = dev(x)
+    b = orc.srht_order_log2(m)
+    Q, R = D.rclupp_factor_sharded(X, 0, s=2 * n, seed=13, kind=rq.SKETCH_SRHT, order_log2=b,
+                                   allreduce=lambda t: t)
+    Q1, R1, _ = rq.rclupp_factor(X, s=2 * n, seed=13, kind=rq.SKETCH_SRHT)
+    assert torch.equal(R, R1) and torch.equal(Q, Q1)

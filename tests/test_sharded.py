@@ -138,6 +138,14 @@ def test_cholqr2_sharded_two_allreduces():
     assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * 1e3
 
 
+def test_srht_needs_the_whole_matrix_order():
+    from paper_2412_06551_gb300 import distributed as D
+    import paper_2412_06551_gb300 as rq
+    with pytest.raises(ValueError):
+        D.rclupp_factor_sharded(np.zeros((10, 2)), 0, kind=rq.SKETCH_SRHT, steps=OracleSteps(None),
+                                allreduce=lambda a: a)
+
+
 def test_row_block_partition():
     from paper_2412_06551_gb300.distributed import row_block
     for m in (1, 7, 100, 3001):
