@@ -67,14 +67,15 @@ def _load():
                 "orc_trmm_upper": ([I64, P, I64, P, I64, P, I64], None),
                 "orc_gepp": ([I64, I64, P, I64, P, P], I32),
                 "orc_householder_r": ([I64, I64, P, I64, P, I64], None),
+                "orc_givens_r": ([I64, I64, P, I64, P, I64], None),
                 "orc_sketch_dense": ([I64, I64, I64, P, I64, P, I64, P, I64], None),
                 "orc_sketch_sparse": ([I64, I64, I64, I32, P, P, P, I64, P, I64], None),
-                "orc_sketch_precond": ([I64, I64, P, I64, P, I64, P], I32),
+                "orc_sketch_precond": ([I64, I64, P, I64, P, I64, P, I32], I32),
                 "orc_cholqr": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
                 "orc_cholqr2": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
                 "orc_lc2": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
-                "orc_rclupp": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P], I32),
-                "orc_rcluppr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P], I32),
+                "orc_rclupp": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P, I32], I32),
+                "orc_rcluppr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P, I32], I32),
                 "orc_philox4x32_10": ([P, P, P], None),
                 "orc_ln_f32": ([ctypes.c_float], ctypes.c_float),
                 "orc_cossin_2pi_f32": ([ctypes.c_float, P, P], None),
@@ -82,7 +83,7 @@ def _load():
                 "orc_gaussian_sketch_matrix": ([I64, I64, U64, P, I64], None),
                 "orc_sparse_sign_column": ([U64, I64, I64, I32, P, P], None),
                 "orc_sparse_sign_pattern": ([I64, I64, I32, U64, P, P], None),
-                "orc_rcholqr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P], I32),
+                "orc_rcholqr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P, I32], I32),
                 "orc_scholqr3": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
                 "orc_scholqr3_shift": ([I64, I64, P, I64], ctypes.c_double),
                 "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
@@ -218,13 +219,26 @@ def sketch_sparse(s: int, zeta: int, rows, signs, x) -> np.ndarray:
     return y
 
 
-def sketch_precond(y, raise_on_error: bool = True):
-    """R1 from the sketched matrix (Algorithm 6 steps 2-4 + sign fix). Returns (R1, status, info)."""
+R0_METHODS = {"householder": 0, "givens": 1}
+
+
+def givens_r(a) -> np.ndarray:
+    """R-factor of A (s x n) by Givens rotations, bottom-up per column."""
+    a = _f(a)
+    s, n = a.shape
+    r = np.zeros((n, n), order="F")
+    _load().orc_givens_r(s, n, _p(a), s, _p(r), n)
+    return r
+
+
+def sketch_precond(y, raise_on_error: bool = True, r0: str = "householder"):
+    """R1 from the sketched matrix (Algorithm 6 steps 2-4 + sign fix), R0 by
+    Householder (the paper's choice) or Givens rotations. Returns (R1, status, info)."""
     y = _f(y)
     s, n = y.shape
     r1 = np.zeros((n, n), order="F")
     info = np.zeros(1, dtype=np.int64)
-    st = _load().orc_sketch_precond(s, n, _p(y), s, _p(r1), n, _p(info))
+    st = _load().orc_sketch_precond(s, n, _p(y), s, _p(r1), n, _p(info), R0_METHODS[r0])
     _check(st, info, raise_on_error)
     return r1, st, int(info[0])
 
@@ -264,7 +278,7 @@ def lc2(x, raise_on_error: bool = True):
     return q, r, st
 
 
-def _rand_driver(fn, x, S=None, sparse=None, raise_on_error=True):
+def _rand_driver(fn, x, S=None, sparse=None, raise_on_error=True, r0="householder"):
     x = _f(x)
     m, n = x.shape
     q, r, info = _qr_out(m, n)
@@ -274,29 +288,30 @@ def _rand_driver(fn, x, S=None, sparse=None, raise_on_error=True):
         rows = np.ascontiguousarray(rows, dtype=np.int32)
         signs = np.ascontiguousarray(signs, dtype=np.int8)
         st = getattr(lib, fn)(m, n, _p(x), m, SKETCH_SPARSE, s, zeta, None, 0, _p(rows), _p(signs),
-                              _p(q), m, _p(r), n, _p(info))
+                              _p(q), m, _p(r), n, _p(info), R0_METHODS[r0])
     else:
         S = _f(S)
         s = S.shape[0]
         st = getattr(lib, fn)(m, n, _p(x), m, SKETCH_DENSE, s, 0, _p(S), s, None, None,
-                              _p(q), m, _p(r), n, _p(info))
+                              _p(q), m, _p(r), n, _p(info), R0_METHODS[r0])
     _check(st, info, raise_on_error)
     return q, r, st
 
 
-def rclupp(x, S=None, sparse=None, raise_on_error: bool = True):
-    """[Q, R] = RCLUPP(X) (Algorithm 6) with dense S or sparse=(s, zeta, rows, signs)."""
-    return _rand_driver("orc_rclupp", x, S, sparse, raise_on_error)
+def rclupp(x, S=None, sparse=None, raise_on_error: bool = True, r0: str = "householder"):
+    """[Q, R] = RCLUPP(X) (Algorithm 6) with dense S or sparse=(s, zeta, rows, signs);
+    r0 = "householder" (the paper's choice) or "givens" for the R-factor R0."""
+    return _rand_driver("orc_rclupp", x, S, sparse, raise_on_error, r0)
 
 
-def rcluppr(x, S=None, sparse=None, raise_on_error: bool = True):
+def rcluppr(x, S=None, sparse=None, raise_on_error: bool = True, r0: str = "householder"):
     """[Q, R] = RCLUPPr(X) (Algorithm 7) with dense S or sparse=(s, zeta, rows, signs)."""
-    return _rand_driver("orc_rcluppr", x, S, sparse, raise_on_error)
+    return _rand_driver("orc_rcluppr", x, S, sparse, raise_on_error, r0)
 
 
-def rcholqr(x, S=None, sparse=None, raise_on_error: bool = True):
+def rcholqr(x, S=None, sparse=None, raise_on_error: bool = True, r0: str = "householder"):
     """[Q, R] = RCholeskyQR(X) (Algorithm 5, one sketch, one CholeskyQR)."""
-    return _rand_driver("orc_rcholqr", x, S, sparse, raise_on_error)
+    return _rand_driver("orc_rcholqr", x, S, sparse, raise_on_error, r0)
 
 
 def scholqr3(x, raise_on_error: bool = True):

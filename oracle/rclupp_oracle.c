@@ -274,6 +274,58 @@ void orc_householder_r(int64_t s, int64_t n, const double *A, int64_t lda, doubl
     free(W);
 }
 
+/* R-factor of A (s x n, s >= n) by Givens rotations, the alternative to the
+ * thin HouseholderQR that Section 1 and the remark after Algorithm 5 allow
+ * for the preconditioning step.  Column by column (k = 0..n-1), the entries
+ * below the diagonal are annihilated from the bottom up: rows (i-1, i) for
+ * i = s-1 down to k+1 are rotated by
+ *     [ c  s' ] [ a ]   [ r ]
+ *     [-s' c  ] [ b ] = [ 0 ],   r = hypot(a, b), c = a / r, s' = b / r,
+ * (no rotation when b = 0), applied to columns k+1..n-1 of the two rows;
+ * column k becomes (r, 0).
+ * r >= 0, so the diagonal is non-negative wherever the column below it was
+ * not already zero.  R = the upper n x n part. */
+void orc_givens_r(int64_t s, int64_t n, const double *A, int64_t lda, double *R, int64_t ldr)
+{
+    double *W = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < s; ++i)
+            W[i + j * s] = IDX(A, lda, i, j);
+    for (int64_t k = 0; k < n; ++k) {
+        for (int64_t i = s - 1; i > k; --i) {
+            double a = W[(i - 1) + k * s], b = W[i + k * s];
+            if (b == 0.0)
+                continue;
+            double r = hypot(a, b);
+            double c = a / r, sn = b / r;
+            for (int64_t j = k + 1; j < n; ++j) {
+                double x = W[(i - 1) + j * s], y = W[i + j * s];
+                W[(i - 1) + j * s] = c * x + sn * y;
+                W[i + j * s] = c * y - sn * x;
+            }
+            W[(i - 1) + k * s] = r;
+            W[i + k * s] = 0.0;
+        }
+    }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i)
+            IDX(R, ldr, i, j) = i <= j ? W[i + j * s] : 0.0;
+    free(W);
+}
+
+/* R-factor methods of the preconditioning step. */
+#define ORC_R0_HOUSEHOLDER 0
+#define ORC_R0_GIVENS 1
+
+static void orc_r0(int method, int64_t s, int64_t n, const double *A, int64_t lda, double *R,
+                   int64_t ldr)
+{
+    if (method == ORC_R0_GIVENS)
+        orc_givens_r(s, n, A, lda, R, ldr);
+    else
+        orc_householder_r(s, n, A, lda, R, ldr);
+}
+
 /* Y = S X with an explicit dense sketch S (s x m, leading dimension lds)
  * (Algorithm 6 step 1, Algorithm 7 step 2; eq. (es)).
  * Y[r][j] = sum_{i=0..m-1} S[r][i] X[i][j], summed in increasing i. */
@@ -425,7 +477,7 @@ static int orc_precond_then_cholqr2(int64_t m, int64_t n, const double *X, int64
  *   [M, N, P] = LU(Y); R0 = R-factor of HouseholderQR(M); R1 = R0 N;
  * then the diagonal sign normalisation of R1.  Y is not modified. */
 int orc_sketch_precond(int64_t s, int64_t n, const double *Y, int64_t ldy, double *R1,
-                       int64_t ldr, int64_t *info)
+                       int64_t ldr, int64_t *info, int r0_method)
 {
     double *A = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
     double *M = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
@@ -441,7 +493,7 @@ int orc_sketch_precond(int64_t s, int64_t n, const double *Y, int64_t ldy, doubl
         if (st == ORC_OK) {
             orc_extract_unit_lower(s, n, A, s, M, s);
             orc_extract_upper(n, A, s, N, n);
-            orc_householder_r(s, n, M, s, R0, n);
+            orc_r0(r0_method, s, n, M, s, R0, n);
             orc_trmm_upper(n, R0, n, N, n, R1, ldr);
             orc_sign_fix_rows(n, R1, ldr);
         }
@@ -474,7 +526,7 @@ static void orc_apply_sketch(int kind, int64_t s, int64_t m, int64_t n, int zeta
  * *info: LU failure -> column; Cholesky failure -> 100000*pass + column. */
 int orc_rclupp(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int64_t s, int zeta,
                const double *S, int64_t lds, const int32_t *rows, const int8_t *signs, double *Q,
-               int64_t ldq, double *R, int64_t ldr, int64_t *info)
+               int64_t ldq, double *R, int64_t ldr, int64_t *info, int r0_method)
 {
     if (m < n || n < 1 || s < n)
         return ORC_ERR_ARG;
@@ -483,7 +535,7 @@ int orc_rclupp(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int
     int st = ORC_ERR_NOMEM;
     if (Y && R1) {
         orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, X, ldx, Y, s);
-        st = orc_sketch_precond(s, n, Y, s, R1, n, info);
+        st = orc_sketch_precond(s, n, Y, s, R1, n, info, r0_method);
         if (st == ORC_OK)
             st = orc_precond_then_cholqr2(m, n, X, ldx, R1, Q, ldq, R, ldr, info);
     }
@@ -498,7 +550,7 @@ int orc_rclupp(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int
  * M is the m x n unit-lower factor in the row order GEPP leaves it. */
 int orc_rcluppr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int64_t s, int zeta,
                 const double *S, int64_t lds, const int32_t *rows, const int8_t *signs, double *Q,
-                int64_t ldq, double *R, int64_t ldr, int64_t *info)
+                int64_t ldq, double *R, int64_t ldr, int64_t *info, int r0_method)
 {
     if (m < n || n < 1 || s < n)
         return ORC_ERR_ARG;
@@ -519,7 +571,7 @@ int orc_rcluppr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, in
             orc_extract_unit_lower(m, n, A, m, M, m);
             orc_extract_upper(n, A, m, N, n);
             orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, M, m, Ms, s);
-            orc_householder_r(s, n, Ms, s, R0, n);
+            orc_r0(r0_method, s, n, Ms, s, R0, n);
             orc_trmm_upper(n, R0, n, N, n, R1, n);
             orc_sign_fix_rows(n, R1, n);
             st = orc_precond_then_cholqr2(m, n, X, ldx, R1, Q, ldq, R, ldr, info);
@@ -603,7 +655,7 @@ int orc_lc2(int64_t m, int64_t n, const double *X, int64_t ldx, double *Q, int64
  *   Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1. */
 int orc_rcholqr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int64_t s, int zeta,
                 const double *S, int64_t lds, const int32_t *rows, const int8_t *signs, double *Q,
-                int64_t ldq, double *R, int64_t ldr, int64_t *info)
+                int64_t ldq, double *R, int64_t ldr, int64_t *info, int r0_method)
 {
     if (m < n || n < 1 || s < n)
         return ORC_ERR_ARG;
@@ -617,7 +669,7 @@ int orc_rcholqr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, in
     int64_t col = -1;
     if (K && R1 && Q1 && G && Z) {
         orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, X, ldx, K, s);
-        orc_householder_r(s, n, K, s, R1, n);
+        orc_r0(r0_method, s, n, K, s, R1, n);
         orc_sign_fix_rows(n, R1, n);
         orc_trsm_right_upper(m, n, X, ldx, R1, n, Q1, m);
         orc_gram(m, n, Q1, m, G, n);

@@ -200,6 +200,68 @@ def test_householder_skips_zero_subcolumn():
     assert r[1, 1] < 0
 
 
+# ---------------------------------------------------------------- Givens ---
+# The alternative R-factor of Section 1 and the remark after Algorithm 5.
+
+@pytest.mark.parametrize("s,n", [(2, 1), (6, 3), (40, 17), (128, 64), (300, 128)])
+def test_givens_r_is_lapack_r_with_nonnegative_diagonal(s, n):
+    # s > n: every column has a subcolumn to rotate, so the diagonal is positive
+    a = np.random.default_rng(s + 7 * n).standard_normal((s, n))
+    r = oracle.givens_r(a)
+    r_ref = np.triu(np.linalg.qr(a, mode="r")[:n])
+    r_ref = np.sign(np.diag(r_ref))[:, None] * r_ref   # the unique positive-diagonal R
+    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+    assert np.max(np.abs(r - r_ref)) <= 1e-13 * np.max(np.abs(r_ref))
+
+
+def test_givens_r_brute_force_mpmath():
+    for seed, (s, n) in enumerate([(5, 3), (9, 8), (12, 6)]):
+        a = np.random.default_rng(100 + seed).standard_normal((s, n))
+        _, r_mp = _mp_qr(a)
+        r = oracle.givens_r(a)
+        assert np.max(np.abs(r - r_mp)) <= 4e-15 * np.max(np.abs(r_mp)), (s, n)
+
+
+def test_givens_r_closed_forms():
+    # one column: r = ||a||; (3, 4) -> 5 exactly (hypot is exact there)
+    assert oracle.givens_r(np.array([[3.0], [4.0]]))[0, 0] == 5.0
+    a = np.random.default_rng(3).standard_normal((50, 1))
+    assert abs(oracle.givens_r(a)[0, 0] - np.linalg.norm(a)) <= 4e-15 * np.linalg.norm(a)
+    # an input that is already upper triangular needs no rotation: R = its top block
+    u = np.triu(np.random.default_rng(4).standard_normal((6, 4)))
+    u[:4][np.diag_indices(4)] = np.abs(np.diag(u[:4])) + 1.0
+    assert np.array_equal(oracle.givens_r(u), u[:4])
+    # a zero subcolumn keeps its diagonal sign (no rotation), like Householder's H_k = I
+    a = np.array([[-2.0, 1.0], [0.0, 3.0], [0.0, 4.0]])
+    r = oracle.givens_r(a)
+    assert r[0, 0] == -2.0 and r[0, 1] == 1.0 and r[1, 1] == 5.0
+
+
+def test_givens_r_invariant_and_householder_agreement():
+    a = synth.svd_matrix(64, 10, 1e5, 4)
+    rg, rh = oracle.givens_r(a), oracle.householder_r(a)
+    assert np.allclose(rg.T @ rg, a.T @ a, atol=1e-14)
+    d = np.sign(np.diag(rh))[:, None]
+    assert np.max(np.abs(rg - d * rh)) <= 1e-13 * np.max(np.abs(rh))
+
+
+@pytest.mark.parametrize("name", ["rclupp", "rcluppr", "rcholqr"])
+def test_drivers_with_givens_r0_match_householder(name):
+    m, n = 2000, 24
+    x = synth.svd_matrix(m, n, 1e6, 8)
+    S = synth.gaussian_sketch(2 * n, m, 9)
+    fn = getattr(oracle, name)
+    qg, rg, st = fn(x, S=S, r0="givens")
+    qh, rh, _ = fn(x, S=S)
+    assert st == 0
+    assert oracle.orthogonality(qg) <= max(2 * oracle.orthogonality(qh), 1e-14)
+    assert oracle.residual(x, qg, rg) <= max(2 * oracle.residual(x, qh, rh), 1e-15)
+    assert np.linalg.norm(rg - rh) / np.linalg.norm(rh) <= 1e-10 * 1e6
+    r1g, _, _ = oracle.sketch_precond(oracle.sketch_dense(S, x), r0="givens")
+    r1h, _, _ = oracle.sketch_precond(oracle.sketch_dense(S, x))
+    assert np.max(np.abs(r1g - r1h)) <= 1e-12 * np.max(np.abs(r1h))
+
+
 # --------------------------------------------------------------- sketches ---
 
 def test_sketch_dense_exact_on_integers():
