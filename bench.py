@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--accuracy-sweep", action="store_true",
                    help="also report orthogonality/residual at kappa 1e10 and 1e15")
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "trsm_emu", "sketch_gauss",
-                                      "sketch_sparse", "sketch_srht", "lu", "rclupp"],
+                                      "sketch_sparse", "sketch_srht", "precond", "lu", "rclupp"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
     p.add_argument("--workload", choices=["side_by_side", "precision", "batched", "small",
                                           "large_sparse"],
@@ -95,6 +95,8 @@ def parse():
     p.add_argument("--prec", type=int, default=0, help="precision tier for --case runs")
     p.add_argument("--kind", type=int, default=0, help="sketch kind for --case rclupp (0 Gaussian, "
                    "1 sparse-sign, 2 SRHT)")
+    p.add_argument("--r0", type=int, default=0, help="R0 method for --case rclupp / precond "
+                   "(0 Householder, 1 Givens)")
     p.add_argument("--m", type=int, default=1 << 18)
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--reps", type=int, default=3)
@@ -631,6 +633,8 @@ def run_case(args):
     X = to_dev(x, torch, device)
     R = to_dev(np.triu(synth.rng(3).standard_normal((n, n))) / math.sqrt(n) + 2 * np.eye(n), torch,
                device)
+    Yp = rq.rclupp_sketch(X, s=2 * n, seed=1) if args.case == "precond" else None
+
     def one():
         if args.case == "trsm_gram":
             rq.rclupp_trsm_gram(X, R)
@@ -650,8 +654,10 @@ def run_case(args):
             rq.rclupp_sketch(X, s=2 * n, kind=rq.SKETCH_SRHT, seed=1)
         elif args.case == "lu":
             rq.rclupp_tall_lupp(X)
+        elif args.case == "precond":
+            rq.rclupp_sketch_precond(Yp, r0=args.r0)
         elif args.case == "rclupp":
-            rq.rclupp_factor(X, s=2 * n, seed=1, prec=args.prec, kind=args.kind)
+            rq.rclupp_factor(X, s=2 * n, seed=1, prec=args.prec, kind=args.kind, r0=args.r0)
 
     one()  # first call: workspace, tensor maps, module load
     torch.cuda.synchronize()

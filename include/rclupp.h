@@ -86,6 +86,13 @@ typedef enum {
                                     binary64, so the accumulation stays binary64 or better */
 } rclupp_precision_t;
 
+/* R-factor of the preconditioning step (Algorithm 6 step 3, Algorithm 7 step
+ * 3, Algorithm 5 step 2). */
+typedef enum {
+    RCLUPP_R0_HOUSEHOLDER = 0, /* thin HouseholderQR, LAPACK larfg signs (the paper's choice) */
+    RCLUPP_R0_GIVENS = 1       /* Givens rotations, r = hypot(a, b) >= 0 (Section 1)         */
+} rclupp_r0_method_t;
+
 /* Sketch options of the randomized algorithms (RCLUPP, RCLUPPr).
  *   kind  : Gaussian, sparse-sign or SRHT.
  *   s     : sketch size, n <= s <= 4096 (the paper uses s = O(n), e.g. n+1 or 2n).
@@ -98,6 +105,13 @@ typedef enum {
  *           Requires m (row0 + m) <= 2^b and s <= 2^b.
  *   S/lds : optional explicit dense sketch (DEVICE, s x m, column-major); when
  *           non-NULL it replaces the generated one (kind and seed are ignored).
+ *   r0_method : R-factor R0 of the preconditioning step (rclupp_r0_method_t):
+ *           Householder (default, the paper's choice) or Givens rotations
+ *           (the alternative of Section 1 and of the remark after Algorithm 5);
+ *           Givens needs the s x n matrix to fit a cluster's shared memory
+ *           (s n <= 25600 doubles per CTA, up to 8 CTAs), else
+ *           RCLUPP_ERR_UNSUPPORTED.
+ *   reserved : 0.
  * The generated S: entry (r, i) depends only on (seed, r, i), so S is never
  * stored.  Gaussian: Philox4x32-10 with counter (i mod 2^32, i div 2^32,
  * r div 4, 0x53474155) and key = seed; words (w0, w1) serve rows 4b, 4b+1 and
@@ -127,6 +141,8 @@ typedef struct {
     int32_t order_log2;
     const double *S;
     int64_t lds;
+    int32_t r0_method;
+    int32_t reserved;
 } rclupp_opts_t;
 
 /* Diagnostic output of a factorization (may be NULL). */
@@ -358,6 +374,23 @@ rclupp_status_t rclupp_tall_lupp(rclupp_handle_t handle, int64_t m, int64_t n, d
  * signs normalised.  Y is not modified.  Errors: ERR_LU_ZERO_PIVOT. */
 rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t n,
                                       const double *Y, int64_t ldy, double *R1, int64_t ldr);
+
+/* rclupp_sketch_precond with the R-factor R0 chosen by r0_method
+ * (rclupp_r0_method_t).  Givens: per column a tree of rotations over the
+ * rows (each CTA's rows, then the CTAs' head rows), r = hypot(a, b) >= 0,
+ * c = a / r, s = b / r; needs the matrix to fit a cluster's shared memory
+ * (else RCLUPP_ERR_UNSUPPORTED). */
+rclupp_status_t rclupp_sketch_precond_r0(rclupp_handle_t handle, int64_t s, int64_t n,
+                                         const double *Y, int64_t ldy, int32_t r0_method, double *R1,
+                                         int64_t ldr);
+
+/* R-factor of an s x n matrix A by Givens rotations (Section 1; remark after
+ * Algorithm 5), as one cluster of CTAs: rows of R with a negative diagonal
+ * entry (possible only where the subcolumn below it was already zero) are
+ * negated, so R has a non-negative diagonal.  A not modified.  The matrix
+ * must fit a cluster's shared memory, else RCLUPP_ERR_UNSUPPORTED. */
+rclupp_status_t rclupp_givens_r(rclupp_handle_t handle, int64_t s, int64_t n, const double *A,
+                                int64_t lda, double *R, int64_t ldr);
 
 /* R-factor of the Householder QR of an s x n matrix A (Algorithm 5 step 2,
  * Algorithm 6 step 3): LAPACK larfg sign convention, A not modified. */

@@ -22,6 +22,7 @@ from . import _build
 
 __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN", "SKETCH_SRHT",
+    "R0_HOUSEHOLDER", "R0_GIVENS", "rclupp_givens_r",
     "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED", "PREC_EMULATED_ALL",
     "load", "library_path", "exported_symbols", "workspace_size", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
@@ -35,6 +36,7 @@ __all__ = [
 ]
 
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN, SKETCH_SRHT = 0, 1, 2
+R0_HOUSEHOLDER, R0_GIVENS = 0, 1
 PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED, PREC_EMULATED_ALL = 0, 1, 2, 3, 4
 
 
@@ -54,7 +56,8 @@ class Opts(ctypes.Structure):
     """rclupp_opts_t: sketch kind, zeta, s, seed, precision, optional explicit S."""
     _fields_ = [("kind", ctypes.c_int32), ("zeta", ctypes.c_int32), ("s", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32), ("order_log2", ctypes.c_int32),
-                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64)]
+                ("S", ctypes.c_void_p), ("lds", ctypes.c_int64), ("r0_method", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -107,6 +110,8 @@ _SIGNATURES = {
     "rclupp_tall_lupp": ([_P, _I64, _I64, _P, _I64, _P, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_givens_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_sketch_precond_r0": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "rclupp_factor_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "rclupp_set_batch_branches": ([_P, _I32], _I32),
@@ -278,8 +283,10 @@ def _handle(t) -> Handle:
     return h
 
 
-def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None, order_log2=0):
+def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None, order_log2=0,
+          r0=R0_HOUSEHOLDER):
     o = Opts()
+    o.r0_method = int(r0)
     o.kind = int(kind)
     o.zeta = int(zeta)
     o.s = int(s if s is not None else 2 * n)
@@ -325,17 +332,17 @@ def _factor(fn_name, X, sketch=True, Q=None, R=None, check=True, **kw):
 
 
 def rclupp_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
-                  Q=None, R=None, check=True):
+                  Q=None, R=None, check=True, r0=R0_HOUSEHOLDER, order_log2=0):
     """[Q, R] = RCLUPP(X) (Algorithm 6).  Returns (Q, R, Info)."""
     return _factor("rclupp_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
-                   prec=prec, S=S)
+                   prec=prec, S=S, r0=r0, order_log2=order_log2)
 
 
 def rclupp_r_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
-                    Q=None, R=None, check=True):
+                    Q=None, R=None, check=True, r0=R0_HOUSEHOLDER, order_log2=0):
     """[Q, R] = RCLUPPr(X) (Algorithm 7).  Returns (Q, R, Info)."""
     return _factor("rclupp_r_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
-                   prec=prec, S=S)
+                   prec=prec, S=S, r0=r0, order_log2=order_log2)
 
 
 def cholqr2_factor(X, *, Q=None, R=None, check=True):
@@ -349,10 +356,10 @@ def lc2_factor(X, *, Q=None, R=None, check=True):
 
 
 def rcholqr_factor(X, *, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0, prec=PREC_FP64, S=None,
-                   Q=None, R=None, check=True):
+                   Q=None, R=None, check=True, r0=R0_HOUSEHOLDER, order_log2=0):
     """[Q, R] = RCholeskyQR(X) (Algorithm 5, one sketch, one CholeskyQR)."""
     return _factor("rcholqr_factor", X, True, Q, R, check, s=s, kind=kind, zeta=zeta, seed=seed,
-                   prec=prec, S=S)
+                   prec=prec, S=S, r0=r0, order_log2=order_log2)
 
 
 def scholqr3_factor(X, *, Q=None, R=None, check=True):
@@ -417,22 +424,22 @@ ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2, ALGO_RCHOLQR, ALGO_SCHOLQR3 =
 
 
 def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
-                          Qs=None, Rs=None, check=True, prec=PREC_FP64):
+                          Qs=None, Rs=None, check=True, prec=PREC_FP64, r0=R0_HOUSEHOLDER):
     """Factor a list of column-major matrices in one batched call (one CUDA
     graph).  s is a per-problem list (or None for 2 n); seed is a list or an
     int (then seed + i for problem i); prec is PREC_FP64 or an emulated tier
     (binary64 sketch).  Returns (Qs, Rs, statuses)."""
-    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec)
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec, r0)
     st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
     _raise("rclupp_factor_batched", st, None, check)
     return a["Qs"], a["Rs"], a["status"]
 
 
 def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,
-                            Qs=None, Rs=None, prec=PREC_FP64):
+                            Qs=None, Rs=None, prec=PREC_FP64, r0=R0_HOUSEHOLDER):
     """Time the batch over candidate branch counts and keep the fastest in
     the handle.  Returns (branches, ms of one batched call)."""
-    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec)
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec, r0)
     best = ctypes.c_int32(0)
     ms = ctypes.c_float(0.0)
     st = load().rclupp_autotune_batched(a["h"], int(algo), a["count"], *a["args"], ctypes.byref(best),
@@ -441,7 +448,7 @@ def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIA
     return int(best.value), float(ms.value)
 
 
-def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0):
+def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0, r0=0):
     import numpy as np
     count = len(Xs)
     Xs = [colmajor(x) for x in Xs]
@@ -465,6 +472,7 @@ def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0):
         opts[i].s = int(s[i] if s is not None else 2 * n[i])
         opts[i].seed = int(seed[i] if isinstance(seed, (list, tuple)) else seed + i)
         opts[i].prec = int(prec)
+        opts[i].r0_method = int(r0)
         opts[i].S = None
         opts[i].lds = 0
     status = np.zeros(count, dtype=np.int32)
@@ -557,14 +565,28 @@ def rclupp_tall_lupp(A, *, check=True):
     return LU, ipiv, st, int(col.value)
 
 
-def rclupp_sketch_precond(Y):
-    """R1 from a sketched matrix (Algorithm 6 steps 2-4, signs normalised)."""
+def rclupp_sketch_precond(Y, r0=R0_HOUSEHOLDER):
+    """R1 from a sketched matrix (Algorithm 6 steps 2-4, signs normalised),
+    R0 by Householder (default) or Givens rotations."""
     Y, ldy = colmajor(Y)
     s, n = Y.shape
     R1 = empty_colmajor(n, n, Y.device)
-    st = load().rclupp_sketch_precond(_handle(Y).bind(), s, n, _ptr(Y), ldy, _ptr(R1), n)
+    if r0 == R0_HOUSEHOLDER:
+        st = load().rclupp_sketch_precond(_handle(Y).bind(), s, n, _ptr(Y), ldy, _ptr(R1), n)
+    else:
+        st = load().rclupp_sketch_precond_r0(_handle(Y).bind(), s, n, _ptr(Y), ldy, int(r0), _ptr(R1), n)
     _raise("rclupp_sketch_precond", st)
     return R1
+
+
+def rclupp_givens_r(A):
+    """R-factor of A by Givens rotations (non-negative diagonal)."""
+    A, lda = colmajor(A)
+    s, n = A.shape
+    R = empty_colmajor(n, n, A.device)
+    st = load().rclupp_givens_r(_handle(A).bind(), s, n, _ptr(A), lda, _ptr(R), n)
+    _raise("rclupp_givens_r", st)
+    return R
 
 
 def rclupp_householder_r(A):

@@ -253,6 +253,10 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
         return RCLUPP_ERR_ARG;
     if ((o.prec == RCLUPP_PREC_SKETCH_BF16 || o.prec == RCLUPP_PREC_SKETCH_FP32) && o.S)
         return RCLUPP_ERR_UNSUPPORTED;
+    if (o.r0_method != RCLUPP_R0_HOUSEHOLDER && o.r0_method != RCLUPP_R0_GIVENS) return RCLUPP_ERR_ARG;
+    // the Givens R0 runs in the cluster form only (the s x n matrix in shared memory)
+    if (o.r0_method == RCLUPP_R0_GIVENS && !precond_cluster_fits(int(o.s), int(n), true))
+        return RCLUPP_ERR_UNSUPPORTED;
     (void)m;
     return RCLUPP_OK;
 }
@@ -428,7 +432,7 @@ rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int
     RQ_TRY(launch_sketch(X, ldx, m, n, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
                          c.st, c.s, 0, o.order_log2));
     RQ_TRY(launch_sketch_precond(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 1,
-                                 c.s));
+                                 c.s, o.r0_method));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
     if (st != RCLUPP_OK) return st;
@@ -443,7 +447,7 @@ rclupp_status_t enqueue_rcluppr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
     RQ_TRY(launch_sketch(L, ldl, m, n, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
                          c.st, c.s, 0, o.order_log2));
-    RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s));
+    RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s, o.r0_method));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
     if (st != RCLUPP_OK) return st;
@@ -474,7 +478,7 @@ rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     const int np = pad16(n);
     // K = S X; R1 = R of HouseholderQR(K)
     RQ_TRY(sketch_step(b, X, ldx, m, n, 0, o, tier, c.st, c.s));
-    RQ_TRY(launch_rcholqr_r1(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], c.s));
+    RQ_TRY(launch_rcholqr_r1(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], c.s, o.r0_method));
     // Q1 = X R1^{-1}; [Q, Z] = CholeskyQR(Q1); R = Z R1
     // the one CholeskyQR's Gram is the final-pass Gram: emulated only when
     // the caller asked for every Gram emulated (o.prec; `tier` is the sketch's)
@@ -636,7 +640,8 @@ rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const dou
     // X_s = S X (step 1); [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M);
     // R1 = R0 N (steps 2-4); then steps 5-7
     auto precond = [&]() {
-        return launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s);
+        return launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s,
+                                     o.r0_method);
     };
     const rclupp_status_t ls =
         randomized_tail(h, b, o, m, ni, X, ldx, 0, precond, X, ldx, Q, ldq, R, ldr, &tier);
@@ -675,7 +680,7 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
         // M_s = S M (step 2); R0 = R of HouseholderQR(M_s); R1 = R0 N (steps 3-4);
         // then steps 5-7.  Q1 overwrites the LU only after M_s is formed.
         auto precond = [&]() {
-            return launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s);
+            return launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s, o.r0_method);
         };
         ls = randomized_tail(h, b, o, m, ni, L, ldl, 1, precond, X, ldx, Q, ldq, R, ldr, &tier);
     } while (0);
@@ -1055,6 +1060,34 @@ rclupp_status_t rclupp_sketch_precond(rclupp_handle_t h, int64_t s, int64_t n, c
     if (st != RCLUPP_OK) return st;
     const cudaError_t e = launch_sketch_precond(Y, ldy, int(s), int(n), b.W, b.RP[0], b.rinv[0], R1,
                                                 ldr, h->d_status, 1, h->stream);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_sketch_precond_r0(rclupp_handle_t h, int64_t s, int64_t n, const double *Y,
+                                         int64_t ldy, int32_t r0_method, double *R1, int64_t ldr) {
+    if (!h || !Y || !R1 || n < 1 || s < n || bad_ld(ldy, s) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (r0_method != RCLUPP_R0_HOUSEHOLDER && r0_method != RCLUPP_R0_GIVENS) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || s > kMaxS) return RCLUPP_ERR_UNSUPPORTED;
+    if (r0_method == RCLUPP_R0_GIVENS && !precond_cluster_fits(int(s), int(n), true))
+        return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, s, int(n), s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_sketch_precond(Y, ldy, int(s), int(n), b.W, b.RP[0], b.rinv[0], R1,
+                                                ldr, h->d_status, 1, h->stream, r0_method);
+    return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_givens_r(rclupp_handle_t h, int64_t s, int64_t n, const double *A, int64_t lda,
+                                double *R, int64_t ldr) {
+    if (!h || !A || !R || n < 1 || s < n || bad_ld(lda, s) || bad_ld(ldr, n)) return RCLUPP_ERR_ARG;
+    if (n > kMaxN || s > kMaxS || !precond_cluster_fits(int(s), int(n), true))
+        return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, s, int(n), s, false, &st);
+    if (st != RCLUPP_OK) return st;
+    const cudaError_t e = launch_givens_r(A, lda, int(s), int(n), b.W, b.RP[0], b.rinv[0], R, ldr,
+                                          h->stream);
     return finish(h, from_cuda(e), nullptr, nullptr);
 }
 

@@ -81,7 +81,9 @@ cudaError_t launch_reduce_sketch(const double *part, int nparts, int s, int n, i
 // mode 0: R1 = R(HouseholderQR(M)) N from the LU P Y = M N (Nbuf: n x n
 // scratch); mode 1: R1 = R(HouseholderQR(Y)) triu(Nsrc) (identity when
 // Nsrc == nullptr).  Outputs as launch_sketch_precond / launch_cholesky.
-bool precond_cluster_fits(int s, int n);
+// mode | kPrecondGivens: R0 by Givens rotations instead of Householder.
+constexpr int kPrecondGivens = 2;
+bool precond_cluster_fits(int s, int n, bool givens = false);
 cudaError_t launch_precond_cluster(const double *Y, int64_t ldy, int s, int n, int mode,
                                    const double *Nsrc, int64_t ldn, double *Nbuf, double *RP,
                                    double *rinv, double *R1, int64_t ldr, DevStatus *st, int step,
@@ -138,20 +140,28 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
 // R1 from the sketch Y (s x n): LU with partial pivoting, Householder R of
 // M, R1 = R0 N, diagonal signs normalised.  Writes R1 into RP/rinv (padded)
 // and, when R1 != nullptr, into R1 (ld ldr).  W: s*n*2 doubles scratch.
+// r0_method 1: R0 by Givens rotations (cluster form only; cudaErrorNotSupported
+// when the matrix does not fit a cluster's shared memory).
 cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, double *W,
                                   double *RP, double *rinv, double *R1, int64_t ldr,
-                                  DevStatus *st, int step_id, cudaStream_t stream);
+                                  DevStatus *st, int step_id, cudaStream_t stream, int r0_method = 0);
 
 // RCLUPPr's R1 from the sketched factor M_s (s x n): Householder R of M_s,
 // R1 = R0 N with N the top of the in-place tall LU (lda), signs normalised.
 // W: 2*s*n scratch.
 cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const double *LU,
                               int64_t lda, double *W, double *RP, double *rinv,
-                              cudaStream_t stream);
+                              cudaStream_t stream, int r0_method = 0);
 
 // RCholeskyQR's R1: Householder R of the sketch K (s x n), signs normalised.
 cudaError_t launch_rcholqr_r1(const double *K, int64_t ldk, int s, int n, double *W, double *RP,
-                              double *rinv, cudaStream_t stream);
+                              double *rinv, cudaStream_t stream, int r0_method = 0);
+
+// R-factor of A (s x n) by Givens rotations, rows with a negative diagonal
+// negated (only where a subcolumn was already zero), into R (ldr) and the
+// padded RP/rinv; cluster form only (cudaErrorNotSupported otherwise).
+cudaError_t launch_givens_r(const double *A, int64_t lda, int s, int n, double *W, double *RP,
+                            double *rinv, double *R, int64_t ldr, cudaStream_t stream);
 
 // Gs = G + s I with SCholeskyQR3's shift s = 11 (mnu + n(n+1)u) max_j G_jj.
 cudaError_t launch_shifted_gram(const double *G, int64_t ldg, int n, int64_t m, double *Gs,

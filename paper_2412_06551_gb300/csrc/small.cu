@@ -237,7 +237,12 @@ __global__ void __launch_bounds__(kSmallThreads)
 
 cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, double *W,
                                   double *RP, double *rinv, double *R1, int64_t ldr,
-                                  DevStatus *st, int step_id, cudaStream_t stream) {
+                                  DevStatus *st, int step_id, cudaStream_t stream, int r0_method) {
+    if (r0_method == 1) {
+        if (!precond_cluster_fits(s, n, true)) return cudaErrorNotSupported;
+        return launch_precond_cluster(Y, ldy, s, n, kPrecondGivens, nullptr, 0, W, RP, rinv, R1, ldr, st,
+                                      step_id, stream);
+    }
     if (precond_cluster_fits(s, n))  // the matrix fits a cluster's shared memory
         return launch_precond_cluster(Y, ldy, s, n, 0, nullptr, 0, W, RP, rinv, R1, ldr, st, step_id,
                                       stream);
@@ -247,7 +252,12 @@ cudaError_t launch_sketch_precond(const double *Y, int64_t ldy, int s, int n, do
 }
 
 cudaError_t launch_rcholqr_r1(const double *K, int64_t ldk, int s, int n, double *W, double *RP,
-                              double *rinv, cudaStream_t stream) {
+                              double *rinv, cudaStream_t stream, int r0_method) {
+    if (r0_method == 1) {
+        if (!precond_cluster_fits(s, n, true)) return cudaErrorNotSupported;
+        return launch_precond_cluster(K, ldk, s, n, 1 | kPrecondGivens, nullptr, 0, W, RP, rinv, nullptr,
+                                      0, nullptr, 0, stream);
+    }
     // mode 1 with N = I: R1 = R-factor of HouseholderQR(K), signs normalised
     if (precond_cluster_fits(s, n))
         return launch_precond_cluster(K, ldk, s, n, 1, nullptr, 0, W, RP, rinv, nullptr, 0, nullptr, 0,
@@ -290,7 +300,12 @@ cudaError_t launch_shifted_gram(const double *G, int64_t ldg, int n, int64_t m, 
 
 cudaError_t launch_rcluppr_r1(const double *Ms, int64_t ldm, int s, int n, const double *LU,
                               int64_t lda, double *W, double *RP, double *rinv,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, int r0_method) {
+    if (r0_method == 1) {
+        if (!precond_cluster_fits(s, n, true)) return cudaErrorNotSupported;
+        return launch_precond_cluster(Ms, ldm, s, n, 1 | kPrecondGivens, LU, lda, W, RP, rinv, nullptr, 0,
+                                      nullptr, 0, stream);
+    }
     if (precond_cluster_fits(s, n))
         return launch_precond_cluster(Ms, ldm, s, n, 1, LU, lda, W, RP, rinv, nullptr, 0, nullptr, 0,
                                       stream);
@@ -314,6 +329,13 @@ __global__ void __launch_bounds__(kSmallThreads)
         const int i = idx % n, j = idx / n;
         R[i + int64_t(j) * ldr] = (i <= j) ? W[i + int64_t(j) * s] : 0.0;
     }
+}
+
+cudaError_t launch_givens_r(const double *A, int64_t lda, int s, int n, double *W, double *RP,
+                            double *rinv, double *R, int64_t ldr, cudaStream_t stream) {
+    if (!precond_cluster_fits(s, n, true)) return cudaErrorNotSupported;
+    return launch_precond_cluster(A, lda, s, n, 1 | kPrecondGivens, nullptr, 0, W, RP, rinv, R, ldr, nullptr,
+                                  0, stream);
 }
 
 cudaError_t launch_householder_r(const double *A, int64_t lda, int s, int n, double *W, double *R,

@@ -13,6 +13,10 @@
 //   mode 1 (RCLUPPr, Algorithm 7 steps 3-4; RCholeskyQR, Algorithm 5): the
 //     Householder R of Y, R1 = R0 N with N the upper triangle of an external
 //     factor, or N = I.
+//   mode | kGivensMode: R0 by Givens rotations instead of Householder (the
+//     alternative of Section 1 and of the remark after Algorithm 5): per
+//     column a binary tree of rotations over each CTA's rows, then over the
+//     CTAs' head rows; r = hypot(a, b) >= 0, c = a / r, s = b / r.
 //   k_cholesky_cluster: upper Cholesky of an n x n Gram matrix (C2, C6),
 //     right-looking, with the same breakdown status as the one-CTA kernel.
 //
@@ -37,6 +41,7 @@ constexpr int kClMaxCtas = 8;
 constexpr size_t kClSmemBudget = 200 * 1024;
 constexpr int kClRowLanes = 128;                     // update loops: rows by tid % 128,
 constexpr int kClColLanes = kClThreads / kClRowLanes;  // columns by tid / 128
+constexpr int kGivensMode = 2;                          // mode bit: R0 by Givens rotations
 
 // Deterministic block sum (shuffle tree, then warps in order), in every thread.
 __device__ __forceinline__ double cl_block_sum(double v, double *red) {
@@ -96,6 +101,7 @@ struct ClShared {
     int piv_g;
     double sigma;
     double beta, tau, scal;  // reflector scalars of the current column
+    double gc, gs;           // rotation of the current cross-CTA pair
 };
 
 // Cluster-wide barrier and remote shared-memory pointers; a single CTA
@@ -142,6 +148,8 @@ __global__ void __launch_bounds__(kClThreads)
     const int tid = threadIdx.x, T = blockDim.x;
     const int r0 = rank * h;
     const int rows = max(0, min(h, s - r0));
+    const bool givens = (mode & kGivensMode) != 0;
+    mode &= ~kGivensMode;
 
     for (int idx = tid; idx < h * n; idx += T) {
         const int i = idx % h, j = idx / h;
@@ -233,6 +241,82 @@ __global__ void __launch_bounds__(kClThreads)
         __syncthreads();
     }
 
+    if (givens) {
+        // ---- R0 by Givens rotations.  Column k: a tree over this slab's rows
+        // g >= k (round d rotates rows lo + 2dq and lo + 2dq + d, zeroing the
+        // second's entry), then a tree over the CTAs' head rows.
+        double *gc = pw + n;                 // cosines of the current round
+        double *gsn = gc + (h + 2) / 2;      // sines
+        for (int k = 0; k < n; ++k) {
+            const int lo = max(0, k - r0);
+            const int cnt = rows - lo;       // the same in every thread of this CTA
+            for (int d = 1; d < cnt; d <<= 1) {
+                const int np = (cnt - d + 2 * d - 1) / (2 * d);
+                for (int p = tid; p < np; p += T) {
+                    const int top = lo + 2 * d * p, bot = top + d;
+                    const double a = A[top + size_t(k) * h], b = A[bot + size_t(k) * h];
+                    double c = 1.0, sn = 0.0;
+                    if (b != 0.0) {
+                        const double r = hypot(a, b);
+                        c = a / r;
+                        sn = b / r;
+                        A[top + size_t(k) * h] = r;
+                        A[bot + size_t(k) * h] = 0.0;
+                    }
+                    gc[p] = c;
+                    gsn[p] = sn;
+                }
+                __syncthreads();
+                // pairs by the low bits of tid, columns by the high bits
+                int pl = 1;
+                while (pl < np && pl < T) pl <<= 1;
+                const int psh = __ffs(pl) - 1;
+                for (int p = tid & (pl - 1); p < np; p += pl) {
+                    const double c = gc[p], sn = gsn[p];
+                    if (sn == 0.0) continue;
+                    const int top = lo + 2 * d * p, bot = top + d;
+                    for (int j = k + 1 + (tid >> psh); j < n; j += T >> psh) {
+                        const double x = A[top + size_t(j) * h], y = A[bot + size_t(j) * h];
+                        A[top + size_t(j) * h] = c * x + sn * y;
+                        A[bot + size_t(j) * h] = c * y - sn * x;
+                    }
+                }
+                __syncthreads();
+            }
+            if (C > 1) {
+                Cl::sync();  // every CTA's tree is done
+                const int rk = k / h, last = (s - 1) / h;
+                for (int d = 1; rk + d <= last; d <<= 1) {
+                    if (rank >= rk && (rank - rk) % (2 * d) == 0 && rank + d <= last) {
+                        // the head of CTA rank + d is its local row 0 (its rows are all > k)
+                        double *B = Cl::at(A, rank + d);
+                        if (tid == 0) {
+                            const double a = A[lo + size_t(k) * h], b = B[size_t(k) * h];
+                            double c = 1.0, sn = 0.0;
+                            if (b != 0.0) {
+                                const double r = hypot(a, b);
+                                c = a / r;
+                                sn = b / r;
+                                A[lo + size_t(k) * h] = r;
+                                B[size_t(k) * h] = 0.0;
+                            }
+                            sh.gc = c;
+                            sh.gs = sn;
+                        }
+                        __syncthreads();
+                        const double c = sh.gc, sn = sh.gs;
+                        if (sn != 0.0)
+                            for (int j = k + 1 + tid; j < n; j += T) {
+                                const double x = A[lo + size_t(j) * h], y = B[size_t(j) * h];
+                                A[lo + size_t(j) * h] = c * x + sn * y;
+                                B[size_t(j) * h] = c * y - sn * x;
+                            }
+                    }
+                    Cl::sync();  // the pair's rows are final before the next round reads them
+                }
+            }
+        }
+    } else {
     // ---- Householder R of the slab matrix (eq. (eh), larfg convention)
     for (int k = 0; k < n; ++k) {
         const int rk = k / h;
@@ -305,6 +389,7 @@ __global__ void __launch_bounds__(kClThreads)
         __syncthreads();
         if (rank == rk && tid == 0) A[(k - rk * h) + size_t(k) * h] = beta;
         __syncthreads();
+    }
     }
     Cl::sync();  // Nbuf written by every CTA before any reads it
 
@@ -424,10 +509,10 @@ __global__ void __launch_bounds__(kClThreads)
 }
 
 // Smallest power-of-two cluster whose slabs fit the shared-memory budget.
-bool cl_shape(int rows, int n, int extra_vectors, int &C, int &h, size_t &smem) {
+bool cl_shape(int rows, int n, int extra_vectors, int &C, int &h, size_t &smem, bool per_row = false) {
     for (C = 1; C <= kClMaxCtas; C *= 2) {
         h = (rows + C - 1) / C;
-        smem = (size_t(h) * n + size_t(extra_vectors) * n) * sizeof(double);
+        smem = (size_t(h) * n + size_t(extra_vectors) * n + (per_row ? size_t(h) + 2 : 0)) * sizeof(double);
         if (smem <= kClSmemBudget) return true;
     }
     return false;
@@ -462,10 +547,10 @@ cudaError_t cl_launch(K1 k1, KC kc, int C, size_t smem, cudaStream_t stream, Arg
 
 }  // namespace
 
-bool precond_cluster_fits(int s, int n) {
+bool precond_cluster_fits(int s, int n, bool givens) {
     int C, h;
     size_t smem;
-    return cl_shape(s, n, 3, C, h, smem);
+    return cl_shape(s, n, 3, C, h, smem, givens);
 }
 
 cudaError_t launch_precond_cluster(const double *Y, int64_t ldy, int s, int n, int mode,
@@ -474,7 +559,7 @@ cudaError_t launch_precond_cluster(const double *Y, int64_t ldy, int s, int n, i
                                    cudaStream_t stream) {
     int C, h;
     size_t smem;
-    if (!cl_shape(s, n, 3, C, h, smem)) return cudaErrorInvalidValue;
+    if (!cl_shape(s, n, 3, C, h, smem, (mode & kGivensMode) != 0)) return cudaErrorInvalidValue;
     cudaError_t e;
     RQ_LAUNCH(KID_SMALL_PRECOND, stream,
               e = cl_launch(k_precond_cluster<false>, k_precond_cluster<true>, C, smem, stream, Y, ldy,
