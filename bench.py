@@ -235,12 +235,21 @@ def to_dev(a, torch, device):
     return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()
 
 
+def run_path(rq, name, X, Q, R):
+    if name == "rclupp":
+        rq.rclupp_factor(X, s=S_SKETCH, seed=SEED_S, Q=Q, R=R)
+    elif name == "rcluppr":
+        rq.rclupp_r_factor(X, s=S_SKETCH, seed=SEED_S, Q=Q, R=R)
+    elif name == "cholqr2":
+        rq.cholqr2_factor(X, Q=Q, R=R)
+    else:
+        rq.lc2_factor(X, Q=Q, R=R)
+
+
 def run_paths(rq, X, outs, torch):
     Qs, Rs = outs
-    rq.rclupp_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[0], R=Rs[0])
-    rq.rclupp_r_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[1], R=Rs[1])
-    rq.cholqr2_factor(X, Q=Qs[2], R=Rs[2])
-    rq.lc2_factor(X, Q=Qs[3], R=Rs[3])
+    for i, name in enumerate(PATHS):
+        run_path(rq, name, X, Qs[i], Rs[i])
 
 
 def accuracy(torch, X, Q, R):
@@ -491,14 +500,7 @@ def run_ours(args):
     for i, name in enumerate(PATHS):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if name == "rclupp":
-            rq.rclupp_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[0], R=Rs[0])
-        elif name == "rcluppr":
-            rq.rclupp_r_factor(X, s=S_SKETCH, seed=SEED_S, Q=Qs[1], R=Rs[1])
-        elif name == "cholqr2":
-            rq.cholqr2_factor(X, Q=Qs[2], R=Rs[2])
-        else:
-            rq.lc2_factor(X, Q=Qs[3], R=Rs[3])
+        run_path(rq, name, X, Qs[i], Rs[i])
         e1.record(stream)
         e1.synchronize()
         path_ms[name] = e0.elapsed_time(e1)
@@ -529,20 +531,49 @@ def run_ours(args):
     value = job_throughput(model_flops, args.steps, t_ms, world)
 
     # ---- end to end: pinned host X in, Q and R of every path out ----
+    # Copies run on a second stream: the next step's X is uploaded into the
+    # other of two device buffers and each path's Q, R are read back while the
+    # next path computes; events order every buffer's reuse.
     xh = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T)).pin_memory()
-    Xd = torch.empty((N, M), dtype=torch.float64, device=device)
+    Xd = [torch.empty((N, M), dtype=torch.float64, device=device) for _ in range(2)]
     qh = [torch.empty((N, M), dtype=torch.float64).pin_memory() for _ in PATHS]
     rh = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in PATHS]
     e2e_steps = max(2, min(args.steps, 5))
+    copy_s = torch.cuda.Stream(device)
+    ev = lambda: torch.cuda.Event()
+    x_ready, x_free = [ev(), ev()], [ev(), ev()]
+    out_free = [ev() for _ in PATHS]
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(e2e_steps):
-        Xd.copy_(xh, non_blocking=True)
-        run_paths(rq, Xd.t(), (Qs, Rs), torch)
-        for i in range(len(PATHS)):
-            qh[i].copy_(Qs[i].t(), non_blocking=True)
-            rh[i].copy_(Rs[i].t(), non_blocking=True)
+    copy_s.wait_event(f0)
+    with torch.cuda.stream(copy_s):
+        Xd[0].copy_(xh, non_blocking=True)
+        x_ready[0].record(copy_s)
+    for k in range(e2e_steps):
+        b = k % 2
+        stream.wait_event(x_ready[b])
+        if k + 1 < e2e_steps:  # upload the next step's X meanwhile
+            with torch.cuda.stream(copy_s):
+                if k >= 1:
+                    copy_s.wait_event(x_free[1 - b])
+                Xd[1 - b].copy_(xh, non_blocking=True)
+                x_ready[1 - b].record(copy_s)
+        for i, name in enumerate(PATHS):
+            if k >= 1:
+                stream.wait_event(out_free[i])  # the previous step's Q, R are read back
+            run_path(rq, name, Xd[b].t(), Qs[i], Rs[i])
+            done = ev()
+            done.record(stream)
+            with torch.cuda.stream(copy_s):
+                copy_s.wait_event(done)
+                qh[i].copy_(Qs[i].t(), non_blocking=True)
+                rh[i].copy_(Rs[i].t(), non_blocking=True)
+                out_free[i].record(copy_s)
+        x_free[b].record(stream)
+    last = ev()
+    last.record(copy_s)
+    stream.wait_event(last)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, device)
@@ -589,8 +620,15 @@ def run_ours(args):
         "sketch_gauss": 2.0 * S_SKETCH * M * N,
     }
     ach = per_launch_flops.get(dom, float("nan")) / (avg_ms / 1e3) / 1e9
+    # DRAM bytes per launch from one ncu capture of the same kernel at m = 262144
+    # (dram__bytes_read.sum + dram__bytes_write.sum = 268.7 + 235.7 MB), scaled
+    # by the rows processed to this workload's m; traffic grows with m.
+    traffic = {"trsm_gram": (268.7e6 + 235.7e6) * (M / 262144)}.get(dom)
     roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "traffic_source": "ncu, m=262144 capture scaled x%g (profiles/trsm_gram_fp64_m262144_n128.md); "
+                                  "algorithmic 16 m n = %.3g bytes" % (M / 262144, 16.0 * M * N)
+                if traffic else None,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
                 "avg_launch_ms": avg_ms, "launches": dom_launches}
     kernel_share = {k: round(v[1] / sum(w[1] for w in tot.values()), 4) for k, v in tot.items()}

@@ -1,6 +1,6 @@
 // Triangular solve Q = A R^{-1} with its block products emulating binary64 on
-// the tensor cores (the precision form of eq. (ewy) / C3, C7), n <= 128 (the
-// 32-column form of emu_trsm32.cu serves larger n): substitution by
+// the tensor cores (the precision form of eq. (ewy) / C3, C7), n <= 160 (the
+// 32-column form of emu_trsm32.cu serves n > 160): substitution by
 // 16-column blocks, the off-diagonal block products as split-bf16 products
 // with exact fp32 sums, the diagonal blocks solved in binary64).
 //
@@ -276,7 +276,7 @@ cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, cons
                             const double *rinv, double *Q, int64_t ldq, void *scratch,
                             DevStatus *st, cudaStream_t stream) {
     if (n < 1 || n > 256 || m < 1) return cudaErrorInvalidValue;
-    if (n > 128)  // wide blocks: fewer re-split K-chunks per row tile
+    if (n > 160)  // wide blocks: fewer re-split K-chunks per row tile (16 columns win up to n = 160)
         return launch_trsm_emu32(A, lda, m, n, RP, rinv, Q, ldq, scratch, st, stream);
     const int n_pad = pad16(n);
     const int nblk = (n + kTeB - 1) / kTeB;
