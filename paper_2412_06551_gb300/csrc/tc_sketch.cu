@@ -118,7 +118,31 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         }
         __syncthreads();
         if (abort_flag) break;
-        // (1) S block: entry (r, i) for 128 sketch rows x 32 rows of X
+        // (0) this stage's X block into registers first: its loads complete
+        // while the threads generate S (the longest part of a stage)
+        // tasks of 8 rows x 1 column: nt * 4 of them, at most 4 per thread
+        const int ntasks = nt * (kTcBK / 8);
+        double xv[4][8];
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int task = tid + kTcThreads * tt;
+            if (task >= ntasks) break;
+            const int kb = task % (kTcBK / 8), c = task / (kTcBK / 8);
+            const int col = c0 + c;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int64_t row = r0 + kb * 8 + t;
+                double x = 0.0;
+                if (row < re && col < n) {
+                    x = __ldg(X + row + int64_t(col) * ldx);
+                    if (unit_lower && row <= col) x = (row == col) ? 1.0 : 0.0;
+                }
+                xv[tt][t] = x;
+            }
+        }
+        // (1) S block: entry (r, i) for 128 sketch rows x 32 rows of X; two
+        // tasks at a time, so that their dependent series chains interleave
+#pragma unroll 2
         for (int task = tid; task < (kTcM / 4) * kTcBK; task += kTcThreads) {
             const int i = task % kTcBK, q = task / kTcBK;
             const int64_t row = r0 + i;
@@ -135,18 +159,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 *reinterpret_cast<uint16_t *>(stage + kmajor_off(4 * q + j, i)) = h[j];
         }
         // (2) X block split into NSL bf16 terms: 8 consecutive rows of one column per task
-        for (int task = tid; task < nt * (kTcBK / 8); task += kTcThreads) {
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int task = tid + kTcThreads * tt;
+            if (task >= ntasks) break;
             const int kb = task % (kTcBK / 8), c = task / (kTcBK / 8);
-            const int col = c0 + c;
             uint16_t hv[NSL][8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int64_t row = r0 + kb * 8 + t;
-                double x = 0.0;
-                if (row < re && col < n) {
-                    x = X[row + int64_t(col) * ldx];
-                    if (unit_lower && row <= col) x = (row == col) ? 1.0 : 0.0;
-                }
+                const double x = xv[tt][t];
                 double rnd;
                 hv[0][t] = bf16_bits_from_f64(x, rnd);
                 if (NSL == 3) {
