@@ -142,6 +142,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 //   ln x = e ln2 + 2t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9 + t^10/11),
 // every operation individually rounded (no contraction), so the value is
 // the same on any IEEE binary32 implementation.
+// Small integers as binary32 without a conversion instruction (those share
+// GB300's slow FP64 pipe): 1.5 * 2^23 + k in the significand, minus 1.5 * 2^23,
+// exact for |k| < 2^22; and 2^23 + k minus 2^23 for 0 <= k <= 2^23.
+__device__ __forceinline__ float sk_small_int_f32(int k) {
+    return __fsub_rn(__int_as_float(0x4B400000 + k), 12582912.0f);
+}
+__device__ __forceinline__ float sk_u23_f32(uint32_t k) {
+    return __fsub_rn(__uint_as_float(0x4B000000u + k), 8388608.0f);
+}
+
 __device__ __forceinline__ float sk_ln(float x) {
     const uint32_t b = __float_as_uint(x);
     int e = static_cast<int>((b >> 23) & 0xffu) - 127;
@@ -159,16 +169,17 @@ __device__ __forceinline__ float sk_ln(float x) {
     p = __fadd_rn(__fmul_rn(p, t2), 0x1.555556p-2f);
     p = __fadd_rn(__fmul_rn(p, t2), 1.0f);
     const float lnf = __fmul_rn(__fmul_rn(2.0f, t), p);
-    return __fadd_rn(__fmul_rn(static_cast<float>(e), 0x1.62e430p-1f), lnf);
+    return __fadd_rn(__fmul_rn(sk_small_int_f32(e), 0x1.62e430p-1f), lnf);
 }
 
 // cos(2 pi u), sin(2 pi u) for u in [0, 1): quadrant q = floor(4u), remainder
 // r; reflect r > 1/2 to 1 - r; phi = a * pi/2; Taylor series of sin to phi^9
 // and cos to phi^10 (Horner); swap for the reflected half; rotate by q.
-__device__ __forceinline__ void sk_cossin_2pi(float u, float &c, float &s) {
-    const float v = __fmul_rn(u, 4.0f);
-    const int q = static_cast<int>(v);
-    const float r = __fsub_rn(v, static_cast<float>(q));
+// u = w 2^-23 is passed as the 23-bit integer w: v = 4u = w 2^-21, so
+// q = floor(v) = w >> 21 and r = v - q = (w mod 2^21) 2^-21, both exact.
+__device__ __forceinline__ void sk_cossin_2pi(uint32_t w, float &c, float &s) {
+    const int q = static_cast<int>(w >> 21);
+    const float r = __fmul_rn(sk_u23_f32(w & 0x1FFFFFu), 0x1p-21f);
     const bool refl = r > 0.5f;
     const float a = refl ? __fsub_rn(1.0f, r) : r;
     const float phi = __fmul_rn(a, 0x1.921fb6p+0f);
@@ -198,11 +209,10 @@ __device__ __forceinline__ void sk_cossin_2pi(float u, float &c, float &s) {
 // Box-Muller pair from two Philox words: u1 = ((we >> 9) + 1) 2^-23 in (0, 1],
 // u2 = (wo >> 9) 2^-23; rho = sqrt(-2 ln u1); (rho cos 2pi u2, rho sin 2pi u2).
 __device__ __forceinline__ float2 sk_box_muller(uint32_t we, uint32_t wo) {
-    const float u1 = __fmul_rn(static_cast<float>((we >> 9) + 1u), 0x1p-23f);
-    const float u2 = __fmul_rn(static_cast<float>(wo >> 9), 0x1p-23f);
+    const float u1 = __fmul_rn(sk_u23_f32((we >> 9) + 1u), 0x1p-23f);
     const float rho = __fsqrt_rn(__fmul_rn(-2.0f, sk_ln(u1)));
     float c, s;
-    sk_cossin_2pi(u2, c, s);
+    sk_cossin_2pi(wo >> 9, c, s);  // u2 = (wo >> 9) 2^-23
     return make_float2(__fmul_rn(rho, c), __fmul_rn(rho, s));
 }
 

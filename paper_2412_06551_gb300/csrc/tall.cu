@@ -713,23 +713,36 @@ __global__ void __launch_bounds__(kThreads, 2)
             int rows_[16], sg[16];
             if (row < m) {
                 sk_sparse_column(seed, row0 + row, s, zeta, rows_, sg);
+                // target row (bits 0..15), this block row (bits 16..23), sign (bit 31)
                 for (int t = 0; t < zeta; ++t)
-                    tgt[threadIdx.x * zeta + t] = rows_[t] | (sg[t] < 0 ? int(0x80000000u) : 0);
+                    tgt[threadIdx.x * zeta + t] =
+                        rows_[t] | (threadIdx.x << 16) | (sg[t] < 0 ? int(0x80000000u) : 0);
             } else {
                 for (int t = 0; t < zeta; ++t) tgt[threadIdx.x * zeta + t] = -1;
             }
         }
         __syncthreads();
+        // warp w owns the accumulator rows r = w (mod 8).  The warp scans the
+        // block's (row, t) entries 32 at a time, a ballot picks its own, and
+        // they are added in increasing (row, t) order: the order of a plain
+        // loop over rows and nonzeros, so every sum is reproducible.
         const int rows = static_cast<int>(std::min<int64_t>(kSparseBM, re - r0));
-        for (int i = 0; i < rows; ++i) {
-            const double x = T2[i * (kSparseNT + 1) + lane];
-            for (int t = 0; t < zeta; ++t) {
-                const int e = tgt[i * zeta + t];
-                const int r = e & 0x7fffffff;
-                if ((r & 7) == warp) {
-                    double *p = acc + r * kSparseNT + lane;
-                    *p = (e < 0) ? (*p - x) : (*p + x);
-                }
+        const int total = rows * zeta;
+        for (int base = 0; base < total; base += 32) {
+            const int e = base + lane < total ? tgt[base + lane] : 0;
+            unsigned mine = __ballot_sync(0xffffffffu, base + lane < total && (e & 7) == warp);
+            while (mine) {
+                const int src = __ffs(mine) - 1;
+                mine &= mine - 1;
+                const int ee = __shfl_sync(0xffffffffu, e, src);
+                const double x = T2[((ee >> 16) & 0xff) * (kSparseNT + 1) + lane];
+                // +-x by the sign bit, one binary64 add
+                const unsigned long long sbit =
+                    static_cast<unsigned long long>(static_cast<uint32_t>(ee) & 0x80000000u) << 32;
+                const double xs = __longlong_as_double(static_cast<long long>(
+                    static_cast<unsigned long long>(__double_as_longlong(x)) ^ sbit));
+                double *p = acc + (ee & 0xffff) * kSparseNT + lane;
+                *p += xs;
             }
         }
         __syncthreads();
