@@ -75,6 +75,26 @@ __device__ __forceinline__ double emu_scale(double v, int e) {
     return ldexp(v, e);
 }
 
+// v 2^e as binary64, rounded to nearest (ties to even), by integer operations:
+// the int64 -> binary64 conversion instruction runs on GB300's slow FP64 pipe.
+// Results that would not be normal numbers take the conversion and emu_scale;
+// both ways give the same bits.
+__device__ __forceinline__ double emu_i64_scaled(long long v, int e) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = static_cast<unsigned long long>(v) & 0x8000000000000000ull;
+    const unsigned long long a = v < 0 ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
+    const int lz = __clzll(static_cast<long long>(a));
+    const int be = 1086 - lz + e;  // biased exponent of the leading bit of a 2^e
+    if (be < 1 || be > 2045) return emu_scale(static_cast<double>(v), e);
+    const unsigned long long an = a << lz;  // leading one at bit 63
+    unsigned long long mant = an >> 11;     // 53 bits with the leading one
+    const unsigned long long rest = an & 0x7FFull;
+    mant += (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    // the leading one adds 1 to the exponent field; a rounding carry adds one more
+    const unsigned long long bits = (static_cast<unsigned long long>(be - 1) << 52) + mant;
+    return __longlong_as_double(static_cast<long long>(bits | sgn));
+}
+
 // A level sum C (an exact integer in fp32, |C| <= 2^24) times 2^k as an
 // integer: exact for k >= 0, rounded (half up) for k < 0.  A window's levels
 // L = 0..7 enter one int64 accumulator with k = 24 - 8L + u, i.e. in units of

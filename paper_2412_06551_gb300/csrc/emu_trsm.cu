@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kTeThreads, kTeCtasPerSm)
                     const int cbit = __ldg(rbits + J * kTeB + q);
                     a -= (rowbits == 0x7ff || cbit == 0x7ff)
                              ? __longlong_as_double(0x7ff8000000000000ll)
-                             : emu_scale(static_cast<double>(acc[q]),
+                             : emu_i64_scaled(acc[q],
                                          emu_exponent(rowbits) + emu_exponent(cbit) - 14 - 24 - kTeUnit);
                 }
                 x[q] = a;

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                         const int cbit = __ldg(rbits + J * kTeB + c);
                         const double u = (rbit == 0x7ff || cbit == 0x7ff)
                                              ? __longlong_as_double(0x7ff8000000000000ll)
-                                             : emu_scale(static_cast<double>(acc[q]),
+                                             : emu_i64_scaled(acc[q],
                                                          emu_exponent(rbit) + emu_exponent(cbit) -
                                                              14 - 24 - kTeUnit);
                         a -= u;
