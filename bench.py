@@ -345,7 +345,13 @@ def run_small(args):
     t0 = time.perf_counter()
     q_o, r_o, _ = oracle.rclupp(x, S=S)
     t_oracle = time.perf_counter() - t0
-    rows = {"oracle": {"ms": t_oracle * 1e3, "cores": oracle.num_threads(),
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)  # the same factorization on one core
+    t0 = time.perf_counter()
+    oracle.rclupp(x, S=S)
+    t_oracle1 = time.perf_counter() - t0
+    oracle.set_num_threads(cores)
+    rows = {"oracle": {"ms": t_oracle * 1e3, "cores": cores, "ms_one_core": t_oracle1 * 1e3,
                        "orth": oracle.orthogonality(q_o), "res": oracle.residual(x, q_o, r_o)}}
     reps = max(20, 10 * args.steps)
     for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED),
@@ -357,6 +363,8 @@ def run_small(args):
         o, r = accuracy(torch, X, Q, R)
         rows[label] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "orth": o, "res": r,
                        "prec_used": int(info.prec_used), "emulated": int(info.emulated)}
+        if label == "fp64":  # realised kappa: the 2-norm condition number of the computed R
+            rows[label]["kappa_realised"] = float(np.linalg.cond(R.cpu().numpy()))
     print(json.dumps({"workload": "RCLUPP, one matrix m=4096, n=64, kappa=1e8, Gaussian s=128 "
                                   "(latency-bound: X is 2 MB, L2-resident)",
                       "m": m, "n": n, "s": s, "kappa": kap, "seed_x": seed, "results": rows}), flush=True)
@@ -640,11 +648,14 @@ def run_ours(args):
         paths[name] = {"ms": path_ms[name], "gflops_2mn2": 2.0 * M * N * N / t / 1e9,
                        "fp64_gflops": f / t / 1e9, "roofline_frac": f / t / 1e9 / FP64_PEAK_GFLOPS,
                        **acc[name]}
+    # realised kappa of X: the 2-norm condition number of the computed R (n x n)
+    kappa_realised = float(np.linalg.cond(Rs[0].cpu().numpy()))
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(), "roofline": roofline, "kernel_share": kernel_share,
+        "config": {**workload_config(), "kappa_realised": kappa_realised},
+        "roofline": roofline, "kernel_share": kernel_share,
         "paths": paths, "gpu_launches": int(launches),
         "e2e": {"value": world * model_flops / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

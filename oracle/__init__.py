@@ -61,6 +61,7 @@ def _load():
             P, I64, I32, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
             sig = {
                 "orc_num_threads": ([], I32),
+                "orc_set_num_threads": ([I32], None),
                 "orc_gram": ([I64, I64, P, I64, P, I64], None),
                 "orc_cholesky": ([I64, P, I64, P, I64, P], I32),
                 "orc_trsm_right_upper": ([I64, I64, P, I64, P, I64, P, I64], None),
@@ -107,6 +108,11 @@ def _f(a) -> np.ndarray:
 
 def _p(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def set_num_threads(k: int) -> None:
+    """Threads the oracle's OpenMP loops use from now on (timing only)."""
+    _load().orc_set_num_threads(int(k))
 
 
 def num_threads() -> int:

@@ -63,6 +63,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads for the following calls (k >= 1); a timing aid, no arithmetic. */
+void orc_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k >= 1)
+        omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense building blocks                                                     */
 /* ------------------------------------------------------------------------ */
