@@ -435,6 +435,7 @@ def run_batched(args):
           for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
     model = float(np.sum(2.0 * ms * ns * ns))
     branches, tune_ms = rq.rclupp_autotune_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base)
+    _, grid_div, fine_tiles = rq.rclupp_get_batch_policy()
     Qs = [rq.empty_colmajor(int(m), int(n), device) for m, n in zip(ms, ns)]
     Rs = [rq.empty_colmajor(int(n), int(n), device) for n in ns]
     call = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs)
@@ -472,7 +473,8 @@ def run_batched(args):
         "workload": "batched RCLUPP: 512 FP64 problems, m=floor(2^U(12,17)), n in {16..128}, "
                     "kappa=10^U(2,12), Gaussian s=2n",
         "problems": len(Xs), "rows_total": int(ms.sum()), "model_flops": model,
-        "branches_autotuned": branches, "ms_per_batch": batch_ms,
+        "branches_autotuned": branches, "grid_div_autotuned": grid_div, "fine_tiles_autotuned": fine_tiles,
+        "ms_per_batch": batch_ms,
         "gflops_2mn2": model / (batch_ms / 1e3) / 1e9,
         "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
         "gpu_launches_per_batch": int(launches), "statuses_nonzero": int(np.count_nonzero(status)),

@@ -279,12 +279,28 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t handle, int32_t algo, int3
 /* Number of parallel branches of the batched graph (1 ..64). */
 rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t handle, int32_t branches);
 
+/* Launch shapes of the kernels inside the batched graph: grid_div (1 ..64)
+ * divides the number of CTAs each tall pass aims for (2 per SM for a single
+ * call), so that concurrent problems use fewer, longer-lived CTAs;
+ * fine_tiles = 1 selects the smaller row tile of the TRSM (n <= 64: 64 rows
+ * instead of 128) and of the Gram (64 instead of 128 rows for n <= 64, 32
+ * instead of 64 for n <= 128).  Results are the same up to the order of the
+ * split-K sums.  Defaults 1 and 0. */
+rclupp_status_t rclupp_set_batch_policy(rclupp_handle_t handle, int32_t grid_div, int32_t fine_tiles);
+
+/* The handle's current branch count and launch shapes (any pointer may be NULL). */
+rclupp_status_t rclupp_get_batch_policy(rclupp_handle_t handle, int32_t *branches, int32_t *grid_div,
+                                        int32_t *fine_tiles);
+
 /* Autotuner of the batched form: runs the batch (same arguments as
  * rclupp_factor_batched; outputs are overwritten) with 4, 8, 16, 32 and 64
- * branches (up to the batch size), times one replay of each cached graph
- * with CUDA events on the handle's stream, keeps the fastest in the handle
- * and returns it in *best_branches and its time in *best_ms (either may be
- * NULL).  A numerical breakdown of a problem does not stop the tuning. */
+ * branches (up to the batch size), then, at the fastest branch count, with
+ * the launch shapes (grid_div, fine_tiles) = (1, 1), (2, 0), (2, 1), (4, 0),
+ * (4, 1), (8, 0); it times one replay of each cached graph with CUDA events
+ * on the handle's stream, keeps the fastest combination in the handle and
+ * returns its branch count in *best_branches and its time in *best_ms
+ * (either may be NULL; rclupp_get_batch_policy reads the rest).  A numerical
+ * breakdown of a problem does not stop the tuning. */
 rclupp_status_t rclupp_autotune_batched(rclupp_handle_t handle, int32_t algo, int32_t count,
                                         const int64_t *m, const int64_t *n,
                                         const double *const *X, const int64_t *ldx,

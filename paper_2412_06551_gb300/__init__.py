@@ -30,6 +30,7 @@ __all__ = [
     "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
+    "rclupp_set_batch_policy", "rclupp_get_batch_policy",
     "ALGO_RCLUPP", "ALGO_RCLUPPR",
     "ALGO_CHOLQR2", "ALGO_LC2",
     "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
@@ -111,6 +112,8 @@ _SIGNATURES = {
     "rclupp_sketch_precond": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_householder_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_givens_r": ([_P, _I64, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_set_batch_policy": ([_P, _I32, _I32], _I32),
+    "rclupp_get_batch_policy": ([_P, _P, _P, _P], _I32),
     "rclupp_sketch_precond_r0": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "rclupp_factor_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
@@ -492,6 +495,29 @@ def rclupp_set_batch_branches(branches: int, device=None):
     _handles[dev.index] = h
     st = load().rclupp_set_batch_branches(h._h, int(branches))
     _raise("rclupp_set_batch_branches", st)
+
+
+def _device_handle(device=None):
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    h = _handles.get(dev.index) or Handle(dev)
+    _handles[dev.index] = h
+    return h
+
+
+def rclupp_set_batch_policy(grid_div: int = 1, fine_tiles: bool = False, device=None):
+    """Launch shapes inside the batched graph: CTA-budget divisor and finer row tiles."""
+    st = load().rclupp_set_batch_policy(_device_handle(device)._h, int(grid_div), int(bool(fine_tiles)))
+    _raise("rclupp_set_batch_policy", st)
+
+
+def rclupp_get_batch_policy(device=None):
+    """(branches, grid_div, fine_tiles) of the handle's batched form."""
+    b, g, f = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    st = load().rclupp_get_batch_policy(_device_handle(device)._h, ctypes.byref(b), ctypes.byref(g),
+                                        ctypes.byref(f))
+    _raise("rclupp_get_batch_policy", st)
+    return int(b.value), int(g.value), int(f.value)
 
 
 def rclupp_gram_noalloc(A, *, G=None):

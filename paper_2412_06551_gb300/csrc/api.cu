@@ -27,6 +27,8 @@ struct rclupp_handle_s {
     DevStatus *h_status = nullptr;  // pinned
     // batched form: parallel branches of the batch graph and the cached graph
     int batch_branches = 16;
+    int batch_grid_div = 1;    // launch policy inside the batch graph (LaunchPolicy)
+    int batch_fine_tiles = 0;
     int nstreams = 0;
     cudaStream_t bstreams[kMaxBranches] = {};
     cudaEvent_t join[kMaxBranches] = {};
@@ -70,7 +72,8 @@ struct Fnv {
 uint64_t batch_signature(int algo, int count, const int64_t *m, const int64_t *n,
                          const double *const *X, const int64_t *ldx, double *const *Q,
                          const int64_t *ldq, double *const *R, const int64_t *ldr,
-                         const rclupp_opts_t *o, int branches, const void *ws) {
+                         const rclupp_opts_t *o, int branches, const void *ws,
+                         const LaunchPolicy &pol) {
     Fnv f;
     f.add(&algo, 1);
     f.add(&count, 1);
@@ -85,6 +88,8 @@ uint64_t batch_signature(int algo, int count, const int64_t *m, const int64_t *n
     f.add(o, count);
     f.add(&branches, 1);
     f.add(&ws, 1);
+    f.add(&pol.grid_div, 1);
+    f.add(&pol.fine_tiles, 1);
     return f.h;
 }
 
@@ -792,8 +797,11 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
 
     // Graph of the whole batch: fork into `branches` streams, matrix i on
     // branch i mod branches, join.  Reused while the batch is unchanged.
+    LaunchPolicy pol;
+    pol.grid_div = h->batch_grid_div;
+    pol.fine_tiles = h->batch_fine_tiles;
     const uint64_t sig = batch_signature(algo, count, m, n, X, ldx, Q, ldq, R, ldr, o.data(),
-                                         branches, h->ws);
+                                         branches, h->ws, pol);
     if (!(h->graph_exec && h->graph_sig == sig)) {
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
@@ -805,6 +813,7 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
         rclupp_status_t ls = RCLUPP_OK;
+        const LaunchPolicyScope policy_scope(pol);  // launch shapes of the captured kernels
         if (cudaMemsetAsync(d_st, 0, size_t(count) * sizeof(DevStatus), h->cap) != cudaSuccess ||
             cudaEventRecord(h->fork, h->cap) != cudaSuccess)
             ls = RCLUPP_ERR_CUDA;
@@ -892,6 +901,22 @@ rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t h, int32_t branches) {
     return RCLUPP_OK;
 }
 
+rclupp_status_t rclupp_set_batch_policy(rclupp_handle_t h, int32_t grid_div, int32_t fine_tiles) {
+    if (!h || grid_div < 1 || grid_div > 64 || (fine_tiles != 0 && fine_tiles != 1)) return RCLUPP_ERR_ARG;
+    h->batch_grid_div = grid_div;
+    h->batch_fine_tiles = fine_tiles;
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_get_batch_policy(rclupp_handle_t h, int32_t *branches, int32_t *grid_div,
+                                        int32_t *fine_tiles) {
+    if (!h) return RCLUPP_ERR_ARG;
+    if (branches) *branches = h->batch_branches;
+    if (grid_div) *grid_div = h->batch_grid_div;
+    if (fine_tiles) *fine_tiles = h->batch_fine_tiles;
+    return RCLUPP_OK;
+}
+
 rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t count,
                                         const int64_t *m, const int64_t *n,
                                         const double *const *X, const int64_t *ldx,
@@ -900,32 +925,56 @@ rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t
                                         int32_t *best_branches, float *best_ms) {
     if (!h) return RCLUPP_ERR_ARG;
     static const int kCandidates[] = {4, 8, 16, 32, 64};
+    // launch shapes tried at the best branch count: CTA budget divisor, finer row tiles
+    static const int kPolicies[][2] = {{1, 1}, {2, 0}, {2, 1}, {4, 0}, {4, 1}, {8, 0}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return RCLUPP_ERR_CUDA;
-    int best = h->batch_branches;
+    int best = h->batch_branches, best_div = 1, best_fine = 0;
     float best_t = 0.f;
     rclupp_status_t st = RCLUPP_OK;
-    for (int b : kCandidates) {
-        if (b > std::max<int>(count, 1) && b != kCandidates[0]) break;
-        h->batch_branches = b;
-        // first call builds and caches the graph; the second one is timed
+    // first call builds and caches the graph; the second one is timed
+    auto trial = [&](float *t) {
         st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
-        if (st != RCLUPP_OK && st != RCLUPP_ERR_CHOL_BREAKDOWN && st != RCLUPP_ERR_LU_ZERO_PIVOT) break;
+        if (st != RCLUPP_OK && st != RCLUPP_ERR_CHOL_BREAKDOWN && st != RCLUPP_ERR_LU_ZERO_PIVOT)
+            return false;
         cudaEventRecord(e0, h->stream);
         st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
         cudaEventRecord(e1, h->stream);
         cudaEventSynchronize(e1);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
+        *t = 0.f;
+        cudaEventElapsedTime(t, e0, e1);
+        return true;
+    };
+    h->batch_grid_div = 1;
+    h->batch_fine_tiles = 0;
+    bool ok = true;
+    for (int b : kCandidates) {
+        if (b > std::max<int>(count, 1) && b != kCandidates[0]) break;
+        h->batch_branches = b;
+        float t;
+        if (!(ok = trial(&t))) break;
         if (best_t == 0.f || t < best_t) {
             best_t = t;
             best = b;
         }
     }
+    h->batch_branches = best;
+    for (int p = 0; ok && p < int(sizeof(kPolicies) / sizeof(kPolicies[0])); ++p) {
+        h->batch_grid_div = kPolicies[p][0];
+        h->batch_fine_tiles = kPolicies[p][1];
+        float t;
+        if (!(ok = trial(&t))) break;
+        if (t < best_t) {
+            best_t = t;
+            best_div = kPolicies[p][0];
+            best_fine = kPolicies[p][1];
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->batch_branches = best;
+    h->batch_grid_div = best_div;
+    h->batch_fine_tiles = best_fine;
     if (best_branches) *best_branches = best;
     if (best_ms) *best_ms = best_t;
     return (st == RCLUPP_ERR_CHOL_BREAKDOWN || st == RCLUPP_ERR_LU_ZERO_PIVOT) ? RCLUPP_OK : st;

@@ -294,7 +294,7 @@ __global__ void k_reduce_gram_emu(const double *__restrict__ part, int nsplit, i
 
 int emu_split(int n, int64_t m) {
     const int tiles = emu_tiles(n);
-    int p = std::max(1, num_sms() / tiles);
+    int p = std::max(1, grid_sms() / tiles);
     const int64_t windows = ceil_div(m, int64_t(kEmuBK) * kEmuWinSteps);
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p, windows)));
 }

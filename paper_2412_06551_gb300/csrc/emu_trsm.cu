@@ -289,7 +289,7 @@ cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, cons
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = ceil_div(m, kTeM);
-    const int64_t grid = std::min<int64_t>(tiles, int64_t(kTeCtasPerSm) * num_sms());
+    const int64_t grid = std::min<int64_t>(tiles, int64_t(kTeCtasPerSm) * grid_sms());
     const int64_t chunk = ceil_div(tiles, grid) * kTeM;
     const int g = static_cast<int>(ceil_div(m, chunk));
     const size_t smem = kTeStageBytes;

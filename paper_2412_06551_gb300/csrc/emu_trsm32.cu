@@ -344,7 +344,7 @@ cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, co
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = ceil_div(m, kTeM);
-    const int64_t grid = std::min<int64_t>(tiles, int64_t(2) * num_sms());
+    const int64_t grid = std::min<int64_t>(tiles, int64_t(2) * grid_sms());
     const int64_t chunk = ceil_div(tiles, grid) * kTeM;
     const int g = static_cast<int>(ceil_div(m, chunk));
     const size_t smem = size_t(kTeStages) * kTeStageBytes;

@@ -30,6 +30,24 @@ struct TallPlan {
     int grid_x;      // CTAs along the rows
 };
 
+// Launch shape of the tall passes, per host thread: `grid_div` divides the
+// number of CTAs a pass aims for (grid_sms() = SMs / grid_div), `fine_tiles`
+// selects the next smaller row tile of the TRSM and Gram passes where a
+// variant exists.  The batched form sets it (RAII scope) while it captures a
+// batch graph, so that many concurrent problems can use smaller launches;
+// single calls use the default {1, 0}.
+struct LaunchPolicy {
+    int grid_div = 1;
+    int fine_tiles = 0;
+};
+LaunchPolicy &launch_policy();
+struct LaunchPolicyScope {
+    LaunchPolicy saved;
+    explicit LaunchPolicyScope(LaunchPolicy p) : saved(launch_policy()) { launch_policy() = p; }
+    ~LaunchPolicyScope() { launch_policy() = saved; }
+};
+int grid_sms();
+
 // Row partition of an m-row pass for a kernel with `ctas_per_sm` resident
 // CTAs, rows per tile bm, and `ytiles` independent column/output tiles.
 TallPlan plan_rows(int64_t m, int bm, int ctas_per_sm, int ytiles);

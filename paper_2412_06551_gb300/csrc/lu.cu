@@ -245,7 +245,7 @@ size_t lu_scratch_bytes(int64_t m, int n) {
 }
 
 static int lu_grid(int64_t rows, int64_t &chunk, int per_sm) {
-    const int64_t maxg = int64_t(per_sm) * num_sms();
+    const int64_t maxg = int64_t(per_sm) * grid_sms();
     int64_t g = std::max<int64_t>(1, std::min<int64_t>(maxg, ceil_div(rows, 2 * kLuThreads)));
     chunk = std::max<int64_t>(1, ceil_div(rows, g));
     g = std::max<int64_t>(1, ceil_div(rows, chunk));

@@ -203,7 +203,7 @@ cudaError_t launch_srht_t(const double *A, int64_t lda, int64_t m, int n, int un
     const int64_t gb0 = row0 / kSrhtBlock;
     const int64_t nblk = (row0 + m - 1) / kSrhtBlock - gb0 + 1;
     const int tiles = static_cast<int>(ceil_div(n, NC));
-    const int64_t want = std::max<int64_t>(1, int64_t(2) * num_sms() / tiles);
+    const int64_t want = std::max<int64_t>(1, int64_t(2) * grid_sms() / tiles);
     const int64_t chunk = ceil_div(nblk, std::min(want, nblk));
     const int grid_x = static_cast<int>(ceil_div(nblk, chunk));
     const size_t smem = size_t(NC) * kSrhtBlock * 8 + size_t(NC) * 8 + 8 * 4 + size_t(s) * 4;

@@ -23,6 +23,13 @@ constexpr int kThreads = 256;
 
 // ------------------------------------------------------------ plumbing ---
 
+LaunchPolicy &launch_policy() {
+    static thread_local LaunchPolicy p;
+    return p;
+}
+
+int grid_sms() { return std::max(1, num_sms() / std::max(1, launch_policy().grid_div)); }
+
 int num_sms() {
     static int cached = 0;
     if (cached == 0) {
@@ -77,7 +84,7 @@ TallPlan plan_rows(int64_t m, int bm, int ctas_per_sm, int ytiles) {
     p.bm = bm;
     p.ncb = 0;
     const int64_t tiles = ceil_div(m, bm);
-    int64_t want = std::max<int64_t>(1, int64_t(num_sms()) * ctas_per_sm / std::max(1, ytiles));
+    int64_t want = std::max<int64_t>(1, int64_t(grid_sms()) * ctas_per_sm / std::max(1, ytiles));
     want = std::min<int64_t>(want, tiles);
     const int64_t tiles_per = ceil_div(tiles, want);
     p.chunk = tiles_per * bm;
@@ -333,7 +340,10 @@ size_t gram_partials_doubles(int64_t m, int n) {
     return p * 3 * 16384;
 }
 
-static int gram_bm(int n) { return n <= 64 ? 128 : (n <= 128 ? 64 : 32); }
+static int gram_bm(int n) {
+    if (launch_policy().fine_tiles) return n <= 64 ? 64 : 32;
+    return n <= 64 ? 128 : (n <= 128 ? 64 : 32);
+}
 
 cudaError_t launch_gram(const double *A, int64_t lda, int64_t m, int n, int unit_lower, double *G,
                         int64_t ldg, double *part, DevStatus *st, cudaStream_t stream) {
@@ -510,7 +520,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (kGram) g.store(part + size_t(blockIdx.x) * 16384);
 }
 
-static int trsm_bm(int n_pad) { return n_pad <= 64 ? 128 : (n_pad <= 128 ? 64 : 32); }
+// (fine tiles: 64 rows for n <= 64; the fused Gram needs 64 or 128 rows, so
+// wider matrices keep their tile)
+static int trsm_bm(int n_pad) {
+    if (launch_policy().fine_tiles && n_pad <= 64) return 64;
+    return n_pad <= 64 ? 128 : (n_pad <= 128 ? 64 : 32);
+}
 
 cudaError_t launch_trsm_gram(const double *A, int64_t lda, int64_t m, int n, const double *RP,
                              const double *rinv, double *Q, int64_t ldq, double *G, int64_t ldg,

@@ -263,7 +263,7 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
     // load latency; each CTA's stages stay below half the SM's shared memory
     const size_t smem = tc_sketch_smem_bytes(n, nterms);
     const int per_sm = smem <= 110 * 1024 ? 2 : 1;
-    int p = std::max(1, per_sm * num_sms() / tiles);
+    int p = std::max(1, per_sm * grid_sms() / tiles);
     int64_t chunk = round_up(ceil_div(m, p), kTcBK);
     p = static_cast<int>(ceil_div(m, chunk));
     const dim3 grid(tiles, p);

@@ -143,3 +143,44 @@ def test_batched_emulated_gaussian_gates(rq, prec):
         q, r = host(Qb[i]), host(Rb[i])
         assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
         assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
+
+
+@pytest.mark.parametrize("grid_div,fine", [(4, True), (2, False), (8, True)])
+def test_batch_policy_changes_only_the_sum_order(rq, grid_div, fine):
+    # smaller launches or row tiles inside the graph: the same factorizations
+    # up to the order of the split-K sums, replayed bit for bit
+    xs, kap = _batch(16, 40 + grid_div)
+    Xs = [dev(x) for x in xs]
+    Qd, Rd, st = rq.rclupp_factor_batched(Xs, algo=0, seed=5)
+    assert np.all(st == 0)
+    try:
+        rq.rclupp_set_batch_policy(grid_div, fine)
+        assert rq.rclupp_get_batch_policy()[1:] == (grid_div, int(fine))
+        Qp, Rp, st2 = rq.rclupp_factor_batched(Xs, algo=0, seed=5)
+        first = [(q.clone(), r.clone()) for q, r in zip(Qp, Rp)]
+        rq.rclupp_factor_batched(Xs, algo=0, seed=5, Qs=Qp, Rs=Rp)  # cached graph, replayed
+    finally:
+        rq.rclupp_set_batch_policy(1, False)
+    assert np.all(st2 == 0)
+    for i, x in enumerate(xs):
+        assert torch.equal(Qp[i], first[i][0]) and torch.equal(Rp[i], first[i][1]), i
+        q, r, qd, rd = host(Qp[i]), host(Rp[i]), host(Qd[i]), host(Rd[i])
+        assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
+        assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(qd), 1e-13), i
+        assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, qd, rd), 1e-13), i
+
+
+def test_autotuner_sets_a_valid_policy(rq):
+    xs, _ = _batch(12, 91)
+    Xs = [dev(x) for x in xs]
+    try:
+        branches, ms = rq.rclupp_autotune_batched(Xs, algo=0, seed=3)
+        b, g, f = rq.rclupp_get_batch_policy()
+        assert b == branches and b in (4, 8, 16) and g in (1, 2, 4, 8) and f in (0, 1) and ms > 0
+        Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=0, seed=3)
+        assert np.all(st == 0)
+        for i, x in enumerate(xs):
+            assert oracle.orthogonality(host(Qb[i])) <= 1e-13
+    finally:
+        rq.rclupp_set_batch_branches(16)
+        rq.rclupp_set_batch_policy(1, False)
