@@ -148,12 +148,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     const int nsteps = re > rb ? static_cast<int>(ceil_div(re - rb, kEmuBK)) : 0;
     const int ncolsB = b_in_a ? 0 : kEmuN;
     const int ntasks = (kEmuM + ncolsB) * (kEmuBK / 8);
-    for (int ks = 0; ks < nsteps; ++ks) {
+    // Load block ks (32 rows) and split it into digits in its stage, once the
+    // MMAs that last read that stage are done.  Runs while the tensor core
+    // works on block ks - 1, also across the drain at a window's end.
+    auto prepare = [&](int ks) {
         const int sidx = ks % nst;
         unsigned char *stage = smem_raw + sidx * stage_bytes;
         const int64_t r0 = rb + int64_t(ks) * kEmuBK;
-        // (1) load this thread's blocks of 8 rows x 1 column (the loads are in
-        // flight while the stage's previous MMAs finish)
+        // (1) this thread's blocks of 8 rows x 1 column (in flight during the wait)
         double xv[kEmuTaskSlots][8];
 #pragma unroll
         for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
@@ -169,8 +171,6 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         if (ks >= nst &&
             !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst - 1) & 1)))
             abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
         // (2) digits, stored as K-major operand tiles
 #pragma unroll
         for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
@@ -195,7 +195,13 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             }
         }
         fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+    };
+    if (nsteps > 0) prepare(0);
+    for (int ks = 0; ks < nsteps; ++ks) {
+        const int sidx = ks % nst;
+        // block ks is in its stage; the previous window's drain is complete
         __syncthreads();
+        if (abort_flag) break;
         // (3) one thread issues the level products of this block
         if (tid == 0) {
             tc_fence_after();
@@ -220,12 +226,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             }
             mma_commit(&bar_mma[sidx]);
         }
-        // (4) end of a window: drain the seven level accumulators
+        // the next block's digits while the tensor core works on this one
+        if (ks + 1 < nsteps) prepare(ks + 1);
+        // (4) end of a window: drain the eight level accumulators
         if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) {
             if (!mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst) & 1)))
                 abort_flag = 1;
-            __syncthreads();
-            if (abort_flag) break;
             tc_fence_after();
             const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
                                 static_cast<uint32_t>(16 * cgrp);
@@ -251,10 +257,10 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
                 flush();
                 windows = 0;
             }
-            tc_fence_before();
-            __syncthreads();  // TMEM read before the next window's first MMAs overwrite it
+            tc_fence_before();  // the next iteration's barrier orders these reads before its MMAs
         }
     }
+    __syncthreads();
     if (abort_flag) {
         if (tid == 0) report(st, kErrTimeout, 0, -1);
     } else {
