@@ -289,10 +289,10 @@ int next_tier(int tier) {
     return tier == RCLUPP_PREC_SKETCH_BF16 ? RCLUPP_PREC_SKETCH_FP32 : RCLUPP_PREC_FP64;
 }
 
-enum class Verdict { Accept, Escalate, Fail };
+enum class FirstPassOutcome { Accept, Escalate, Fail };
 
-// Synchronizes the stream and judges the first Cholesky of a reduced tier.
-Verdict judge_first_pass(rclupp_handle_t h, const Bufs &b, int n) {
+// Synchronizes the stream and assesses the first Cholesky of a reduced tier.
+FirstPassOutcome assess_first_pass(rclupp_handle_t h, const Bufs &b, int n) {
     const int np = pad16(n);
     double diag[256];
     if (cudaMemcpyAsync(h->h_status, h->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
@@ -300,16 +300,18 @@ Verdict judge_first_pass(rclupp_handle_t h, const Bufs &b, int n) {
         cudaMemcpy2DAsync(diag, sizeof(double), b.RP[1], size_t(np + 1) * sizeof(double),
                           sizeof(double), size_t(n), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
-        return Verdict::Fail;
+        return FirstPassOutcome::Fail;
     const DevStatus &ds = *h->h_status;
-    if (ds.code != 0) return (ds.code == RCLUPP_ERR_CHOL_BREAKDOWN && ds.step == 3) ? Verdict::Escalate
-                                                                                   : Verdict::Fail;
+    if (ds.code != 0)
+        return (ds.code == RCLUPP_ERR_CHOL_BREAKDOWN && ds.step == 3) ? FirstPassOutcome::Escalate
+                                                                       : FirstPassOutcome::Fail;
     double lo = diag[0], hi = diag[0];
     for (int i = 1; i < n; ++i) {
         lo = std::min(lo, diag[i]);
         hi = std::max(hi, diag[i]);
     }
-    return (!(lo > 0.0) || hi / lo > kEscalateRatio) ? Verdict::Escalate : Verdict::Accept;
+    return (!(lo > 0.0) || hi / lo > kEscalateRatio) ? FirstPassOutcome::Escalate
+                                                      : FirstPassOutcome::Accept;
 }
 
 #define RQ_TRY(expr)                                     \
@@ -383,7 +385,7 @@ rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, 
 
 // Randomized drivers after the sketch: R1 from the sketch (the preconditioner
 // `precond`, steps 2-4 of Algorithm 6 or 3-4 of Algorithm 7), then CholeskyQR2
-// of Q1 = X R1^{-1}.  At a reduced sketch tier the first Cholesky is judged
+// of Q1 = X R1^{-1}.  At a reduced sketch tier the first Cholesky is assessed
 // and, if it broke down or shows Q1 too ill-conditioned, the sketch is redone
 // at the next tier (bf16 -> three-term bf16 -> binary64).  *tier_used reports
 // the tier that produced the result.
@@ -410,9 +412,9 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
             first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq, emulated, emulated);
         if (st != RCLUPP_OK) return st;
         if (tier == RCLUPP_PREC_FP64) break;
-        const Verdict v = judge_first_pass(h, b, n);
-        if (v == Verdict::Fail) break;  // the status is reported by finish()
-        if (v == Verdict::Accept) break;
+        const FirstPassOutcome v = assess_first_pass(h, b, n);
+        if (v == FirstPassOutcome::Fail) break;  // the status is reported by finish()
+        if (v == FirstPassOutcome::Accept) break;
         tier = next_tier(tier);
         if (cudaMemsetAsync(h->d_status, 0, sizeof(DevStatus), h->stream) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
