@@ -11,7 +11,6 @@ gamma32_k = k 2^-24 / (1 - k 2^-24).  |S_bf16| <= (1 + 2^-8) |z| and
 The drivers must meet the same gates as the binary64 path against the
 binary64 oracle, reporting the tier that produced the result.
 """
-import math
 
 import numpy as np
 import pytest

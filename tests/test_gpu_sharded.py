@@ -7,7 +7,6 @@ corresponding partial of the whole matrix's generated sketch, and the
 driver with one rank (the all-reduce an identity) gives the single-call
 factorization bit for bit, since it runs the same kernels in the same order.
 """
-import math
 
 import numpy as np
 import pytest
