@@ -195,8 +195,11 @@ const char *rclupp_status_string(int status);
  * X: m x n (ldx >= m); Q: m x n (ldq >= m), may alias X; R: n x n (ldr >= n).
  * opts: sketch options (NULL = Gaussian, s = 2n, seed 0, FP64).
  * Requires 1 <= n <= 256, n <= m, n <= s.  Errors: ERR_ARG, ERR_UNSUPPORTED,
- * ERR_LU_ZERO_PIVOT (sketch rank-deficient), ERR_CHOL_BREAKDOWN, ERR_CUDA,
- * ERR_NOMEM, ERR_TIMEOUT. */
+ * ERR_LU_ZERO_PIVOT (sketch rank-deficient), ERR_NONFINITE (a column of the
+ * sketch without a finite non-zero pivot candidate: the LU pivot searches
+ * skip NaN), ERR_CHOL_BREAKDOWN, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT; info
+ * (may be NULL) names the failing step and column.  A NaN or an infinite
+ * entry of X ends in ERR_NONFINITE or ERR_CHOL_BREAKDOWN. */
 rclupp_status_t rclupp_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
                               int64_t ldx, const rclupp_opts_t *opts, double *Q, int64_t ldq,
                               double *R, int64_t ldr, rclupp_info_t *info);
@@ -218,7 +221,8 @@ rclupp_status_t cholqr2_factor(rclupp_handle_t handle, int64_t m, int64_t n, con
 
 /* [Q, R] = LC2(X) -- Algorithm 4 (Section 2.3): [M, N, P] = LU(X);
  * S = chol(M^T M); R1 = S N (signs normalised); Q1 = X R1^{-1};
- * [Q, Z] = CholeskyQR(Q1); R = Z R1. */
+ * [Q, Z] = CholeskyQR(Q1); R = Z R1.  Errors as rclupp_factor; LU failures
+ * come from the tall LU of X (failed_step 2). */
 rclupp_status_t lc2_factor(rclupp_handle_t handle, int64_t m, int64_t n, const double *X,
                            int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
                            rclupp_info_t *info);
@@ -381,13 +385,16 @@ rclupp_status_t rclupp_trmm_upper(rclupp_handle_t handle, int64_t n, const doubl
  * implied), its top n x n upper triangle holds N, and ipiv (DEVICE, n int32)
  * holds 0-based row interchanges (row k swapped with ipiv[k] >= k).  The
  * pivot is the first row of largest magnitude (smallest index on ties).
- * Returns ERR_LU_ZERO_PIVOT with *col = k for a zero pivot. */
+ * Returns ERR_LU_ZERO_PIVOT with *col = k for a zero pivot, ERR_NONFINITE
+ * with *col = k when column k has no finite candidate (NaN candidates are
+ * skipped). */
 rclupp_status_t rclupp_tall_lupp(rclupp_handle_t handle, int64_t m, int64_t n, double *A,
                                  int64_t lda, int32_t *ipiv, int64_t *col);
 
 /* R1 from a sketched s x n matrix Y (Algorithm 6 steps 2-4): LU with partial
  * pivoting of Y, R-factor of the Householder QR of M, R1 = R0 N, diagonal
- * signs normalised.  Y is not modified.  Errors: ERR_LU_ZERO_PIVOT. */
+ * signs normalised.  Y is not modified.  Errors: ERR_LU_ZERO_PIVOT,
+ * ERR_NONFINITE (as rclupp_tall_lupp). */
 rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t n,
                                       const double *Y, int64_t ldy, double *R1, int64_t ldr);
 
