@@ -86,8 +86,8 @@ typedef enum {
                                     binary64, so the accumulation stays binary64 or better */
 } rclupp_precision_t;
 
-/* R-factor of the preconditioning step (Algorithm 6 step 3, Algorithm 7 step
- * 3, Algorithm 5 step 2). */
+/* R-factor R0 of the preconditioning step: of M in Algorithm 6, of M_s in
+ * Algorithm 7, of the sketch S X in Algorithm 5. */
 typedef enum {
     RCLUPP_R0_HOUSEHOLDER = 0, /* thin HouseholderQR, LAPACK larfg signs (the paper's choice) */
     RCLUPP_R0_GIVENS = 1       /* Givens rotations, r = hypot(a, b) >= 0 (Section 1)         */
@@ -314,8 +314,8 @@ rclupp_status_t rclupp_autotune_batched(rclupp_handle_t handle, int32_t algo, in
 
 /* ---- individual steps of the tall path (each is one row of the path) ---- */
 
-/* Y = S A (s x n, ldy >= s): the sketch of Algorithm 6 step 1 (S X) and of
- * Algorithm 7 step 2 (S M).  unit_lower != 0 reads A as the unit-lower
+/* Y = S A (s x n, ldy >= s): the sketch S X of Algorithm 6 and S M of
+ * Algorithm 7.  unit_lower != 0 reads A as the unit-lower
  * trapezoidal factor of an in-place LU (ones on the diagonal, zeros above).
  * Sum order is a fixed split over row chunks and a fixed-order reduction, so
  * results are bitwise reproducible for a given device. */
@@ -333,13 +333,13 @@ rclupp_status_t rclupp_sketch_rows(rclupp_handle_t handle, int64_t m, int64_t n,
                                    int64_t lda, int64_t row0, int32_t unit_lower,
                                    const rclupp_opts_t *opts, double *Y, int64_t ldy);
 
-/* G = A^T A (n x n, ldg >= n, both triangles written): Algorithm 1 step 1,
- * C1/C5 of Theorem 4.1; unit_lower as in rclupp_sketch (LC2's M^T M). */
+/* G = A^T A (n x n, ldg >= n, both triangles written): the Gram product of
+ * Algorithm 1, C1/C5 of Theorem 4.1; unit_lower as in rclupp_sketch (LC2's M^T M). */
 rclupp_status_t rclupp_gram(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                             int64_t lda, int32_t unit_lower, double *G, int64_t ldg);
 
 /* G = A^T A (n x n, both triangles) as binary64-emulating products on the
- * tensor cores: the Gram product of the CholeskyQR pass (Algorithm 1 step 1,
+ * tensor cores: the Gram product of the CholeskyQR pass (Algorithm 1,
  * C1) in the precision form RCLUPP_PREC_EMULATED.  Each element is written as
  * a_ij = 2^(E_j - 7) sum_{s=0..7} d_s 2^(-8s) with integer digits |d_s| <= 128
  * (E_j: 2^E_j exceeds every |a_ij| of column j; round to nearest, half away
@@ -371,7 +371,7 @@ rclupp_status_t rclupp_trsm_gram(rclupp_handle_t handle, int64_t m, int64_t n, c
                                  int64_t lda, const double *R, int64_t ldr, double *Q, int64_t ldq,
                                  double *G, int64_t ldg);
 
-/* Upper Cholesky factor of an SPD n x n G (Algorithm 1 step 2; C2, C6).
+/* Upper Cholesky factor of an SPD n x n G (the Cholesky factorization of Algorithm 1; C2, C6).
  * Returns ERR_CHOL_BREAKDOWN with *col (if non-NULL) = failing column. */
 rclupp_status_t rclupp_cholesky(rclupp_handle_t handle, int64_t n, const double *G, int64_t ldg,
                                 double *R, int64_t ldr, int64_t *col);
@@ -380,8 +380,8 @@ rclupp_status_t rclupp_cholesky(rclupp_handle_t handle, int64_t n, const double 
 rclupp_status_t rclupp_trmm_upper(rclupp_handle_t handle, int64_t n, const double *A, int64_t lda,
                                   const double *B, int64_t ldb, double *C, int64_t ldc);
 
-/* Tall LU with partial pivoting, in place (Algorithm 4 step 1, Algorithm 7
- * step 1): on return the strict lower part of A holds M (unit diagonal
+/* Tall LU with partial pivoting, in place ([M, N, P] = LU(X) of Algorithms 4
+ * and 7): on return the strict lower part of A holds M (unit diagonal
  * implied), its top n x n upper triangle holds N, and ipiv (DEVICE, n int32)
  * holds 0-based row interchanges (row k swapped with ipiv[k] >= k).  The
  * pivot is the first row of largest magnitude (smallest index on ties).
@@ -391,7 +391,7 @@ rclupp_status_t rclupp_trmm_upper(rclupp_handle_t handle, int64_t n, const doubl
 rclupp_status_t rclupp_tall_lupp(rclupp_handle_t handle, int64_t m, int64_t n, double *A,
                                  int64_t lda, int32_t *ipiv, int64_t *col);
 
-/* R1 from a sketched s x n matrix Y (Algorithm 6 steps 2-4): LU with partial
+/* R1 from a sketched s x n matrix Y (the preconditioner of Algorithm 6): LU with partial
  * pivoting of Y, R-factor of the Householder QR of M, R1 = R0 N, diagonal
  * signs normalised.  Y is not modified.  Errors: ERR_LU_ZERO_PIVOT,
  * ERR_NONFINITE (as rclupp_tall_lupp). */
@@ -415,8 +415,8 @@ rclupp_status_t rclupp_sketch_precond_r0(rclupp_handle_t handle, int64_t s, int6
 rclupp_status_t rclupp_givens_r(rclupp_handle_t handle, int64_t s, int64_t n, const double *A,
                                 int64_t lda, double *R, int64_t ldr);
 
-/* R-factor of the Householder QR of an s x n matrix A (Algorithm 5 step 2,
- * Algorithm 6 step 3): LAPACK larfg sign convention, A not modified. */
+/* R-factor of the Householder QR of an s x n matrix A (R0 in Algorithms 5 and
+ * 6): LAPACK larfg sign convention, A not modified. */
 rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t n,
                                      const double *A, int64_t lda, double *R, int64_t ldr);
 

@@ -134,7 +134,7 @@ def _check(st: int, info: np.ndarray, raise_on_error: bool):
 # ---------------------------------------------------------------- blocks ---
 
 def gram(x) -> np.ndarray:
-    """G = X^T X (Algorithm 1 step 1)."""
+    """G = X^T X (the Gram product of Algorithm 1)."""
     x = _f(x)
     m, n = x.shape
     g = np.zeros((n, n), order="F")
@@ -143,7 +143,8 @@ def gram(x) -> np.ndarray:
 
 
 def cholesky(g, raise_on_error: bool = True):
-    """Upper R with G = R^T R (Algorithm 1 step 2). Returns (R, status, info)."""
+    """Upper R with G = R^T R (the Cholesky factorization of Algorithm 1).
+    Returns (R, status, info)."""
     g = _f(g)
     n = g.shape[0]
     r = np.zeros((n, n), order="F")
@@ -154,7 +155,7 @@ def cholesky(g, raise_on_error: bool = True):
 
 
 def trsm(x, r) -> np.ndarray:
-    """Q = X R^{-1} by row-wise substitution (Algorithm 1 step 3)."""
+    """Q = X R^{-1} by row-wise substitution (the solve of Algorithm 1)."""
     x, r = _f(x), _f(r)
     m, n = x.shape
     q = np.zeros((m, n), order="F")
@@ -238,7 +239,7 @@ def givens_r(a) -> np.ndarray:
 
 
 def sketch_precond(y, raise_on_error: bool = True, r0: str = "householder"):
-    """R1 from the sketched matrix (Algorithm 6 steps 2-4 + sign fix), R0 by
+    """R1 from the sketched matrix (the preconditioner of Algorithm 6 + sign fix), R0 by
     Householder (the paper's choice) or Givens rotations. Returns (R1, status, info)."""
     y = _f(y)
     s, n = y.shape

@@ -78,7 +78,8 @@ void orc_set_num_threads(int k)
 /* Dense building blocks                                                     */
 /* ------------------------------------------------------------------------ */
 
-/* G = X^T X (Algorithm 1, step 1; C1 and C5 in the proof of Theorem 4.1).
+/* G = X^T X (the Gram product of Algorithm 1; C1 and C5 in the proof of
+ * Theorem 4.1).
  * G is n x n with leading dimension ldg; both triangles are written. */
 void orc_gram(int64_t m, int64_t n, const double *X, int64_t ldx, double *G, int64_t ldg)
 {
@@ -97,7 +98,7 @@ void orc_gram(int64_t m, int64_t n, const double *X, int64_t ldx, double *G, int
 }
 
 /* Upper Cholesky factor R of a symmetric positive definite G = R^T R
- * (Algorithm 1, step 2; C2 and C6).  Column-by-column: for column j,
+ * (Algorithm 1; C2 and C6).  Column-by-column: for column j,
  *   R[i][j] = (G[i][j] - sum_{k<i} R[k][i] R[k][j]) / R[i][i],   i < j
  *   R[j][j] = sqrt(G[j][j] - sum_{k<j} R[k][j]^2).
  * Returns ORC_OK, or ORC_CHOL_BREAKDOWN with *info = j when the radicand of
@@ -130,7 +131,7 @@ int orc_cholesky(int64_t n, const double *G, int64_t ldg, double *R, int64_t ldr
     return ORC_OK;
 }
 
-/* Q = X R^{-1} for upper-triangular R (Algorithm 1, step 3; eq. (es) row E_e,
+/* Q = X R^{-1} for upper-triangular R (the solve of Algorithm 1; eq. (es) row E_e,
  * C3 and C7).  Row-wise forward substitution:
  *   q_ij = (x_ij - sum_{k<j} q_ik r_kj) / r_jj.
  * Q may alias X (the solve is row-local and reads x_ij before writing q_ij). */
@@ -236,7 +237,7 @@ void orc_extract_upper(int64_t n, const double *A, int64_t lda, double *N, int64
 }
 
 /* R-factor of the thin Householder QR of A (s x n, s >= n), A unchanged
- * (Algorithm 5 step 2, Algorithm 6 step 3, Algorithm 7 step 3; eq. (eh)).
+ * (R0 in Algorithms 5, 6 and 7; eq. (eh)).
  * For k = 0..n-1 on the working copy W:
  *   alpha = W[k][k], sigma = sum_{i>k} W[i][k]^2;
  *   if sigma == 0: no reflection, R[k][k] = alpha;
@@ -338,7 +339,7 @@ static void orc_r0(int method, int64_t s, int64_t n, const double *A, int64_t ld
 }
 
 /* Y = S X with an explicit dense sketch S (s x m, leading dimension lds)
- * (Algorithm 6 step 1, Algorithm 7 step 2; eq. (es)).
+ * (S X in Algorithm 6, S M in Algorithm 7; eq. (es)).
  * Y[r][j] = sum_{i=0..m-1} S[r][i] X[i][j], summed in increasing i. */
 void orc_sketch_dense(int64_t s, int64_t m, int64_t n, const double *S, int64_t lds,
                       const double *X, int64_t ldx, double *Y, int64_t ldy)
@@ -434,8 +435,8 @@ int orc_cholqr2(int64_t m, int64_t n, const double *X, int64_t ldx, double *Q, i
     return st;
 }
 
-/* Steps shared by RCLUPP and RCLUPPr after R1 is known (Algorithm 6 steps
- * 5-7, evaluated as C1..C8 of the proof of Theorem 4.1):
+/* Steps shared by RCLUPP and RCLUPPr after R1 is known (the CholeskyQR2 of
+ * Q1 in Algorithm 6, evaluated as C1..C8 of the proof of Theorem 4.1):
  *   Q1 = X R1^{-1}; G = Q1^T Q1; R2 = chol(G); Q2 = Q1 R2^{-1}; R3 = R2 R1;
  *   G1 = Q2^T Q2; R4 = chol(G1); Q = Q2 R4^{-1}; R = R4 R3.
  * *info encodes the failing Cholesky as 100000*pass + column (pass 1 or 2). */
@@ -484,7 +485,7 @@ static int orc_precond_then_cholqr2(int64_t m, int64_t n, const double *X, int64
     return st;
 }
 
-/* R1 from a sketched s x n matrix Y (Algorithm 6 steps 2-4):
+/* R1 from a sketched s x n matrix Y (the preconditioner of Algorithm 6):
  *   [M, N, P] = LU(Y); R0 = R-factor of HouseholderQR(M); R1 = R0 N;
  * then the diagonal sign normalisation of R1.  Y is not modified. */
 int orc_sketch_precond(int64_t s, int64_t n, const double *Y, int64_t ldy, double *R1,

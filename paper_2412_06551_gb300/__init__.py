@@ -592,7 +592,7 @@ def rclupp_tall_lupp(A, *, check=True):
 
 
 def rclupp_sketch_precond(Y, r0=R0_HOUSEHOLDER):
-    """R1 from a sketched matrix (Algorithm 6 steps 2-4, signs normalised),
+    """R1 from a sketched matrix (the preconditioner of Algorithm 6, signs normalised),
     R0 by Householder (default) or Givens rotations."""
     Y, ldy = colmajor(Y)
     s, n = Y.shape

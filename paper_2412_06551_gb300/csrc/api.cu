@@ -384,7 +384,7 @@ rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, 
 }
 
 // Randomized drivers after the sketch: R1 from the sketch (the preconditioner
-// `precond`, steps 2-4 of Algorithm 6 or 3-4 of Algorithm 7), then CholeskyQR2
+// `precond` of Algorithm 6 or 7), then CholeskyQR2
 // of Q1 = X R1^{-1}.  At a reduced sketch tier the first Cholesky is assessed
 // and, if it broke down or shows Q1 too ill-conditioned, the sketch is redone
 // at the next tier (bf16 -> three-term bf16 -> binary64).  *tier_used reports
@@ -644,8 +644,8 @@ rclupp_status_t rclupp_factor(rclupp_handle_t h, int64_t m, int64_t n, const dou
     DevStatus *ds = h->d_status;
     const int ni = int(n), si = int(o.s);
     int tier = o.prec;
-    // X_s = S X (step 1); [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M);
-    // R1 = R0 N (steps 2-4); then steps 5-7
+    // X_s = S X; [M, N, P] = LU(X_s); R0 = R of HouseholderQR(M); R1 = R0 N;
+    // then CholeskyQR2 of Q1 = X R1^{-1} (Algorithm 6)
     auto precond = [&]() {
         return launch_sketch_precond(b.Y, o.s, si, ni, b.W, b.RP[0], b.rinv[0], nullptr, 0, ds, 1, s,
                                      o.r0_method);
@@ -681,11 +681,11 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
     int tier = o.prec;
     do {
         if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
-        // [M, N, P] = LU(X) (step 1)
+        // [M, N, P] = LU(X) (Algorithm 7)
         if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
             ls = RCLUPP_ERR_CUDA; break; }
-        // M_s = S M (step 2); R0 = R of HouseholderQR(M_s); R1 = R0 N (steps 3-4);
-        // then steps 5-7.  Q1 overwrites the LU only after M_s is formed.
+        // M_s = S M; R0 = R of HouseholderQR(M_s); R1 = R0 N; then CholeskyQR2
+        // of Q1 = X R1^{-1}.  Q1 overwrites the LU only after M_s is formed.
         auto precond = [&]() {
             return launch_rcluppr_r1(b.Y, o.s, si, ni, L, ldl, b.W, b.RP[0], b.rinv[0], s, o.r0_method);
         };

@@ -1,6 +1,6 @@
 // Gram product G = A^T A emulating binary64 on the tensor cores (the
 // precision form of the CholeskyQR pass: Gram as split-bf16 products with
-// fp32 accumulation, Algorithm 1 step 1 / C1).
+// fp32 accumulation; Algorithm 1, C1).
 //
 // Splitting (emu.cuh): per column j of A, with 2^E_j above every |a_ij|,
 // a_ij = 2^(E_j - 7) sum_{s=0..7} d_s 2^(-8s) up to 2^(E_j - 64), |d_s| <= 128.

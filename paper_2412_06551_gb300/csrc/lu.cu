@@ -1,5 +1,5 @@
 // Tall LU with partial pivoting of an m x n FP64 matrix, in place
-// (Algorithm 4 step 1; Algorithm 7 step 1): PX = MN with the pivot of
+// ([M, N, P] = LU(X) of Algorithms 4 and 7): PX = MN with the pivot of
 // column k the first row of largest magnitude among rows >= k.
 //
 // Blocked right-looking schedule with panels of NB columns:

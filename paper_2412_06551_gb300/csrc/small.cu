@@ -1,6 +1,6 @@
 // Small dense FP64 factorizations that stay on the device (s x n and n x n,
-// n <= 256): the LU with partial pivoting of the sketch (Algorithm 6 step 2,
-// eq. (elu)), the R-factor of a thin Householder QR (step 3, eq. (eh)), the
+// n <= 256): the LU with partial pivoting of the sketch (Algorithm 6,
+// eq. (elu)), the R-factor of a thin Householder QR (eq. (eh)), the
 // triangular products R1 = R0 N, R3 = R2 R1, R = R4 R3 (eq. (ey), C4, C8),
 // and the Cholesky factorizations of the Gram matrices (C2, C6) with a
 // breakdown status instead of NaNs.  This file holds the general one-CTA
@@ -196,8 +196,8 @@ __device__ void copy_out_upper(const double *RP, int n, int n_pad, double *R, in
     }
 }
 
-// mode 0 (RCLUPP, Algorithm 6 steps 2-4): LU of Y, Householder R of M,
-//   R1 = R0 N.   mode 1 (RCLUPPr, Algorithm 7 steps 3-4): Y is already M_s;
+// mode 0 (RCLUPP, Algorithm 6): LU of Y, Householder R of M,
+//   R1 = R0 N.   mode 1 (RCLUPPr, Algorithm 7): Y is already M_s;
 //   Householder R of Y, R1 = R0 N with N the top of an in-place tall LU (ldn).
 __global__ void __launch_bounds__(kSmallThreads)
     k_small_precond(const double *__restrict__ Y, int64_t ldy, int s, int n, int mode,

@@ -5,12 +5,12 @@
 // sums and the pivot row move between the CTAs through distributed shared
 // memory; two cluster barriers per column order them.
 //
-//   k_precond_cluster, mode 0 (RCLUPP, Algorithm 6 steps 2-4): LU with
+//   k_precond_cluster, mode 0 (RCLUPP, Algorithm 6): LU with
 //     partial pivoting of Y (eq. (elu); first largest magnitude, smallest row
 //     on ties), R0 = R-factor of the Householder QR of M (eq. (eh), LAPACK
 //     larfg convention), R1 = R0 N (eq. (ey)) with rows of negative diagonal
 //     negated.
-//   mode 1 (RCLUPPr, Algorithm 7 steps 3-4; RCholeskyQR, Algorithm 5): the
+//   mode 1 (RCLUPPr, Algorithm 7; RCholeskyQR, Algorithm 5): the
 //     Householder R of Y, R1 = R0 N with N the upper triangle of an external
 //     factor, or N = I.
 //   mode | kGivensMode: R0 by Givens rotations instead of Householder (the

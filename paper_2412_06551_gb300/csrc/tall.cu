@@ -1,7 +1,7 @@
-// Tall m x n passes over X (FP64): the sketch S X (Algorithm 6 step 1,
-// Algorithm 7 step 2), the Gram product A^T A (Algorithm 1 step 1, C1/C5),
-// and the triangular solve A R^{-1} fused with the Gram of its result
-// (Algorithm 1 step 3 with C1; C3 + C5; C7).
+// Tall m x n passes over X (FP64): the sketch S X (Algorithm 6; S M in
+// Algorithm 7), the Gram product A^T A (Algorithm 1, C1/C5), and the
+// triangular solve A R^{-1} fused with the Gram of its result (Algorithm 1,
+// C1; C3 + C5; C7).
 //
 // Design (GB300, FP64 pipe bound): each CTA owns a contiguous chunk of rows
 // and walks it in row tiles of BM x ncols staged in shared memory by a 2-D

@@ -1,7 +1,7 @@
 // Reduced-precision Gaussian sketch on the 5th-generation tensor cores
 // (tcgen05, kind::f16 with bf16 operands, fp32 accumulation in TMEM).
 //
-// The sketch of Algorithm 6 step 1 (and of Algorithm 7 step 2) only has to
+// The sketch S X of Algorithm 6 (and S M of Algorithm 7) only has to
 // be a subspace embedding (Section 3), so its product may run at reduced
 // precision.  Y = S X with S generated on the fly: each CTA owns one tile of
 // 128 sketch rows x NT columns of Y (M = 128, N = NT <= 256) and a contiguous

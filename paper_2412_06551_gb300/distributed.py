@@ -99,11 +99,11 @@ def rclupp_factor_sharded(X_local, row0: int, *, s: Optional[int] = None, kind: 
             raise ValueError("the SRHT of a row-sharded matrix needs order_log2 = ceil(log2(m)) "
                              "of the whole matrix")
         sk["order_log2"] = order_log2
-    # step 1: X_s = S X as a sum of the ranks' partials (all-reduce 1)
+    # X_s = S X as a sum of the ranks' partials (all-reduce 1)
     Y = allreduce(steps.sketch(X_local, **sk))
-    # steps 2-4 on every rank: LU of X_s, Householder R of M, R1 = R0 N
+    # on every rank: LU of X_s, Householder R of M, R1 = R0 N
     R1 = steps.precond(Y)
-    # steps 5-7: CholeskyQR2 of Q1 = X R1^{-1} (all-reduces 2 and 3)
+    # CholeskyQR2 of Q1 = X R1^{-1} (all-reduces 2 and 3)
     Q1, G1 = steps.trsm_gram(X_local, R1, gram=True)
     R2 = _cholesky_or_raise(steps, allreduce(G1), 1)
     Q2, G2 = steps.trsm_gram(Q1, R2, gram=True)

@@ -96,7 +96,7 @@ def test_zero_column_status_matches_oracle(rq, name):
     assert info.failed_step == ZERO_COL_STEP[name] and info.info == 7, (info.failed_step, info.info)
     o_pass, o_col = divmod(eo.value.info, 100000)
     assert o_col == 7
-    if o_pass:  # the oracle's CholeskyQR pass p is the device's step 2 + p
+    if o_pass:  # the oracle's CholeskyQR pass p is the device's failed_step 2 + p
         assert info.failed_step == 2 + o_pass
     _still_works(rq, name)
 
