@@ -180,7 +180,8 @@ rclupp_status_t rclupp_workspace_bytes(rclupp_handle_t handle, size_t *bytes);
  * triangular factors, and for RCLUPPr / LC2 an m x n copy of the LU factor
  * when q_aliases_x != 0 (or, for RCLUPPr, at a non-binary64 tier).  A handle
  * grows its workspace to this size on the first such call.  No GPU work;
- * errors as the drivers' argument checks. */
+ * without a visible device the size is the one a GB300 (152 SMs) needs.
+ * Errors as the drivers' argument checks. */
 rclupp_status_t rclupp_workspace_size(int32_t algo, int64_t m, int64_t n, const rclupp_opts_t *opts,
                                       int32_t q_aliases_x, size_t *bytes);
 /* Human-readable name of a status code (static string). */

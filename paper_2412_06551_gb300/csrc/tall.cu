@@ -36,7 +36,9 @@ int num_sms() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-        if (cached <= 0) cached = 1;
+        // no visible device (a host-only size query): the GB300's 152 SMs,
+        // the only GPU this build targets
+        if (cached <= 0) cached = 152;
     }
     return cached;
 }

@@ -77,6 +77,11 @@ def test_workspace_size_query_needs_no_gpu():
     assert lu_alias - lu >= m * n * 8
     assert rq.workspace_size(rq.ALGO_LC2, m, n, q_aliases_x=True) - rq.workspace_size(rq.ALGO_LC2, m, n) >= m * n * 8
     assert rq.workspace_size(rq.ALGO_RCLUPPR, m, n, prec=rq.PREC_EMULATED) >= lu_alias - 256
+    # sized for the GB300's 152 SMs: per-CTA partial sums of up to 2 * 152 + 8
+    # CTAs (three 128 x 128 Gram slots; an s x n sketch tile at s = 4096)
+    slots = 2 * 152 + 8
+    assert a >= slots * 3 * 128 * 128 * 8
+    assert rq.workspace_size(rq.ALGO_RCLUPP, 10 ** 6, 256, s=4096) >= slots * 4096 * 256 * 8
     with pytest.raises(rq.RclupError):
         rq.workspace_size(rq.ALGO_RCLUPP, 10, 20)        # m < n
     with pytest.raises(rq.RclupError):
