@@ -155,3 +155,64 @@ def test_row_block_partition():
             assert sum(b[1] for b in blocks) == m
             for (a0, an), (b0, _) in zip(blocks, blocks[1:]):
                 assert a0 + an == b0
+
+
+def _failing_worker(rank, world, port, algo, q):
+    # a numerical failure is decided on replicated, all-reduced data, so every
+    # rank raises at the same point and none is left waiting in a collective
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from paper_2412_06551_gb300 import distributed as D
+    m, n = 3000, 24
+    x, S = _problem(m, n, 1e12 if algo == "cholqr2" else 1e4)
+    if algo == "rclupp":
+        x[:, 7] = 0.0  # the sketch has a zero column: zero pivot in its LU
+    row0, rows = D.row_block(m, world, rank)
+    sizes = []
+
+    def allreduce(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        sizes.append(tuple(a.shape))
+        return np.asfortranarray(t.numpy())
+
+    xl = np.asfortranarray(x[row0:row0 + rows])
+    try:
+        if algo == "rclupp":
+            D.rclupp_factor_sharded(xl, row0, s=2 * n, seed=77, steps=OracleSteps(S), allreduce=allreduce)
+        else:
+            D.cholqr2_factor_sharded(xl, steps=OracleSteps(S), allreduce=allreduce)
+        q.put((rank, "ok", None, None, sizes))
+    except oracle.OracleError as e:
+        q.put((rank, "oracle", e.status, e.info, sizes))
+    except Exception as e:  # the library's error type
+        q.put((rank, type(e).__name__, getattr(e, "status", None), getattr(e, "column", None), sizes))
+    dist.barrier()  # every rank is past the failure: nobody waits in a collective
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("algo,port", [("cholqr2", 29563), ("rclupp", 29564)])
+def test_sharded_failure_is_raised_on_every_rank(algo, port):
+    import oracle
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_failing_worker, args=(r, world, port, algo, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted([q.get(timeout=240) for _ in range(world)], key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    kinds = {o[1:4] for o in out}
+    assert len(kinds) == 1, out  # the same failure, status and column on every rank
+    kind, status, col = kinds.pop()
+    if algo == "cholqr2":
+        assert kind == "RclupError" and status == oracle.CHOL_BREAKDOWN and col >= 1
+        assert all(o[4] == [(24, 24)] for o in out)  # failed in the first pass, after one all-reduce
+    else:
+        # the replicated preconditioner's LU (through the oracle here) finds the zero pivot
+        assert kind == "oracle" and status == oracle.LU_ZERO_PIVOT and col == 7
+        assert all(o[4] == [(48, 24)] for o in out)  # only the sketch was all-reduced
