@@ -20,6 +20,11 @@
  *     returned.  Entry points marked "async" only enqueue.
  *   - On any status other than RCLUPP_OK the contents of the outputs are
  *     unspecified.  Argument errors are detected before any GPU work.
+ *   - Errors every entry point may return besides those it lists: ERR_ARG
+ *     (a NULL pointer, a size below 1, a leading dimension below the number
+ *     of rows), ERR_UNSUPPORTED (n > 256, m >= 2^31, s > 4096), ERR_NOMEM
+ *     (the workspace could not grow), ERR_CUDA (a CUDA call failed) and
+ *     ERR_TIMEOUT (a bounded device wait gave up after 2 s).
  *   - R outputs are n x n upper triangular with the strict lower triangle set
  *     to zero and a positive diagonal (the unique thin QR).
  *   - Q may alias X for rclupp_factor and cholqr2_factor (every tall pass is
