@@ -86,3 +86,47 @@ def test_workspace_size_query_needs_no_gpu():
         rq.workspace_size(rq.ALGO_RCLUPP, 10, 20)        # m < n
     with pytest.raises(rq.RclupError):
         rq.workspace_size(rq.ALGO_RCLUPP, 1000, 300)     # n > 256
+
+
+def test_product_sources_never_reach_the_oracle():
+    # the package and its CUDA sources name neither the oracle nor the input
+    # generators: no import, no include, no path
+    import ast
+    pkg = os.path.join(ROOT, "paper_2412_06551_gb300")
+    checked = 0
+    for dirpath, dirs, files in os.walk(pkg):
+        dirs[:] = [d for d in dirs if d not in ("_build", "__pycache__")]
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                tree = ast.parse(open(path).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        names = [a.name for a in node.names]
+                    elif isinstance(node, ast.ImportFrom):
+                        names = [node.module or ""]
+                    else:
+                        continue
+                    assert not any(nm.split(".")[0] in ("oracle", "synth") for nm in names), (path, names)
+            elif f.endswith((".cu", ".cuh", ".h", ".c", ".cpp")):
+                src = open(path).read().lower()
+                assert "oracle" not in src and "synth" not in src, path
+            else:
+                continue
+            checked += 1
+    assert checked >= 15
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import subprocess
+    import sys
+    code = ("import paper_2412_06551_gb300 as rq\n"
+            "from paper_2412_06551_gb300 import _build\n"
+            "_build.LIB = %r\n"
+            "try:\n"
+            "    rq.load(build=False)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n") % str(tmp_path / "absent.so")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "raised: librclupp.so is missing" in r.stdout
