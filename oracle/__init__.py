@@ -77,6 +77,7 @@ def _load():
                 "orc_lc2": ([I64, I64, P, I64, P, I64, P, I64, P], I32),
                 "orc_rclupp": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P, I32], I32),
                 "orc_rcluppr": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I64, P, I32], I32),
+                "orc_rcluppr_precond": ([I64, I64, P, I64, I32, I64, I32, P, I64, P, P, P, I64, P, I32], I32),
                 "orc_philox4x32_10": ([P, P, P], None),
                 "orc_ln_f32": ([ctypes.c_float], ctypes.c_float),
                 "orc_cossin_2pi_f32": ([ctypes.c_float, P, P], None),
@@ -246,6 +247,29 @@ def sketch_precond(y, raise_on_error: bool = True, r0: str = "householder"):
     r1 = np.zeros((n, n), order="F")
     info = np.zeros(1, dtype=np.int64)
     st = _load().orc_sketch_precond(s, n, _p(y), s, _p(r1), n, _p(info), R0_METHODS[r0])
+    _check(st, info, raise_on_error)
+    return r1, st, int(info[0])
+
+
+def rcluppr_precond(x, S=None, sparse=None, raise_on_error: bool = True, r0: str = "householder"):
+    """R1 of RCLUPPr (the preconditioner of Algorithm 7): [M, N, P] = LU(X),
+    R0 = R-factor of S M, R1 = R0 N, signs normalised; dense S or
+    sparse=(s, zeta, rows, signs). Returns (R1, status, info)."""
+    x = _f(x)
+    m, n = x.shape
+    r1 = np.zeros((n, n), order="F")
+    info = np.zeros(1, dtype=np.int64)
+    lib = _load()
+    if sparse is not None:
+        s, zeta, rows, signs = sparse
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        signs = np.ascontiguousarray(signs, dtype=np.int8)
+        st = lib.orc_rcluppr_precond(m, n, _p(x), m, SKETCH_SPARSE, s, zeta, None, 0, _p(rows), _p(signs),
+                                     _p(r1), n, _p(info), R0_METHODS[r0])
+    else:
+        S = _f(S)
+        st = lib.orc_rcluppr_precond(m, n, _p(x), m, SKETCH_DENSE, S.shape[0], 0, _p(S), S.shape[0], None,
+                                     None, _p(r1), n, _p(info), R0_METHODS[r0])
     _check(st, info, raise_on_error)
     return r1, st, int(info[0])
 

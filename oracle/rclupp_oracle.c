@@ -556,6 +556,48 @@ int orc_rclupp(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int
     return st;
 }
 
+/* R1 of RCLUPPr (the preconditioner of Algorithm 7):
+ *   [M, N, P] = LU(X); M_s = S M (M in the row order the LU leaves it);
+ *   R0 = R-factor of M_s (HouseholderQR, or Givens rotations); R1 = R0 N;
+ * then the diagonal sign normalisation of R1.  X is not modified; R1 is
+ * n x n with leading dimension ldr.  Returns the LU's status (*info = the
+ * column of a zero pivot). */
+int orc_rcluppr_precond(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, int64_t s,
+                        int zeta, const double *S, int64_t lds, const int32_t *rows,
+                        const int8_t *signs, double *R1, int64_t ldr, int64_t *info, int r0_method)
+{
+    if (m < n || n < 1 || s < n)
+        return ORC_ERR_ARG;
+    size_t mn = (size_t)m * (size_t)n, nn = (size_t)n * (size_t)n;
+    double *A = (double *)malloc(sizeof(double) * mn);
+    double *M = (double *)malloc(sizeof(double) * mn);
+    double *N = (double *)malloc(sizeof(double) * nn);
+    double *Ms = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
+    double *R0 = (double *)malloc(sizeof(double) * nn);
+    int32_t *ipiv = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int st = ORC_ERR_NOMEM;
+    if (A && M && N && Ms && R0 && ipiv) {
+        for (int64_t j = 0; j < n; ++j)
+            memcpy(A + j * m, X + j * ldx, sizeof(double) * (size_t)m);
+        st = orc_gepp(m, n, A, m, ipiv, info);
+        if (st == ORC_OK) {
+            orc_extract_unit_lower(m, n, A, m, M, m);
+            orc_extract_upper(n, A, m, N, n);
+            orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, M, m, Ms, s);
+            orc_r0(r0_method, s, n, Ms, s, R0, n);
+            orc_trmm_upper(n, R0, n, N, n, R1, ldr);
+            orc_sign_fix_rows(n, R1, ldr);
+        }
+    }
+    free(ipiv);
+    free(R0);
+    free(Ms);
+    free(N);
+    free(M);
+    free(A);
+    return st;
+}
+
 /* [Q, R] = RCLUPPr(X) (Algorithm 7):
  *   [M, N, P] = LU(X); M_s = S M; R0 = R of HouseholderQR(M_s); R1 = R0 N;
  *   Q1 = X R1^{-1}; [Q, Z] = CholeskyQR2(Q1); R = Z R1.
@@ -566,36 +608,15 @@ int orc_rcluppr(int64_t m, int64_t n, const double *X, int64_t ldx, int kind, in
 {
     if (m < n || n < 1 || s < n)
         return ORC_ERR_ARG;
-    size_t mn = (size_t)m * (size_t)n, nn = (size_t)n * (size_t)n;
-    double *A = (double *)malloc(sizeof(double) * mn);
-    double *M = (double *)malloc(sizeof(double) * mn);
-    double *N = (double *)malloc(sizeof(double) * nn);
-    double *Ms = (double *)malloc(sizeof(double) * (size_t)s * (size_t)n);
-    double *R0 = (double *)malloc(sizeof(double) * nn);
-    double *R1 = (double *)malloc(sizeof(double) * nn);
-    int32_t *ipiv = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *R1 = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
     int st = ORC_ERR_NOMEM;
-    if (A && M && N && Ms && R0 && R1 && ipiv) {
-        for (int64_t j = 0; j < n; ++j)
-            memcpy(A + j * m, X + j * ldx, sizeof(double) * (size_t)m);
-        st = orc_gepp(m, n, A, m, ipiv, info);
-        if (st == ORC_OK) {
-            orc_extract_unit_lower(m, n, A, m, M, m);
-            orc_extract_upper(n, A, m, N, n);
-            orc_apply_sketch(kind, s, m, n, zeta, S, lds, rows, signs, M, m, Ms, s);
-            orc_r0(r0_method, s, n, Ms, s, R0, n);
-            orc_trmm_upper(n, R0, n, N, n, R1, n);
-            orc_sign_fix_rows(n, R1, n);
+    if (R1) {
+        st = orc_rcluppr_precond(m, n, X, ldx, kind, s, zeta, S, lds, rows, signs, R1, n, info,
+                                 r0_method);
+        if (st == ORC_OK)
             st = orc_precond_then_cholqr2(m, n, X, ldx, R1, Q, ldq, R, ldr, info);
-        }
     }
-    free(ipiv);
     free(R1);
-    free(R0);
-    free(Ms);
-    free(N);
-    free(M);
-    free(A);
     return st;
 }
 

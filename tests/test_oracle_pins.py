@@ -322,6 +322,66 @@ def test_gaussian_sketch_statistics():
     assert oracle.gauss_entry(123, 5, 17) != oracle.gauss_entry(124, 5, 17)
 
 
+def test_gaussian_sketch_rows_are_uncorrelated():
+    # S = G / sqrt(s) with G's entries independent (Section 3): across many
+    # columns, the sample correlation of any two rows is O(1/sqrt(columns)).
+    # Rows 4b .. 4b+3 share one Philox block, so this also pins that each
+    # lane draws its own value from the block.
+    cols = 20000
+    S = oracle.gaussian_sketch_matrix(8, cols, 31)
+    c = np.corrcoef(S)
+    off = c[~np.eye(8, dtype=bool)]
+    assert np.max(np.abs(off)) < 6.0 / math.sqrt(cols)
+
+
+def test_cholqr2_stage_recovers_from_a_weak_sketch():
+    # A sketch that only sees the first s rows, where X's first column is 1e-4
+    # times smaller than elsewhere, is a poor embedding for this X: Q1 = X R1^-1
+    # has kappa ~ 6e4 (a Gaussian s = 2n sketch gives ~ 5), and not by a column
+    # scaling -- the under-sketched direction lies along the first row of
+    # R1^-1, which mixes all columns -- so the first CholeskyQR pass leaves
+    # Q2 visibly non-orthogonal and R4 far from I.  CholeskyQR2 still returns
+    # an orthonormal Q while kappa(Q1) is far below u^(-1/2) (Lemma 3.1), and R
+    # = R4 R2 R1 (C4, C8) is X's R-factor to first order in kappa(Q1) u.
+    m, n, s = 3000, 16, 32
+    u = 2.0 ** -53
+    rng = np.random.default_rng(91)
+    x = rng.standard_normal((m, n))
+    x[:s, 0] *= 1e-4
+    S = np.zeros((s, m))
+    S[:, :s] = rng.standard_normal((s, s)) / math.sqrt(s)
+    R1, _, _ = oracle.sketch_precond(S @ x)
+    Q1 = oracle.trsm(x, R1)
+    k1 = np.linalg.cond(Q1 / np.sqrt(np.sum(Q1 * Q1, axis=0)))  # after column equilibration
+    assert k1 > 1e4
+    rh = np.linalg.qr(x, mode="r")
+    rh = np.sign(np.diag(rh))[:, None] * rh
+    q, r, _ = oracle.rclupp(x, S=S)
+    assert oracle.orthogonality(q) <= 1e-13
+    assert oracle.residual(x, q, r) <= 20 * k1 * u
+    assert np.linalg.norm(r - rh) <= 20 * k1 * u * np.linalg.norm(rh)
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e12])
+def test_rcluppr_preconditioner_is_the_r_factor_of_the_sketched_pivoted_x(kappa):
+    # Algorithm 7: [M, N, P] = LU(X), R1 = R(S M) N.  P X = M N and N is upper
+    # triangular, so R(S M) N = R(S M N) = R(S P X) up to row signs: the
+    # preconditioner of Algorithm 6 for the row-permuted X.  Q1 = X R1^-1 is
+    # then as well conditioned as a Gaussian sketch with s = 2n makes it
+    # (about (1 + sqrt(n/s)) / (1 - sqrt(n/s)) ~ 5.8), whatever kappa(X) is.
+    from scipy import linalg as sla
+    m, n = 2000, 32
+    x = synth.svd_matrix(m, n, kappa, 5)
+    S = oracle.gaussian_sketch_matrix(2 * n, m, 3)
+    R1, _, _ = oracle.rcluppr_precond(x, S=S)
+    assert np.array_equal(R1, np.triu(R1)) and np.all(np.diag(R1) > 0)
+    assert np.linalg.cond(np.linalg.solve(R1.T, x.T).T) <= 20
+    P, _, _ = sla.lu(x)  # x = P L U: LAPACK getrf's pivots, which GEPP reproduces
+    ref = np.linalg.qr(S @ (P.T @ x), mode="r")
+    ref = np.sign(np.diag(ref))[:, None] * ref
+    assert np.linalg.norm(R1 - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_sparse_sign_pattern_properties():
     s, m, zeta = 64, 5000, 8
     rows, signs = oracle.sparse_sign_pattern(s, m, zeta, seed=3)
