@@ -8,6 +8,7 @@ must fail.  A control run of the unchanged copy must pass, and the copy must
 be the module the subprocess imports.  CPU only; nothing here touches the
 product library.
 """
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -19,7 +20,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"),
         os.path.join(ROOT, "tests", "test_oracle_srht.py")]
 
-# (name, original text, planted mistake); each original occurs exactly once
+# (name, original text, planted mistake); each original occurs exactly once.
+# Mistakes that no output can show are left out (e.g. keeping the LU
+# multipliers below N's diagonal: the triangular product reads only N's
+# upper triangle).
 MUTANTS = [
     ("gram_drops_last_row",
      "for (int64_t i = 0; i < m; ++i)\n                acc += xk[i] * xj[i];",
@@ -81,6 +85,66 @@ MUTANTS = [
     ("scholqr3_shift_without_n",
      "11.0 * ((double)m * (double)n * u + (double)n * (double)(n + 1) * u) * g",
      "11.0 * ((double)m * (double)n * u + (double)(n + 1) * u) * g"),
+    ("unit_lower_keeps_the_diagonal",
+     "IDX(M, ldm, i, j) = i > j ? IDX(A, lda, i, j) : (i == j ? 1.0 : 0.0);",
+     "IDX(M, ldm, i, j) = i >= j ? IDX(A, lda, i, j) : 0.0;"),
+    ("lc2_gram_of_x_not_m",
+     "orc_gram(m, n, M, m, G, n);",
+     "orc_gram(m, n, X, ldx, G, n);"),
+    ("rcholqr_sign_normalisation_dropped",
+     "orc_r0(r0_method, s, n, K, s, R1, n);\n        orc_sign_fix_rows(n, R1, n);",
+     "orc_r0(r0_method, s, n, K, s, R1, n);"),
+    ("cholqr2_product_order",
+     "            if (st == ORC_OK)\n                orc_trmm_upper(n, Z, n, R1, n, R, ldr);",
+     "            if (st == ORC_OK)\n                orc_trmm_upper(n, R1, n, Z, n, R, ldr);"),
+    ("sparse_duplicate_rows_allowed",
+     "            if (dup)\n                continue;\n            rows[cnt] = row;",
+     "            if (dup && 0)\n                continue;\n            rows[cnt] = row;"),
+    ("sparse_sign_from_the_top_bit",
+     "signs[cnt] = (w[t] & 1u) ? (int8_t)-1 : (int8_t)1;",
+     "signs[cnt] = (w[t] >> 31) ? (int8_t)-1 : (int8_t)1;"),
+    ("bf16_truncates",
+     "if (rnd && (sticky || lsb))",
+     "if (0)"),
+    ("bf16_ties_away_from_zero",
+     "if (rnd && (sticky || lsb))",
+     "if (rnd)"),
+    ("bf16_split_wrong_residual",
+     "const double x3 = orc_round_bf16(r1 - x2);",
+     "const double x3 = orc_round_bf16(x - x2);"),
+    ("bf16_sketch_scaled_twice",
+     "            IDX(Y, ldy, r, j) *= scale;",
+     "            IDX(Y, ldy, r, j) *= scale * scale;"),
+    ("feistel_widths_not_swapped",
+     "        int t = wl;\n        wl = wr;\n        wr = t;",
+     "        int t = wl;\n        wl = t;\n        wr = wr;"),
+    ("srht_sign_bit_layout",
+     "d[i] = ((w[k >> 5] >> (k & 31u)) & 1u)",
+     "d[i] = ((w[k & 3u] >> (k >> 2)) & 1u)"),
+    ("srht_missing_scale",
+     "IDX(S, lds, r, i) = (d[i] < 0 ? -h : h) * scale;",
+     "IDX(S, lds, r, i) = (d[i] < 0 ? -h : h);"),
+    ("gaussian_sketch_missing_scale",
+     "IDX(S, lds, r, i) = (double)orc_gauss_entry(seed, r, i) * scale;",
+     "IDX(S, lds, r, i) = (double)orc_gauss_entry(seed, r, i);"),
+    ("gepp_rows_not_swapped",
+     "        if (p != k)\n            for (int64_t j = 0; j < n; ++j) {\n                double t = IDX(A, lda, k, j);",
+     "        if (0)\n            for (int64_t j = 0; j < n; ++j) {\n                double t = IDX(A, lda, k, j);"),
+    ("gepp_multiplier_times_pivot",
+     "IDX(A, lda, i, k) = IDX(A, lda, i, k) / piv;",
+     "IDX(A, lda, i, k) = IDX(A, lda, i, k) * piv;"),
+    ("householder_tau_sign",
+     "double tau = (beta - alpha) / beta;",
+     "double tau = (alpha - beta) / beta;"),
+    ("trsm_divides_by_the_first_diagonal",
+     "row[j] = acc / IDX(R, ldr, j, j);",
+     "row[j] = acc / IDX(R, ldr, 0, 0);"),
+    ("gram_one_triangle_only",
+     "            IDX(G, ldg, k, j) = acc;\n            IDX(G, ldg, j, k) = acc;",
+     "            IDX(G, ldg, k, j) = acc;"),
+    ("scholqr3_shift_first_diagonal_not_max",
+     "        if (IDX(G, ldg, j, j) > g)\n            g = IDX(G, ldg, j, j);",
+     "        if (j == 0)\n            g = IDX(G, ldg, j, j);"),
 ]
 
 
@@ -89,38 +153,52 @@ def _source():
         return f.read()
 
 
-def _run_pins(tmp_path, src):
+def _run_pins(tmp_path, src, pins=PINS):
     """Run the pin suites against an oracle package built from `src`."""
     pkg = tmp_path / "oracle"
     pkg.mkdir()
     shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), pkg / "__init__.py")
     (pkg / "rclupp_oracle.c").write_text(src)
     # the copy comes first (the working directory); the repository root, after
-    # it, supplies the input generators and the test configuration
-    env = dict(os.environ, PYTHONPATH=os.pathsep.join([ROOT] + [p for p in [os.environ.get("PYTHONPATH")] if p]))
+    # it, supplies the input generators and the test configuration; one
+    # OpenMP thread per run, since several runs go at once
+    env = dict(os.environ, OMP_NUM_THREADS="1",
+               PYTHONPATH=os.pathsep.join([ROOT] + [p for p in [os.environ.get("PYTHONPATH")] if p]))
     which = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"],
-                           cwd=tmp_path, env=env, capture_output=True, text=True, timeout=120)
+                           cwd=tmp_path, env=env, capture_output=True, text=True, timeout=300)
     assert which.returncode == 0 and which.stdout.strip().startswith(str(tmp_path)), which
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + PINS,
-                          cwd=tmp_path, env=env, capture_output=True, text=True, timeout=900)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + list(pins),
+                          cwd=tmp_path, env=env, capture_output=True, text=True, timeout=1200)
 
 
 @pytest.fixture(scope="module")
-def source():
+def runs(tmp_path_factory):
+    """The control and every mutant, run concurrently (each in its own
+    directory and process); name -> CompletedProcess."""
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    return _source()
+    source = _source()
+    jobs = {"control": (source, PINS)}
+    for name, old, new in MUTANTS:
+        assert source.count(old) == 1, name
+        # the SRHT's own pins first for its mistakes (-x stops at the first failure)
+        jobs[name] = (source.replace(old, new),
+                      PINS[::-1] if name.startswith(("srht", "feistel")) else PINS)
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {name: ex.submit(_run_pins, tmp_path_factory.mktemp(name), src, pins)
+                for name, (src, pins) in jobs.items()}
+        return {name: f.result() for name, f in futs.items()}
 
 
-def test_control_copy_passes_the_pins(tmp_path, source):
-    r = _run_pins(tmp_path, source)
+def test_control_copy_passes_the_pins(runs):
+    r = runs["control"]
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(tmp_path, source, name, old, new):
-    assert source.count(old) == 1, name
-    r = _run_pins(tmp_path, source.replace(old, new))
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(runs, name):
+    r = runs[name]
     # exit code 1: tests ran and at least one failed (not a build or collection error)
     assert r.returncode == 1, (name, r.returncode, r.stdout[-3000:], r.stderr[-2000:])
     assert " failed" in r.stdout, (name, r.stdout[-2000:])

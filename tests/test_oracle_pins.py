@@ -382,6 +382,18 @@ def test_rcluppr_preconditioner_is_the_r_factor_of_the_sketched_pivoted_x(kappa)
     assert np.linalg.norm(R1 - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_sparse_signs_are_independent_of_the_rows():
+    # The sparse-sign sketch draws each nonzero's row and its sign
+    # independently (a fair sign, Section 3's CountSketch with zeta = 1): for
+    # every row, the signs that land in it average to ~0.
+    s, m, zeta = 64, 20000, 8
+    rows, signs = oracle.sparse_sign_pattern(s, m, zeta, seed=5)
+    rows, signs = np.asarray(rows).ravel(), np.asarray(signs).ravel().astype(np.float64)
+    for r in range(s):
+        sel = signs[rows == r]
+        assert len(sel) > 1000 and abs(sel.mean()) < 5.0 / math.sqrt(len(sel)), r
+
+
 def test_sparse_sign_pattern_properties():
     s, m, zeta = 64, 5000, 8
     rows, signs = oracle.sparse_sign_pattern(s, m, zeta, seed=3)

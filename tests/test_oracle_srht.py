@@ -63,7 +63,7 @@ def test_signs_follow_philox_words():
     seed = 0x1234_5678_9ABC
     d = oracle.srht_signs(300, seed, row0=1000)
     key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
-    for i in (0, 1, 23, 24, 151, 152, 299):
+    for i in range(300):  # every bit position k = 0..127, across three Philox blocks
         g = 1000 + i
         q = g >> 7
         w = oracle.philox4x32_10(np.array([q & 0xFFFFFFFF, q >> 32, 0, 0x53524844], dtype=np.uint32), key)
