@@ -1,12 +1,12 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case plants one mistake in a copy of the oracle's C source (a dropped
-term, a wrong sign, a transposed operand, a wrong index, a wrong constant,
-a wrong operand order) and runs the pin suites (test_oracle_pins.py,
-test_oracle_srht.py) against that copy in a subprocess: at least one pin
-must fail.  A control run of the unchanged copy must pass, and the copy must
-be the module the subprocess imports.  CPU only; nothing here touches the
-product library.
+Each case plants one mistake in a copy of the oracle, in its C source or
+its Python layer (a dropped term, a wrong sign, a transposed operand, a
+wrong index, a wrong constant, a wrong operand order), and runs the pin
+suites (test_oracle_pins.py, test_oracle_srht.py) against that copy in a
+subprocess: at least one pin must fail.  A control run of the unchanged copy
+must pass, and the copy must be the module the subprocess imports.  CPU
+only; nothing here touches the product library.
 """
 import concurrent.futures
 import os
@@ -20,7 +20,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"),
         os.path.join(ROOT, "tests", "test_oracle_srht.py")]
 
-# (name, original text, planted mistake); each original occurs exactly once.
+# (name, original text, planted mistake[, "py" for the Python layer]); each
+# original occurs exactly once.
 # Mistakes that no output can show are left out (e.g. keeping the LU
 # multipliers below N's diagonal: the triangular product reads only N's
 # upper triangle).
@@ -145,19 +146,42 @@ MUTANTS = [
     ("scholqr3_shift_first_diagonal_not_max",
      "        if (IDX(G, ldg, j, j) > g)\n            g = IDX(G, ldg, j, j);",
      "        if (j == 0)\n            g = IDX(G, ldg, j, j);"),
+    # the oracle's Python layer (numpy helpers the tests use as references)
+    ("py_sparse_to_dense_scale",
+     "val = 1.0 / np.sqrt(zeta)",
+     "val = 1.0 / zeta", "py"),
+    ("py_sparse_to_dense_sign",
+     "np.where(np.asarray(signs) > 0, val, -val)",
+     "np.where(np.asarray(signs) > 0, -val, val)", "py"),
+    ("py_orthogonality_without_the_identity",
+     "q.T @ q - np.eye(n)",
+     "q.T @ q - 0.0 * np.eye(n)", "py"),
+    ("py_residual_not_relative",
+     '/ np.linalg.norm(x, "fro"))',
+     ")", "py"),
+    ("py_srht_order_off_by_one",
+     "    while (1 << b) < m:",
+     "    while (1 << b) <= m:", "py"),
+    ("py_bf16_split_third_term",
+     "x3 = r(x - x1 - x2)",
+     "x3 = r(x - x2)", "py"),
 ]
 
 
-def _source():
+def _sources():
+    """(C source, Python layer) of the oracle."""
     with open(os.path.join(ROOT, "oracle", "rclupp_oracle.c")) as f:
-        return f.read()
+        c = f.read()
+    with open(os.path.join(ROOT, "oracle", "__init__.py")) as f:
+        py = f.read()
+    return c, py
 
 
-def _run_pins(tmp_path, src, pins=PINS):
-    """Run the pin suites against an oracle package built from `src`."""
+def _run_pins(tmp_path, src, py, pins=PINS):
+    """Run the pin suites against an oracle package made of `src` (C) and `py`."""
     pkg = tmp_path / "oracle"
     pkg.mkdir()
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), pkg / "__init__.py")
+    (pkg / "__init__.py").write_text(py)
     (pkg / "rclupp_oracle.c").write_text(src)
     # the copy comes first (the working directory); the repository root, after
     # it, supplies the input generators and the test configuration; one
@@ -177,17 +201,18 @@ def runs(tmp_path_factory):
     directory and process); name -> CompletedProcess."""
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    source = _source()
-    jobs = {"control": (source, PINS)}
-    for name, old, new in MUTANTS:
-        assert source.count(old) == 1, name
+    c, py = _sources()
+    jobs = {"control": (c, py, PINS)}
+    for name, old, new, *target in MUTANTS:
+        text = py if target == ["py"] else c
+        assert text.count(old) == 1, name
+        c_m, py_m = (c, py.replace(old, new)) if target == ["py"] else (c.replace(old, new), py)
         # the SRHT's own pins first for its mistakes (-x stops at the first failure)
-        jobs[name] = (source.replace(old, new),
-                      PINS[::-1] if name.startswith(("srht", "feistel")) else PINS)
+        jobs[name] = (c_m, py_m, PINS[::-1] if "srht" in name or "feistel" in name else PINS)
     workers = max(1, min(8, os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {name: ex.submit(_run_pins, tmp_path_factory.mktemp(name), src, pins)
-                for name, (src, pins) in jobs.items()}
+        futs = {name: ex.submit(_run_pins, tmp_path_factory.mktemp(name), src, pysrc, pins)
+                for name, (src, pysrc, pins) in jobs.items()}
         return {name: f.result() for name, f in futs.items()}
 
 
