@@ -146,6 +146,24 @@ MUTANTS = [
     ("scholqr3_shift_first_diagonal_not_max",
      "        if (IDX(G, ldg, j, j) > g)\n            g = IDX(G, ldg, j, j);",
      "        if (j == 0)\n            g = IDX(G, ldg, j, j);"),
+    ("sparse_apply_scale",
+     "double val = 1.0 / sqrt((double)zeta);",
+     "double val = 1.0 / (double)zeta;"),
+    ("sparse_apply_ignores_signs",
+     "double sv = signs[i * zeta + t] > 0 ? val : -val;",
+     "double sv = val;"),
+    ("sparse_apply_first_nonzero_only",
+     "            for (int t = 0; t < zeta; ++t) {\n                int64_t r = rows[i * zeta + t];",
+     "            for (int t = 0; t < 1; ++t) {\n                int64_t r = rows[i * zeta + t];"),
+    ("cholqr2_second_pass_on_x",
+     "st = orc_cholqr(m, n, Q1, m, Q, ldq, Z, n, info);",
+     "st = orc_cholqr(m, n, X, ldx, Q, ldq, Z, n, info);"),
+    ("givens_rotates_only_zeros",
+     "            if (b == 0.0)\n                continue;",
+     "            if (b != 0.0)\n                continue;"),
+    ("sign_normalisation_of_the_diagonal_only",
+     "            for (int64_t j = i; j < n; ++j)\n                IDX(R, ldr, i, j) = -IDX(R, ldr, i, j);",
+     "            for (int64_t j = i; j < i + 1; ++j)\n                IDX(R, ldr, i, j) = -IDX(R, ldr, i, j);"),
     # the oracle's Python layer (numpy helpers the tests use as references)
     ("py_sparse_to_dense_scale",
      "val = 1.0 / np.sqrt(zeta)",
