@@ -130,3 +130,62 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert "raised: librclupp.so is missing" in r.stdout
+
+
+_ARG_SCRIPT = r'''
+import ctypes, json, sys
+import paper_2412_06551_gb300 as rq
+lib = rq.load()
+# argument checks run before the handle or any pointer is used: a zeroed
+# host block stands in for the handle and the matrices
+block = ctypes.create_string_buffer(1 << 16)
+h = ctypes.c_void_p(ctypes.addressof(block))
+X = Q = R = ctypes.c_void_p(ctypes.addressof(block))
+info = rq.Info()
+def opts(**kw):
+    o = rq.Opts()
+    o.kind, o.zeta, o.s, o.seed, o.prec = 0, 8, 0, 0, 0
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+out = {}
+rand = {"rclupp": lib.rclupp_factor, "rcluppr": lib.rclupp_r_factor, "rcholqr": lib.rcholqr_factor}
+plain = {"cholqr2": lib.cholqr2_factor, "lc2": lib.lc2_factor, "scholqr3": lib.scholqr3_factor}
+sizes = {"n0": (10, 0, 10, 10, 1), "m0": (0, 1, 1, 1, 1), "m_lt_n": (3, 5, 3, 3, 5),
+         "ldx_lt_m": (10, 4, 9, 10, 4), "ldq_lt_m": (10, 4, 10, 9, 4), "ldr_lt_n": (10, 4, 10, 10, 3),
+         "n_257": (600, 257, 600, 600, 257), "m_2_31": (1 << 31, 4, 1 << 31, 1 << 31, 4)}
+for name, f in list(rand.items()) + list(plain.items()):
+    for case, (m, n, ldx, ldq, ldr) in sizes.items():
+        args = (h, m, n, X, ldx) + ((None,) if name in rand else ()) + (Q, ldq, R, ldr, ctypes.byref(info))
+        out[name + ":" + case] = f(*args)
+for name, f in rand.items():
+    for case, o in {"s_lt_n": opts(s=3), "s_4097": opts(s=4097), "kind_7": opts(s=8, kind=7),
+                    "prec_9": opts(s=8, prec=9), "r0_5": opts(s=8, r0_method=5),
+                    "zeta_0": opts(s=8, kind=1, zeta=0), "zeta_17": opts(s=64, kind=1, zeta=17),
+                    "sparse_s_769": opts(s=769, kind=1, zeta=8), "srht_b_40": opts(s=8, kind=2, order_log2=40),
+                    "srht_order_too_small": opts(s=8, kind=2, order_log2=3),
+                    "explicit_lds_lt_s": opts(s=8, S=ctypes.addressof(block), lds=7),
+                    "givens_too_big": opts(s=4096, r0_method=1)}.items():
+        out[name + ":" + case] = f(h, 10000, 4 if case != "givens_too_big" else 256, X, 10000,
+                                   ctypes.byref(o), Q, 10000, R, 256, ctypes.byref(info))
+print(json.dumps(out))
+'''
+
+
+def test_argument_errors_are_found_before_the_handle_is_used():
+    # every driver rejects bad sizes, leading dimensions and options on the
+    # host, before it touches the handle, the matrices or the GPU (run in a
+    # subprocess: a check that let a case through would reach the dummy handle)
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _ARG_SCRIPT], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    ARG, UNSUP = rq.Status.ERR_ARG, rq.Status.ERR_UNSUPPORTED
+    expect_unsup = ("n_257", "m_2_31", "s_4097", "zeta_17", "sparse_s_769", "givens_too_big")
+    assert len(out) == 6 * 8 + 3 * 12
+    for key, st in out.items():
+        case = key.split(":")[1]
+        assert st == (UNSUP if case in expect_unsup else ARG), (key, st)
