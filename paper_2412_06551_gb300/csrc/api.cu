@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/rclupp.h"
@@ -35,7 +36,7 @@ struct rclupp_handle_s {
     cudaEvent_t fork = nullptr;
     cudaStream_t cap = nullptr;  // origin stream of the batch graph's capture
     cudaGraphExec_t graph_exec = nullptr;
-    uint64_t graph_sig = 0;
+    std::vector<unsigned char> graph_desc;  // description the cached graph was captured for
     unsigned long long graph_kernels = 0;
 };
 
@@ -56,25 +57,25 @@ rclupp_status_t ensure_streams(rclupp_handle_t h, int k) {
     return RCLUPP_OK;
 }
 
-// FNV-1a over the batch description (graph cache key).
-struct Fnv {
-    uint64_t h = 1469598103934665603ull;
+// Byte image of the batch description (graph cache key): the cached graph is
+// replayed only when every byte of the new description equals the stored one.
+struct DescBytes {
+    std::vector<unsigned char> b;
     template <class T>
     void add(const T *p, size_t count) {
-        const unsigned char *b = reinterpret_cast<const unsigned char *>(p);
-        for (size_t i = 0; i < count * sizeof(T); ++i) {
-            h ^= b[i];
-            h *= 1099511628211ull;
-        }
+        const unsigned char *q = reinterpret_cast<const unsigned char *>(p);
+        b.insert(b.end(), q, q + count * sizeof(T));
     }
 };
 
-uint64_t batch_signature(int algo, int count, const int64_t *m, const int64_t *n,
-                         const double *const *X, const int64_t *ldx, double *const *Q,
-                         const int64_t *ldq, double *const *R, const int64_t *ldr,
-                         const rclupp_opts_t *o, int branches, const void *ws,
-                         const LaunchPolicy &pol) {
-    Fnv f;
+std::vector<unsigned char> batch_description(int algo, int count, const int64_t *m,
+                                             const int64_t *n, const double *const *X,
+                                             const int64_t *ldx, double *const *Q,
+                                             const int64_t *ldq, double *const *R,
+                                             const int64_t *ldr, const rclupp_opts_t *o,
+                                             int branches, const void *ws,
+                                             const LaunchPolicy &pol) {
+    DescBytes f;
     f.add(&algo, 1);
     f.add(&count, 1);
     f.add(m, count);
@@ -90,7 +91,7 @@ uint64_t batch_signature(int algo, int count, const int64_t *m, const int64_t *n
     f.add(&ws, 1);
     f.add(&pol.grid_div, 1);
     f.add(&pol.fine_tiles, 1);
-    return f.h;
+    return std::move(f.b);
 }
 
 constexpr int kMaxN = 256;
@@ -802,9 +803,9 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
     LaunchPolicy pol;
     pol.grid_div = h->batch_grid_div;
     pol.fine_tiles = h->batch_fine_tiles;
-    const uint64_t sig = batch_signature(algo, count, m, n, X, ldx, Q, ldq, R, ldr, o.data(),
-                                         branches, h->ws, pol);
-    if (!(h->graph_exec && h->graph_sig == sig)) {
+    std::vector<unsigned char> desc = batch_description(algo, count, m, n, X, ldx, Q, ldq, R, ldr,
+                                                        o.data(), branches, h->ws, pol);
+    if (!(h->graph_exec && h->graph_desc == desc)) {
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
             h->graph_exec = nullptr;
@@ -880,7 +881,7 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
             h->graph_exec = nullptr;
             return RCLUPP_ERR_CUDA;
         }
-        h->graph_sig = sig;
+        h->graph_desc = std::move(desc);
     }
     if (cudaGraphLaunch(h->graph_exec, h->stream) != cudaSuccess) return RCLUPP_ERR_CUDA;
     prof_add_launches(h->graph_kernels);
