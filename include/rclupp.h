@@ -170,8 +170,10 @@ typedef struct {
 
 /* Create a handle bound to the CUDA stream `stream` (a cudaStream_t; NULL =
  * the legacy default stream) on the current device.  Allocates a small
- * status buffer; the workspace is allocated lazily.  Errors: ERR_ARG (NULL
- * out-pointer), ERR_CUDA, ERR_NOMEM. */
+ * status buffer; the workspace is allocated lazily.  A handle serves one call
+ * at a time: it has one stream binding and one workspace and takes no lock,
+ * so host threads that call the library concurrently each need their own
+ * handle.  Errors: ERR_ARG (NULL out-pointer), ERR_CUDA, ERR_NOMEM. */
 rclupp_status_t rclupp_create(rclupp_handle_t *handle, void *stream);
 /* Release the handle and its workspace (synchronizes its stream first). */
 rclupp_status_t rclupp_destroy(rclupp_handle_t handle);

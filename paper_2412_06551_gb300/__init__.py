@@ -274,16 +274,38 @@ class Handle:
             pass
 
 
-_handles = {}
+# One handle per (host thread, device).  A handle holds one stream binding and
+# one workspace that a single call at a time may use, and the C calls run
+# without the GIL: threads that shared a handle could rebind its stream under
+# each other's call and overlap in its workspace.
+_local = threading.local()
+
+
+def _thread_handles() -> dict:
+    d = getattr(_local, "handles", None)
+    if d is None:
+        d = _local.handles = {}
+    return d
+
+
+def _device_index(device) -> int:
+    torch = _torch()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    return torch.cuda.current_device() if dev.index is None else int(dev.index)
+
+
+def _device_handle(device=None) -> Handle:
+    """The calling thread's handle on `device` (default: the current device)."""
+    idx = _device_index(device)
+    handles = _thread_handles()
+    h = handles.get(idx)
+    if h is None:
+        h = handles[idx] = Handle("cuda:%d" % idx)
+    return h
 
 
 def _handle(t) -> Handle:
-    idx = t.device.index
-    h = _handles.get(idx)
-    if h is None:
-        h = Handle(t.device)
-        _handles[idx] = h
-    return h
+    return _device_handle(t.device)
 
 
 def _opts(kind=SKETCH_GAUSSIAN, s=None, zeta=8, seed=0, prec=PREC_FP64, S=None, n=None, order_log2=0,
@@ -488,25 +510,14 @@ def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0, r0=0):
 
 
 def rclupp_set_batch_branches(branches: int, device=None):
-    """Parallel branches of the batched graph on the current handle."""
-    torch = _torch()
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    h = _handles.get(dev.index) or Handle(dev)
-    _handles[dev.index] = h
-    st = load().rclupp_set_batch_branches(h._h, int(branches))
+    """Parallel branches of the batched graph on the calling thread's handle."""
+    st = load().rclupp_set_batch_branches(_device_handle(device)._h, int(branches))
     _raise("rclupp_set_batch_branches", st)
 
 
-def _device_handle(device=None):
-    torch = _torch()
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    h = _handles.get(dev.index) or Handle(dev)
-    _handles[dev.index] = h
-    return h
-
-
 def rclupp_set_batch_policy(grid_div: int = 1, fine_tiles: bool = False, device=None):
-    """Launch shapes inside the batched graph: CTA-budget divisor and finer row tiles."""
+    """Launch shapes inside the batched graph (calling thread's handle): CTA-budget
+    divisor and finer row tiles."""
     st = load().rclupp_set_batch_policy(_device_handle(device)._h, int(grid_div), int(bool(fine_tiles)))
     _raise("rclupp_set_batch_policy", st)
 

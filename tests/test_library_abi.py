@@ -189,3 +189,47 @@ def test_argument_errors_are_found_before_the_handle_is_used():
     for key, st in out.items():
         case = key.split(":")[1]
         assert st == (UNSUP if case in expect_unsup else ARG), (key, st)
+
+
+def test_each_thread_gets_its_own_handle_per_device(monkeypatch):
+    """A handle serves one call at a time (one stream binding, one workspace),
+    and the C calls run without the GIL, so the binding keeps one handle per
+    (host thread, device).  A stand-in Handle records what was created."""
+    import threading
+
+    import torch
+
+    made = []
+
+    class FakeHandle:
+        def __init__(self, device):
+            self.device = torch.device(device)
+            made.append(self)
+
+    monkeypatch.setattr(rq, "Handle", FakeHandle)
+    monkeypatch.setattr(rq, "_local", threading.local())
+
+    class FakeTensor:
+        def __init__(self, dev):
+            self.device = torch.device(dev)
+
+    h0 = rq._device_handle("cuda:0")
+    assert rq._device_handle("cuda:0") is h0
+    assert rq._handle(FakeTensor("cuda:0")) is h0
+    h1 = rq._device_handle("cuda:1")
+    assert h1 is not h0 and h1.device == torch.device("cuda:1")
+
+    other = {}
+
+    def worker():
+        other["h0"] = rq._device_handle("cuda:0")
+        other["again"] = rq._handle(FakeTensor("cuda:0"))
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert other["h0"] is other["again"]
+    assert other["h0"] is not h0 and other["h0"].device == torch.device("cuda:0")
+    assert len(made) == 3
+    # the main thread's handles are unchanged by the other thread
+    assert rq._device_handle("cuda:0") is h0
