@@ -7,7 +7,9 @@ partial n x n Gram matrices (the communication-avoiding property of
 Section 1): RCLUPP needs three all-reduces (S X, Q1^T Q1, Q2^T Q2),
 CholeskyQR2 two.  The small factorizations (sketch LU, Householder R,
 Cholesky, triangular products) run replicated on every rank from identical
-inputs, so every rank ends with the same R and its own rows of Q.
+inputs, so every rank ends with the same R and its own rows of Q.  A rank
+without rows (more ranks than rows) adds zero partials and returns an empty
+block of Q, so it still takes part in every all-reduce.
 
 RCLUPPr and LC2 are not sharded: their tall LU with partial pivoting needs an
 argmax across all ranks for every column and the exchange of pivot rows.
@@ -57,6 +59,11 @@ class LibrarySteps:
     def trmm(self, A, B):
         return rclupp_trmm_upper(A, B)
 
+    def zeros(self, like, rows, cols):
+        """Column-major rows x cols zeros on the device of `like`."""
+        import torch
+        return torch.zeros((cols, rows), dtype=torch.float64, device=like.device).t()
+
 
 def torch_allreduce(group=None) -> Callable:
     """In-place sum over the ranks of `group` (torch.distributed: NCCL for
@@ -79,6 +86,15 @@ def _cholesky_or_raise(steps, G, pass_no):
     return R
 
 
+def _trsm_gram(steps, A, R, gram, empty):
+    """This rank's Q = A R^{-1} and, if asked, its partial Gram Q^T Q; a rank
+    without rows returns an empty Q and a zero partial."""
+    if not empty:
+        return steps.trsm_gram(A, R, gram=gram)
+    n = A.shape[1]
+    return steps.zeros(A, 0, n), (steps.zeros(A, n, n) if gram else None)
+
+
 def rclupp_factor_sharded(X_local, row0: int, *, s: Optional[int] = None, kind: int = SKETCH_GAUSSIAN,
                           zeta: int = 8, seed: int = 0, steps=None, allreduce: Optional[Callable] = None,
                           group=None, order_log2: int = 0):
@@ -99,16 +115,17 @@ def rclupp_factor_sharded(X_local, row0: int, *, s: Optional[int] = None, kind: 
             raise ValueError("the SRHT of a row-sharded matrix needs order_log2 = ceil(log2(m)) "
                              "of the whole matrix")
         sk["order_log2"] = order_log2
+    empty = X_local.shape[0] == 0
     # X_s = S X as a sum of the ranks' partials (all-reduce 1)
-    Y = allreduce(steps.sketch(X_local, **sk))
+    Y = allreduce(steps.zeros(X_local, s, n) if empty else steps.sketch(X_local, **sk))
     # on every rank: LU of X_s, Householder R of M, R1 = R0 N
     R1 = steps.precond(Y)
     # CholeskyQR2 of Q1 = X R1^{-1} (all-reduces 2 and 3)
-    Q1, G1 = steps.trsm_gram(X_local, R1, gram=True)
+    Q1, G1 = _trsm_gram(steps, X_local, R1, True, empty)
     R2 = _cholesky_or_raise(steps, allreduce(G1), 1)
-    Q2, G2 = steps.trsm_gram(Q1, R2, gram=True)
+    Q2, G2 = _trsm_gram(steps, Q1, R2, True, empty)
     R4 = _cholesky_or_raise(steps, allreduce(G2), 2)
-    Q, _ = steps.trsm_gram(Q2, R4, gram=False)
+    Q, _ = _trsm_gram(steps, Q2, R4, False, empty)
     R = steps.trmm(R4, steps.trmm(R2, R1))  # R3 = R2 R1 (C4), R = R4 R3 (C8)
     return Q, R
 
@@ -118,8 +135,11 @@ def cholqr2_factor_sharded(X_local, *, steps=None, allreduce: Optional[Callable]
     the ranks (two all-reduces of n x n Gram partials)."""
     steps = steps or LibrarySteps()
     allreduce = allreduce or torch_allreduce(group)
-    R1 = _cholesky_or_raise(steps, allreduce(steps.gram(X_local)), 1)
-    Q1, G1 = steps.trsm_gram(X_local, R1, gram=True)
+    n = X_local.shape[1]
+    empty = X_local.shape[0] == 0
+    R1 = _cholesky_or_raise(steps, allreduce(steps.zeros(X_local, n, n) if empty
+                                             else steps.gram(X_local)), 1)
+    Q1, G1 = _trsm_gram(steps, X_local, R1, True, empty)
     R2 = _cholesky_or_raise(steps, allreduce(G1), 2)
-    Q, _ = steps.trsm_gram(Q1, R2, gram=False)
+    Q, _ = _trsm_gram(steps, Q1, R2, False, empty)
     return Q, steps.trmm(R2, R1)

@@ -26,6 +26,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def _rows(A):
+    # the library's tall steps take m >= 1 rows (RCLUPP_ERR_ARG otherwise);
+    # the scaffolding keeps that contract so a driver cannot rely on less
+    if A.shape[0] < 1:
+        raise ValueError("tall step called with no rows")
+    return A
+
+
 class OracleSteps:
     """The per-rank steps on the CPU through the oracle (test scaffolding)."""
 
@@ -34,7 +42,7 @@ class OracleSteps:
 
     def sketch(self, A, *, s, kind, zeta, seed, row0):
         import oracle
-        return oracle.sketch_dense(self.S_full[:, row0:row0 + A.shape[0]], A)
+        return oracle.sketch_dense(self.S_full[:, row0:row0 + A.shape[0]], _rows(A))
 
     def precond(self, Y):
         import oracle
@@ -42,12 +50,12 @@ class OracleSteps:
 
     def trsm_gram(self, A, R, *, gram):
         import oracle
-        Q = oracle.trsm(A, R)
+        Q = oracle.trsm(_rows(A), R)
         return Q, (oracle.gram(Q) if gram else None)
 
     def gram(self, A):
         import oracle
-        return oracle.gram(A)
+        return oracle.gram(_rows(A))
 
     def cholesky(self, G):
         import oracle
@@ -56,6 +64,9 @@ class OracleSteps:
     def trmm(self, A, B):
         import oracle
         return oracle.trmm_upper(A, B)
+
+    def zeros(self, like, rows, cols):
+        return np.zeros((rows, cols), order="F")
 
 
 def _problem(m, n, kappa):
@@ -135,6 +146,27 @@ def test_cholqr2_sharded_two_allreduces():
     assert all(o[4] == [(n, n), (n, n)] for o in out)
     q_o, r_o, _ = oracle.cholqr2(x)
     assert oracle.orthogonality(Q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+    assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * 1e3
+
+
+@pytest.mark.parametrize("algo,port", [("rclupp", 29565), ("cholqr2", 29566)])
+def test_rank_without_rows_still_joins_every_allreduce(algo, port):
+    # three ranks, two rows: rank 2 holds none and adds zero partials; all
+    # ranks make the same all-reduces and end with the same R
+    import oracle
+    world, m, n = 3, 2, 2
+    out = _run(world, port, algo, m, n, 1e3)
+    assert [o[2].shape[0] for o in out] == [1, 1, 0]
+    x, S = _problem(m, n, 1e3)
+    Q = np.vstack([o[2] for o in out])
+    R = out[0][3]
+    expect = [(2 * n, n), (n, n), (n, n)] if algo == "rclupp" else [(n, n), (n, n)]
+    for o in out:
+        assert np.array_equal(o[3], R)
+        assert o[4] == expect
+    q_o, r_o, _ = oracle.rclupp(x, S=S) if algo == "rclupp" else oracle.cholqr2(x)
+    assert oracle.orthogonality(Q) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+    assert oracle.residual(x, Q, R) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
     assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * 1e3
 
 
