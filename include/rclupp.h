@@ -166,7 +166,7 @@ typedef struct {
                             every Gram did too (RCLUPP_PREC_EMULATED_ALL), else 0 */
 } rclupp_info_t;
 
-/* ---- handle -------------------------------------------------------------- */
+/* ---- handle (no counterpart in the paper: stream binding, workspace) ------ */
 
 /* Create a handle bound to the CUDA stream `stream` (a cudaStream_t; NULL =
  * the legacy default stream) on the current device.  Allocates a small
@@ -254,7 +254,8 @@ rclupp_status_t scholqr3_factor(rclupp_handle_t handle, int64_t m, int64_t n, co
                                 int64_t ldx, double *Q, int64_t ldq, double *R, int64_t ldr,
                                 rclupp_info_t *info);
 
-/* ---- batched form ---------------------------------------------------------- */
+/* ---- batched form (no counterpart in the paper: many independent
+ * factorizations by Algorithms 2-7 in one call) ---------------------------- */
 
 typedef enum {
     RCLUPP_ALGO_RCLUPP = 0,  /* Algorithm 6 */
@@ -406,8 +407,10 @@ rclupp_status_t rclupp_tall_lupp(rclupp_handle_t handle, int64_t m, int64_t n, d
 rclupp_status_t rclupp_sketch_precond(rclupp_handle_t handle, int64_t s, int64_t n,
                                       const double *Y, int64_t ldy, double *R1, int64_t ldr);
 
-/* rclupp_sketch_precond with the R-factor R0 chosen by r0_method
- * (rclupp_r0_method_t).  Givens: per column a tree of rotations over the
+/* rclupp_sketch_precond (Algorithm 6's preconditioner) with the R-factor R0
+ * chosen by r0_method (rclupp_r0_method_t): Householder as in Algorithm 6, or
+ * Givens rotations (Section 1; remark after Algorithm 5).  Givens: per
+ * column a tree of rotations over the
  * rows (each CTA's rows, then the CTAs' head rows), r = hypot(a, b) >= 0,
  * c = a / r, s = b / r; needs the matrix to fit a cluster's shared memory
  * (else RCLUPP_ERR_UNSUPPORTED). */

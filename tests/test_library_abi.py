@@ -233,3 +233,26 @@ def test_each_thread_gets_its_own_handle_per_device(monkeypatch):
     assert len(made) == 3
     # the main thread's handles are unchanged by the other thread
     assert rq._device_handle("cuda:0") is h0
+
+
+def test_every_entry_point_cites_its_passage_or_says_it_has_none():
+    """Each declaration in include/*.h is preceded by a comment (or sits under
+    a section banner) that names the passage of the paper defining the
+    operation, or states that the paper has no counterpart."""
+    cite = re.compile(r"Section \d|Algorithms? \d|eq\. \(|Lemma \d|Theorem \d|\bC\d\b|"
+                      r"no counterpart in the paper")
+    decl = re.compile(r"^(?:rclupp_status_t|const char \*|void|int|unsigned long long)\s*\*?\s*"
+                      r"(\w+)\s*\(", re.M)
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if not fname.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fname)).read()
+        comments = [(mt.start(), mt.end(), mt.group(0)) for mt in re.finditer(r"/\*.*?\*/", txt, re.S)]
+        banners = [c for c in comments if c[2].startswith("/* ----")]
+        for mt in decl.finditer(txt):
+            before = [c for c in comments if c[1] <= mt.start()]
+            assert before, mt.group(1)
+            own = before[-1][2]
+            banner = [b[2] for b in banners if b[1] <= mt.start()]
+            ok = cite.search(own) or (banner and cite.search(banner[-1]))
+            assert ok, "%s: %s has no citation" % (fname, mt.group(1))
