@@ -17,8 +17,9 @@
  *     rows of a triangular solve, entries of a sketch), never inside a sum.
  *   - Unit roundoff u = 2^-53 (the paper's setting, Section 1).
  *
- * Each routine names the step of the paper it follows (algorithm and step,
- * or equation).  The readings taken where the paper is silent are:
+ * Each routine names the passage of the paper it follows (the algorithm and
+ * the operation in it, or the equation).  The readings taken where the paper
+ * is silent are:
  *   - LU "[M,N,P] = LU(.)" is Gaussian elimination with partial pivoting,
  *     LAPACK getf2 layout: M unit lower trapezoidal (strict lower part stored),
  *     N upper triangular, P as a sequence of row interchanges ipiv[k] (row k

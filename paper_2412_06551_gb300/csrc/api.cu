@@ -329,7 +329,7 @@ struct Ctx {
 
 Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
 
-// Steps 5-7 of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
+// The CholeskyQR2 stage of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
 // b.RP[0]; CholeskyQR2 of Q1 into Q (in place after the first pass);
 // R = R4 (R2 R1).
 // First CholeskyQR step on Q1 = X R1^{-1}: G = Q1^T Q1 (C1), R2 = chol(G) (C2).
