@@ -279,7 +279,8 @@ typedef enum {
  * branches (streams; problem i runs on branch i mod B, B set by
  * rclupp_set_batch_branches, default 16) so that small problems fill the GPU
  * together, and joins.  The instantiated graph is cached in the handle and
- * replayed while the batch (sizes, pointers, options) is unchanged.  The
+ * replayed while the batch is unchanged: sizes, pointers, options, branch
+ * count, launch shapes and workspace, compared byte for byte.  The
  * workspace holds B per-branch slices sized for the largest problem.
  * status[i] (may be NULL) receives problem i's status; the return value is
  * the first non-OK status, or RCLUPP_OK.  Synchronous like the other calls. */
