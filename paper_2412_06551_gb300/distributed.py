@@ -67,11 +67,25 @@ class LibrarySteps:
 
 def torch_allreduce(group=None) -> Callable:
     """In-place sum over the ranks of `group` (torch.distributed: NCCL for
-    CUDA tensors, gloo for CPU tensors)."""
+    CUDA tensors, gloo for CPU tensors).
+
+    NCCL takes only contiguous tensors, while the library returns
+    column-major matrices (transposed views of contiguous memory).  A sum is
+    elementwise, so such a matrix is reduced in place through its contiguous
+    alias; any other layout goes through a contiguous copy."""
     import torch.distributed as dist
 
     def reduce_(t):
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        if t.is_contiguous():
+            alias = t
+        elif t.dim() == 2 and t.t().is_contiguous():
+            alias = t.t()
+        else:
+            c = t.contiguous()
+            dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
+            t.copy_(c)
+            return t
+        dist.all_reduce(alias, op=dist.ReduceOp.SUM, group=group)
         return t
     return reduce_
 

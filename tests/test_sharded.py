@@ -170,6 +170,34 @@ def test_rank_without_rows_still_joins_every_allreduce(algo, port):
     assert np.linalg.norm(R - r_o) / np.linalg.norm(r_o) <= 1e-10 * 1e3
 
 
+def test_torch_allreduce_passes_contiguous_tensors_and_sums_in_place(monkeypatch):
+    # NCCL rejects non-contiguous tensors; the library's matrices are
+    # column-major views.  A stand-in all_reduce that insists on contiguous
+    # input and doubles it (two ranks holding the same values) checks that
+    # every layout is reduced in place with the right result.
+    from paper_2412_06551_gb300 import distributed as D
+    seen = []
+
+    def fake_all_reduce(t, op=None, group=None):
+        assert t.is_contiguous()
+        seen.append(tuple(t.shape))
+        t.mul_(2)
+
+    monkeypatch.setattr(dist, "all_reduce", fake_all_reduce)
+    reduce_ = D.torch_allreduce()
+    base = torch.arange(12, dtype=torch.float64)
+    col = base.clone().reshape(3, 4).t()                   # 4 x 3 column-major (ld = 4)
+    row = base.clone().reshape(4, 3)                       # row-major
+    padded = base.clone().reshape(3, 4).t()[:3]            # 3 x 3 column-major, ld = 4
+    for t in (col, row, padded):
+        before = t.clone()
+        ptr = t.data_ptr()
+        out = reduce_(t)
+        assert out is t and t.data_ptr() == ptr
+        assert torch.equal(t, 2 * before)
+    assert seen == [(3, 4), (4, 3), (3, 3)]
+
+
 def test_srht_needs_the_whole_matrix_order():
     from paper_2412_06551_gb300 import distributed as D
     import paper_2412_06551_gb300 as rq
