@@ -314,7 +314,9 @@ rclupp_status_t rclupp_get_batch_policy(rclupp_handle_t handle, int32_t *branche
  * on the handle's stream, keeps the fastest combination in the handle and
  * returns its branch count in *best_branches and its time in *best_ms
  * (either may be NULL; rclupp_get_batch_policy reads the rest).  A numerical
- * breakdown of a problem does not stop the tuning. */
+ * failure of a problem (breakdown, zero pivot, non-finite input) does not
+ * stop the tuning and is not returned; any other failure stops it and is
+ * returned. */
 rclupp_status_t rclupp_autotune_batched(rclupp_handle_t handle, int32_t algo, int32_t count,
                                         const int64_t *m, const int64_t *n,
                                         const double *const *X, const int64_t *ldx,

@@ -936,15 +936,21 @@ rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t
     int best = h->batch_branches, best_div = 1, best_fine = 0;
     float best_t = 0.f;
     rclupp_status_t st = RCLUPP_OK;
+    // a problem's own numerical failure is part of the batch's result, not a
+    // reason to stop tuning
+    auto numerical = [](rclupp_status_t s) {
+        return s == RCLUPP_ERR_CHOL_BREAKDOWN || s == RCLUPP_ERR_LU_ZERO_PIVOT ||
+               s == RCLUPP_ERR_NONFINITE;
+    };
     // first call builds and caches the graph; the second one is timed
     auto trial = [&](float *t) {
         st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
-        if (st != RCLUPP_OK && st != RCLUPP_ERR_CHOL_BREAKDOWN && st != RCLUPP_ERR_LU_ZERO_PIVOT)
-            return false;
+        if (st != RCLUPP_OK && !numerical(st)) return false;
         cudaEventRecord(e0, h->stream);
         st = rclupp_factor_batched(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, nullptr);
         cudaEventRecord(e1, h->stream);
         cudaEventSynchronize(e1);
+        if (st != RCLUPP_OK && !numerical(st)) return false;
         *t = 0.f;
         cudaEventElapsedTime(t, e0, e1);
         return true;
@@ -980,7 +986,7 @@ rclupp_status_t rclupp_autotune_batched(rclupp_handle_t h, int32_t algo, int32_t
     h->batch_fine_tiles = best_fine;
     if (best_branches) *best_branches = best;
     if (best_ms) *best_ms = best_t;
-    return (st == RCLUPP_ERR_CHOL_BREAKDOWN || st == RCLUPP_ERR_LU_ZERO_PIVOT) ? RCLUPP_OK : st;
+    return numerical(st) ? RCLUPP_OK : st;
 }
 
 // ---- individual steps ----
