@@ -274,7 +274,9 @@ typedef enum {
  * randomized algorithms: the sketch is always binary64 here (a graph cannot
  * escalate), prec may be RCLUPP_PREC_FP64 or one of the emulated tiers, whose
  * emulated solves and Gram products are kept (the reduced sketch tiers return
- * RCLUPP_ERR_UNSUPPORTED).  Each problem obeys the single-problem rules.
+ * RCLUPP_ERR_UNSUPPORTED).  Each problem obeys the single-problem rules;
+ * problems run concurrently, so the outputs of different problems must not
+ * overlap (inputs may be shared).
  * The whole batch is enqueued as one CUDA graph: it forks into B parallel
  * branches (streams; problem i runs on branch i mod B, B set by
  * rclupp_set_batch_branches, default 16) so that small problems fill the GPU
