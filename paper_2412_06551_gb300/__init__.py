@@ -503,7 +503,9 @@ def _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec=0, r0=0):
     status = np.zeros(count, dtype=np.int32)
     p = lambda a: ctypes.c_void_p(a.ctypes.data)
     h = _handle(Xs[0][0])
-    keep = (m, n, xp, ldx, opts, qp, ldq, rp, ldr, status)
+    # everything the pointers above refer to stays referenced until the call
+    # returns, the column-major copies of inputs given in another layout too
+    keep = (m, n, xp, ldx, opts, qp, ldq, rp, ldr, status, [x for x, _ in Xs])
     return {"h": h.bind(), "count": count, "keep": keep, "status": status, "pst": p(status),
             "args": (p(m), p(n), p(xp), p(ldx), ctypes.cast(opts, _P), p(qp), p(ldq), p(rp), p(ldr)),
             "Qs": [q for q, _ in qc], "Rs": [r for r, _ in rc]}

@@ -256,3 +256,46 @@ def test_every_entry_point_cites_its_passage_or_says_it_has_none():
             banner = [b[2] for b in banners if b[1] <= mt.start()]
             ok = cite.search(own) or (banner and cite.search(banner[-1]))
             assert ok, "%s: %s has no citation" % (fname, mt.group(1))
+
+
+def test_batched_arguments_keep_every_pointer_target_alive(monkeypatch):
+    """The batched binding passes device pointers of column-major copies when
+    an input comes in another layout; those copies must stay referenced until
+    the C call returns, not go back to the allocator when the argument
+    builder returns.  Stand-ins replace the layout copy and the handle."""
+    import torch
+
+    made = []
+
+    def fake_colmajor(t):
+        c = t.clone()  # stands in for the layout copy
+        made.append(c)
+        return c, t.shape[0]
+
+    class FakeHandle:
+        def bind(self):
+            return None
+
+    monkeypatch.setattr(rq, "colmajor", fake_colmajor)
+    monkeypatch.setattr(rq, "_handle", lambda t: FakeHandle())
+    shapes = [(5, 2), (7, 3)]
+    Xs = [torch.zeros(s, dtype=torch.float64) for s in shapes]
+    Qs = [torch.zeros(s, dtype=torch.float64) for s in shapes]
+    Rs = [torch.zeros((s[1], s[1]), dtype=torch.float64) for s in shapes]
+    a = rq._batch_args(Xs, Qs, Rs, None, rq.SKETCH_GAUSSIAN, 8, 0)
+    del Xs, Qs, Rs
+
+    def refs(obj, out):
+        if isinstance(obj, (list, tuple)):
+            for o in obj:
+                refs(o, out)
+        else:
+            out.append(obj)
+        return out
+
+    held = refs([a["keep"], a["Qs"], a["Rs"]], [])
+    passed = {int(p) for arr in (a["keep"][2], a["keep"][5], a["keep"][7]) for p in arr}
+    assert len(made) == 6
+    for c in made:
+        assert c.data_ptr() in passed
+        assert any(c is h for h in held), "a tensor whose pointer is passed is not kept"
