@@ -464,13 +464,18 @@ rclupp_status_t rclupp_gram_noalloc(int64_t m, int64_t n, const double *A, int64
  * library launches increments a process-wide counter.  When profiling is
  * enabled, a CUDA event pair is recorded on the launching stream around each
  * kernel; rclupp_profile_get synchronizes on the recorded events and returns,
- * for one kernel class (0 <= kid < 14), the number of timed launches, their
+ * for one kernel class (0 <= kid < 18), the number of timed launches, their
  * summed duration in milliseconds and the class name (static string).
  * Classes: 0 sketch_gauss, 1 sketch_sparse, 2 gram, 3 trsm_gram (fused
  * TRSM + Gram), 4 trsm, 5 reduce, 6 lu_col, 7 lu_trailing, 8 lu_u12,
  * 9 small_precond, 10 cholesky, 11 trmm, 12 pad, 13 sketch_tc (tensor-core
- * sketch).  Returns ERR_ARG for an
- * invalid class. */
+ * sketch), 14 gram_emu, 15 emu_aux (exponent and digit-preparation kernels
+ * of the emulated products), 16 trsm_emu, 17 sketch_srht.  Returns ERR_ARG
+ * for an invalid class.  The open event of a launch is kept per kernel
+ * class for the whole process, so enable timing only while one host thread
+ * launches; the launch counter is exact with any number of threads.
+ * Kernels launched inside a captured graph are counted when the graph is
+ * launched and are not timed. */
 void rclupp_profile_enable(int enable);
 void rclupp_profile_reset(void);
 int rclupp_profile_get(int kid, long long *launches, double *total_ms, const char **name);

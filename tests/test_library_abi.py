@@ -299,3 +299,29 @@ def test_batched_arguments_keep_every_pointer_target_alive(monkeypatch):
     for c in made:
         assert c.data_ptr() in passed
         assert any(c is h for h in held), "a tensor whose pointer is passed is not kept"
+
+
+def test_profiler_classes_agree_across_header_library_and_binding():
+    """The kernel classes rclupp_profile_get names (callable without a GPU
+    while nothing is pending), the list in include/rclupp.h and the
+    binding's KERNEL_CLASSES are the same, in the same order."""
+    lib = ctypes.CDLL(_build.build())
+    lib.rclupp_profile_get.restype = ctypes.c_int
+    lib.rclupp_profile_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_char_p)]
+    names = []
+    for k in range(64):
+        nm = ctypes.c_char_p()
+        st = lib.rclupp_profile_get(k, None, None, ctypes.byref(nm))
+        if st != 0:
+            assert st == rq.Status.ERR_ARG
+            break
+        names.append(nm.value.decode())
+    assert names == rq.KERNEL_CLASSES
+    txt = open(os.path.join(ROOT, "include", "rclupp.h")).read()
+    block = txt[txt.index("rclupp_profile_get synchronizes"):txt.index("void rclupp_profile_enable")]
+    block = re.sub(r"\s*\*\s*", " ", block)
+    assert "0 <= kid < %d" % len(names) in block
+    listed = re.findall(r"\b(\d+) ([a-z_0-9]+)", block[block.index("Classes:"):])
+    assert [(int(i), nm) for i, nm in listed] == list(enumerate(names))
