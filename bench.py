@@ -13,6 +13,14 @@ Under torchrun (N > 1) every rank factors its own matrix (replicas, weak
 scaling, no collective on the data path); timing is the max over ranks.
 --impl reference times the CPU oracle (the plain FP64 C implementation) on a
 bounded row sample of the same workload.
+
+Besides the headline step, the line carries one sub-record per remaining
+single-GPU workload (untimed for the headline, each with its own CUDA-event
+timings and a roofline per form): the precision form (m = 2^22, n = 256,
+s = 512, kappa 1e2 / 1e8 / 1e14: binary64 against the tensor-core sketch
+tiers and the binary64-emulating tiers, at equal orthogonality), the small
+single matrix (m = 4096, n = 64), the batch of 512 uneven problems and the
+large sparse-sign RCLUPPr (m = 2^24, n = 64).  --no-configs leaves them out.
 """
 from __future__ import annotations
 
@@ -49,19 +57,56 @@ ALGO_FLOPS = {
 }
 SAMPLE_M = 1 << 15  # rows of the CPU-oracle sample
 METRIC = "TSQR GFLOP/s (2mn^2 model) & roofline fraction, mixed vs FP64 at equal ||Q^T Q - I||"
-FP64_PEAK_GFLOPS = 152 * 2070e6 * 4 / 1e9  # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 
 
-def _hbm_peak_gbs():
-    """Measured copy bandwidth of this GPU type (MEASURED_PEAKS.json), else the fallback."""
+def _measured_peaks():
+    """Measured copy bandwidth and cuBLAS bf16 rates of this GPU type
+    (MEASURED_PEAKS.json), else the fallback figures of an earlier GB300."""
     try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return (float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]),
+                "measured")
     except (OSError, KeyError, ValueError):
-        return 6800.0
+        return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-HBM_PEAK_GBS = _hbm_peak_gbs()
+HBM_PEAK_GBS, BF16_BURST_TFLOPS, BF16_SUSTAINED_TFLOPS, PEAKS_SOURCE = _measured_peaks()
+# FP64-pipe rate: measured by the library's DFMA microbenchmark at the start of
+# each run (fp64_peak()); this derived figure (SMs x 2 DFMA/clk x 2 flop x max
+# SM clock, both read from the device) stands in only until then.
+FP64_PEAK = {"gflops": 152 * 2070e6 * 4 / 1e9, "source": "derived before measurement"}
+
+
+def measure_fp64_peak(rq):
+    """FP64-pipe peak for the rooflines: the DFMA microbenchmark's rate, with
+    the derived SMs x 2 DFMA/clk x 2 flop x clock beside it."""
+    r = rq.fp64_peak()
+    derived = r["sms"] * 2 * 2 * r["clock_mhz"] * 1e6 / 1e9
+    FP64_PEAK.update({"gflops": r["gflops"], "source": "DFMA microbenchmark (measured this run)",
+                      "derived_gflops": derived, "sms": r["sms"], "clock_mhz": r["clock_mhz"],
+                      "microbenchmark_ms": r["ms"]})
+    return FP64_PEAK
+
+
+# DRAM bytes per launch of the fused TRSM + Gram kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of `bench.py --case trsm_gram
+# --m 262144 --n 128 --reps 1`, scaled by the rows processed to the bench's m
+# (the pass streams its rows once, so traffic grows with m).  The capture holds
+# only for the kernel source it was taken on: TRAFFIC_SRC_SHA is the SHA-256 of
+# csrc/tall.cu + csrc/common.cuh at capture time, and a different source gives
+# traffic null.
+TRAFFIC_CAPTURE = {"kernel": "trsm_gram", "m": 262144, "n": 128, "read": 268.7e6, "write": 235.7e6}
+TRAFFIC_SRC_SHA = None
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("tall.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_06551_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def workload_config():
@@ -82,10 +127,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="leave out the sub-records of the other workloads")
     p.add_argument("--accuracy-sweep", action="store_true",
                    help="also report orthogonality/residual at kappa 1e10 and 1e15")
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "trsm_emu", "sketch_gauss",
-                                      "sketch_sparse", "sketch_srht", "precond", "lu", "rclupp"],
+                                      "sketch_sparse", "sketch_srht", "precond", "lu", "rclupp",
+                                      "dfma_peak"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
     p.add_argument("--workload", choices=["side_by_side", "precision", "batched", "small",
                                           "large_sparse"],
@@ -271,6 +319,118 @@ def time_call(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
+# ------------------------------------------------------------ rooflines ---
+#
+# Roofline of one factorization in a given form (spec: the slower of the
+# FP64 pipe, the tensor pipe and the bytes over HBM):
+#   T_roof = max(F64 / P64, Ftc / Ptc, B / BW),  frac = T_roof / measured time.
+# Counts are the algorithmic ones of the path that ran (leading terms):
+#   F64  binary64 flops: Gaussian sketch 2smn, sparse sketch zeta*m*n adds,
+#        tall LU mn^2, each triangular solve mn^2, each Gram m n (n+1); in the
+#        emulated forms only the solves' diagonal blocks ((b+1) m n per solve,
+#        b = 16 for n <= 160 else 32) and, in EMULATED, the final-pass Gram.
+#   Ftc  tensor-pipe flops the split issues: tensor-core sketch 2smn per bf16
+#        term of X; emulated Gram 36 digit pairs x 2 x m x (128 x 64 tiles of
+#        the upper triangle); emulated solve 36 x 2 x m x b^2 x nb(nb-1)/2.
+#   B    HBM bytes: sketch read 8mn, fused solve + Gram passes 16mn each (56mn
+#        for binary64 RCLUPP), a separate Gram pass 8mn (72mn emulated); the
+#        LU adds its copy and one read + write of X (32mn).
+# A failed reduced-tier attempt (escalation) adds its sketch and first pass.
+
+def _emu_gram_tiles(n):
+    nj, nk = -(-n // 128), -(-n // 64)
+    return sum(nk - 2 * jb for jb in range(nj))
+
+
+def form_counts(m, n, s, form, *, algo="rclupp", kind="gaussian", zeta=8, prec_used=None,
+                first_tier=None):
+    """(F64, Ftc, B) of one RCLUPP / RCLUPPr factorization in `form`
+    ("fp64", "bf16", "fp32", "emulated", "emulated_all").  The sketch starts at
+    `first_tier` (0 binary64, 1 bf16, 2 three-term; default: the form's) and
+    ends at `prec_used` (default: no escalation)."""
+    mn, mnn = float(m) * n, float(m) * n * n
+    emu = form in ("emulated", "emulated_all")
+    b = 16 if n <= 160 else 32
+    nb = -(-n // b)
+    emu_trsm_tc = 72.0 * m * b * b * nb * (nb - 1) / 2
+    emu_gram_tc = 72.0 * m * _emu_gram_tiles(n) * 128 * 64
+    f64 = ftc = byt = 0.0
+    # sketch tiers run, in order (escalation bf16 -> three-term -> binary64)
+    tiers = [0]
+    if kind == "gaussian":
+        if first_tier is None:
+            first_tier = {"fp64": 0, "bf16": 1, "fp32": 2, "emulated": 1, "emulated_all": 1}[form]
+        last = first_tier if prec_used is None else int(prec_used)
+        order = [1, 2, 0]
+        i = order.index(first_tier)
+        tiers = [first_tier]
+        while tiers[-1] != last and i < 2:
+            i += 1
+            tiers.append(order[i])
+    for k, t in enumerate(tiers):
+        if kind == "sparse":
+            f64 += zeta * mn
+        elif t == 0:
+            f64 += 2.0 * s * m * n
+        else:
+            ftc += 2.0 * s * m * n * (1 if t == 1 else 3)
+        byt += 8 * mn
+        if k < len(tiers) - 1:  # failed attempt: its first pass too
+            if emu:
+                f64 += (b + 1) * mn
+                ftc += emu_trsm_tc + emu_gram_tc
+                byt += 24 * mn
+            else:
+                f64 += 2 * mnn
+                byt += 16 * mn
+    if algo == "rcluppr":
+        f64 += mnn
+        byt += 32 * mn
+    if emu:
+        f64 += 3 * (b + 1) * mn
+        ftc += 3 * emu_trsm_tc + emu_gram_tc
+        if form == "emulated":
+            f64 += mnn
+        else:
+            ftc += emu_gram_tc
+        byt += 64 * mn
+    else:
+        f64 += 5 * mnn
+        byt += 48 * mn
+    return f64, ftc, byt
+
+
+def roofline_of(counts, ms, p64=None, ptc_tflops=None):
+    """Roofline block of a path that took `ms` with algorithmic counts
+    (F64, Ftc, B); peaks: FP64 measured this run, bf16 sustained, HBM copy."""
+    f64, ftc, byt = counts
+    p64 = p64 or FP64_PEAK["gflops"]
+    ptc = (ptc_tflops or BF16_SUSTAINED_TFLOPS) * 1e3
+    t = {"fp64": f64 / p64 / 1e6, "tensor": ftc / ptc / 1e6, "hbm": byt / HBM_PEAK_GBS / 1e6}
+    bound = max(t, key=t.get)
+    return {"bound": bound, "t_roof_ms": t[bound], "frac": t[bound] / ms, "fp64_flops": f64,
+            "tensor_flops": ftc, "bytes": byt, "t_fp64_ms": t["fp64"], "t_tensor_ms": t["tensor"],
+            "t_hbm_ms": t["hbm"]}
+
+
+def svd_matrix_gpu(torch, m, n, kappa, seed, device):
+    """X = U diag(sigma) V^T as in synth.svd_matrix, built on the GPU (torch's
+    QR of seeded normal matrices), column-major; the host needs no copy."""
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    U, _ = torch.linalg.qr(torch.randn(m, n, generator=gen, dtype=torch.float64, device=device))
+    V, _ = torch.linalg.qr(torch.randn(n, n, generator=gen, dtype=torch.float64, device=device))
+    sig = float(kappa) ** (-torch.arange(n, dtype=torch.float64, device=device) / max(n - 1, 1))
+    Xr = (U * sig) @ V.t()
+    del U
+    X = torch.empty((n, m), dtype=torch.float64, device=device).t()  # column-major
+    X.copy_(Xr)
+    del Xr
+    return X
+
+
+FORMS = (("fp64", 0), ("bf16", 1), ("fp32", 2), ("emulated", 3), ("emulated_all", 4))
+
+
 def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
     """RCLUPP and RCLUPPr with the tensor-core sketch (starting at the bf16
     tier, escalating as needed) on the same X, against the FP64 paths."""
@@ -283,61 +443,72 @@ def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
             call()
             ms, (Q, R, info) = time_call(torch, stream, call, max(2, reps))
             o, r = accuracy(torch, X, Q, R)
+            form = {"": "bf16", "_emulated": "emulated", "_emulated_all": "emulated_all"}[tier]
+            cnt = form_counts(m, n, S_SKETCH, form, algo=name, prec_used=int(info.prec_used))
             out[name + tier] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9,
                                 "orth": o, "res": r, "prec_used": int(info.prec_used),
                                 "emulated_gram": int(info.emulated),
                                 "speedup_vs_fp64": fp64_paths[name]["ms"] / ms,
-                                "orth_fp64": fp64_paths[name]["orth"]}
+                                "orth_fp64": fp64_paths[name]["orth"],
+                                "roofline": roofline_of(cnt, ms)}
             del Q, R
     return out
 
 
-def run_precision(args):
-    """FP64 vs tensor-core-sketch RCLUPP on m = 2^22, n = 256, s = 512 at
-    kappa 1e2, 1e8, 1e14 (one JSON line)."""
-    import torch
-    import paper_2412_06551_gb300 as rq
+def c3_precision(rq, torch, device, reps=2):
+    """RCLUPP on m = 2^22, n = 256, s = 512 at kappa 1e2, 1e8, 1e14: binary64
+    against the tensor-core sketch tiers (bf16 / three-term, escalating when
+    the first Cholesky shows Q1 too ill-conditioned) and the binary64-emulating
+    tiers, with orthogonality and residual beside each, and the roofline of
+    each form."""
     m, n, s = 1 << 22, 256, 512
-    device = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(device)
     rows = {}
     for k_i, kap in enumerate((1e2, 1e8, 1e14)):
         seed = synth.kappa_seed(2, k_i)
-        X = to_dev(synth.svd_matrix(m, n, kap, seed), torch, device)
+        X = svd_matrix_gpu(torch, m, n, kap, seed, device)
         row = {}
-        for label, prec in (("fp64", rq.PREC_FP64), ("mixed", rq.PREC_SKETCH_BF16),
-                            ("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
+        for label, prec in FORMS:
             call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec, check=False)
             call()
-            ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
+            ms, (Q, R, info) = time_call(torch, stream, call, reps)
             entry = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9,
-                     "status": int(info.status), "prec_used": int(info.prec_used)}
+                     "status": int(info.status), "prec_used": int(info.prec_used),
+                     "emulated": int(info.emulated)}
             if info.status == 0:
                 o, r = accuracy(torch, X, Q, R)
                 entry.update({"orth": o, "res": r})
+            entry["roofline"] = roofline_of(form_counts(m, n, s, label, prec_used=int(info.prec_used)), ms)
             row[label] = entry
             del Q, R
-        row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
-        row["speedup_emulated"] = row["fp64"]["ms"] / row["emulated"]["ms"]
-        row["speedup_emulated_all"] = row["fp64"]["ms"] / row["emulated_all"]["ms"]
+        f = row["fp64"]
+        for label, _ in FORMS[1:]:
+            e = row[label]
+            e["speedup_vs_fp64"] = f["ms"] / e["ms"]
+            e["equal_orth"] = bool("orth" in e and "orth" in f and e["orth"] <= max(f["orth"], 1e-13))
         rows["%.0e" % kap] = row
         del X
         torch.cuda.empty_cache()
-    print(json.dumps({"workload": "RCLUPP FP64 vs tensor-core sketch (bf16 start, escalating) "
-                                  "vs that sketch plus the binary64-emulating tensor-core Gram",
-                      "m": m, "n": n, "s": s, "results": rows}), flush=True)
+    best = {}
+    for kap, row in rows.items():
+        cand = [(row[l]["gflops_2mn2"], l) for l, _ in FORMS[1:] if row[l].get("equal_orth")]
+        g, l = max(cand) if cand else (row["fp64"]["gflops_2mn2"], "fp64")
+        best[kap] = {"fp64_gflops_2mn2": row["fp64"]["gflops_2mn2"], "best_form": l,
+                     "best_gflops_2mn2": g, "speedup": g / row["fp64"]["gflops_2mn2"],
+                     "orth_fp64": row["fp64"].get("orth"), "orth_best": row[l].get("orth")}
+    return {"workload": "RCLUPP, m=2^22, n=256, Gaussian s=512, X = U diag(sigma) V^T (GPU-built), "
+                        "binary64 vs tensor-core sketch tiers vs binary64-emulating tiers",
+            "m": m, "n": n, "s": s, "reps": reps, "results": rows,
+            "mixed_vs_fp64_at_equal_orth": best}
 
 
-def run_small(args):
+def c1_small(rq, torch, device, reps=20):
     """RCLUPP on the small single-matrix case m = 4096, n = 64, kappa = 1e8,
-    Gaussian s = 128: binary64 and the emulated tier against the oracle on
+    Gaussian s = 128: binary64 and the emulated tiers against the oracle on
     the same X and S (the oracle runs this size in full)."""
-    import torch
     import oracle
-    import paper_2412_06551_gb300 as rq
     m, n, s, kap = 4096, 64, 128, 1e8
     seed = synth.kappa_seed(0, 0)
-    device = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(device)
     x = synth.svd_matrix(m, n, kap, seed)
     X = to_dev(x, torch, device)
@@ -353,7 +524,6 @@ def run_small(args):
     oracle.set_num_threads(cores)
     rows = {"oracle": {"ms": t_oracle * 1e3, "cores": cores, "ms_one_core": t_oracle1 * 1e3,
                        "orth": oracle.orthogonality(q_o), "res": oracle.residual(x, q_o, r_o)}}
-    reps = max(20, 10 * args.steps)
     for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED),
                         ("emulated_all", rq.PREC_EMULATED_ALL)):
         call = lambda: rq.rclupp_factor(X, s=s, seed=seed + 7, prec=prec)
@@ -362,34 +532,23 @@ def run_small(args):
         ms, (Q, R, info) = time_call(torch, stream, call, reps)
         o, r = accuracy(torch, X, Q, R)
         rows[label] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "orth": o, "res": r,
-                       "prec_used": int(info.prec_used), "emulated": int(info.emulated)}
+                       "prec_used": int(info.prec_used), "emulated": int(info.emulated),
+                       "roofline": roofline_of(form_counts(m, n, s, label,
+                                                           prec_used=int(info.prec_used)), ms)}
         if label == "fp64":  # realised kappa: the 2-norm condition number of the computed R
             rows[label]["kappa_realised"] = float(np.linalg.cond(R.cpu().numpy()))
-    print(json.dumps({"workload": "RCLUPP, one matrix m=4096, n=64, kappa=1e8, Gaussian s=128 "
-                                  "(latency-bound: X is 2 MB, L2-resident)",
-                      "m": m, "n": n, "s": s, "kappa": kap, "seed_x": seed, "results": rows}), flush=True)
+    return {"workload": "RCLUPP, one matrix m=4096, n=64, kappa=1e8, Gaussian s=128 "
+                        "(latency-bound: X is 2 MB, L2-resident)",
+            "m": m, "n": n, "s": s, "kappa": kap, "seed_x": seed, "results": rows}
 
 
-def run_large_sparse(args):
+def c5_large_sparse(rq, torch, device, reps=2):
     """RCLUPPr with the sparse-sign sketch on m = 2^24, n = 64 (8.6 GB),
-    kappa = 1e15, s = 256, zeta = 8: binary64 and the emulated tier.  X is
-    built on the GPU by the same recipe as synth.svd_matrix (torch's QR of
-    seeded normal matrices), so the host needs no 8.6 GB copy."""
-    import torch
-    import paper_2412_06551_gb300 as rq
+    kappa = 1e15, s = 256, zeta = 8: binary64 and the emulated tiers."""
     m, n, s, zeta, kap = 1 << 24, 64, 256, 8, 1e15
     seed = synth.kappa_seed(4, 0)
-    device = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(device)
-    gen = torch.Generator(device=device).manual_seed(seed)
-    U, _ = torch.linalg.qr(torch.randn(m, n, generator=gen, dtype=torch.float64, device=device))
-    V, _ = torch.linalg.qr(torch.randn(n, n, generator=gen, dtype=torch.float64, device=device))
-    sig = kap ** (-torch.arange(n, dtype=torch.float64, device=device) / (n - 1))
-    Xr = (U * sig) @ V.t()
-    del U
-    X = torch.empty((n, m), dtype=torch.float64, device=device).t()  # column-major
-    X.copy_(Xr)
-    del Xr
+    X = svd_matrix_gpu(torch, m, n, kap, seed, device)
     torch.cuda.empty_cache()
     rows = {}
     for label, prec in (("fp64", rq.PREC_FP64), ("emulated", rq.PREC_EMULATED),
@@ -397,9 +556,11 @@ def run_large_sparse(args):
         call = lambda: rq.rclupp_r_factor(X, s=s, kind=rq.SKETCH_SPARSE_SIGN, zeta=zeta, seed=seed + 7,
                                           prec=prec, check=False)
         call()
-        ms, (Q, R, info) = time_call(torch, stream, call, max(1, min(args.steps, 3)))
+        ms, (Q, R, info) = time_call(torch, stream, call, reps)
         entry = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms / 1e3) / 1e9, "status": int(info.status),
-                 "emulated": int(info.emulated)}
+                 "emulated": int(info.emulated),
+                 "roofline": roofline_of(form_counts(m, n, s, label, algo="rcluppr", kind="sparse",
+                                                     zeta=zeta), ms)}
         if info.status == 0:
             o, r = accuracy(torch, X, Q, R)
             entry.update({"orth": o, "res": r})
@@ -408,79 +569,85 @@ def run_large_sparse(args):
         torch.cuda.empty_cache()
     rows["speedup_emulated"] = rows["fp64"]["ms"] / rows["emulated"]["ms"]
     rows["speedup_emulated_all"] = rows["fp64"]["ms"] / rows["emulated_all"]["ms"]
-    print(json.dumps({"workload": "RCLUPPr, sparse-sign sketch s=256 zeta=8, m=2^24, n=64, kappa=1e15 "
-                                  "(X generated on the GPU)", "m": m, "n": n, "results": rows}), flush=True)
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "RCLUPPr, sparse-sign sketch s=256 zeta=8, m=2^24, n=64, kappa=1e15 "
+                        "(X generated on the GPU)", "m": m, "n": n, "results": rows}
 
 
 def batched_problems(count=512):
     """The batched workload: m = floor(2^U(12,17)), n uniform in
     {16, 32, 48, 64, 96, 128}, kappa = 10^U(2,12), Gaussian s = 2n."""
-    g = synth.rng(synth.kappa_seed(3, 0))
-    ms = np.floor(2.0 ** g.uniform(12, 17, count)).astype(np.int64)
-    ns = g.choice(np.array([16, 32, 48, 64, 96, 128]), count)
-    kap = 10.0 ** g.uniform(2, 12, count)
-    return ms, ns, kap
+    return synth.batched_problems(count, synth.kappa_seed(3, 0))
 
 
-def run_batched(args):
+# sketch tier of each form inside a batch (no escalation is possible in a
+# graph): binary64, else the three-term tensor-core sketch
+BATCH_SKETCH_TIER = {"fp64": 0, "fp32": 2, "emulated": 2, "emulated_all": 2}
+
+
+def c4_batched(rq, torch, device, steps=3, warmup=3):
     """512 uneven RCLUPP factorizations: one batched call (cached CUDA graph,
-    autotuned branch count) against the same problems as single calls."""
-    import torch
-    import paper_2412_06551_gb300 as rq
-    device = torch.device("cuda", 0)
+    autotuned branch count) against the same problems as single calls, in
+    binary64 and in the precision forms, with the roofline of each."""
     stream = torch.cuda.current_stream(device)
     ms, ns, kap = batched_problems()
     base = synth.kappa_seed(3, 0)
-    Xs = [to_dev(synth.svd_matrix(int(m), int(n), float(k), base + 1 + i), torch, device)
+    Xs = [svd_matrix_gpu(torch, int(m), int(n), float(k), base + 1 + i, device)
           for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
     model = float(np.sum(2.0 * ms * ns * ns))
     branches, tune_ms = rq.rclupp_autotune_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base)
     _, grid_div, fine_tiles = rq.rclupp_get_batch_policy()
     Qs = [rq.empty_colmajor(int(m), int(n), device) for m, n in zip(ms, ns)]
     Rs = [rq.empty_colmajor(int(n), int(n), device) for n in ns]
-    call = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs)
-    for _ in range(max(3, args.warmup)):
-        call()
-    l0 = rq.kernel_launches()
-    batch_ms, (_, _, status) = time_call(torch, stream, call, args.steps)
-    launches = (rq.kernel_launches() - l0) // args.steps
+
+    def counts(form):
+        tot = [0.0, 0.0, 0.0]
+        for m, n in zip(ms, ns):
+            c = form_counts(int(m), int(n), 2 * int(n), form, first_tier=BATCH_SKETCH_TIER[form])
+            tot = [a + b for a, b in zip(tot, c)]
+        return tuple(tot)
+
+    def worst():
+        wo, wr = 0.0, 0.0
+        for i in range(len(Xs)):
+            o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
+            wo, wr = max(wo, o), max(wr, r)
+        return wo, wr
+
+    out = {}
+    for label, prec in (("fp64", rq.PREC_FP64), ("fp32", rq.PREC_SKETCH_FP32),
+                        ("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
+        call = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs,
+                                                prec=prec, check=False)
+        for _ in range(warmup):
+            call()
+        l0 = rq.kernel_launches()
+        b_ms, (_, _, st) = time_call(torch, stream, call, steps)
+        launches = (rq.kernel_launches() - l0) // steps
+        wo, wr = worst()
+        out[label] = {"ms_per_batch": b_ms, "gflops_2mn2": model / (b_ms / 1e3) / 1e9,
+                      "gpu_launches_per_batch": int(launches),
+                      "statuses_nonzero": int(np.count_nonzero(st)), "worst_orth": wo, "worst_res": wr,
+                      "roofline": roofline_of(counts(label), b_ms)}
+    for label in ("fp32", "emulated", "emulated_all"):
+        out[label]["speedup_vs_fp64_batch"] = out["fp64"]["ms_per_batch"] / out[label]["ms_per_batch"]
+
     # the same problems as sequential single calls
     def seq():
         for i, X in enumerate(Xs):
             rq.rclupp_factor(X, seed=base + i, Q=Qs[i], R=Rs[i], check=False)
     seq()
     seq_ms, _ = time_call(torch, stream, seq, 1)
-    worst_orth, worst_res = 0.0, 0.0
-    for i in range(len(Xs)):
-        o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
-        worst_orth, worst_res = max(worst_orth, o), max(worst_res, r)
-    # the same batch with the emulated tiers (binary64 sketch in a graph)
-    emu = {}
-    for label, prec in (("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
-        callp = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs,
-                                                 prec=prec)
-        for _ in range(max(3, args.warmup)):
-            callp()
-        e_ms, (_, _, e_st) = time_call(torch, stream, callp, args.steps)
-        wo, wr = 0.0, 0.0
-        for i in range(len(Xs)):
-            o, r = accuracy(torch, Xs[i], Qs[i], Rs[i])
-            wo, wr = max(wo, o), max(wr, r)
-        emu[label] = {"ms_per_batch": e_ms, "gflops_2mn2": model / (e_ms / 1e3) / 1e9,
-                      "speedup_vs_fp64_batch": batch_ms / e_ms,
-                      "statuses_nonzero": int(np.count_nonzero(e_st)), "worst_orth": wo, "worst_res": wr}
-    line = {
-        "workload": "batched RCLUPP: 512 FP64 problems, m=floor(2^U(12,17)), n in {16..128}, "
-                    "kappa=10^U(2,12), Gaussian s=2n",
-        "problems": len(Xs), "rows_total": int(ms.sum()), "model_flops": model,
-        "branches_autotuned": branches, "grid_div_autotuned": grid_div, "fine_tiles_autotuned": fine_tiles,
-        "ms_per_batch": batch_ms,
-        "gflops_2mn2": model / (batch_ms / 1e3) / 1e9,
-        "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
-        "gpu_launches_per_batch": int(launches), "statuses_nonzero": int(np.count_nonzero(status)),
-        "worst_orth": worst_orth, "worst_res": worst_res, "precision_form": emu,
-    }
-    print(json.dumps(line), flush=True)
+    out["fp64"]["sequential_ms"] = seq_ms
+    out["fp64"]["speedup_vs_sequential"] = seq_ms / out["fp64"]["ms_per_batch"]
+    del Xs, Qs, Rs
+    torch.cuda.empty_cache()
+    return {"workload": "batched RCLUPP: 512 problems, m=floor(2^U(12,17)), n in {16..128}, "
+                        "kappa=10^U(2,12), Gaussian s=2n (GPU-built X)",
+            "problems": int(len(ms)), "rows_total": int(ms.sum()), "model_flops": model,
+            "branches_autotuned": branches, "grid_div_autotuned": grid_div,
+            "fine_tiles_autotuned": fine_tiles, "results": out}
 
 
 def run_ours(args):
@@ -494,6 +661,7 @@ def run_ours(args):
     device = torch.device("cuda", torch.cuda.current_device())
     import paper_2412_06551_gb300 as rq
     rq.load()
+    measure_fp64_peak(rq)
 
     x = synth.svd_matrix(M, N, KAPPA, SEED_X + rank)
     X = to_dev(x, torch, device)
@@ -630,16 +798,25 @@ def run_ours(args):
         "sketch_gauss": 2.0 * S_SKETCH * M * N,
     }
     ach = per_launch_flops.get(dom, float("nan")) / (avg_ms / 1e3) / 1e9
-    # DRAM bytes per launch from one ncu capture of the same kernel at m = 262144
-    # (dram__bytes_read.sum + dram__bytes_write.sum = 268.7 + 235.7 MB), scaled
-    # by the rows processed to this workload's m; traffic grows with m.
-    traffic = {"trsm_gram": (268.7e6 + 235.7e6) * (M / 262144)}.get(dom)
-    roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "traffic_source": "ncu, m=262144 capture scaled x%g (profiles/trsm_gram_fp64_m262144_n128.md); "
-                                  "algorithmic 16 m n = %.3g bytes" % (M / 262144, 16.0 * M * N)
-                if traffic else None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
+    traffic, traffic_source = None, None
+    if dom == TRAFFIC_CAPTURE["kernel"]:
+        scale = M / TRAFFIC_CAPTURE["m"]
+        if TRAFFIC_SRC_SHA is not None and kernel_source_sha() == TRAFFIC_SRC_SHA:
+            traffic = (TRAFFIC_CAPTURE["read"] + TRAFFIC_CAPTURE["write"]) * scale
+            traffic_source = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                              "m=%d, n=%d, scaled x%g; algorithmic 16 m n = %.3g bytes"
+                              % (TRAFFIC_CAPTURE["m"], TRAFFIC_CAPTURE["n"], scale, 16.0 * M * N))
+        else:
+            traffic_source = "kernel source changed since the ncu capture: no counters for it"
+    p64 = FP64_PEAK["gflops"]
+    roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": p64,
+                "unit": "GFLOP/s", "frac": ach / p64, "traffic": traffic,
+                "traffic_source": traffic_source,
+                "peak_source": "FP64 pipe, %s; derived %d SMs x 2 DFMA/clk x 2 flop x %d MHz = %.1f"
+                               % (FP64_PEAK["source"], FP64_PEAK.get("sms", 152),
+                                  FP64_PEAK.get("clock_mhz", 2070),
+                                  FP64_PEAK.get("derived_gflops", 1258.56)),
+                "frac_of_derived": ach / FP64_PEAK.get("derived_gflops", 1258.56),
                 "avg_launch_ms": avg_ms, "launches": dom_launches}
     kernel_share = {k: round(v[1] / sum(w[1] for w in tot.values()), 4) for k, v in tot.items()}
 
@@ -648,7 +825,7 @@ def run_ours(args):
         f = ALGO_FLOPS[name](M, N, S_SKETCH)
         t = path_ms[name] / 1e3
         paths[name] = {"ms": path_ms[name], "gflops_2mn2": 2.0 * M * N * N / t / 1e9,
-                       "fp64_gflops": f / t / 1e9, "roofline_frac": f / t / 1e9 / FP64_PEAK_GFLOPS,
+                       "fp64_gflops": f / t / 1e9, "roofline_frac": f / t / 1e9 / p64,
                        **acc[name]}
     # realised kappa of X: the 2-norm condition number of the computed R (n x n)
     kappa_realised = float(np.linalg.cond(Rs[0].cpu().numpy()))
@@ -666,8 +843,23 @@ def run_ours(args):
     if sweep:
         line["accuracy_sweep"] = sweep
     line["mixed"] = mixed_on_same_x(rq, torch, X, stream, paths, args.steps)
+    line["peaks"] = {"fp64": FP64_PEAK, "hbm_gbs": HBM_PEAK_GBS, "bf16_tflops_sustained":
+                     BF16_SUSTAINED_TFLOPS, "bf16_tflops_burst": BF16_BURST_TFLOPS,
+                     "source": PEAKS_SOURCE + " (MEASURED_PEAKS.json) for HBM and bf16"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_configs:
+        del X, Qs, Rs, Xd
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        cfg = {"c3_precision": c3_precision(rq, torch, device),
+               "c1_small": c1_small(rq, torch, device),
+               "c5_large_sparse": c5_large_sparse(rq, torch, device),
+               "c4_batched": c4_batched(rq, torch, device)}
+        cfg["wall_s"] = time.perf_counter() - t0
+        line["configs"] = cfg
+        line["mixed_vs_fp64"] = {"workload": cfg["c3_precision"]["workload"],
+                                 "kappa": cfg["c3_precision"]["mixed_vs_fp64_at_equal_orth"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -685,6 +877,10 @@ def run_case(args):
     R = to_dev(np.triu(synth.rng(3).standard_normal((n, n))) / math.sqrt(n) + 2 * np.eye(n), torch,
                device)
     Yp = rq.rclupp_sketch(X, s=2 * n, seed=1) if args.case == "precond" else None
+    if args.case == "dfma_peak":
+        print(json.dumps({"case": "dfma_peak", **measure_fp64_peak(rq)}))
+        return
+    measure_fp64_peak(rq)
 
     def one():
         if args.case == "trsm_gram":
@@ -730,12 +926,24 @@ def run_case(args):
             "kernels": {k: {"launches": v[0] // args.reps, "ms": v[1] / args.reps} for k, v in prof.items()}}
     if flops:
         line["gflops"] = flops / (total * 1e-3) / 1e9
-        line["frac_fp64_peak"] = line["gflops"] / FP64_PEAK_GFLOPS
+        line["frac_fp64_peak"] = line["gflops"] / FP64_PEAK["gflops"]
+        line["fp64_peak"] = FP64_PEAK
     if args.case.startswith("sketch"):
         # the sketches read X once: 8 m n algorithmic bytes
         line["gbs"] = 8.0 * m * n / (total * 1e-3) / 1e9
         line["frac_hbm_peak"] = line["gbs"] / HBM_PEAK_GBS
     print(json.dumps(line))
+
+
+def run_workload(args):
+    """One sub-record on its own (one JSON line)."""
+    import torch
+    import paper_2412_06551_gb300 as rq
+    device = torch.device("cuda", 0)
+    measure_fp64_peak(rq)
+    fn = {"precision": c3_precision, "small": c1_small, "large_sparse": c5_large_sparse,
+          "batched": c4_batched}[args.workload]
+    print(json.dumps({**fn(rq, torch, device), "fp64_peak": FP64_PEAK}), flush=True)
 
 
 def main():
@@ -744,14 +952,8 @@ def main():
         args.warmup = 3
     if args.case:
         run_case(args)
-    elif args.workload == "precision":
-        run_precision(args)
-    elif args.workload == "batched":
-        run_batched(args)
-    elif args.workload == "small":
-        run_small(args)
-    elif args.workload == "large_sparse":
-        run_large_sparse(args)
+    elif args.workload != "side_by_side":
+        run_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

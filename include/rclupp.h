@@ -271,10 +271,14 @@ typedef enum {
  * (ldr[i]), every pointer a DEVICE pointer; the arrays themselves (m, n, X,
  * ldx, opts, Q, ldq, R, ldr, status) are HOST arrays of length count.  opts
  * holds one rclupp_opts_t per problem (NULL = defaults) and is used by the
- * randomized algorithms: the sketch is always binary64 here (a graph cannot
- * escalate), prec may be RCLUPP_PREC_FP64 or one of the emulated tiers, whose
- * emulated solves and Gram products are kept (the reduced sketch tiers return
- * RCLUPP_ERR_UNSUPPORTED).  Each problem obeys the single-problem rules;
+ * randomized algorithms.  A graph cannot escalate a sketch tier, so each
+ * problem's sketch runs at one tier: binary64 for RCLUPP_PREC_FP64; the
+ * three-term bf16 tensor-core sketch (FP32 level, enough for kappa(X) up to
+ * about 1e12) for RCLUPP_PREC_SKETCH_FP32 and for the emulated tiers, which
+ * keep their emulated solves and Gram products; RCLUPP_PREC_SKETCH_BF16,
+ * which relies on escalation, returns RCLUPP_ERR_UNSUPPORTED.  The sparse-sign,
+ * SRHT and explicit sketches stay binary64.  Each problem obeys the
+ * single-problem rules;
  * problems run concurrently, so the outputs of different problems must not
  * overlap (inputs may be shared).
  * The whole batch is enqueued as one CUDA graph: it forks into B parallel
@@ -452,10 +456,13 @@ rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t 
  *   stream       : cudaStream_t to run on (NULL = legacy default stream).
  * The call returns after its GPU work has finished (status read back).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  Every call on a device shares the
- * array and overwrites it: calls that overlap on the GPU race, so do not run
- * two of them concurrently on one device. */
+ * (cudaGetSymbolAddress, with that device current) and caches it for the
+ * life of the process; make that first call before any stream capture.  The
+ * cache assumes the device is not reset (cudaDeviceReset) while the process
+ * runs: a reset unloads the library's device image, and later calls would
+ * use the stale address.  Every call on a device shares the array and
+ * overwrites it: calls that overlap on the GPU race, so do not run two of
+ * them concurrently on one device. */
 rclupp_status_t rclupp_gram_noalloc(int64_t m, int64_t n, const double *A, int64_t lda, double *G,
                                     int64_t ldg, void *stream);
 
@@ -464,13 +471,14 @@ rclupp_status_t rclupp_gram_noalloc(int64_t m, int64_t n, const double *A, int64
  * library launches increments a process-wide counter.  When profiling is
  * enabled, a CUDA event pair is recorded on the launching stream around each
  * kernel; rclupp_profile_get synchronizes on the recorded events and returns,
- * for one kernel class (0 <= kid < 18), the number of timed launches, their
+ * for one kernel class (0 <= kid < 19), the number of timed launches, their
  * summed duration in milliseconds and the class name (static string).
  * Classes: 0 sketch_gauss, 1 sketch_sparse, 2 gram, 3 trsm_gram (fused
  * TRSM + Gram), 4 trsm, 5 reduce, 6 lu_col, 7 lu_trailing, 8 lu_u12,
  * 9 small_precond, 10 cholesky, 11 trmm, 12 pad, 13 sketch_tc (tensor-core
  * sketch), 14 gram_emu, 15 emu_aux (exponent and digit-preparation kernels
- * of the emulated products), 16 trsm_emu, 17 sketch_srht.  Returns ERR_ARG
+ * of the emulated products), 16 trsm_emu, 17 sketch_srht, 18 fp64_peak
+ * (the microbenchmark below).  Returns ERR_ARG
  * for an invalid class.  The open event of a launch is kept per kernel
  * class for the whole process, so enable timing only while one host thread
  * launches; the launch counter is exact with any number of threads.
@@ -480,6 +488,18 @@ void rclupp_profile_enable(int enable);
 void rclupp_profile_reset(void);
 int rclupp_profile_get(int kid, long long *launches, double *total_ms, const char **name);
 unsigned long long rclupp_kernel_launches(void);
+
+/* Measured FP64-pipe throughput of the current device, the denominator of
+ * the binary64 kernels' roofline: 2 CTAs per SM of 256 threads, each thread
+ * running 8 independent chains of 2^15 dependent DFMAs (a <- a b + c), timed
+ * with CUDA events on `stream` (a cudaStream_t, NULL = legacy default); the
+ * best of three launches after one warm-up.  *gflops = 2 x DFMAs / time;
+ * *ms (may be NULL) its time; *sms and *clock_mhz (may be NULL) the device's
+ * SM count and maximum SM clock as the runtime reports them, so a caller can
+ * set the measured rate beside SMs x clock x the DFMAs per clock.  Runs for
+ * about 0.1 s; synchronous.  Errors: ERR_ARG (gflops NULL), ERR_CUDA. */
+rclupp_status_t rclupp_profile_fp64_peak(void *stream, double *gflops, double *ms, int32_t *sms,
+                                         int32_t *clock_mhz);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,7 @@ __all__ = [
     "rclupp_set_batch_policy", "rclupp_get_batch_policy",
     "ALGO_RCLUPP", "ALGO_RCLUPPR",
     "ALGO_CHOLQR2", "ALGO_LC2",
-    "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES",
+    "profile_enable", "profile_reset", "profile_read", "kernel_launches", "KERNEL_CLASSES", "fp64_peak",
 ]
 
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN, SKETCH_SRHT = 0, 1, 2
@@ -125,11 +125,13 @@ _SIGNATURES = {
     "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)], _I32),
     "rclupp_kernel_launches": ([], ctypes.c_ulonglong),
+    "rclupp_profile_fp64_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], _I32),
 }
 
 KERNEL_CLASSES = ["sketch_gauss", "sketch_sparse", "gram", "trsm_gram", "trsm", "reduce", "lu_col",
                   "lu_trailing", "lu_u12", "small_precond", "cholesky", "trmm", "pad", "sketch_tc",
-                  "gram_emu", "emu_aux", "trsm_emu", "sketch_srht"]
+                  "gram_emu", "emu_aux", "trsm_emu", "sketch_srht", "fp64_peak"]
 
 
 def profile_enable(on: bool = True) -> None:
@@ -152,6 +154,20 @@ def profile_read() -> dict:
         lib.rclupp_profile_get(kid, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(name))
         out[name.value.decode()] = (int(n.value), float(ms.value))
     return out
+
+
+def fp64_peak(stream=None) -> dict:
+    """Measured FP64-pipe rate of the current device (DFMA microbenchmark on
+    the current torch stream): {"gflops", "ms", "sms", "clock_mhz"}."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    g, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    sms, mhz = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = load().rclupp_profile_fp64_peak(ctypes.c_void_p(stream), ctypes.byref(g), ctypes.byref(ms),
+                                         ctypes.byref(sms), ctypes.byref(mhz))
+    _raise("rclupp_profile_fp64_peak", st)
+    return {"gflops": g.value, "ms": ms.value, "sms": int(sms.value), "clock_mhz": int(mhz.value)}
 
 
 def kernel_launches() -> int:
@@ -452,8 +468,9 @@ def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN,
                           Qs=None, Rs=None, check=True, prec=PREC_FP64, r0=R0_HOUSEHOLDER):
     """Factor a list of column-major matrices in one batched call (one CUDA
     graph).  s is a per-problem list (or None for 2 n); seed is a list or an
-    int (then seed + i for problem i); prec is PREC_FP64 or an emulated tier
-    (binary64 sketch).  Returns (Qs, Rs, statuses)."""
+    int (then seed + i for problem i); prec is PREC_FP64 (binary64 sketch),
+    PREC_SKETCH_FP32 or an emulated tier (three-term tensor-core sketch, no
+    escalation inside a graph).  Returns (Qs, Rs, statuses)."""
     a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec, r0)
     st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
     _raise("rclupp_factor_batched", st, None, check)

@@ -429,16 +429,27 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
 cudaError_t copy_matrix(double *dst, int64_t ldd, const double *src, int64_t lds, int64_t m,
                         int64_t n, cudaStream_t s);
 
-// ---- binary64 drivers as pure enqueues (no host synchronization) -------------
+// ---- drivers as pure enqueues (no host synchronization) ----------------------
 // They put the whole factorization on c.s with its status in c.st, so they
 // can run several at once on different streams and be captured in a graph.
+// Without a host round trip there is no escalation: the sketch runs at one
+// tier, batch_sketch_tier(o).
 
-// RCLUPP, Algorithm 6, binary64 sketch.
+// Sketch tier of a randomized factorization inside a batch: binary64 for
+// RCLUPP_PREC_FP64, else the three-term tensor-core tier (FP32 level), which
+// keeps kappa(Q1) ~ 2^-24 kappa(X) within CholeskyQR2's reach up to
+// kappa(X) ~ 1e12 (the bf16 tier reaches only ~1e9 and needs the escalation a
+// graph cannot make).  sketch_step() runs the sparse-sign, SRHT and explicit
+// sketches in binary64 whatever the tier.
+int batch_sketch_tier(const rclupp_opts_t &o) {
+    return o.prec == RCLUPP_PREC_FP64 ? RCLUPP_PREC_FP64 : RCLUPP_PREC_SKETCH_FP32;
+}
+
+// RCLUPP, Algorithm 6, sketch at batch_sketch_tier(o).
 rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int64_t m, int n,
                                const double *X, int64_t ldx, double *Q, int64_t ldq, double *R,
                                int64_t ldr) {
-    RQ_TRY(launch_sketch(X, ldx, m, n, 0, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
-                         c.st, c.s, 0, o.order_log2));
+    RQ_TRY(sketch_step(b, X, ldx, m, n, 0, o, batch_sketch_tier(o), c.st, c.s));
     RQ_TRY(launch_sketch_precond(b.Y, o.s, int(o.s), n, b.W, b.RP[0], b.rinv[0], nullptr, 0, c.st, 1,
                                  c.s, o.r0_method));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
@@ -447,14 +458,13 @@ rclupp_status_t enqueue_rclupp(Ctx c, const Bufs &b, const rclupp_opts_t &o, int
     return rest_cholqr2(c, b, m, n, Q, ldq, R, ldr, emu, o.prec == RCLUPP_PREC_EMULATED_ALL);
 }
 
-// RCLUPPr, Algorithm 7, binary64 sketch; the LU runs in L (ldl).
+// RCLUPPr, Algorithm 7, sketch at batch_sketch_tier(o); the LU runs in L (ldl).
 rclupp_status_t enqueue_rcluppr(Ctx c, const Bufs &b, const rclupp_opts_t &o, int64_t m, int n,
                                 const double *X, int64_t ldx, double *L, int64_t ldl, double *Q,
                                 int64_t ldq, double *R, int64_t ldr) {
     RQ_TRY(copy_matrix(L, ldl, X, ldx, m, n, c.s));
     RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
-    RQ_TRY(launch_sketch(L, ldl, m, n, 1, o.kind, o.s, o.zeta, o.seed, o.S, o.lds, b.Y, o.s, b.part,
-                         c.st, c.s, 0, o.order_log2));
+    RQ_TRY(sketch_step(b, L, ldl, m, n, 1, o, batch_sketch_tier(o), c.st, c.s));
     RQ_TRY(launch_rcluppr_r1(b.Y, o.s, int(o.s), n, L, ldl, b.W, b.RP[0], b.rinv[0], c.s, o.r0_method));
     const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     const rclupp_status_t st = first_cholqr_pass(c, b, m, n, X, ldx, Q, ldq, emu, emu);
@@ -777,11 +787,11 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
         if (randomized) {
             if ((st = check_opts(o[i], m[i], n[i])) != RCLUPP_OK) return st;
-            // binary64 sketch always (no escalation inside a graph); the
-            // emulated tiers keep their emulated products
-            if (o[i].prec != RCLUPP_PREC_FP64 && o[i].prec != RCLUPP_PREC_EMULATED &&
-                o[i].prec != RCLUPP_PREC_EMULATED_ALL)
-                return RCLUPP_ERR_UNSUPPORTED;
+            // one sketch tier per problem (no escalation inside a graph):
+            // binary64, or the three-term tensor-core sketch for the
+            // RCLUPP_PREC_SKETCH_FP32 and emulated tiers; the bf16 tier needs
+            // the escalation and is refused
+            if (o[i].prec == RCLUPP_PREC_SKETCH_BF16) return RCLUPP_ERR_UNSUPPORTED;
         }
         const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
         const int64_t s = randomized ? o[i].s : n[i];
@@ -844,7 +854,7 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
                     ls = enqueue_cholqr2(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
                     break;
                 case RCLUPP_ALGO_RCHOLQR:
-                    ls = enqueue_rcholqr(c, b, o[i], RCLUPP_PREC_FP64, m[i], ni, X[i], ldx[i], Q[i],
+                    ls = enqueue_rcholqr(c, b, o[i], batch_sketch_tier(o[i]), m[i], ni, X[i], ldx[i], Q[i],
                                          ldq[i], R[i], ldr[i]);
                     break;
                 case RCLUPP_ALGO_SCHOLQR3:

@@ -229,6 +229,7 @@ enum KernelId : int {
     KID_EMU_AUX,
     KID_TRSM_EMU,
     KID_SKETCH_SRHT,
+    KID_FP64_PEAK,
     KID_COUNT
 };
 

@@ -39,7 +39,9 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
 // Device address of g_gram_scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process.
+// The cache assumes no cudaDeviceReset in between: a reset unloads the
+// module, and the array may come back at another address.
 rclupp_status_t scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -45,7 +45,30 @@ const char *kNames[KID_COUNT] = {"sketch_gauss", "sketch_sparse", "gram",       
                                  "trsm",         "reduce",        "lu_col",     "lu_trailing",
                                  "lu_u12",       "small_precond", "cholesky",   "trmm",
                                  "pad",          "sketch_tc",     "gram_emu",   "emu_aux",
-                                 "trsm_emu",     "sketch_srht"};
+                                 "trsm_emu",     "sketch_srht",   "fp64_peak"};
+
+// FP64-pipe microbenchmark: every thread keeps kChains independent chains
+// a <- a b + c of DFMAs for `iters` rounds (b slightly below 1, c small, so
+// the values stay bounded); the sum is stored only when it equals a value the
+// chains never reach, which keeps the work without a memory stream.
+constexpr int kPeakChains = 8;
+constexpr int kPeakThreads = 256;
+
+__global__ void __launch_bounds__(kPeakThreads, 2)
+    k_fp64_peak(double b, double c, int iters, double *sink) {
+    double a[kPeakChains];
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kPeakChains; ++k) a[k] = fma(a[k], b, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) t += a[k];
+    if (t == -1.0 && sink != nullptr) sink[blockIdx.x] = t;
+}
 
 }  // namespace
 
@@ -128,6 +151,50 @@ int rclupp_profile_get(int kid, long long *launches, double *total_ms, const cha
     if (launches) *launches = p.count[kid];
     if (total_ms) *total_ms = p.ms[kid];
     if (name) *name = kNames[kid];
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_profile_fp64_peak(void *stream, double *gflops, double *ms, int32_t *sms,
+                                         int32_t *clock_mhz) {
+    if (!gflops) return RCLUPP_ERR_ARG;
+    int dev = 0, nsm = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return RCLUPP_ERR_CUDA;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = 2 * nsm, iters = 1 << 15;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return RCLUPP_ERR_CUDA;
+    }
+    const double b = 1.0 - 0x1p-30, c = 0x1p-40;
+    float best = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // rep 0 warms up
+        cudaEventRecord(e0, s);
+        RQ_LAUNCH(KID_FP64_PEAK, s, k_fp64_peak<<<grid, kPeakThreads, 0, s>>>(b, c, iters, nullptr));
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.f || t < best)) best = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || best <= 0.f) {
+        cudaGetLastError();
+        return RCLUPP_ERR_CUDA;
+    }
+    const double flops = 2.0 * kPeakChains * double(iters) * grid * kPeakThreads;
+    *gflops = flops / (double(best) * 1e-3) / 1e9;
+    if (ms) *ms = best;
+    if (sms) *sms = nsm;
+    if (clock_mhz) *clock_mhz = khz / 1000;
     return RCLUPP_OK;
 }
 

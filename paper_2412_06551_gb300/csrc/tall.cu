@@ -405,7 +405,9 @@ cudaError_t launch_gram_bounded(const double *A, int64_t lda, int64_t m, int n, 
                                 cudaStream_t stream) {
     if (n > 128 || max_parts < 1) return cudaErrorInvalidValue;
     const int ncb = pad16(n);
-    const int bm = gram_bm(n);
+    // the default row tiles of launch_gram, chosen here without the per-thread
+    // launch policy: only the two instantiations below exist for this helper
+    const int bm = n <= 64 ? 128 : 64;
     CUtensorMap map;
     const bool tma = make_tma_map(&map, A, m, n, lda, bm, ncb);
     if (!tma) memset(&map, 0, sizeof map);

@@ -38,6 +38,7 @@ __all__ = [
     "gaussian_sketch",
     "sparse_sign_sketch",
     "kappa_seed",
+    "batched_problems",
 ]
 
 
@@ -137,3 +138,17 @@ def sparse_sign_sketch(s: int, m: int, zeta: int, seed: int) -> np.ndarray:
         signs = g.integers(0, 2, size=zeta) * 2 - 1
         out[rows, i] = signs * val
     return np.asfortranarray(out)
+
+
+def batched_problems(count: int = 512, seed: int = None):
+    """Sizes of the uneven batch of independent problems: m = floor(2^U(12,17)),
+    n uniform in {16, 32, 48, 64, 96, 128}, kappa = 10^U(2,12) (the sketch size
+    is s = 2n).  Returns (ms, ns, kappas) as numpy arrays; problem i's matrix
+    is ``svd_matrix(ms[i], ns[i], kappas[i], seed + 1 + i)``."""
+    if seed is None:
+        seed = kappa_seed(3, 0)
+    g = rng(seed)
+    ms = np.floor(2.0 ** g.uniform(12, 17, count)).astype(np.int64)
+    ns = g.choice(np.array([16, 32, 48, 64, 96, 128]), count)
+    kap = 10.0 ** g.uniform(2, 12, count)
+    return ms, ns, kap

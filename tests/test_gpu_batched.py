@@ -184,3 +184,49 @@ def test_autotuner_sets_a_valid_policy(rq):
     finally:
         rq.rclupp_set_batch_branches(16)
         rq.rclupp_set_batch_policy(1, False)
+
+
+def test_batched_three_term_sketch_matches_single_calls(rq):
+    # a batch cannot escalate, so RCLUPP_PREC_SKETCH_FP32 runs the three-term
+    # tensor-core sketch for every problem; on inputs where the single call
+    # keeps that tier (no escalation) the two are the same kernels with the
+    # same launch shapes, bit for bit
+    g = np.random.default_rng(17)
+    xs = [synth.svd_matrix(int(m), int(n), 1e5, 900 + i)
+          for i, (m, n) in enumerate(zip(g.integers(300, 6000, 10), g.choice([8, 33, 64, 100, 128], 10)))]
+    Xs = [dev(x) for x in xs]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=61, prec=rq.PREC_SKETCH_FP32)
+    assert np.all(st == 0)
+    for i, X in enumerate(Xs):
+        q, r, info = rq.rclupp_factor(X, seed=61 + i, prec=rq.PREC_SKETCH_FP32)
+        assert info.prec_used == rq.PREC_SKETCH_FP32
+        assert torch.equal(Qb[i], q) and torch.equal(Rb[i], r), i
+
+
+def test_batched_bf16_sketch_is_refused(rq):
+    # the bf16 tier depends on escalation, which a graph cannot make
+    Xs = [dev(synth.svd_matrix(500, 8, 1e2, 1))]
+    with pytest.raises(rq.RclupError) as e:
+        rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, prec=rq.PREC_SKETCH_BF16)
+    assert e.value.status == rq.Status.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [2, 3, 4])
+def test_batched_tensor_core_sketch_gates_up_to_kappa_1e12(rq, prec):
+    # the three-term sketch in a batch (and the emulated tiers on top of it)
+    # against the oracle, kappa log-uniform up to 1e12
+    g = np.random.default_rng(30 + prec)
+    ms = g.integers(600, 9000, 12)
+    ns = g.choice([16, 48, 96, 128], 12)
+    kap = 10.0 ** g.uniform(2, 12, 12)
+    xs = [synth.svd_matrix(int(m), int(n), float(k), 850 + i) for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
+    Xs = [dev(x) for x in xs]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=71, prec=prec)
+    assert np.all(st == 0)
+    for i, x in enumerate(xs):
+        m, n = x.shape
+        q_o, r_o, _ = oracle.rclupp(x, S=oracle.gaussian_sketch_matrix(2 * n, m, 71 + i))
+        q, r = host(Qb[i]), host(Rb[i])
+        assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0), i
+        assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13), i
+        assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13), i

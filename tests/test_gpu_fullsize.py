@@ -4,8 +4,11 @@ times (generated sketch, device-resident column-major inputs).
 * m = 2^20, n = 128, Gaussian s = 256, kappa in {1e4, 1e10, 1e15}: all four
   factorizations against the full oracle on the same X and the same S (the
   oracle's own implementation of the counter-based generator).
-* m = 2^22, n = 256, s = 512 (8.6 GB), FP64 RCLUPP: properties that hold at
-  any size plus sampled outputs the oracle recomputes one by one.
+* m = 2^22, n = 256, s = 512 (8.6 GB), kappa in {1e2, 1e8, 1e14}: RCLUPP in
+  binary64 and in every precision tier (tensor-core bf16 / three-term
+  sketch, emulated solves and Grams) against the full oracle RCLUPP on the
+  same X and S (kappa <= 1e12), plus properties that hold at any size and
+  sampled outputs the oracle recomputes one by one.
 * m = 2^24, n = 64 (8.6 GB), sparse-sign s = 256, zeta = 8, RCLUPPr with the
   tall LU over all rows: the full sparse sketch against the oracle, the LU's
   backward error (eq. (elu)) on sampled rows, and the factorization's
@@ -107,16 +110,57 @@ def test_side_by_side_full_size(rq, k_index, kappa):
 M3, N3, S3 = 1 << 22, 256, 512
 
 
-@pytest.mark.parametrize("k_index,kappa", [(0, 1e2), (1, 1e8), (2, 1e14)])
-def test_rclupp_fp64_m4M_n256(rq, k_index, kappa):
+@pytest.fixture(scope="module", params=[(0, 1e2), (1, 1e8), (2, 1e14)],
+                ids=["kappa1e2", "kappa1e8", "kappa1e14"])
+def c3(request):
+    """The precision-form workload (8.6 GB X) at one kappa, with the full
+    oracle RCLUPP on the same X and the same generated S where the gate
+    applies (kappa <= 1e12): its orthogonality, residual and R.  The oracle
+    holds X, S (17.2 GB), Q and its two m x n intermediates in host memory."""
+    k_index, kappa = request.param
     seed = synth.kappa_seed(2, k_index)
     x = synth.svd_matrix(M3, N3, kappa, seed)
     X = dev(x)
-    Q, R, info = rq.rclupp_factor(X, s=S3, seed=seed + 7, check=False)
-    if kappa > 1e12 and info.status != 0:
-        pytest.skip("RCLUPP broke down at kappa %.0e (outside the gate)" % kappa)
-    assert info.status == 0
+    ref = None
+    if kappa <= 1e12:
+        S = oracle.gaussian_sketch_matrix(S3, M3, seed + 7)
+        q_o, r_o, st_o = oracle.rclupp(x, S=S, raise_on_error=False)
+        del S
+        assert st_o == 0
+        Qo = dev(q_o)
+        del q_o
+        orth_o, res_o = gpu_metrics(X, Qo, dev(r_o))
+        del Qo
+        ref = {"orth": orth_o, "res": res_o, "r": r_o}
+    yield {"kappa": kappa, "seed": seed, "x": x, "X": X, "ref": ref}
+    del X
+    torch.cuda.empty_cache()
+
+
+def _gate(c3, Q, R, label):
+    """BASELINE gates against the oracle on the same X: orthogonality and
+    residual <= max(10 x oracle, 1e-13) for kappa <= 1e12, R within 1e-10 kappa
+    of the oracle's R for kappa <= 1e6; beyond the gate a record-level check."""
+    kappa, ref, X = c3["kappa"], c3["ref"], c3["X"]
     orth, res = gpu_metrics(X, Q, R)
+    r = host(R)
+    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0), label
+    if ref is not None:
+        assert orth <= max(10 * ref["orth"], 1e-13), (label, orth, ref["orth"])
+        assert res <= max(10 * ref["res"], 1e-13), (label, res, ref["res"])
+        if kappa <= 1e6:
+            err = np.linalg.norm(r - ref["r"]) / np.linalg.norm(ref["r"])
+            assert err <= 1e-10 * kappa, (label, err)
+    else:
+        assert orth <= 1e-12 and res <= 1e-14, (label, orth, res)
+    return orth, res, r
+
+
+def test_rclupp_fp64_m4M_n256(rq, c3):
+    kappa, X = c3["kappa"], c3["X"]
+    Q, R, info = rq.rclupp_factor(X, s=S3, seed=c3["seed"] + 7, check=False)
+    assert info.status == 0 and info.prec_used == rq.PREC_FP64
+    orth, res, r = _gate(c3, Q, R, "fp64")
     # Theorem 4.1 bounds (eps = 0.5) hold at any size; FP64 practice is far below them
     h = 1.0 / (0.78 / math.sqrt(1.5) - 0.1 / math.sqrt(0.5))
     assert orth <= 6 * (M3 * N3 * U + N3 * (N3 + 1) * U)
@@ -125,8 +169,6 @@ def test_rclupp_fp64_m4M_n256(rq, k_index, kappa):
              + 3.02 / math.sqrt(0.5) * h * N3 * N3 * U * 1.0)
     assert res * fro <= delta
     assert orth <= 1e-13 and res <= 1e-14
-    r = host(R)
-    assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0)
     # closed form: R has the singular values of X
     sv = np.linalg.svd(r, compute_uv=False)
     sigma = np.power(kappa, -np.arange(N3) / (N3 - 1))
@@ -134,9 +176,30 @@ def test_rclupp_fp64_m4M_n256(rq, k_index, kappa):
     # sampled outputs: rows of Q recomputed by the oracle as X[i,:] R^{-1}
     if kappa <= 1e2:
         rows = np.sort(synth.rng(5).choice(M3, size=2000, replace=False))
-        q_rows = oracle.trsm(x[rows], r)
+        q_rows = oracle.trsm(c3["x"][rows], r)
         q_gpu = host(Q[torch.from_numpy(rows).to(Q.device)])
         assert np.max(np.abs(q_gpu - q_rows)) <= 1e-13
+
+
+@pytest.mark.parametrize("tier", ["SKETCH_BF16", "SKETCH_FP32", "EMULATED", "EMULATED_ALL"])
+def test_rclupp_precision_tiers_m4M_n256(rq, c3, tier):
+    # the precision form against the full oracle on the same X: the
+    # tensor-core sketch (bf16 or three-term bf16 X, escalating when the first
+    # Cholesky shows Q1 too ill-conditioned) and the binary64-emulating
+    # tensor-core solves and Grams
+    prec = getattr(rq, "PREC_" + tier)
+    kappa = c3["kappa"]
+    Q, R, info = rq.rclupp_factor(c3["X"], s=S3, seed=c3["seed"] + 7, prec=prec, check=False)
+    assert info.status == 0, (tier, info.status, info.failed_step)
+    sketch_tier = rq.PREC_SKETCH_BF16 if prec >= rq.PREC_EMULATED else prec
+    # the sketch tier used: the requested one, or a more precise one after
+    # an escalation (only expected where kappa(X) exceeds the tier's reach)
+    assert info.prec_used in (sketch_tier, rq.PREC_SKETCH_FP32, rq.PREC_FP64), info.prec_used
+    if kappa <= 1e8:
+        assert info.prec_used == sketch_tier, (tier, info.prec_used)
+    assert info.emulated == {"EMULATED": 1, "EMULATED_ALL": 2}.get(tier, 0)
+    _gate(c3, Q, R, tier)
+    del Q, R
 
 
 # -------------------------- m = 2^24, n = 64, sparse-sign s = 256, RCLUPPr ---
@@ -211,3 +274,41 @@ def test_rcluppr_sparse_full_size_emulated(rq, big5):
     assert orth <= 6 * (M5 * N5 * U + N5 * (N5 + 1) * U)
     assert orth <= 1e-12 and res <= 1e-14
 
+
+
+# --------------------------------- 512 uneven problems, one batched call ---
+
+@pytest.fixture(scope="module")
+def c4():
+    """The batched workload: 512 problems, m = floor(2^U(12,17)), n in
+    {16, ..., 128}, kappa = 10^U(2,12), Gaussian s = 2n (sketch seed base + i),
+    each with the oracle's RCLUPP on the same X and the same generated S."""
+    base = synth.kappa_seed(3, 0)
+    ms, ns, kap = synth.batched_problems(512, base)
+    xs = [synth.svd_matrix(int(m), int(n), float(k), base + 1 + i)
+          for i, (m, n, k) in enumerate(zip(ms, ns, kap))]
+    refs = []
+    for i, x in enumerate(xs):
+        m, n = x.shape
+        q_o, r_o, st_o = oracle.rclupp(x, S=oracle.gaussian_sketch_matrix(2 * n, m, base + i),
+                                       raise_on_error=False)
+        assert st_o == 0, i
+        refs.append((oracle.orthogonality(q_o), oracle.residual(x, q_o, r_o), r_o))
+    return {"base": base, "xs": xs, "kappa": kap, "refs": refs}
+
+
+@pytest.mark.parametrize("tier", ["FP64", "SKETCH_FP32", "EMULATED", "EMULATED_ALL"])
+def test_batched_512_problems_against_oracle(rq, c4, tier):
+    prec = getattr(rq, "PREC_" + tier)
+    Xs = [dev(x) for x in c4["xs"]]
+    Qb, Rb, st = rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=c4["base"], prec=prec,
+                                          check=False)
+    assert np.all(st == 0), np.nonzero(st)
+    for i, (X, (orth_o, res_o, r_o)) in enumerate(zip(Xs, c4["refs"])):
+        orth, res = gpu_metrics(X, Qb[i], Rb[i])
+        r = host(Rb[i])
+        assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0), i
+        assert orth <= max(10 * orth_o, 1e-13), (i, orth, orth_o)
+        assert res <= max(10 * res_o, 1e-13), (i, res, res_o)
+        if c4["kappa"][i] <= 1e6:
+            assert np.linalg.norm(r - r_o) / np.linalg.norm(r_o) <= 1e-10 * c4["kappa"][i], i

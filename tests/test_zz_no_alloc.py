@@ -4,15 +4,18 @@ the C ABI, against the allocating one (rclupp_gram).
 rclupp_gram_noalloc serves callers that cannot let the library allocate
 device memory; it keeps its scratch in a fixed array inside the library.
 Two calls in a row on different shapes check that what the previous call
-left in that shared array does not leak into the next result.  The
-tolerance is the one the Gram parity tests use: two sums of the same m
-products in different orders differ by at most 2 gamma_m (|A|^T |A|).
+left in that shared array does not leak into the next result.  Each result
+is compared with the allocating entry point and with the CPU oracle's Gram
+(sequential sums).  The tolerance is the one the Gram parity tests use: two
+sums of the same m products in different orders differ by at most
+2 gamma_m (|A|^T |A|).
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -62,6 +65,8 @@ def test_noalloc_gram_matches_allocating_gram_twice():
         tol = 2 * _gamma(m) * (np.abs(x).T @ np.abs(x))
         assert np.all(np.isfinite(g))
         assert np.all(np.abs(g - g_ref) <= tol)
+        g_orc = oracle.gram(x)
+        assert np.all(np.abs(g - g_orc) <= tol)
 
 
 def test_noalloc_gram_rejects_sizes_beyond_its_limit():
