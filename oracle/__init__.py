@@ -90,6 +90,9 @@ def _load():
                 "orc_scholqr3_shift": ([I64, I64, P, I64], ctypes.c_double),
                 "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
                 "orc_sketch_bf16": ([I64, I64, I64, U64, I32, P, I64, P, I64], I32),
+                "orc_normal_quantile": ([ctypes.c_double], ctypes.c_double),
+                "orc_bf16_gauss_table": ([P], None),
+                "orc_bf16_sketch_entries": ([I64, I64, U64, P, I64], I32),
                 "orc_srht_perm_one": ([I32, U64, I64], I64),
                 "orc_srht_perm": ([I32, I64, U64, P], None),
                 "orc_srht_signs": ([U64, I64, I64, P], None),
@@ -455,9 +458,31 @@ def round_bf16(x: float) -> float:
     return float(_load().orc_round_bf16(float(x)))
 
 
+def normal_quantile(p: float) -> float:
+    """Phi^{-1}(p) of the standard normal (bisection on erfc)."""
+    return float(_load().orc_normal_quantile(float(p)))
+
+
+def bf16_gauss_table() -> np.ndarray:
+    """The reduced tier's 4096 levels T[j] = bf16(Phi^{-1}((j + 1/2) / 4096))."""
+    t = np.zeros(4096)
+    _load().orc_bf16_gauss_table(_p(t))
+    return t
+
+
+def bf16_sketch_z(s: int, m: int, seed: int) -> np.ndarray:
+    """Unscaled reduced-tier sketch z_b (s x m); the sketch is z_b / sqrt(s)."""
+    z = np.zeros((s, m), order="F")
+    st = _load().orc_bf16_sketch_entries(s, m, seed, _p(z), s)
+    if st != OK:
+        raise OracleError(st, -1)
+    return z
+
+
 def sketch_bf16(s: int, seed: int, nterms: int, x) -> np.ndarray:
-    """Y = S_bf16 X_split / sqrt(s): the tensor-core tier's sketch definition
-    (S entries z(r, i) rounded to bf16; X in one or three bf16 terms)."""
+    """Y = z_b X_split / sqrt(s): the tensor-core tier's sketch definition
+    (S entries z_b(r, i) from the discretised normal, bf16; X in one or three
+    bf16 terms)."""
     x = _f(x)
     m, n = x.shape
     y = np.zeros((s, n), order="F")

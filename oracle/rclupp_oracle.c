@@ -966,12 +966,13 @@ void orc_sparse_sign_column(uint64_t seed, int64_t i, int64_t s, int zeta, int32
 /* Reduced-precision sketch definition (the library's tensor-core tier)      */
 /*                                                                          */
 /* The sketch only has to be an embedding, so its product may run in bf16   */
-/* with fp32 sums: S's entries are z(r, i) rounded to bf16, and each x of X */
-/* is either rounded to bf16 (one term) or split into three bf16 terms      */
-/* x ~ x1 + x2 + x3 with x1 = bf16(x), x2 = bf16(x - x1),                    */
-/* x3 = bf16(x - x1 - x2) (the differences are exact in binary64).  All      */
-/* roundings are to nearest, ties to even.  The result is then              */
-/* Y = (sum_i bf16(z) (x1 + x2 + x3)) / sqrt(s), evaluated here in binary64. */
+/* with fp32 sums: S's entries z_b(r, i) are bf16 values of a discretised   */
+/* standard normal (defined below), and each x of X is either rounded to    */
+/* bf16 (one term) or split into three bf16 terms x ~ x1 + x2 + x3 with     */
+/* x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (the differences */
+/* are exact in binary64).  All roundings are to nearest, ties to even.     */
+/* The result is Y = (sum_i z_b (x1 + x2 + x3)) / sqrt(s), evaluated here   */
+/* in binary64.                                                             */
 /* ------------------------------------------------------------------------ */
 
 /* Round a binary64 value to the nearest bf16 value (8 significant bits,
@@ -996,13 +997,74 @@ double orc_round_bf16(double x)
     return y;
 }
 
-/* bf16 rounding of a binary32 value (ties to even), as binary64. */
-double orc_round_bf16_f32(float z)
+/* The reduced tier's S is not the binary64 tier's S rounded: since only an
+ * embedding is needed, its entries come from a 4096-level quantile
+ * discretisation of the standard normal, rounded to bf16,
+ *   T[j] = bf16( Phi^{-1}((j + 1/2) / 4096) ),  j = 0 .. 4095,
+ * and entry (r, i) of the unscaled sketch is
+ *   z_b(r, i) = T[ h >> 4 ],  h = bits 16 (t mod 2) .. 16 (t mod 2) + 15 of
+ *   word w_{t div 2} of Philox4x32-10 with counter (q mod 2^32, q div 2^32,
+ *   r, 0x53424631) and key = seed, where q = i div 8 and t = i mod 8
+ * (eight entries of one sketch row per Philox block).  S = z_b / sqrt(s). */
+
+/* Standard normal quantile Phi^{-1}(p), 0 < p < 1: bisection on
+ * Phi(x) = erfc(-x / sqrt(2)) / 2 until the bracket [lo, hi] holds two
+ * neighbouring binary64 numbers; returns hi, the smaller of the two with
+ * Phi(x) >= p.  p > 1/2 by the symmetry Phi^{-1}(p) = -Phi^{-1}(1 - p). */
+double orc_normal_quantile(double p)
 {
-    return orc_round_bf16((double)z);
+    if (p > 0.5)
+        return -orc_normal_quantile(1.0 - p);
+    double lo = -40.0, hi = 0.0;
+    for (int it = 0; it < 4000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi)
+            break;
+        const double phi = 0.5 * erfc(-mid / sqrt(2.0));
+        if (phi < p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return hi;
 }
 
-/* Y = (sum_i bf16(z(r, i)) * xs(i, j)) / sqrt(s) with xs the one- or
+/* T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)), j = 0 .. 4095. */
+void orc_bf16_gauss_table(double *T)
+{
+    for (int j = 0; j < 4096; ++j)
+        T[j] = orc_round_bf16(orc_normal_quantile(((double)j + 0.5) / 4096.0));
+}
+
+/* z_b(r, i) of the reduced tier, given the table T. */
+static double orc_bf16_gauss_entry_t(uint64_t seed, int64_t r, int64_t i, const double *T)
+{
+    const uint64_t q = (uint64_t)i >> 3;
+    const int t = (int)(i & 7);
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)(uint64_t)r, 0x53424631u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const uint32_t h = (w[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+    return T[h >> 4];
+}
+
+/* Unscaled reduced-tier sketch z_b (s x m, leading dimension ldz). */
+int orc_bf16_sketch_entries(int64_t s, int64_t m, uint64_t seed, double *Z, int64_t ldz)
+{
+    double *T = (double *)malloc(sizeof(double) * 4096);
+    if (!T)
+        return ORC_ERR_NOMEM;
+    orc_bf16_gauss_table(T);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t r = 0; r < s; ++r)
+            IDX(Z, ldz, r, i) = orc_bf16_gauss_entry_t(seed, r, i, T);
+    free(T);
+    return ORC_OK;
+}
+
+/* Y = (sum_i z_b(r, i) * xs(i, j)) / sqrt(s) with xs the one- or
  * three-term bf16 split of X, sums in increasing i (binary64).
  * nterms is 1 or 3. */
 int orc_sketch_bf16(int64_t s, int64_t m, int64_t n, uint64_t seed, int nterms, const double *X,
@@ -1010,16 +1072,11 @@ int orc_sketch_bf16(int64_t s, int64_t m, int64_t n, uint64_t seed, int nterms, 
 {
     double *Sb = (double *)malloc(sizeof(double) * (size_t)s * (size_t)m);
     double *Xs = (double *)malloc(sizeof(double) * (size_t)m * (size_t)n);
-    if (!Sb || !Xs) {
+    if (!Sb || !Xs || orc_bf16_sketch_entries(s, m, seed, Sb, s) != ORC_OK) {
         free(Sb);
         free(Xs);
         return ORC_ERR_NOMEM;
     }
-    /* S entries rounded to bf16 */
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < m; ++i)
-        for (int64_t r = 0; r < s; ++r)
-            Sb[r + i * s] = orc_round_bf16_f32(orc_gauss_entry(seed, r, i));
     /* X as the sum of its bf16 terms; x1 + x2 + x3 is exact in binary64
      * (the three terms cover disjoint runs of at most 8 bits) */
 #pragma omp parallel for schedule(static)

@@ -113,6 +113,18 @@ MUTANTS = [
     ("bf16_split_wrong_residual",
      "const double x3 = orc_round_bf16(r1 - x2);",
      "const double x3 = orc_round_bf16(x - x2);"),
+    ("bf16_levels_without_the_half",
+     "orc_normal_quantile(((double)j + 0.5) / 4096.0)",
+     "orc_normal_quantile(((double)j + 1.0) / 4097.0)"),
+    ("bf16_quantile_symmetry_sign",
+     "        return -orc_normal_quantile(1.0 - p);",
+     "        return orc_normal_quantile(1.0 - p);"),
+    ("bf16_counter_words_swapped",
+     "uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)(uint64_t)r, 0x53424631u};",
+     "uint32_t ctr[4] = {(uint32_t)(uint64_t)r, (uint32_t)(q >> 32), (uint32_t)q, 0x53424631u};"),
+    ("bf16_entries_share_a_half",
+     "const uint32_t h = (w[t >> 1] >> (16 * (t & 1))) & 0xffffu;",
+     "const uint32_t h = (w[t >> 1] >> (16 * 0)) & 0xffffu;"),
     ("bf16_sketch_scaled_twice",
      "            IDX(Y, ldy, r, j) *= scale;",
      "            IDX(Y, ldy, r, j) *= scale * scale;"),

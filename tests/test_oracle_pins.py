@@ -594,19 +594,79 @@ def test_bf16_split_keeps_24_bits():
     assert np.all(np.abs(x - x1) <= 2.0 ** -8 * np.abs(x))
 
 
+def test_bf16_gauss_table_against_library_quantile():
+    # T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)): scipy's ndtri (an independent
+    # implementation of the normal quantile) rounded by the independent bf16
+    # formula above gives every level bit for bit
+    from scipy.special import ndtri
+    t = oracle.bf16_gauss_table()
+    ref = np.array([_rne_bf16_reference(float(ndtri((j + 0.5) / 4096))) for j in range(4096)])
+    assert np.array_equal(t, ref)
+    # symmetric, increasing, and a unit variance up to the discretisation
+    assert np.array_equal(t, -t[::-1]) and np.all(np.diff(t) >= 0)
+    assert t[2047] < 0 < t[2048] and abs(t.var() - 1.0) < 1e-3
+    # the quantile itself at closed-form points
+    assert oracle.normal_quantile(0.5 - 1e-17) <= 0.0
+    assert abs(oracle.normal_quantile(0.8413447460685429) - 1.0) < 1e-12
+    assert abs(oracle.normal_quantile(0.022750131948179195) + 2.0) < 1e-12
+
+
+def test_bf16_sketch_entries_follow_philox():
+    # entry (r, i) = T[top 12 bits of 16-bit half (i mod 8) mod 2 of word
+    # (i mod 8) div 2 of Philox4x32-10 at counter (i div 8, 0, r, 0x53424631)]
+    # -- Philox itself is pinned by its known-answer vectors
+    t = oracle.bf16_gauss_table()
+    seed, s, m = 0x1234_5678_9ABC, 5, 37
+    z = oracle.bf16_sketch_z(s, m, seed)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for r in range(s):
+        for i in range(m):
+            w = oracle.philox4x32_10([i // 8, 0, r, 0x53424631], key)
+            h = (int(w[(i % 8) // 2]) >> (16 * (i % 2))) & 0xFFFF
+            assert z[r, i] == t[h >> 4], (r, i)
+
+
+def test_bf16_sketch_statistics():
+    # uniform levels, independent entries across rows and along a row (the
+    # eight entries of one Philox block are separate draws), unit variance
+    from scipy import stats
+    z = oracle.bf16_sketch_z(16, 20000, 77)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    t = oracle.bf16_gauss_table()
+    lv = np.searchsorted(np.unique(t), z.ravel())
+    counts = np.bincount(lv, minlength=len(np.unique(t)))
+    expect = np.array([np.sum(t == v) for v in np.unique(t)], dtype=np.float64) / 4096 * z.size
+    assert stats.chisquare(counts, expect).pvalue > 1e-4
+    c = np.corrcoef(z)
+    assert np.max(np.abs(c[~np.eye(16, dtype=bool)])) < 6.0 / math.sqrt(20000)
+    lag = [np.corrcoef(z[:, :-d].ravel(), z[:, d:].ravel())[0, 1] for d in range(1, 9)]
+    assert np.max(np.abs(lag)) < 6.0 / math.sqrt(z.size)
+
+
 @pytest.mark.parametrize("nterms", [1, 3])
 def test_sketch_bf16_definition(nterms):
     m, n, s, seed = 700, 9, 24, 5
     x = synth.svd_matrix(m, n, 1e3, 2)
     y = oracle.sketch_bf16(s, seed, nterms, x)
-    z = oracle.gaussian_sketch_matrix(s, m, seed) * math.sqrt(s)  # unscaled z, exact
-    Sb = np.vectorize(oracle.round_bf16)(np.float32(z).astype(np.float64))
-    ref = oracle.sketch_dense(Sb, oracle.bf16_split(x, nterms)) / math.sqrt(s)
+    z = oracle.bf16_sketch_z(s, m, seed)
+    ref = oracle.sketch_dense(z, oracle.bf16_split(x, nterms)) / math.sqrt(s)
     assert np.allclose(y, ref, rtol=0, atol=1e-14 * np.max(np.abs(ref)))
-    # and the reduced-precision sketch is close to the binary64 one
-    full = oracle.sketch_dense(oracle.gaussian_sketch_matrix(s, m, seed), x)
-    tol = (2.0 ** -8 if nterms == 1 else 2.0 ** -7) * np.abs(Sb / math.sqrt(s)) @ np.abs(x) * 3
-    assert np.all(np.abs(y - full) <= tol + 1e-300)
+    # exact on integers: small-integer X is its own bf16 split, and every
+    # product and sum of bf16 levels times small integers is exact in binary64
+    xi = synth.integer_matrix(300, 4, 8)
+    yi = oracle.sketch_bf16(s, seed, nterms, xi)
+    zi = oracle.bf16_sketch_z(s, 300, seed)
+    assert np.array_equal(yi, (zi @ xi) * (1.0 / math.sqrt(s)))
+
+
+def test_bf16_sketch_is_an_embedding_eq_s2():
+    # the discretised normal is sub-Gaussian with (nearly) unit variance, so
+    # z_b / sqrt(s) embeds like the Gaussian sketch (eq. (s2), eps = 0.5)
+    m, n, s = 3000, 8, 256
+    x = synth.orthonormal(m, n, 21)
+    y = oracle.sketch_dense(oracle.bf16_sketch_z(s, m, 9) / math.sqrt(s), x)
+    sv = np.linalg.svd(y, compute_uv=False)
+    assert sv.max() <= math.sqrt(1.5) and sv.min() >= math.sqrt(0.5)
 
 
 # ------------------------------------- comparison paths (Algorithms 3, 5) ---
