@@ -66,10 +66,14 @@ typedef enum {
 /* Precision form.  The sketch only has to be an embedding (Section 3): the
  * reduced tiers run the generated Gaussian sketch on the tensor cores
  * (tcgen05, bf16 operands, fp32 accumulation in tensor memory): S's entries
- * z(r, i) are rounded to bf16 and every x of X is either rounded to bf16
- * (BF16) or split into three bf16 terms x1 = bf16(x), x2 = bf16(x - x1),
- * x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums are combined in
- * binary64.  EMULATED adds binary64-emulating tensor-core products for the
+ * are bf16 levels of a discretised standard normal, z_b(r, i) = T[h >> 4]
+ * with T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)) and h the 16-bit half
+ * (i mod 8) mod 2 of word (i mod 8) div 2 of Philox4x32-10 at counter
+ * (i div 8 mod 2^32, i div 2^35, r, 0x53424631), key = seed (so the reduced
+ * tiers' S differs from the binary64 tier's), and every x of X is either
+ * rounded to bf16 (BF16) or split into three bf16 terms x1 = bf16(x),
+ * x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums
+ * are combined in binary64.  EMULATED adds binary64-emulating tensor-core products for the
  * solves and the first Gram.  Other steps stay in binary64.  The sparse-sign
  * and SRHT sketches only add and always run in binary64 (their results report
  * RCLUPP_PREC_FP64 as the tier used); an explicit S requires

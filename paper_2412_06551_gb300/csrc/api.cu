@@ -571,6 +571,13 @@ rclupp_status_t rclupp_create(rclupp_handle_t *handle, void *stream) {
         return RCLUPP_ERR_CUDA;
     }
     cudaMemset(h->d_status, 0, sizeof(DevStatus));
+    if (ensure_sketch_levels() != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->d_status);
+        cudaFreeHost(h->h_status);
+        delete h;
+        return RCLUPP_ERR_CUDA;
+    }
     *handle = h;
     return RCLUPP_OK;
 }

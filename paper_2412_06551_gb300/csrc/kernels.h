@@ -112,12 +112,15 @@ cudaError_t launch_cholesky_cluster(const double *G, int64_t ldg, int n, double 
                                     cudaStream_t stream);
 
 // ---- tensor-core sketch (tc_sketch.cu) ----
-// Y = S X with S's entries rounded to bf16 and X split into nterms (1 or 3)
-// bf16 terms, fp32 accumulation on tcgen05 (n <= 256).
+// Y = S X with S's entries bf16 levels of a discretised normal and X split
+// into nterms (1 or 3) bf16 terms, fp32 accumulation on tcgen05 (n <= 256).
 cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
                              int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
                              double *part, DevStatus *st, cudaStream_t stream, int64_t row0 = 0);
 size_t tc_sketch_smem_bytes(int n, int nterms);
+// The reduced tier's level table (bf16 levels of the discretised normal) on
+// the current device, written once per device; called at handle creation.
+cudaError_t ensure_sketch_levels();
 
 // ---- binary64-emulating Gram on the tensor cores (emu_gram.cu) ----
 // G = A^T A (n <= 256) from seven balanced base-256 digits of every element

@@ -6,8 +6,7 @@
 // precision.  Y = S X with S generated on the fly: each CTA owns one tile of
 // 128 sketch rows x NT columns of Y (M = 128, N = NT <= 256) and a contiguous
 // chunk of rows of X (split-K).  For every 32 rows of X the 256 threads
-//   * draw the 128 x 32 block of z (the same Philox4x32-10 / Box-Muller
-//     definition as the FP64 sketch) and round it to bf16,
+//   * draw the 128 x 32 block of S (bf16 levels, defined below),
 //   * load the 32 x NT block of X (binary64) and split each value into one
 //     or three bf16 terms x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2),
 //   * store both as K-major operand tiles (8 x 8 bf16 core matrices) in
@@ -18,9 +17,18 @@
 // end the fp32 accumulator is read from TMEM (tcgen05.ld), scaled by
 // 1/sqrt(s) in binary64 and written as this CTA's partial; partials are
 // summed in a fixed order by the same reduction as the FP64 sketch.
+//
+// S at this tier: since only an embedding is needed, its entries are bf16
+// levels of a discretised standard normal, T[j] = bf16(Phi^{-1}((j + 1/2) /
+// 4096)), drawn eight at a time: entry (r, i) = T[h >> 4] with h the 16-bit
+// half (i mod 8) mod 2 of word (i mod 8) div 2 of Philox4x32-10 at counter
+// (i div 8 mod 2^32, i div 2^35, r, 0x53424631), key = seed.  One Philox
+// block, eight table reads from shared memory and one 16-byte store give the
+// eight K-consecutive entries of one operand row.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -33,6 +41,12 @@ constexpr int kTcThreads = 256;
 constexpr int kTcBK = 32;      // rows of X per stage
 constexpr int kTcStages = 3;
 constexpr int kTcM = 128;      // sketch rows per CTA tile
+constexpr int kLevels = 4096;  // levels of the discretised normal
+constexpr uint32_t kLevelsDomain = 0x53424631u;
+
+// bf16 bits of T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)), written once per
+// device by k_gauss_levels_init (ensure_sketch_levels()).
+__device__ __align__(16) uint16_t g_gauss_levels[kLevels];
 
 // ---- bf16 rounding (nearest, ties to even) ----------------------------------
 
@@ -57,17 +71,49 @@ __device__ __forceinline__ uint16_t bf16_bits_from_f64(double x, double &rounded
     return static_cast<uint16_t>((sign << 15) | (static_cast<unsigned>(e) << 7) | frac);
 }
 
-// binary32 -> nearest bf16, ties to even (finite inputs).
-__device__ __forceinline__ uint16_t bf16_bits_from_f32(float z) {
-    const uint32_t b = __float_as_uint(z);
-    return static_cast<uint16_t>((b + 0x7fffu + ((b >> 16) & 1u)) >> 16);
-}
-
 // Byte offset of element (row, k) inside a K-major operand tile of BK
 // columns laid out as [row/8][k/8][row%8][k%8] (bf16).
 __device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
     return static_cast<uint32_t>(((row >> 3) * (kTcBK / 8) + (k >> 3)) * 128 + (row & 7) * 16 +
                                  (k & 7) * 2);
+}
+
+// T[j] from CUDA's normcdfinv in binary64, rounded to nearest bf16 (ties
+// to even).
+__global__ void k_gauss_levels_init() {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kLevels) return;
+    double rounded;
+    g_gauss_levels[j] = bf16_bits_from_f64(normcdfinv((double(j) + 0.5) / double(kLevels)), rounded);
+}
+
+// Eight entries (r, g0 .. g0 + 7) of the reduced tier's S as packed bf16;
+// `lv` is the level table in shared memory.  g0 need not be a multiple of 8.
+__device__ __forceinline__ uint4 sk_levels8(uint64_t seed, int r, int64_t g0, const uint16_t *lv) {
+    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    const uint64_t q = static_cast<uint64_t>(g0) >> 3;
+    const int off = static_cast<int>(g0 & 7);
+    const uint4 a = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                             static_cast<uint32_t>(r), kLevelsDomain), k0, k1);
+    uint32_t h[8];
+    if (off == 0) {  // one block: word t / 2, half t % 2
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) h[t] = lv[((w[t >> 1] >> (16 * (t & 1))) & 0xffffu) >> 4];
+    } else {  // entries off .. off + 7 of two consecutive blocks, selected without indexing
+        const uint64_t q1 = q + 1;
+        const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(q1), static_cast<uint32_t>(q1 >> 32),
+                                                 static_cast<uint32_t>(r), kLevelsDomain), k0, k1);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int e = off + t, k = (e >> 1) & 3;
+            const uint4 v = (e >> 3) ? b : a;
+            const uint32_t w = k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+            h[t] = lv[((w >> (16 * (e & 1))) & 0xffffu) >> 4];
+        }
+    }
+    return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                      h[6] | (h[7] << 16));
 }
 
 template <int NSL>
@@ -79,6 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __shared__ __align__(8) uint64_t bar_mma[kTcStages];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ __align__(16) uint16_t lv[kLevels];
 
     const int a_bytes = kTcM * kTcBK * 2;       // 8 KB
     const int b_bytes = nt * kTcBK * 2;         // per bf16 term of X
@@ -96,6 +143,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         fence_mbar_init();
         abort_flag = 0;
     }
+    for (int k = tid; k < kLevels / 8; k += kTcThreads)
+        reinterpret_cast<uint4 *>(lv)[k] = reinterpret_cast<const uint4 *>(g_gauss_levels)[k];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -140,23 +189,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 xv[tt][t] = x;
             }
         }
-        // (1) S block: entry (r, i) for 128 sketch rows x 32 rows of X; two
-        // tasks at a time, so that their dependent series chains interleave
+        // (1) S block: entries (r, i) for 128 sketch rows x 32 rows of X, one
+        // task per 8 K-consecutive entries of a row (X's rows past the end
+        // are zero, so those entries need no masking)
 #pragma unroll 2
-        for (int task = tid; task < (kTcM / 4) * kTcBK; task += kTcThreads) {
-            const int i = task % kTcBK, q = task / kTcBK;
-            const int64_t row = r0 + i;
-            uint16_t h[4] = {0, 0, 0, 0};
-            if (row < re) {
-                const float4 z = sk_gauss4(seed, row0 + row, (rt0 >> 2) + q);
-                h[0] = bf16_bits_from_f32(z.x);
-                h[1] = bf16_bits_from_f32(z.y);
-                h[2] = bf16_bits_from_f32(z.z);
-                h[3] = bf16_bits_from_f32(z.w);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                *reinterpret_cast<uint16_t *>(stage + kmajor_off(4 * q + j, i)) = h[j];
+        for (int task = tid; task < kTcM * (kTcBK / 8); task += kTcThreads) {
+            const int kb = task % (kTcBK / 8), r = task / (kTcBK / 8);
+            const uint4 v = sk_levels8(seed, rt0 + r, row0 + r0 + 8 * kb, lv);
+            *reinterpret_cast<uint4 *>(stage + kmajor_off(r, 8 * kb)) = v;
         }
         // (2) X block split into NSL bf16 terms: 8 consecutive rows of one column per task
 #pragma unroll
@@ -244,6 +284,29 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
 }  // namespace
 
+// Writes the level table of the reduced tier's S on the current device,
+// once per device, on a private stream, and waits for it.  Called when a
+// handle is created, so that no launch that reads the table (or a graph
+// captured later) can run before it is written.
+cudaError_t ensure_sketch_levels() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (done[dev]) return cudaSuccess;
+    cudaStream_t s = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    RQ_LAUNCH(KID_SKETCH_TC, s, k_gauss_levels_init<<<kLevels / 256, 256, 0, s>>>());
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 size_t tc_sketch_smem_bytes(int n, int nterms) {
     const int nt = std::min(pad16(n), 256);
     return size_t(kTcStages) * (size_t(kTcM) * kTcBK * 2 + size_t(nterms) * nt * kTcBK * 2);
@@ -262,7 +325,7 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
     // memory both fit, so that one CTA's generation of S covers the other's
     // load latency; each CTA's stages stay below half the SM's shared memory
     const size_t smem = tc_sketch_smem_bytes(n, nterms);
-    const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+    const int per_sm = smem <= 100 * 1024 ? 2 : 1;  // plus 8 KB of levels each
     int p = std::max(1, per_sm * grid_sms() / tiles);
     int64_t chunk = round_up(ceil_div(m, p), kTcBK);
     p = static_cast<int>(ceil_div(m, chunk));

@@ -1,12 +1,14 @@
 """Reduced-precision sketch tier (tensor cores) against the oracle.
 
-The tensor-core sketch computes Y = S_bf16 X_split / sqrt(s) with fp32 sums
-inside each CTA and binary64 sums across CTAs.  The oracle evaluates the same
-definition (bf16 rounding of z, one- or three-term bf16 split of X) in
-binary64; every product is exact in fp32, so the two differ only by the fp32
-summation: |Y_gpu - Y_ref| <= gamma32_m (|S_bf16| |X_split|) / sqrt(s) with
-gamma32_k = k 2^-24 / (1 - k 2^-24).  |S_bf16| <= (1 + 2^-8) |z| and
-|X_split| <= (1 + 2^-7) |X| bound the right-hand side from the binary64 S.
+The tensor-core sketch computes Y = z_b X_split / sqrt(s) with fp32 sums
+inside each CTA and binary64 sums across CTAs, z_b the bf16 levels of a
+discretised normal drawn by Philox.  The oracle evaluates the same
+definition (levels, one- or three-term bf16 split of X) in binary64; every
+product is exact in fp32, so the two differ only by the fp32 summation:
+|Y_gpu - Y_ref| <= gamma32_m (|z_b| |X_split|) / sqrt(s) with
+gamma32_k = k 2^-24 / (1 - k 2^-24), and |X_split| <= (1 + 2^-7) |X|.
+A sketch of unit columns has one product per entry, so it reproduces S
+itself bit for bit: that pins the device's level table and draw.
 
 The drivers must meet the same gates as the binary64 path against the
 binary64 oracle, reporting the tier that produced the result.
@@ -53,14 +55,37 @@ def test_tc_sketch_matches_definition(rq, prec, nterms, m, n, s):
     seed = 1234 + m
     y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=prec))
     ref = oracle.sketch_bf16(s, seed, nterms, x)
-    S = oracle.gaussian_sketch_matrix(s, m, seed)  # z / sqrt(s) in binary64
-    mag = (1 + 2.0 ** -8) * (1 + 2.0 ** -7) * (np.abs(S) @ np.abs(x))
+    S = oracle.bf16_sketch_z(s, m, seed) / np.sqrt(s)  # z_b / sqrt(s) in binary64
+    mag = (1 + 2.0 ** -7) * (np.abs(S) @ np.abs(x))
     assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
-    # and close to the binary64 sketch: S's bf16 rounding (2^-9 relative) plus
-    # X's (2^-9 for one term, 2^-23 for three) plus the fp32 sums
+    # and close to the same S times the unrounded X: X's rounding (2^-9 for
+    # one term, 2^-23 for three) plus the fp32 sums
     full = oracle.sketch_dense(S, x)
     rel = np.max(np.abs(y - full) / (mag + 1e-300))
-    assert rel <= 2.0 ** -9 + (2.0 ** -9 if nterms == 1 else 2.0 ** -23) + gamma32(m)
+    assert rel <= (2.0 ** -9 if nterms == 1 else 2.0 ** -23) + gamma32(m)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tc_sketch_of_unit_columns_is_s_itself(rq, prec):
+    # Y = S [e_0 .. e_255]: one product per entry, exact in fp32, so Y holds
+    # 512 x 256 entries of S bit for bit -- about 32 draws of each of the 4096
+    # levels, so the device's level table is compared in full
+    m, s, seed = 256, 512, 99
+    y = host(rq.rclupp_sketch(dev(np.eye(m)), s=s, seed=seed, prec=prec))
+    assert np.array_equal(y, oracle.sketch_bf16(s, seed, 1, np.eye(m)))
+    levels = np.unique(np.abs(y * np.sqrt(s)))
+    assert len(levels) >= 1900  # of the 2048 magnitudes
+
+
+@pytest.mark.parametrize("row0", [0, 3, 8, 13])
+def test_tc_sketch_row_block_draws_the_global_entries(rq, row0):
+    # a row block starting at global row row0 (not necessarily a multiple of
+    # the 8 entries one Philox block gives) uses the entries (r, row0 + i)
+    m, n, s, seed = 300, 5, 64, 17
+    x = synth.integer_matrix(m, n, row0 + 1)
+    y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=1, row0=row0))
+    z = oracle.bf16_sketch_z(s, row0 + m, seed)[:, row0:]
+    assert np.array_equal(y, (z @ x) * (1.0 / np.sqrt(s)))
 
 
 def test_tc_sketch_unit_lower(rq):
@@ -70,7 +95,7 @@ def test_tc_sketch_unit_lower(rq):
     M = oracle.unit_lower(lu)
     y = host(rq.rclupp_sketch(dev(lu), s=s, seed=4, prec=2, unit_lower=True))
     ref = oracle.sketch_bf16(s, 4, 3, M)
-    S = oracle.gaussian_sketch_matrix(s, m, 4)
+    S = oracle.bf16_sketch_z(s, m, 4) / np.sqrt(s)
     mag = 1.02 * (np.abs(S) @ np.abs(M))
     assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
 
