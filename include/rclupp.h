@@ -444,6 +444,32 @@ rclupp_status_t rclupp_givens_r(rclupp_handle_t handle, int64_t s, int64_t n, co
 rclupp_status_t rclupp_householder_r(rclupp_handle_t handle, int64_t s, int64_t n,
                                      const double *A, int64_t lda, double *R, int64_t ldr);
 
+/* ---- bounded waits and fault injection (no counterpart in the paper) -----
+ * The tall LU (rclupp_r_factor, lc2_factor, rclupp_tall_lupp) runs each
+ * panel's column steps in one cooperative launch whose CTAs meet at a
+ * grid-wide barrier after every pivot selection; each wait there is bounded
+ * and, when it runs out, the call returns RCLUPP_ERR_TIMEOUT (failed_step 2,
+ * info / *col = the column whose pivot was being waited for) with the handle
+ * still usable.  Under stream capture (and where the device refuses the
+ * cooperative launch) every column step is its own launch and no device
+ * wait exists.  These two calls let a caller (or a test of the failure path)
+ * bound and exercise that wait. */
+
+/* Limit of each grid-barrier wait of the handle's tall LUs, in nanoseconds of
+ * %globaltimer time; 0 restores the default of 2 s.  Errors: ERR_ARG. */
+rclupp_status_t rclupp_set_wait_limit(rclupp_handle_t handle, uint64_t limit_ns);
+
+typedef enum {
+    RCLUPP_FAULT_NONE = 0,             /* clear a pending injection */
+    RCLUPP_FAULT_LU_BARRIER_STALL = 1  /* the next tall LU's first grid barrier expects one
+                                          arrival more than its grid has, so its wait runs
+                                          out (no device memory is touched wrongly) */
+} rclupp_fault_t;
+
+/* Arm (or clear) a one-shot fault for the handle's next tall LU; the call
+ * that runs it consumes it.  Errors: ERR_ARG (unknown fault). */
+rclupp_status_t rclupp_inject_fault(rclupp_handle_t handle, int32_t fault);
+
 /* ---- allocation-free Gram (no counterpart in the paper) ------------------
  * G = A^T A (n x n, ldg >= n, both triangles), the same kernels as
  * rclupp_gram, for callers that cannot let a library allocate device memory:

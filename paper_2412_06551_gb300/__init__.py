@@ -125,6 +125,8 @@ _SIGNATURES = {
     "rclupp_profile_get": ([ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)], _I32),
     "rclupp_kernel_launches": ([], ctypes.c_ulonglong),
+    "rclupp_set_wait_limit": ([_P, ctypes.c_uint64], _I32),
+    "rclupp_inject_fault": ([_P, _I32], _I32),
     "rclupp_profile_fp64_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], _I32),
 }

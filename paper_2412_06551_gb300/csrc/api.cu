@@ -38,6 +38,10 @@ struct rclupp_handle_s {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<unsigned char> graph_desc;  // description the cached graph was captured for
     unsigned long long graph_kernels = 0;
+    // bounded waits of the tall LU's grid-wide barrier: limit (0 = default)
+    // and the one-shot stall a test injects (rclupp_inject_fault)
+    uint64_t lu_wait_limit_ns = 0;
+    int lu_stall = 0;
 };
 
 namespace {
@@ -327,6 +331,15 @@ struct Ctx {
     DevStatus *st;
 };
 
+// The tall LU's wait options of a single call; consumes the one-shot stall.
+LuWaitOptions take_lu_wait(rclupp_handle_t h) {
+    LuWaitOptions w;
+    w.limit_ns = h->lu_wait_limit_ns;
+    w.stall = h->lu_stall;
+    h->lu_stall = 0;
+    return w;
+}
+
 Ctx ctx_of(rclupp_handle_t h) { return Ctx{h->stream, h->d_status}; }
 
 // The CholeskyQR2 stage of Algorithms 6 and 7 (C1-C8): Q1 = X R1^{-1} with R1 in
@@ -528,11 +541,11 @@ rclupp_status_t enqueue_scholqr3(Ctx c, const Bufs &b, int64_t m, int n, const d
 // LC2, Algorithm 4; the LU runs in L (ldl).
 rclupp_status_t enqueue_lc2(Ctx c, const Bufs &b, int64_t m, int n, const double *X, int64_t ldx,
                             double *L, int64_t ldl, double *Q, int64_t ldq, double *R,
-                            int64_t ldr) {
+                            int64_t ldr, const LuWaitOptions *wopt = nullptr) {
     const int np = pad16(n);
     RQ_TRY(copy_matrix(L, ldl, X, ldx, m, n, c.s));
     // [M, N, P] = LU(X)
-    RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s));
+    RQ_TRY(launch_tall_lupp(L, ldl, m, n, b.ipiv, b.lu, c.st, 2, c.s, wopt));
     // G = M^T M; S = chol(G); R1 = S N
     RQ_TRY(launch_gram(L, ldl, m, n, 1, b.G, n, b.part, c.st, c.s));
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[4], b.rinv[4], nullptr, 0, c.st, 3, c.s));
@@ -697,10 +710,11 @@ rclupp_status_t rclupp_r_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
     const int64_t ldl = own_lu ? m : ldq;
     rclupp_status_t ls = RCLUPP_OK;
     int tier = o.prec;
+    const LuWaitOptions w = take_lu_wait(h);
     do {
         if (copy_matrix(L, ldl, X, ldx, m, n, s) != cudaSuccess) { ls = RCLUPP_ERR_CUDA; break; }
         // [M, N, P] = LU(X) (Algorithm 7)
-        if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s) != cudaSuccess) {
+        if (launch_tall_lupp(L, ldl, m, ni, b.ipiv, b.lu, ds, 2, s, &w) != cudaSuccess) {
             ls = RCLUPP_ERR_CUDA; break; }
         // M_s = S M; R0 = R of HouseholderQR(M_s); R1 = R0 N; then CholeskyQR2
         // of Q1 = X R1^{-1}.  Q1 overwrites the LU only after M_s is formed.
@@ -737,7 +751,8 @@ rclupp_status_t lc2_factor(rclupp_handle_t h, int64_t m, int64_t n, const double
     if (st != RCLUPP_OK) return st;
     double *L = alias ? b.LUbuf : Q;
     const int64_t ldl = alias ? m : ldq;
-    return finish(h, enqueue_lc2(ctx_of(h), b, m, int(n), X, ldx, L, ldl, Q, ldq, R, ldr), info,
+    const LuWaitOptions w = take_lu_wait(h);
+    return finish(h, enqueue_lc2(ctx_of(h), b, m, int(n), X, ldx, L, ldl, Q, ldq, R, ldr, &w), info,
                   nullptr);
 }
 
@@ -1122,8 +1137,21 @@ rclupp_status_t rclupp_tall_lupp(rclupp_handle_t h, int64_t m, int64_t n, double
     rclupp_status_t st;
     Bufs b = prepare(h, m, int(n), n, false, &st);
     if (st != RCLUPP_OK) return st;
-    const cudaError_t e = launch_tall_lupp(A, lda, m, int(n), ipiv, b.lu, h->d_status, 2, h->stream);
+    const LuWaitOptions w = take_lu_wait(h);
+    const cudaError_t e = launch_tall_lupp(A, lda, m, int(n), ipiv, b.lu, h->d_status, 2, h->stream, &w);
     return finish(h, from_cuda(e), nullptr, col);
+}
+
+rclupp_status_t rclupp_set_wait_limit(rclupp_handle_t h, uint64_t limit_ns) {
+    if (!h) return RCLUPP_ERR_ARG;
+    h->lu_wait_limit_ns = limit_ns;
+    return RCLUPP_OK;
+}
+
+rclupp_status_t rclupp_inject_fault(rclupp_handle_t h, int32_t fault) {
+    if (!h || (fault != RCLUPP_FAULT_NONE && fault != RCLUPP_FAULT_LU_BARRIER_STALL)) return RCLUPP_ERR_ARG;
+    h->lu_stall = fault == RCLUPP_FAULT_LU_BARRIER_STALL ? 1 : 0;
+    return RCLUPP_OK;
 }
 
 rclupp_status_t rclupp_sketch_precond(rclupp_handle_t h, int64_t s, int64_t n, const double *Y,

@@ -153,9 +153,18 @@ cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, do
 
 
 // ---- tall LU with partial pivoting (lu.cu) ----
+// Bounded-wait options of the panel launches: limit_ns (0 = the default
+// limit) for each wait at the grid-wide barrier; stall = 1 makes the first
+// barrier of the first panel launch expect one arrival more than the grid has,
+// so that its wait runs out (fault injection for tests).
+struct LuWaitOptions {
+    uint64_t limit_ns = 0;
+    int stall = 0;
+};
 size_t lu_scratch_bytes(int64_t m, int n);
 cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *ipiv,
-                             void *scratch, DevStatus *st, int step_id, cudaStream_t stream);
+                             void *scratch, DevStatus *st, int step_id, cudaStream_t stream,
+                             const LuWaitOptions *wopt = nullptr);
 
 // ---- small dense factorizations on one CTA (small.cu) ----
 // R1 from the sketch Y (s x n): LU with partial pivoting, Householder R of

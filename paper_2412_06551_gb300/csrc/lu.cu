@@ -11,9 +11,17 @@
 //     panel's first column.
 // The global pivot of each column is chosen by the last CTA to finish
 // (atomic ticket, no waiting): it combines the per-CTA candidates, records
-// ipiv, and swaps the two rows across all n columns before the next launch.
+// ipiv, and swaps the two rows across all n columns.
 // Updates subtract in increasing elimination index, the order of the
 // unblocked algorithm.  Selection is exact, so pivots are deterministic.
+//
+// A panel's column steps run in one cooperative launch (k_lu_panel): after
+// each pivot selection every CTA waits at a grid-wide barrier, so that the
+// swapped rows are in place before the next column; the barrier's wait is
+// bounded (the kernel reports a timeout and returns) and it reads rows that
+// other CTAs may have swapped through L2.  Where a cooperative launch is not
+// possible (stream capture, or the launch is refused) each column step is a
+// launch of its own (k_lu_col) and the launch boundary is the barrier.
 #include <algorithm>
 
 #include "common.cuh"
@@ -175,6 +183,115 @@ __global__ void __launch_bounds__(kLuThreads, 2)
     finish_pivot(mine, cands, ticket, A, lda, n, k + 1, ipiv, st, step);
 }
 
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Thread 0
+// of each CTA reads the generation, arrives on `count`, and waits until the
+// generation moves on; the last of `expected` arrivals resets `count` and
+// advances the generation.  Every wait gives up after limit_ns of
+// %globaltimer time; the return value (the same in all threads of the CTA)
+// says whether the barrier completed.  With expected > gridDim.x the barrier
+// cannot complete (fault injection for tests).
+__device__ bool grid_barrier_bounded(unsigned *count, unsigned *gen, unsigned expected,
+                                     uint64_t limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = atomicAdd(gen, 0u);
+        __threadfence();  // this CTA's writes before its arrival
+        if (atomicAdd(count, 1u) == expected - 1u) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 1; atomicAdd(gen, 0u) == g; ++it) {
+                __nanosleep(64);
+                if ((it & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// All column steps k0 .. pe-1 of one panel in a cooperative launch.  Column
+// k's pivot row is in place on entry (for k0: the previous trailing update
+// chose it; later columns: the previous iteration).  Per column every CTA
+// scales column k below the diagonal in its rows, updates the panel's
+// remaining columns and proposes its candidate for column k+1; the last CTA
+// to take a ticket picks the pivot, records it and swaps the two rows across
+// all n columns; then the grid waits at the bounded barrier.  Loads of A go
+// through L2 (__ldcg): a swap by another CTA in this launch is not in this
+// SM's L1.  `stall` makes the first barrier expect one arrival too many.
+__global__ void __launch_bounds__(kLuThreads, 2)
+    k_lu_panel(double *A, int64_t lda, int64_t m, int n, int k0, int pe, int64_t chunk,
+               ArgCand *cands, unsigned *ticket, unsigned *bar_count, unsigned *bar_gen,
+               int32_t *ipiv, DevStatus *st, int step, uint64_t limit_ns, int stall) {
+    constexpr int NC = kLuNB - 1;
+    __shared__ double urow[kLuNB];
+    // after a failure earlier in this factorization (a timed-out barrier
+    // leaves the barrier's counters behind) the remaining panels do nothing
+    if (*reinterpret_cast<volatile int *>(&st->code) != 0) return;
+    const int64_t rb = k0 + 1 + int64_t(blockIdx.x) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    for (int k = k0; k < pe; ++k) {
+        const int ncol = pe - k - 1;  // panel columns right of k
+        if (threadIdx.x < ncol) urow[threadIdx.x] = __ldcg(A + k + int64_t(k + 1 + threadIdx.x) * lda);
+        __syncthreads();
+        const double rcp = 1.0 / __ldcg(A + k + int64_t(k) * lda);
+        double u[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) u[c] = (c < ncol) ? urow[c] : 0.0;
+        double bv = -1.0;
+        long long bi = 0x7fffffffffffffffll;
+        double *colk = A + int64_t(k) * lda;
+        double *col1 = A + int64_t(k + 1) * lda;
+        const int64_t r0 = std::max<int64_t>(rb, k + 1);
+        for (int64_t i0 = r0 + threadIdx.x; i0 < re; i0 += int64_t(kLuThreads) * kColRows) {
+            double l[kColRows], a[kColRows][NC];
+#pragma unroll
+            for (int r = 0; r < kColRows; ++r) {
+                const int64_t i = i0 + int64_t(r) * kLuThreads;
+                const bool in = i < re;
+                l[r] = in ? __ldcg(colk + i) : 0.0;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    a[r][c] = (in && c < ncol) ? __ldcg(col1 + i + int64_t(c) * lda) : 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < kColRows; ++r) {
+                const int64_t i = i0 + int64_t(r) * kLuThreads;
+                if (i >= re) break;
+                const double li = l[r] * rcp;
+                colk[i] = li;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c >= ncol) break;
+                    const double v = fma(-li, u[c], a[r][c]);
+                    col1[i + int64_t(c) * lda] = v;
+                    if (c == 0 && cand_better(fabs(v), i, bv, bi)) {
+                        bv = fabs(v);
+                        bi = i;
+                    }
+                }
+            }
+        }
+        if (k + 1 >= pe) break;  // the next panel's first pivot: the trailing update
+        __threadfence();  // this thread's updates before the CTA's ticket
+        const ArgCand mine = block_argmax(bv, bi);
+        finish_pivot(mine, cands, ticket, A, lda, n, k + 1, ipiv, st, step);
+        const unsigned expected = gridDim.x + ((stall && k == k0) ? 1u : 0u);
+        if (!grid_barrier_bounded(bar_count, bar_gen, expected, limit_ns)) {
+            if (threadIdx.x == 0) report(st, kErrTimeout, step, k + 1);
+            return;
+        }
+    }
+}
+
 // U12 = L11^{-1} A12: rows k0 .. pe-1, columns pe .. n-1 (one CTA).
 __global__ void __launch_bounds__(kLuThreads)
     k_lu_u12(double *A, int64_t lda, int n, int k0, int pe) {
@@ -238,6 +355,8 @@ constexpr int kMaxCtasPerSm = 6;
 
 static size_t cand_slots() { return size_t(kMaxCtasPerSm) * num_sms() + 8; }
 
+// Scratch: the candidates, then three counters (ticket, barrier arrivals,
+// barrier generation), zeroed at the start of every factorization.
 size_t lu_scratch_bytes(int64_t m, int n) {
     (void)m;
     (void)n;
@@ -252,13 +371,39 @@ static int lu_grid(int64_t rows, int64_t &chunk, int per_sm) {
     return static_cast<int>(g);
 }
 
+// CTAs of a panel launch: co-resident (cooperative), at most two per SM, and
+// about two row blocks of the column-step size per CTA.
+static int panel_grid(int64_t rows, int64_t &chunk) {
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (per_sm[dev] == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lu_panel, kLuThreads, 0) != cudaSuccess)
+            nb = 1;
+        per_sm[dev] = std::max(1, std::min(nb, kColCtasPerSm));
+    }
+    return lu_grid(rows, chunk, per_sm[dev]);
+}
+
+static bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *ipiv,
-                             void *scratch, DevStatus *st, int step_id, cudaStream_t stream) {
+                             void *scratch, DevStatus *st, int step_id, cudaStream_t stream,
+                             const LuWaitOptions *wopt) {
     ArgCand *cands = reinterpret_cast<ArgCand *>(scratch);
     unsigned *ticket =
         reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + cand_slots() * sizeof(ArgCand));
-    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream);
+    unsigned *bar_count = ticket + 1, *bar_gen = ticket + 2;
+    cudaError_t e = cudaMemsetAsync(ticket, 0, 3 * sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
+    const uint64_t limit_ns = wopt && wopt->limit_ns ? wopt->limit_ns : kWaitLimitNs;
+    int stall = wopt ? wopt->stall : 0;
+    bool coop = !stream_capturing(stream);
     const size_t smax = size_t(kLuNB) * n * sizeof(double);
     cudaFuncSetAttribute(k_lu_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax));
     int64_t chunk;
@@ -268,7 +413,28 @@ cudaError_t launch_tall_lupp(double *A, int64_t lda, int64_t m, int n, int32_t *
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int k0 = 0; k0 < n; k0 += kLuNB) {
         const int pe = std::min(n, k0 + kLuNB);
-        for (int k = k0; k < pe; ++k) {
+        bool done = false;
+        if (coop && m - k0 - 1 > 0) {
+            int64_t pchunk;
+            const int pg = panel_grid(m - k0 - 1, pchunk);
+            int k0v = k0, pev = pe, stallv = stall;
+            int64_t mv = m, ldav = lda;
+            int nv = n, stepv = step_id;
+            uint64_t limv = limit_ns;
+            void *args[] = {&A, &ldav, &mv, &nv, &k0v, &pev, &pchunk, &cands, &ticket, &bar_count,
+                            &bar_gen, &ipiv, &st, &stepv, &limv, &stallv};
+            RQ_LAUNCH(KID_LU_COL, stream,
+                      e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_lu_panel), pg,
+                                                      kLuThreads, args, 0, stream));
+            if (e == cudaSuccess) {
+                done = true;
+                stall = 0;
+            } else {
+                cudaGetLastError();  // refused (e.g. too large): column launches from here on
+                coop = false;
+            }
+        }
+        for (int k = k0; k < pe && !done; ++k) {
             const int64_t rows = m - k - 1;
             if (rows <= 0) break;
             g = lu_grid(rows, chunk, kColCtasPerSm);

@@ -160,46 +160,75 @@ __device__ __forceinline__ bool check_abort(int *abort_flag, bool ok, DevStatus 
 // --------------------------------------------------- Gram accumulation ---
 
 // Warp tiles of a 16-aligned output block (rows jn = 16*ntj, cols 16*ntk).
-// diag: only tiles (a, b) with a <= b.  Warp w takes tiles w, w+8, w+16...
-// Lane (a, b) = (lane / 4, lane % 4) owns rows 2a, 2a+1 and cols 4b..4b+3.
-// Coordinates (a, b) of the t-th warp tile in row-major order over a grid of
-// ntj x ntk tiles (upper triangle a <= b only, when diag).  False if t is
-// past the last tile.
+// Lane (a, b) = (lane / 4, lane % 4) of a full tile owns rows 2a, 2a+1 and
+// cols 4b..4b+3.  In a diagonal block (diag) warp w < ntj owns the diagonal
+// tile (w, w) and the tiles (a, b) with a < b go round-robin to warps
+// (t + ntj) mod 8; otherwise all ntj x ntk tiles go to warps t mod 8.
+// Coordinates (a, b) of the t-th of those tiles in row-major order (strict
+// upper triangle when diag).  False if t is past the last tile.
 __device__ __forceinline__ bool warp_tile_coords(int t, int ntj, int ntk, bool diag, int &a,
                                                  int &b) {
     a = 0;
     b = 0;
     int cnt = 0;
     for (int aa = 0; aa < ntj; ++aa) {
-        const int len = diag ? (ntk - aa) : ntk;
-        if (t < cnt + len) {
+        const int len = diag ? (ntk - aa - 1) : ntk;
+        if (len > 0 && t < cnt + len) {
             a = aa;
-            b = (diag ? aa : 0) + (t - cnt);
+            b = (diag ? aa + 1 : 0) + (t - cnt);
             return true;
         }
-        cnt += len;
+        cnt += max(len, 0);
     }
     return false;
 }
 
-template <int MAXW>
-struct GramAcc {
-    double acc[MAXW][8];
-    int tj[MAXW], tk[MAXW];
-    int nw;
+// A diagonal warp tile needs only its upper triangle: its 136 entries
+// (r <= c, row-major) go to lane e % 32, slot e / 32, i.e. five FMAs per row
+// instead of the eight of a full tile (lanes 8..31 idle in slot 4).  Each
+// entry still sums its rows in order, so the values are those of a full tile.
+constexpr int kDiagSlots = 5;
 
-    __device__ __forceinline__ void init(int ntj, int ntk, bool diag) {
-        const int warp = threadIdx.x >> 5;
+// NOFF full (off-diagonal) tiles per warp; DIAG: the block is a diagonal
+// block and warps w < ntj also own the diagonal tile (w, w).
+template <int NOFF, bool DIAG>
+struct GramAcc {
+    double acc[NOFF][8];
+    double dacc[DIAG ? kDiagSlots : 1];
+    int tj[NOFF], tk[NOFF];
+    int drc[DIAG ? kDiagSlots : 1];  // this lane's diagonal-tile entry per slot: (r << 4) | c, or -1
+    int nw;
+    int dtile;  // the warp's diagonal tile, or -1
+
+    __device__ __forceinline__ void init(int ntj, int ntk) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int shift = DIAG ? ntj : 0;
         nw = 0;
 #pragma unroll
-        for (int w = 0; w < MAXW; ++w) {
+        for (int w = 0; w < NOFF; ++w) {
             int a, b;
-            if (warp_tile_coords(warp + 8 * w, ntj, ntk, diag, a, b)) nw = w + 1;
+            // tiles t with (t + shift) mod 8 == warp
+            const int t = ((warp - shift) % 8 + 8) % 8 + 8 * w;
+            if (warp_tile_coords(t, ntj, ntk, DIAG, a, b)) nw = w + 1;
             tj[w] = a;
             tk[w] = b;
         }
+        dtile = (DIAG && warp < ntj) ? warp : -1;
 #pragma unroll
-        for (int w = 0; w < MAXW; ++w)
+        for (int q = 0; q < (DIAG ? kDiagSlots : 1); ++q) {
+            int e = lane + 32 * q, r = 0;
+            drc[q] = -1;
+            if (DIAG && e < 136) {
+                while (e >= 16 - r) {
+                    e -= 16 - r;
+                    ++r;
+                }
+                drc[q] = (r << 4) | (r + e);
+            }
+            dacc[q] = 0.0;
+        }
+#pragma unroll
+        for (int w = 0; w < NOFF; ++w)
 #pragma unroll
             for (int e = 0; e < 8; ++e) acc[w][e] = 0.0;
     }
@@ -211,8 +240,18 @@ struct GramAcc {
         const int lane = threadIdx.x & 31;
         const int a = lane >> 2, b = lane & 3;
         for (int i = 0; i < rows; ++i) {
+            if (DIAG && dtile >= 0) {
 #pragma unroll
-            for (int w = 0; w < MAXW; ++w) {
+                for (int q = 0; q < (DIAG ? kDiagSlots : 1); ++q) {
+                    if (drc[q] >= 0) {
+                        const double x = TJ[(dtile * 16 + (drc[q] >> 4)) * BM + i];
+                        const double y = TK[(dtile * 16 + (drc[q] & 15)) * BM + i];
+                        dacc[q] = fma(x, y, dacc[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < NOFF; ++w) {
                 if (w < nw) {
                     const double *pj = TJ + (tj[w] * 16 + 2 * a) * BM + i;
                     const double *pk = TK + (tk[w] * 16 + 4 * b) * BM + i;
@@ -231,12 +270,23 @@ struct GramAcc {
         }
     }
 
-    // Store the block partial (128 x 128 column-major slot) to part.
+    // Store the block partial (128 x 128 column-major slot) to part; a
+    // diagonal tile stores its upper triangle (the reduction reads j <= k).
     __device__ __forceinline__ void store(double *part) const {
         const int lane = threadIdx.x & 31;
         const int a = lane >> 2, b = lane & 3;
+        if (DIAG && dtile >= 0) {
 #pragma unroll
-        for (int w = 0; w < MAXW; ++w) {
+            for (int q = 0; q < (DIAG ? kDiagSlots : 1); ++q) {
+                if (drc[q] >= 0) {
+                    const int j = dtile * 16 + (drc[q] >> 4);
+                    const int k = dtile * 16 + (drc[q] & 15);
+                    part[k * 128 + j] = dacc[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < NOFF; ++w) {
             if (w < nw) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -272,8 +322,12 @@ __global__ void __launch_bounds__(kThreads, (MAXW > 5 ? 1 : 2))
         if (use_tma) prefetch_tensormap(&map);
     }
     __syncthreads();
-    GramAcc<MAXW> g;
-    g.init(nj / 16, nk / 16, diag != 0);
+    // MAXW warp tiles per warp: <BM, 5> serves diagonal blocks (one diagonal
+    // tile and up to four full tiles per warp), <32, 8> the off-diagonal
+    // block (eight full tiles per warp)
+    constexpr bool kDiagBlock = MAXW <= 5;
+    GramAcc<kDiagBlock ? MAXW - 1 : MAXW, kDiagBlock> g;
+    g.init(nj / 16, nk / 16);
     uint32_t phase = 0;
     const int64_t rb = int64_t(blockIdx.x) * chunk;
     const int64_t re = std::min<int64_t>(m, rb + chunk);
@@ -472,8 +526,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (use_tma) prefetch_tensormap(&map);
     }
     __syncthreads();
-    GramAcc<kGram ? (BM == 128 ? 2 : 5) : 1> g;
-    if (kGram) g.init(n_pad / 16, n_pad / 16, true);
+    GramAcc<kGram ? (BM == 128 ? 1 : 4) : 1, kGram> g;
+    if (kGram) g.init(n_pad / 16, n_pad / 16);
     uint32_t phase = 0;
     const int tid = threadIdx.x;
     const int p = tid % P, ti = tid / P;
