@@ -91,8 +91,9 @@ def _load():
                 "orc_round_bf16": ([ctypes.c_double], ctypes.c_double),
                 "orc_sketch_bf16": ([I64, I64, I64, U64, I32, P, I64, P, I64], I32),
                 "orc_normal_quantile": ([ctypes.c_double], ctypes.c_double),
-                "orc_bf16_gauss_table": ([P], None),
-                "orc_bf16_sketch_entries": ([I64, I64, U64, P, I64], I32),
+                "orc_tier_levels": ([P], None),
+                "orc_tier_sketch_entries": ([I64, I64, U64, P, I64], I32),
+                "orc_sketch_digits": ([I64, I64, I64, U64, P, I64, P, I64], I32),
                 "orc_srht_perm_one": ([I32, U64, I64], I64),
                 "orc_srht_perm": ([I32, I64, U64, P], None),
                 "orc_srht_signs": ([U64, I64, I64, P], None),
@@ -463,26 +464,38 @@ def normal_quantile(p: float) -> float:
     return float(_load().orc_normal_quantile(float(p)))
 
 
-def bf16_gauss_table() -> np.ndarray:
-    """The reduced tier's 4096 levels T[j] = bf16(Phi^{-1}((j + 1/2) / 4096))."""
+def tier_levels() -> np.ndarray:
+    """The tensor-core tiers' 4096 levels T[j] = round(32 Phi^{-1}((j + 1/2) / 4096)) / 32."""
     t = np.zeros(4096)
-    _load().orc_bf16_gauss_table(_p(t))
+    _load().orc_tier_levels(_p(t))
     return t
 
 
-def bf16_sketch_z(s: int, m: int, seed: int) -> np.ndarray:
-    """Unscaled reduced-tier sketch z_b (s x m); the sketch is z_b / sqrt(s)."""
+def tier_sketch_z(s: int, m: int, seed: int) -> np.ndarray:
+    """Unscaled sketch z_b of the tensor-core tiers (s x m); the sketch is z_b / sqrt(s)."""
     z = np.zeros((s, m), order="F")
-    st = _load().orc_bf16_sketch_entries(s, m, seed, _p(z), s)
+    st = _load().orc_tier_sketch_entries(s, m, seed, _p(z), s)
     if st != OK:
         raise OracleError(st, -1)
     return z
 
 
+def sketch_digits(s: int, seed: int, x) -> np.ndarray:
+    """Y = z_b X~ / sqrt(s) with X~ the six-digit (48-bit, per-column exponent)
+    rounding of X, the integer sum taken exactly: the digit tier's definition."""
+    x = _f(x)
+    m, n = x.shape
+    y = np.zeros((s, n), order="F")
+    st = _load().orc_sketch_digits(s, m, n, seed, _p(x), m, _p(y), s)
+    if st != OK:
+        raise OracleError(st, -1)
+    return y
+
+
 def sketch_bf16(s: int, seed: int, nterms: int, x) -> np.ndarray:
     """Y = z_b X_split / sqrt(s): the tensor-core tier's sketch definition
-    (S entries z_b(r, i) from the discretised normal, bf16; X in one or three
-    bf16 terms)."""
+    (S entries z_b(r, i) on the grid of the discretised normal; X in one or
+    three bf16 terms)."""
     x = _f(x)
     m, n = x.shape
     y = np.zeros((s, n), order="F")

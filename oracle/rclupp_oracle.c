@@ -997,11 +997,13 @@ double orc_round_bf16(double x)
     return y;
 }
 
-/* The reduced tier's S is not the binary64 tier's S rounded: since only an
- * embedding is needed, its entries come from a 4096-level quantile
- * discretisation of the standard normal, rounded to bf16,
- *   T[j] = bf16( Phi^{-1}((j + 1/2) / 4096) ),  j = 0 .. 4095,
- * and entry (r, i) of the unscaled sketch is
+/* The tensor-core tiers' S is not the binary64 tier's S rounded: since only
+ * an embedding is needed, its entries lie on the grid k / 32 of a 4096-level
+ * quantile discretisation of the standard normal,
+ *   T[j] = k_j / 32,  k_j = round(32 Phi^{-1}((j + 1/2) / 4096))  (|k_j| <= 117),
+ * rounded half to even (zero as +0), so every entry is an integer k over 32 (an exact
+ * bf16, and an exact digit of the integer products of the digit tier), and
+ * entry (r, i) of the unscaled sketch is
  *   z_b(r, i) = T[ h >> 4 ],  h = bits 16 (t mod 2) .. 16 (t mod 2) + 15 of
  *   word w_{t div 2} of Philox4x32-10 with counter (q mod 2^32, q div 2^32,
  *   r, 0x53424631) and key = seed, where q = i div 8 and t = i mod 8
@@ -1029,15 +1031,15 @@ double orc_normal_quantile(double p)
     return hi;
 }
 
-/* T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)), j = 0 .. 4095. */
-void orc_bf16_gauss_table(double *T)
+/* T[j] = k_j / 32, k_j = round(32 Phi^{-1}((j + 1/2) / 4096)), j = 0 .. 4095. */
+void orc_tier_levels(double *T)
 {
     for (int j = 0; j < 4096; ++j)
-        T[j] = orc_round_bf16(orc_normal_quantile(((double)j + 0.5) / 4096.0));
+        T[j] = nearbyint(32.0 * orc_normal_quantile(((double)j + 0.5) / 4096.0)) / 32.0 + 0.0;
 }
 
-/* z_b(r, i) of the reduced tier, given the table T. */
-static double orc_bf16_gauss_entry_t(uint64_t seed, int64_t r, int64_t i, const double *T)
+/* z_b(r, i) of the tensor-core tiers, given the table T. */
+static double orc_tier_entry_t(uint64_t seed, int64_t r, int64_t i, const double *T)
 {
     const uint64_t q = (uint64_t)i >> 3;
     const int t = (int)(i & 7);
@@ -1049,17 +1051,17 @@ static double orc_bf16_gauss_entry_t(uint64_t seed, int64_t r, int64_t i, const 
     return T[h >> 4];
 }
 
-/* Unscaled reduced-tier sketch z_b (s x m, leading dimension ldz). */
-int orc_bf16_sketch_entries(int64_t s, int64_t m, uint64_t seed, double *Z, int64_t ldz)
+/* Unscaled sketch z_b of the tensor-core tiers (s x m, leading dimension ldz). */
+int orc_tier_sketch_entries(int64_t s, int64_t m, uint64_t seed, double *Z, int64_t ldz)
 {
     double *T = (double *)malloc(sizeof(double) * 4096);
     if (!T)
         return ORC_ERR_NOMEM;
-    orc_bf16_gauss_table(T);
+    orc_tier_levels(T);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i)
         for (int64_t r = 0; r < s; ++r)
-            IDX(Z, ldz, r, i) = orc_bf16_gauss_entry_t(seed, r, i, T);
+            IDX(Z, ldz, r, i) = orc_tier_entry_t(seed, r, i, T);
     free(T);
     return ORC_OK;
 }
@@ -1072,7 +1074,7 @@ int orc_sketch_bf16(int64_t s, int64_t m, int64_t n, uint64_t seed, int nterms, 
 {
     double *Sb = (double *)malloc(sizeof(double) * (size_t)s * (size_t)m);
     double *Xs = (double *)malloc(sizeof(double) * (size_t)m * (size_t)n);
-    if (!Sb || !Xs || orc_bf16_sketch_entries(s, m, seed, Sb, s) != ORC_OK) {
+    if (!Sb || !Xs || orc_tier_sketch_entries(s, m, seed, Sb, s) != ORC_OK) {
         free(Sb);
         free(Xs);
         return ORC_ERR_NOMEM;
@@ -1100,6 +1102,57 @@ int orc_sketch_bf16(int64_t s, int64_t m, int64_t n, uint64_t seed, int nterms, 
             IDX(Y, ldy, r, j) *= scale;
     free(Xs);
     free(Sb);
+    return ORC_OK;
+}
+
+/* The digit tier: X in six balanced base-256 digits per column and exact
+ * integer sums.  Column j's exponent E_j = b_j - 1022 with b_j the largest
+ * biased binary64 exponent field of the column (so 2^E_j > |x_ij|; b_j = 0
+ * for a column of zeros and subnormals), every x_ij is rounded to
+ *   F_ij = round(x_ij 2^(47 - E_j))   (half away from zero; |F_ij| < 2^47,
+ *                                      x_ij = F_ij 2^(E_j - 47) up to 2^(E_j - 48)),
+ * and Y(r, j) = (sum_i k(r, i) F_ij) 2^(E_j - 52) / sqrt(s), k = 32 z_b, the
+ * integer sum taken exactly (128-bit) and rounded once to binary64.  A column
+ * holding a NaN or an infinity gives a NaN column. */
+int orc_sketch_digits(int64_t s, int64_t m, int64_t n, uint64_t seed, const double *X, int64_t ldx,
+                      double *Y, int64_t ldy)
+{
+    double *Z = (double *)malloc(sizeof(double) * (size_t)s * (size_t)m);
+    int64_t *F = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    if (!Z || !F || orc_tier_sketch_entries(s, m, seed, Z, s) != ORC_OK) {
+        free(Z);
+        free(F);
+        return ORC_ERR_NOMEM;
+    }
+    const double scale = 1.0 / sqrt((double)s);
+    for (int64_t j = 0; j < n; ++j) {
+        int bmax = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            uint64_t b;
+            const double x = IDX(X, ldx, i, j);
+            memcpy(&b, &x, sizeof b);
+            const int e = (int)((b >> 52) & 0x7ff);
+            if (e > bmax)
+                bmax = e;
+        }
+        if (bmax == 0x7ff) {
+            for (int64_t r = 0; r < s; ++r)
+                IDX(Y, ldy, r, j) = NAN;
+            continue;
+        }
+        const int E = bmax - 1022;
+        for (int64_t i = 0; i < m; ++i)
+            F[i] = (int64_t)round(ldexp(IDX(X, ldx, i, j), 47 - E));
+#pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < s; ++r) {
+            __int128 acc = 0;
+            for (int64_t i = 0; i < m; ++i)
+                acc += (__int128)(int64_t)(32.0 * IDX(Z, s, r, i)) * F[i];
+            IDX(Y, ldy, r, j) = ldexp((double)acc, E - 52) * scale;
+        }
+    }
+    free(F);
+    free(Z);
     return ORC_OK;
 }
 

@@ -113,16 +113,28 @@ MUTANTS = [
     ("bf16_split_wrong_residual",
      "const double x3 = orc_round_bf16(r1 - x2);",
      "const double x3 = orc_round_bf16(x - x2);"),
-    ("bf16_levels_without_the_half",
+    ("tier_levels_without_the_half",
      "orc_normal_quantile(((double)j + 0.5) / 4096.0)",
      "orc_normal_quantile(((double)j + 1.0) / 4097.0)"),
-    ("bf16_quantile_symmetry_sign",
+    ("tier_levels_truncated",
+     "T[j] = nearbyint(32.0 * orc_normal_quantile(",
+     "T[j] = trunc(32.0 * orc_normal_quantile("),
+    ("digits_five_instead_of_six",
+     "F[i] = (int64_t)round(ldexp(IDX(X, ldx, i, j), 47 - E));",
+     "F[i] = (int64_t)round(ldexp(IDX(X, ldx, i, j), 39 - E)) * 256;"),
+    ("digits_truncate_instead_of_round",
+     "F[i] = (int64_t)round(ldexp(IDX(X, ldx, i, j), 47 - E));",
+     "F[i] = (int64_t)trunc(ldexp(IDX(X, ldx, i, j), 47 - E));"),
+    ("digits_exponent_off_by_one",
+     "        const int E = bmax - 1022;",
+     "        const int E = bmax - 1023;"),
+    ("tier_quantile_symmetry_sign",
      "        return -orc_normal_quantile(1.0 - p);",
      "        return orc_normal_quantile(1.0 - p);"),
-    ("bf16_counter_words_swapped",
+    ("tier_counter_words_swapped",
      "uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)(uint64_t)r, 0x53424631u};",
      "uint32_t ctr[4] = {(uint32_t)(uint64_t)r, (uint32_t)(q >> 32), (uint32_t)q, 0x53424631u};"),
-    ("bf16_entries_share_a_half",
+    ("tier_entries_share_a_half",
      "const uint32_t h = (w[t >> 1] >> (16 * (t & 1))) & 0xffffu;",
      "const uint32_t h = (w[t >> 1] >> (16 * 0)) & 0xffffu;"),
     ("bf16_sketch_scaled_twice",

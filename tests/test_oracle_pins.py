@@ -594,30 +594,34 @@ def test_bf16_split_keeps_24_bits():
     assert np.all(np.abs(x - x1) <= 2.0 ** -8 * np.abs(x))
 
 
-def test_bf16_gauss_table_against_library_quantile():
-    # T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)): scipy's ndtri (an independent
-    # implementation of the normal quantile) rounded by the independent bf16
-    # formula above gives every level bit for bit
+def test_tier_levels_against_library_quantile():
+    # T[j] = round(32 Phi^{-1}((j + 1/2) / 4096)) / 32: scipy's ndtri (an
+    # independent implementation of the normal quantile) gives every level,
+    # numpy's rint (half to even) the rounding
     from scipy.special import ndtri
-    t = oracle.bf16_gauss_table()
-    ref = np.array([_rne_bf16_reference(float(ndtri((j + 0.5) / 4096))) for j in range(4096)])
+    t = oracle.tier_levels()
+    ref = np.rint(32.0 * ndtri((np.arange(4096) + 0.5) / 4096)) / 32.0
     assert np.array_equal(t, ref)
-    # symmetric, increasing, and a unit variance up to the discretisation
-    assert np.array_equal(t, -t[::-1]) and np.all(np.diff(t) >= 0)
-    assert t[2047] < 0 < t[2048] and abs(t.var() - 1.0) < 1e-3
+    # symmetric, increasing, integers over 32 within bf16's 8 bits, zero as +0,
+    # and a unit variance up to the discretisation
+    assert np.array_equal(t, -t[::-1] + 0.0) and np.all(np.diff(t) >= 0)
+    k = 32 * t
+    assert np.array_equal(k, np.round(k)) and np.max(np.abs(k)) <= 128
+    assert not np.any(np.signbit(t[t == 0]))
+    assert abs(t.var() - 1.0) < 2e-3
     # the quantile itself at closed-form points
     assert oracle.normal_quantile(0.5 - 1e-17) <= 0.0
     assert abs(oracle.normal_quantile(0.8413447460685429) - 1.0) < 1e-12
     assert abs(oracle.normal_quantile(0.022750131948179195) + 2.0) < 1e-12
 
 
-def test_bf16_sketch_entries_follow_philox():
+def test_tier_sketch_entries_follow_philox():
     # entry (r, i) = T[top 12 bits of 16-bit half (i mod 8) mod 2 of word
     # (i mod 8) div 2 of Philox4x32-10 at counter (i div 8, 0, r, 0x53424631)]
     # -- Philox itself is pinned by its known-answer vectors
-    t = oracle.bf16_gauss_table()
+    t = oracle.tier_levels()
     seed, s, m = 0x1234_5678_9ABC, 5, 37
-    z = oracle.bf16_sketch_z(s, m, seed)
+    z = oracle.tier_sketch_z(s, m, seed)
     key = [seed & 0xFFFFFFFF, seed >> 32]
     for r in range(s):
         for i in range(m):
@@ -626,16 +630,16 @@ def test_bf16_sketch_entries_follow_philox():
             assert z[r, i] == t[h >> 4], (r, i)
 
 
-def test_bf16_sketch_statistics():
-    # uniform levels, independent entries across rows and along a row (the
-    # eight entries of one Philox block are separate draws), unit variance
+def test_tier_sketch_statistics():
+    # uniform table indices, independent entries across rows and along a row
+    # (the eight entries of one Philox block are separate draws), unit variance
     from scipy import stats
-    z = oracle.bf16_sketch_z(16, 20000, 77)
+    z = oracle.tier_sketch_z(16, 20000, 77)
     assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
-    t = oracle.bf16_gauss_table()
-    lv = np.searchsorted(np.unique(t), z.ravel())
-    counts = np.bincount(lv, minlength=len(np.unique(t)))
-    expect = np.array([np.sum(t == v) for v in np.unique(t)], dtype=np.float64) / 4096 * z.size
+    t = oracle.tier_levels()
+    lv = np.unique(t)
+    counts = np.bincount(np.searchsorted(lv, z.ravel()), minlength=len(lv))
+    expect = np.array([np.sum(t == v) for v in lv], dtype=np.float64) / 4096 * z.size
     assert stats.chisquare(counts, expect).pvalue > 1e-4
     c = np.corrcoef(z)
     assert np.max(np.abs(c[~np.eye(16, dtype=bool)])) < 6.0 / math.sqrt(20000)
@@ -648,25 +652,75 @@ def test_sketch_bf16_definition(nterms):
     m, n, s, seed = 700, 9, 24, 5
     x = synth.svd_matrix(m, n, 1e3, 2)
     y = oracle.sketch_bf16(s, seed, nterms, x)
-    z = oracle.bf16_sketch_z(s, m, seed)
+    z = oracle.tier_sketch_z(s, m, seed)
     ref = oracle.sketch_dense(z, oracle.bf16_split(x, nterms)) / math.sqrt(s)
     assert np.allclose(y, ref, rtol=0, atol=1e-14 * np.max(np.abs(ref)))
     # exact on integers: small-integer X is its own bf16 split, and every
     # product and sum of bf16 levels times small integers is exact in binary64
     xi = synth.integer_matrix(300, 4, 8)
     yi = oracle.sketch_bf16(s, seed, nterms, xi)
-    zi = oracle.bf16_sketch_z(s, 300, seed)
+    zi = oracle.tier_sketch_z(s, 300, seed)
     assert np.array_equal(yi, (zi @ xi) * (1.0 / math.sqrt(s)))
 
 
-def test_bf16_sketch_is_an_embedding_eq_s2():
+def test_tier_sketch_is_an_embedding_eq_s2():
     # the discretised normal is sub-Gaussian with (nearly) unit variance, so
     # z_b / sqrt(s) embeds like the Gaussian sketch (eq. (s2), eps = 0.5)
     m, n, s = 3000, 8, 256
     x = synth.orthonormal(m, n, 21)
-    y = oracle.sketch_dense(oracle.bf16_sketch_z(s, m, 9) / math.sqrt(s), x)
+    y = oracle.sketch_dense(oracle.tier_sketch_z(s, m, 9) / math.sqrt(s), x)
     sv = np.linalg.svd(y, compute_uv=False)
     assert sv.max() <= math.sqrt(1.5) and sv.min() >= math.sqrt(0.5)
+
+
+def test_sketch_digits_exact_on_integers():
+    # small integers are their own six-digit rounding, and k x sums exactly:
+    # Y = (k X) 2^-5 / sqrt(s) with one rounding of the exact sum
+    s, seed = 24, 7
+    x = synth.integer_matrix(500, 6, 3)
+    y = oracle.sketch_digits(s, seed, x)
+    k = 32 * oracle.tier_sketch_z(s, 500, seed)
+    assert np.array_equal(y, ((k @ x) * 2.0 ** -5) * (1.0 / math.sqrt(s)))
+
+
+def test_sketch_digits_rounds_x_to_48_bits_of_its_column():
+    # a column with largest entry in [1, 2) has E = 1 and keeps 2^-46 steps,
+    # rounding half away from zero: 1 + 2^-47 -> 1 + 2^-46, 1 + 2^-48 -> 1
+    s, seed = 8, 11
+    k = 32 * oracle.tier_sketch_z(s, 4, seed)
+    cols = {1.0 + 2.0 ** -47: 1.0 + 2.0 ** -46, 1.0 + 2.0 ** -48: 1.0,
+            -(1.0 + 2.0 ** -47): -(1.0 + 2.0 ** -46), 1.5 + 3 * 2.0 ** -48: 1.5 + 2.0 ** -46}
+    for v, kept in cols.items():
+        x = np.array([[v], [1.25], [-1.0], [0.5]])
+        F = [int(f) for f in np.array([kept, 1.25, -1.0, 0.5]) * 2.0 ** 46]  # exact integers
+        y = oracle.sketch_digits(s, seed, x)
+        # the exact integer sum (Python integers), rounded once to binary64
+        ref = [math.ldexp(float(sum(int(k[r, i]) * F[i] for i in range(4))), -51) * (1.0 / math.sqrt(s))
+               for r in range(s)]
+        assert np.array_equal(y[:, 0], np.array(ref)), v
+    # a NaN makes its column NaN, the others stay finite
+    x = np.ones((4, 2))
+    x[2, 1] = np.nan
+    y = oracle.sketch_digits(s, seed, x)
+    assert np.all(np.isfinite(y[:, 0])) and np.all(np.isnan(y[:, 1]))
+
+
+def test_sketch_digits_close_to_the_binary64_product():
+    # |Y - z_b X / sqrt(s)| <= (2^-48 max_i |x_ij| sum_i |k_ri| / 32 + binary64
+    # rounding of the reference) / sqrt(s): 48 bits of each column kept
+    m, n, s, seed = 2000, 7, 32, 4
+    x = synth.svd_matrix(m, n, 1e6, 9) * np.array([1e-200, 1.0, 3.0, 1e100, 1e-3, 7.0, 1e5])
+    y = oracle.sketch_digits(s, seed, x)
+    z = oracle.tier_sketch_z(s, m, seed)
+    ref = oracle.sketch_dense(z, x) / math.sqrt(s)
+    cmax = np.max(np.abs(x), axis=0)
+    bound = (2.0 ** -48 * np.abs(z).sum(axis=1)[:, None] * cmax[None, :]
+             + 4 * m * 2.0 ** -53 * (np.abs(z) @ np.abs(x))) / math.sqrt(s)
+    assert np.all(np.abs(y - ref) <= bound)
+    # and scaling a column by a power of two scales its sketch exactly
+    x2 = x * np.array([2.0 ** 300, 1, 1, 2.0 ** -500, 1, 1, 1])
+    y2 = oracle.sketch_digits(s, seed, x2)
+    assert np.array_equal(y2, y * np.array([2.0 ** 300, 1, 1, 2.0 ** -500, 1, 1, 1]))
 
 
 # ------------------------------------- comparison paths (Algorithms 3, 5) ---
