@@ -330,7 +330,7 @@ def time_call(torch, stream, fn, reps):
 #        emulated forms only the solves' diagonal blocks ((b+1) m n per solve,
 #        b = 16 for n <= 160 else 32) and, in EMULATED, the final-pass Gram.
 #   Ftc  tensor-pipe flops the split issues: tensor-core sketch 2smn per bf16
-#        term of X; emulated Gram 36 digit pairs x 2 x m x (128 x 64 tiles of
+#        term (or digit: six at the digit tier) of X; emulated Gram 36 digit pairs x 2 x m x (128 x 64 tiles of
 #        the upper triangle); emulated solve 36 x 2 x m x b^2 x nb(nb-1)/2.
 #   B    HBM bytes: sketch read 8mn, fused solve + Gram passes 16mn each (56mn
 #        for binary64 RCLUPP), a separate Gram pass 8mn (72mn emulated); the
@@ -355,26 +355,29 @@ def form_counts(m, n, s, form, *, algo="rclupp", kind="gaussian", zeta=8, prec_u
     emu_trsm_tc = 72.0 * m * b * b * nb * (nb - 1) / 2
     emu_gram_tc = 72.0 * m * _emu_gram_tiles(n) * 128 * 64
     f64 = ftc = byt = 0.0
-    # sketch tiers run, in order (escalation bf16 -> three-term -> binary64)
+    # sketch tiers run, in order (escalation bf16 -> three-term -> binary64;
+    # the digit tier, 5, is never escalated)
     tiers = [0]
     if kind == "gaussian":
         if first_tier is None:
-            first_tier = {"fp64": 0, "bf16": 1, "fp32": 2, "emulated": 1, "emulated_all": 1}[form]
-        last = first_tier if prec_used is None else int(prec_used)
-        order = [1, 2, 0]
-        i = order.index(first_tier)
+            first_tier = {"fp64": 0, "bf16": 1, "fp32": 2, "digits": 5, "emulated": 5,
+                          "emulated_all": 5}[form]
         tiers = [first_tier]
-        while tiers[-1] != last and i < 2:
-            i += 1
-            tiers.append(order[i])
+        if first_tier in (1, 2):
+            last = first_tier if prec_used is None else int(prec_used)
+            order = [1, 2, 0]
+            i = order.index(first_tier)
+            while tiers[-1] != last and i < 2:
+                i += 1
+                tiers.append(order[i])
     for k, t in enumerate(tiers):
         if kind == "sparse":
             f64 += zeta * mn
         elif t == 0:
             f64 += 2.0 * s * m * n
         else:
-            ftc += 2.0 * s * m * n * (1 if t == 1 else 3)
-        byt += 8 * mn
+            ftc += 2.0 * s * m * n * {1: 1, 2: 3, 5: 6}[t]
+        byt += (16 if t == 5 else 8) * mn  # the digit tier's column-exponent pass reads X once more
         if k < len(tiers) - 1:  # failed attempt: its first pass too
             if emu:
                 f64 += (b + 1) * mn
@@ -428,7 +431,7 @@ def svd_matrix_gpu(torch, m, n, kappa, seed, device):
     return X
 
 
-FORMS = (("fp64", 0), ("bf16", 1), ("fp32", 2), ("emulated", 3), ("emulated_all", 4))
+FORMS = (("fp64", 0), ("bf16", 1), ("fp32", 2), ("digits", 5), ("emulated", 3), ("emulated_all", 4))
 
 
 def mixed_on_same_x(rq, torch, X, stream, fp64_paths, reps):
@@ -582,8 +585,8 @@ def batched_problems(count=512):
 
 
 # sketch tier of each form inside a batch (no escalation is possible in a
-# graph): binary64, else the three-term tensor-core sketch
-BATCH_SKETCH_TIER = {"fp64": 0, "fp32": 2, "emulated": 2, "emulated_all": 2}
+# graph): binary64, the three-term tensor-core sketch, or the digit tier
+BATCH_SKETCH_TIER = {"fp64": 0, "fp32": 2, "digits": 5, "emulated": 5, "emulated_all": 5}
 
 
 def c4_batched(rq, torch, device, steps=3, warmup=3):
@@ -617,7 +620,8 @@ def c4_batched(rq, torch, device, steps=3, warmup=3):
 
     out = {}
     for label, prec in (("fp64", rq.PREC_FP64), ("fp32", rq.PREC_SKETCH_FP32),
-                        ("emulated", rq.PREC_EMULATED), ("emulated_all", rq.PREC_EMULATED_ALL)):
+                        ("digits", rq.PREC_SKETCH_DIGITS), ("emulated", rq.PREC_EMULATED),
+                        ("emulated_all", rq.PREC_EMULATED_ALL)):
         call = lambda: rq.rclupp_factor_batched(Xs, algo=rq.ALGO_RCLUPP, seed=base, Qs=Qs, Rs=Rs,
                                                 prec=prec, check=False)
         for _ in range(warmup):
@@ -630,7 +634,7 @@ def c4_batched(rq, torch, device, steps=3, warmup=3):
                       "gpu_launches_per_batch": int(launches),
                       "statuses_nonzero": int(np.count_nonzero(st)), "worst_orth": wo, "worst_res": wr,
                       "roofline": roofline_of(counts(label), b_ms)}
-    for label in ("fp32", "emulated", "emulated_all"):
+    for label in ("fp32", "digits", "emulated", "emulated_all"):
         out[label]["speedup_vs_fp64_batch"] = out["fp64"]["ms_per_batch"] / out[label]["ms_per_batch"]
 
     # the same problems as sequential single calls

@@ -65,34 +65,45 @@ typedef enum {
 
 /* Precision form.  The sketch only has to be an embedding (Section 3): the
  * reduced tiers run the generated Gaussian sketch on the tensor cores
- * (tcgen05, bf16 operands, fp32 accumulation in tensor memory): S's entries
- * are bf16 levels of a discretised standard normal, z_b(r, i) = T[h >> 4]
- * with T[j] = bf16(Phi^{-1}((j + 1/2) / 4096)) and h the 16-bit half
- * (i mod 8) mod 2 of word (i mod 8) div 2 of Philox4x32-10 at counter
- * (i div 8 mod 2^32, i div 2^35, r, 0x53424631), key = seed (so the reduced
- * tiers' S differs from the binary64 tier's), and every x of X is either
- * rounded to bf16 (BF16) or split into three bf16 terms x1 = bf16(x),
- * x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (FP32); per-CTA partial sums
- * are combined in binary64.  EMULATED adds binary64-emulating tensor-core products for the
- * solves and the first Gram.  Other steps stay in binary64.  The sparse-sign
- * and SRHT sketches only add and always run in binary64 (their results report
- * RCLUPP_PREC_FP64 as the tier used); an explicit S requires
- * RCLUPP_PREC_FP64 or one of the emulated tiers (whose sketch is then binary64). */
+ * (tcgen05, bf16 operands, fp32 accumulation in tensor memory) with S on an
+ * integer grid: z_b(r, i) = T[h >> 4] with T[j] = k_j / 32,
+ * k_j = round(32 Phi^{-1}((j + 1/2) / 4096)) (half to even, |k_j| <= 117),
+ * and h the 16-bit half (i mod 8) mod 2 of word (i mod 8) div 2 of
+ * Philox4x32-10 at counter (i div 8 mod 2^32, i div 2^35, r, 0x53424631),
+ * key = seed (so these tiers' S differs from the binary64 tier's), and
+ * S = z_b / sqrt(s).  Every x of X is rounded to bf16 (BF16), split into
+ * three bf16 terms x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)
+ * (FP32), or rounded to 48 bits of its column with exact integer sums
+ * (DIGITS, below); per-CTA partial sums are combined in binary64.  EMULATED
+ * sketches at the DIGITS tier and adds binary64-emulating tensor-core
+ * products for the solves and the first Gram.  Other steps stay in binary64.
+ * The sparse-sign and SRHT sketches only add and always run in binary64
+ * (their results report RCLUPP_PREC_FP64 as the tier used); an explicit S
+ * requires RCLUPP_PREC_FP64 or one of the emulated tiers (whose sketch is
+ * then binary64). */
 typedef enum {
     RCLUPP_PREC_FP64 = 0,        /* every step in binary64 */
     RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
     RCLUPP_PREC_SKETCH_FP32 = 2, /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
-    RCLUPP_PREC_EMULATED = 3,    /* the BF16 sketch tier; the triangular solves' block products
+    RCLUPP_PREC_EMULATED = 3,    /* the DIGITS sketch tier; the triangular solves' block products
                                     (rclupp_trsm_emulated) and the Gram of the first CholeskyQR
                                     pass (Q1^T Q1, rclupp_gram_emulated) as binary64-emulating
                                     split-bf16 products on the tensor cores; the final-pass Gram,
                                     the diagonal blocks of the solves and the n x n
                                     factorizations stay in binary64.  An explicit S or the
                                     sparse-sign or SRHT sketch keeps a binary64 sketch. */
-    RCLUPP_PREC_EMULATED_ALL = 4 /* EMULATED, and the final-pass Gram (C5; for RCholeskyQR its
+    RCLUPP_PREC_EMULATED_ALL = 4, /* EMULATED, and the final-pass Gram (C5; for RCholeskyQR its
                                     one Gram) emulated as well: its digit products are exact and
                                     are summed exactly in fp32 windows, then in int64 and
                                     binary64, so the accumulation stays binary64 or better */
+    RCLUPP_PREC_SKETCH_DIGITS = 5 /* tensor-core sketch with the S of BF16 (the integers k on
+                                    the tensor cores, 1/32 in the scale) and X rounded to 48 bits
+                                    of each column's largest entry (six balanced base-256 digits
+                                    of F = round(x 2^(47 - E_j)), half away from zero, 2^E_j above
+                                    the column); the integer sums k F are exact on the tensor
+                                    cores (fp32 windows of 1024 rows, int64 drains), then summed
+                                    in binary64.  Needs no escalation up to kappa(X) ~ 1e15;
+                                    the emulated tiers sketch at this tier. */
 } rclupp_precision_t;
 
 /* R-factor R0 of the preconditioning step: of M in Algorithm 6, of M_s in
@@ -161,10 +172,12 @@ typedef struct {
                             CholeskyQR passes; 4 second one; 6 shifted Cholesky
                             (SCholeskyQR3) */
     int64_t info;        /* failing column for breakdown / zero pivot, else -1 */
-    int32_t prec_used;   /* sketch tier that produced the result (rclupp_precision_t);
+    int32_t prec_used;   /* sketch tier that produced the result (rclupp_precision_t):
                             RCLUPP/RCLUPPr escalate bf16 -> three-term bf16 -> FP64 when
                             the first Cholesky breaks down or the spread of its diagonal
-                            exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2) */
+                            exceeds 1e4 (Q1 too ill-conditioned for CholeskyQR2); the
+                            emulated tiers report RCLUPP_PREC_SKETCH_DIGITS (FP64 with an
+                            explicit, sparse-sign or SRHT sketch), which never escalates */
     int32_t emulated;    /* 1 when the solves and the first pass's Gram ran on the
                             binary64-emulating tensor-core path (RCLUPP_PREC_EMULATED), 2 when
                             every Gram did too (RCLUPP_PREC_EMULATED_ALL), else 0 */
@@ -278,9 +291,10 @@ typedef enum {
  * randomized algorithms.  A graph cannot escalate a sketch tier, so each
  * problem's sketch runs at one tier: binary64 for RCLUPP_PREC_FP64; the
  * three-term bf16 tensor-core sketch (FP32 level, enough for kappa(X) up to
- * about 1e12) for RCLUPP_PREC_SKETCH_FP32 and for the emulated tiers, which
- * keep their emulated solves and Gram products; RCLUPP_PREC_SKETCH_BF16,
- * which relies on escalation, returns RCLUPP_ERR_UNSUPPORTED.  The sparse-sign,
+ * about 1e12) for RCLUPP_PREC_SKETCH_FP32; the digit tier for
+ * RCLUPP_PREC_SKETCH_DIGITS and for the emulated tiers, which keep their
+ * emulated solves and Gram products; RCLUPP_PREC_SKETCH_BF16, which relies
+ * on escalation, returns RCLUPP_ERR_UNSUPPORTED.  The sparse-sign,
  * SRHT and explicit sketches stay binary64.  Each problem obeys the
  * single-problem rules;
  * problems run concurrently, so the outputs of different problems must not

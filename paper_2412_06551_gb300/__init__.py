@@ -24,6 +24,7 @@ __all__ = [
     "Status", "RclupError", "Opts", "Info", "SKETCH_GAUSSIAN", "SKETCH_SPARSE_SIGN", "SKETCH_SRHT",
     "R0_HOUSEHOLDER", "R0_GIVENS", "rclupp_givens_r",
     "PREC_FP64", "PREC_SKETCH_BF16", "PREC_SKETCH_FP32", "PREC_EMULATED", "PREC_EMULATED_ALL",
+    "PREC_SKETCH_DIGITS",
     "load", "library_path", "exported_symbols", "workspace_size", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
@@ -39,6 +40,7 @@ __all__ = [
 SKETCH_GAUSSIAN, SKETCH_SPARSE_SIGN, SKETCH_SRHT = 0, 1, 2
 R0_HOUSEHOLDER, R0_GIVENS = 0, 1
 PREC_FP64, PREC_SKETCH_BF16, PREC_SKETCH_FP32, PREC_EMULATED, PREC_EMULATED_ALL = 0, 1, 2, 3, 4
+PREC_SKETCH_DIGITS = 5
 
 
 class Status:
@@ -471,8 +473,9 @@ def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN,
     """Factor a list of column-major matrices in one batched call (one CUDA
     graph).  s is a per-problem list (or None for 2 n); seed is a list or an
     int (then seed + i for problem i); prec is PREC_FP64 (binary64 sketch),
-    PREC_SKETCH_FP32 or an emulated tier (three-term tensor-core sketch, no
-    escalation inside a graph).  Returns (Qs, Rs, statuses)."""
+    PREC_SKETCH_FP32 (three-term tensor-core sketch), PREC_SKETCH_DIGITS or an
+    emulated tier (digit-tier sketch); no escalation inside a graph.
+    Returns (Qs, Rs, statuses)."""
     a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec, r0)
     st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
     _raise("rclupp_factor_batched", st, None, check)

@@ -133,7 +133,8 @@ Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *t
     Bufs b;
     const int n_pad = pad16(n);
     const size_t part = std::max({gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0),
-                                  gram_emu_partials_doubles(n), trsm_emu_scratch_bytes(n) / 8 + 1});
+                                  sketch_digits_partials_doubles(s, n), gram_emu_partials_doubles(n),
+                                  trsm_emu_scratch_bytes(n) / 8 + 1});
     b.part = c.take<double>(part);
     b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
     b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
@@ -259,9 +260,10 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
     }
     if (o.prec != RCLUPP_PREC_FP64 && o.prec != RCLUPP_PREC_SKETCH_BF16 &&
         o.prec != RCLUPP_PREC_SKETCH_FP32 && o.prec != RCLUPP_PREC_EMULATED &&
-        o.prec != RCLUPP_PREC_EMULATED_ALL)
+        o.prec != RCLUPP_PREC_EMULATED_ALL && o.prec != RCLUPP_PREC_SKETCH_DIGITS)
         return RCLUPP_ERR_ARG;
-    if ((o.prec == RCLUPP_PREC_SKETCH_BF16 || o.prec == RCLUPP_PREC_SKETCH_FP32) && o.S)
+    if ((o.prec == RCLUPP_PREC_SKETCH_BF16 || o.prec == RCLUPP_PREC_SKETCH_FP32 ||
+         o.prec == RCLUPP_PREC_SKETCH_DIGITS) && o.S)
         return RCLUPP_ERR_UNSUPPORTED;
     if (o.r0_method != RCLUPP_R0_HOUSEHOLDER && o.r0_method != RCLUPP_R0_GIVENS) return RCLUPP_ERR_ARG;
     // the Givens R0 runs in the cluster form only (the s x n matrix in shared memory)
@@ -277,6 +279,8 @@ rclupp_status_t check_opts(const rclupp_opts_t &o, int64_t m, int64_t n) {
 cudaError_t sketch_step(const Bufs &b, const double *A, int64_t lda, int64_t m, int n,
                         int unit_lower, const rclupp_opts_t &o, int tier, DevStatus *ds,
                         cudaStream_t s) {
+    if (tier == RCLUPP_PREC_SKETCH_DIGITS && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
+        return launch_sketch_digits(A, lda, m, n, unit_lower, o.s, o.seed, b.Y, o.s, b.part, ds, s);
     if (tier != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
         return launch_sketch_tc(A, lda, m, n, unit_lower, o.s, o.seed,
                                 tier == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, b.Y, o.s, b.part, ds, s);
@@ -408,11 +412,11 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
                                 int64_t m, int n, const double *SA, int64_t ldsa, int unit_lower,
                                 Precond precond, const double *X, int64_t ldx, double *Q,
                                 int64_t ldq, double *R, int64_t ldr, int *tier_used) {
-    // the emulated tier sketches like the bf16 one (on the tensor cores when
+    // the emulated tiers sketch at the digit tier (on the tensor cores when
     // the Gaussian sketch is generated, else in binary64)
     const bool emulated = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
     int tier = o.prec;
-    if (emulated) tier = RCLUPP_PREC_SKETCH_BF16;
+    if (emulated) tier = RCLUPP_PREC_SKETCH_DIGITS;
     // only the generated Gaussian sketch has reduced tiers; the others are binary64
     if (o.kind != RCLUPP_SKETCH_GAUSSIAN || o.S) tier = RCLUPP_PREC_FP64;
     for (;;) {
@@ -425,7 +429,8 @@ rclupp_status_t randomized_tail(rclupp_handle_t h, const Bufs &b, const rclupp_o
         const rclupp_status_t st =
             first_cholqr_pass(ctx_of(h), b, m, n, X, ldx, Q, ldq, emulated, emulated);
         if (st != RCLUPP_OK) return st;
-        if (tier == RCLUPP_PREC_FP64) break;
+        // binary64 and the digit tier (48 bits, exact sums) are not escalated
+        if (tier == RCLUPP_PREC_FP64 || tier == RCLUPP_PREC_SKETCH_DIGITS) break;
         const FirstPassOutcome v = assess_first_pass(h, b, n);
         if (v == FirstPassOutcome::Fail) break;  // the status is reported by finish()
         if (v == FirstPassOutcome::Accept) break;
@@ -449,13 +454,15 @@ cudaError_t copy_matrix(double *dst, int64_t ldd, const double *src, int64_t lds
 // tier, batch_sketch_tier(o).
 
 // Sketch tier of a randomized factorization inside a batch: binary64 for
-// RCLUPP_PREC_FP64, else the three-term tensor-core tier (FP32 level), which
-// keeps kappa(Q1) ~ 2^-24 kappa(X) within CholeskyQR2's reach up to
-// kappa(X) ~ 1e12 (the bf16 tier reaches only ~1e9 and needs the escalation a
+// RCLUPP_PREC_FP64, the three-term tensor-core tier (FP32 level, within
+// CholeskyQR2's reach up to kappa(X) ~ 1e12) for RCLUPP_PREC_SKETCH_FP32, and
+// the digit tier (48 bits, exact sums, reach ~1e15) for the digit and
+// emulated tiers (the bf16 tier reaches only ~1e9 and needs the escalation a
 // graph cannot make).  sketch_step() runs the sparse-sign, SRHT and explicit
 // sketches in binary64 whatever the tier.
 int batch_sketch_tier(const rclupp_opts_t &o) {
-    return o.prec == RCLUPP_PREC_FP64 ? RCLUPP_PREC_FP64 : RCLUPP_PREC_SKETCH_FP32;
+    if (o.prec == RCLUPP_PREC_FP64 || o.prec == RCLUPP_PREC_SKETCH_FP32) return o.prec;
+    return RCLUPP_PREC_SKETCH_DIGITS;
 }
 
 // RCLUPP, Algorithm 6, sketch at batch_sketch_tier(o).
@@ -765,12 +772,13 @@ rclupp_status_t rcholqr_factor(rclupp_handle_t h, int64_t m, int64_t n, const do
     if ((st = check_opts(o, m, n)) != RCLUPP_OK) return st;
     Bufs b = prepare(h, m, int(n), o.s, false, &st);
     if (st != RCLUPP_OK) return st;
+    const bool tc_sketch = o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S;
+    const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
+    const int tier = emu ? RCLUPP_PREC_SKETCH_DIGITS : o.prec;
     const rclupp_status_t r = finish(
-        h, enqueue_rcholqr(ctx_of(h), b, o, o.prec, m, int(n), X, ldx, Q, ldq, R, ldr), info, nullptr);
+        h, enqueue_rcholqr(ctx_of(h), b, o, tier, m, int(n), X, ldx, Q, ldq, R, ldr), info, nullptr);
     if (info) {
-        const bool tc_sketch = o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S;
-        const bool emu = o.prec == RCLUPP_PREC_EMULATED || o.prec == RCLUPP_PREC_EMULATED_ALL;
-        info->prec_used = !emu ? o.prec : (tc_sketch ? RCLUPP_PREC_SKETCH_BF16 : RCLUPP_PREC_FP64);
+        info->prec_used = tc_sketch ? tier : RCLUPP_PREC_FP64;
         info->emulated = o.prec == RCLUPP_PREC_EMULATED ? 1 : (o.prec == RCLUPP_PREC_EMULATED_ALL ? 2 : 0);
     }
     return r;

@@ -25,17 +25,20 @@ __device__ __forceinline__ uint32_t emu_off(int row, int k) {
                                  (k & 7) * 2);
 }
 
-// Balanced base-256 digits of F = round(x 2^(63 - E)), for |x| < 2^E: the
-// digits of |F| (bytes with a carry into the next one when a byte is >= 128),
-// negated for negative x.  Every digit lies in [-128, 128].
-__device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
+// Balanced base-256 digits d_0 (top) .. d_{ND-1} of F = round(x 2^(8 ND - 1 - E))
+// (half away from zero), for |x| < 2^E: the digits of |F| (bytes with a carry
+// into the next one when a byte is >= 128), negated for negative x.  Every
+// digit lies in [-128, 128]; |F| < 2^(8 ND - 1).
+template <int ND>
+__device__ __forceinline__ void emu_digits_n(double x, int E, int (&d)[ND]) {
+    static_assert(ND >= 2 && ND <= 8, "one to eight bytes");
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
     const int e = static_cast<int>((b >> 52) & 0x7ff);
     unsigned long long M = b & 0xFFFFFFFFFFFFFull;
     if (e != 0) M |= 1ull << 52;
-    // |F| = M 2^sh; sh <= 10 for normal x as |x| < 2^E, 11 for subnormals of a
-    // column whose largest exponent is subnormal; |F| < 2^63
-    const int sh = (e != 0 ? e : 1) - 1012 - E;
+    // |F| = M 2^sh; for eight digits sh <= 10 for normal x as |x| < 2^E, 11 for
+    // subnormals of a column whose largest exponent is subnormal
+    const int sh = (e != 0 ? e : 1) - 1076 + 8 * ND - E;
     unsigned long long F;
     if (sh >= 0)
         F = M << (sh & 15);
@@ -47,15 +50,20 @@ __device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]
     const int neg = static_cast<int>(b >> 63);
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < kEmuDigits - 1; ++q) {
+    for (int q = 0; q < ND - 1; ++q) {
         const uint32_t byte = ((q < 4 ? lo : hi) >> (8 * (q & 3))) & 0xffu;
         const uint32_t u = byte + c + 128u;
         const int dq = static_cast<int>(u & 0xffu) - 128;
         c = u >> 8;
-        d[kEmuDigits - 1 - q] = neg ? -dq : dq;
+        d[ND - 1 - q] = neg ? -dq : dq;
     }
-    const int top = static_cast<int>((hi >> 24) + c);
+    const int top = static_cast<int>((ND > 4 ? (hi >> (8 * (ND - 5))) : (lo >> (8 * (ND - 1)))) + c);
     d[0] = neg ? -top : top;
+}
+
+// The eight digits of the emulated Gram and solve (F = round(x 2^(63 - E))).
+__device__ __forceinline__ void emu_digits(double x, int E, int (&d)[kEmuDigits]) {
+    emu_digits_n<kEmuDigits>(x, E, d);
 }
 
 // bf16 bits of an integer |d| <= 256 (exact): 1.5 * 2^23 + d in binary32,

@@ -118,6 +118,13 @@ cudaError_t launch_sketch_tc(const double *X, int64_t ldx, int64_t m, int n, int
                              int64_t s, uint64_t seed, int nterms, double *Y, int64_t ldy,
                              double *part, DevStatus *st, cudaStream_t stream, int64_t row0 = 0);
 size_t tc_sketch_smem_bytes(int n, int nterms);
+// The digit tier's sketch (tc_sketch.cu): the same S, X rounded to 48 bits of
+// each column (six base-256 digits), exact integer sums on the tensor cores,
+// binary64 across windows and CTAs.  part: sketch_digits_partials_doubles().
+cudaError_t launch_sketch_digits(const double *X, int64_t ldx, int64_t m, int n, int unit_lower,
+                                 int64_t s, uint64_t seed, double *Y, int64_t ldy, double *part,
+                                 DevStatus *st, cudaStream_t stream, int64_t row0 = 0);
+size_t sketch_digits_partials_doubles(int64_t s, int n);
 // The reduced tier's level table (bf16 levels of the discretised normal) on
 // the current device, written once per device; called at handle creation.
 cudaError_t ensure_sketch_levels();

@@ -211,7 +211,7 @@ def test_batched_bf16_sketch_is_refused(rq):
     assert e.value.status == rq.Status.ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("prec", [2, 3, 4])
+@pytest.mark.parametrize("prec", [2, 3, 4, 5])
 def test_batched_tensor_core_sketch_gates_up_to_kappa_1e12(rq, prec):
     # the three-term sketch in a batch (and the emulated tiers on top of it)
     # against the oracle, kappa log-uniform up to 1e12

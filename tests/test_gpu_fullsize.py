@@ -181,7 +181,7 @@ def test_rclupp_fp64_m4M_n256(rq, c3):
         assert np.max(np.abs(q_gpu - q_rows)) <= 1e-13
 
 
-@pytest.mark.parametrize("tier", ["SKETCH_BF16", "SKETCH_FP32", "EMULATED", "EMULATED_ALL"])
+@pytest.mark.parametrize("tier", ["SKETCH_BF16", "SKETCH_FP32", "SKETCH_DIGITS", "EMULATED", "EMULATED_ALL"])
 def test_rclupp_precision_tiers_m4M_n256(rq, c3, tier):
     # the precision form against the full oracle on the same X: the
     # tensor-core sketch (bf16 or three-term bf16 X, escalating when the first
@@ -191,11 +191,12 @@ def test_rclupp_precision_tiers_m4M_n256(rq, c3, tier):
     kappa = c3["kappa"]
     Q, R, info = rq.rclupp_factor(c3["X"], s=S3, seed=c3["seed"] + 7, prec=prec, check=False)
     assert info.status == 0, (tier, info.status, info.failed_step)
-    sketch_tier = rq.PREC_SKETCH_BF16 if prec >= rq.PREC_EMULATED else prec
+    sketch_tier = rq.PREC_SKETCH_DIGITS if prec in (rq.PREC_EMULATED, rq.PREC_EMULATED_ALL) else prec
     # the sketch tier used: the requested one, or a more precise one after
-    # an escalation (only expected where kappa(X) exceeds the tier's reach)
+    # an escalation (only expected where kappa(X) exceeds the bf16 or
+    # three-term tier's reach; the digit tier never escalates)
     assert info.prec_used in (sketch_tier, rq.PREC_SKETCH_FP32, rq.PREC_FP64), info.prec_used
-    if kappa <= 1e8:
+    if kappa <= 1e8 or sketch_tier == rq.PREC_SKETCH_DIGITS:
         assert info.prec_used == sketch_tier, (tier, info.prec_used)
     assert info.emulated == {"EMULATED": 1, "EMULATED_ALL": 2}.get(tier, 0)
     _gate(c3, Q, R, tier)
@@ -297,7 +298,7 @@ def c4():
     return {"base": base, "xs": xs, "kappa": kap, "refs": refs}
 
 
-@pytest.mark.parametrize("tier", ["FP64", "SKETCH_FP32", "EMULATED", "EMULATED_ALL"])
+@pytest.mark.parametrize("tier", ["FP64", "SKETCH_FP32", "SKETCH_DIGITS", "EMULATED", "EMULATED_ALL"])
 def test_batched_512_problems_against_oracle(rq, c4, tier):
     prec = getattr(rq, "PREC_" + tier)
     Xs = [dev(x) for x in c4["xs"]]

@@ -146,3 +146,79 @@ def test_escalation_reaches_binary64_when_needed(rq):
     assert info.prec_used != 1
     if st_o == 0 and info.status == 0:
         assert oracle.orthogonality(host(Q)) <= max(1e3 * oracle.orthogonality(q_o), 1e-12)
+
+
+# ------------------------------------------------------------- digit tier ---
+
+def _digit_tol(z, x, s, m):
+    """|Y_gpu - Y_exact| for the digit tier: binary64 roundings of the int64
+    flushes and of the ordered sums over windows and CTAs (at most m/1024 + 2
+    of them per entry, each 2^-53 of |k| |F|), and level 5's rounding to units
+    of 2^8 per 1024-row window (2^(E - 45) each, in units of Y times sqrt(s))."""
+    k = np.abs(32 * z)
+    E = np.floor(np.log2(np.max(np.abs(x), axis=0) + 1e-300)) + 1
+    mag = (k @ (np.abs(x) + 2.0 ** (E - 48))) * 2.0 ** -5
+    w = m / 1024 + 2
+    return (4 * w * 2.0 ** -53 * mag + w * 2.0 ** (E - 45)) / np.sqrt(s)
+
+
+@pytest.mark.parametrize("m,n,s", [(1, 1, 1), (100, 7, 8), (4096, 64, 128), (20001, 128, 256),
+                                   (3001, 200, 300), (2048, 256, 512), (70000, 33, 66)])
+def test_digit_sketch_matches_definition(rq, m, n, s):
+    x = synth.svd_matrix(m, n, 1e6, m + n) if m >= n else synth.integer_matrix(m, n, 1)
+    seed = 4321 + m
+    y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=rq.PREC_SKETCH_DIGITS))
+    ref = oracle.sketch_digits(s, seed, x)
+    z = oracle.tier_sketch_z(s, m, seed)
+    assert np.all(np.abs(y - ref) <= _digit_tol(z, x, s, m) + 1e-300)
+
+
+def test_digit_sketch_exact_on_integers_and_scaling(rq):
+    # small integers: every digit sum is exact, so the result is the oracle's
+    # bit for bit; scaling a column by a power of two scales its sketch exactly
+    m, n, s, seed = 5000, 6, 64, 12
+    x = synth.integer_matrix(m, n, 4)
+    y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=rq.PREC_SKETCH_DIGITS))
+    assert np.array_equal(y, oracle.sketch_digits(s, seed, x))
+    sc = 2.0 ** np.array([300, 0, -500, 7, -20, 1000])
+    y2 = host(rq.rclupp_sketch(dev(x * sc), s=s, seed=seed, prec=rq.PREC_SKETCH_DIGITS))
+    assert np.array_equal(y2, y * sc)
+
+
+def test_digit_sketch_unit_lower_row_blocks_and_nonfinite(rq):
+    m, n, s = 3000, 24, 48
+    x = synth.svd_matrix(m, n, 1e4, 8)
+    lu, _, _, _ = oracle.gepp(x)
+    M = oracle.unit_lower(lu)
+    y = host(rq.rclupp_sketch(dev(lu), s=s, seed=4, prec=rq.PREC_SKETCH_DIGITS, unit_lower=True))
+    ref = oracle.sketch_digits(s, 4, M)
+    assert np.all(np.abs(y - ref) <= _digit_tol(oracle.tier_sketch_z(s, m, 4), M, s, m) + 1e-300)
+    # a row block starting at global row row0 draws the global entries
+    xi = synth.integer_matrix(301, 5, 2)
+    for row0 in (0, 5, 1024):
+        yb = host(rq.rclupp_sketch(dev(xi), s=32, seed=9, prec=rq.PREC_SKETCH_DIGITS, row0=row0))
+        z = oracle.tier_sketch_z(32, row0 + 301, 9)[:, row0:]
+        assert np.array_equal(yb, ((32 * z @ xi) * 2.0 ** -5) * (1.0 / np.sqrt(32))), row0
+    # a NaN makes its column NaN, the others are unaffected
+    xn = synth.svd_matrix(2000, 4, 10.0, 3)
+    xn[77, 2] = np.nan
+    yn = host(rq.rclupp_sketch(dev(xn), s=16, seed=1, prec=rq.PREC_SKETCH_DIGITS))
+    assert np.all(np.isnan(yn[:, 2])) and np.all(np.isfinite(np.delete(yn, 2, axis=1)))
+
+
+@pytest.mark.parametrize("algo", ["rclupp", "rcluppr", "rcholqr"])
+@pytest.mark.parametrize("kappa", [1e2, 1e8, 1e12, 1e15])
+def test_driver_digit_tier_needs_no_escalation(rq, algo, kappa):
+    # 48 bits and exact sums leave Q1 well conditioned at any kappa here: the
+    # result comes from the digit tier itself, with the binary64 gates
+    m, n, s = 8192, 64, 128
+    x = synth.svd_matrix(m, n, kappa, 91)
+    fn = {"rclupp": rq.rclupp_factor, "rcluppr": rq.rclupp_r_factor, "rcholqr": rq.rcholqr_factor}[algo]
+    Q, R, info = fn(dev(x), s=s, seed=8, prec=rq.PREC_SKETCH_DIGITS, check=False)
+    assert info.status == 0 and info.prec_used == rq.PREC_SKETCH_DIGITS
+    q_o, r_o, st_o = getattr(oracle, algo)(x, S=oracle.gaussian_sketch_matrix(s, m, 8), raise_on_error=False)
+    if kappa <= 1e12:
+        _gate(x, host(Q), host(R), q_o, r_o, kappa)
+    elif algo != "rcholqr":
+        assert oracle.orthogonality(host(Q)) <= max(10 * oracle.orthogonality(q_o), 1e-13)
+        assert oracle.residual(x, host(Q), host(R)) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13)
