@@ -86,11 +86,13 @@ typedef enum {
     RCLUPP_PREC_SKETCH_BF16 = 1, /* tensor-core sketch: bf16 S, bf16 X, fp32 sums          */
     RCLUPP_PREC_SKETCH_FP32 = 2, /* tensor-core sketch: bf16 S, three-term bf16 X, fp32 sums */
     RCLUPP_PREC_EMULATED = 3,    /* the DIGITS sketch tier; the triangular solves' block products
-                                    (rclupp_trsm_emulated) and the Gram of the first CholeskyQR
-                                    pass (Q1^T Q1, rclupp_gram_emulated) as binary64-emulating
-                                    split-bf16 products on the tensor cores; the final-pass Gram,
-                                    the diagonal blocks of the solves and the n x n
-                                    factorizations stay in binary64.  An explicit S or the
+                                    (rclupp_trsm_emulated for the first solve by R1,
+                                    rclupp_trsm_emulated_wellcond for the solves by R2 and R4)
+                                    and the Gram of the first CholeskyQR pass (Q1^T Q1,
+                                    rclupp_gram_emulated) as binary64-emulating split-bf16
+                                    products on the tensor cores; the final-pass Gram, the
+                                    diagonal blocks of the first solve, the inverses of R2 and R4
+                                    and the n x n factorizations stay in binary64.  An explicit S or the
                                     sparse-sign or SRHT sketch keeps a binary64 sketch. */
     RCLUPP_PREC_EMULATED_ALL = 4, /* EMULATED, and the final-pass Gram (C5; for RCholeskyQR its
                                     one Gram) emulated as well: its digit products are exact and
@@ -399,6 +401,22 @@ rclupp_status_t rclupp_gram_emulated(rclupp_handle_t handle, int64_t m, int64_t 
 rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t handle, int64_t m, int64_t n, const double *A,
                                      int64_t lda, const double *R, int64_t ldr, double *Q,
                                      int64_t ldq);
+
+/* Q = A R^{-1} for an R expected to be well conditioned, the form the
+ * emulated tiers use for the second and final solves of CholeskyQR2 (C3, C7:
+ * R2 and R4 have the condition numbers of Q1 and Q2).  W = R^{-1} is formed
+ * in binary64 by substitution, with the estimate kappa_1 = ||R||_1 ||W||_1;
+ * if kappa_1 <= 100, Q = A W runs as one binary64-emulating product on the
+ * tensor cores (digits of A's rows with one exponent per row over all n
+ * columns, of W's columns with one per column; levels <= 7 exact in fp32 over
+ * <= 128 K-columns, int64 drains), whose backward error carries a factor
+ * kappa_1 next to eq. (ewy)'s; else the substitution of
+ * rclupp_trsm_emulated runs.  The choice is made on the device.  *form (may
+ * be NULL) receives 1 for the product, 0 for the substitution.  Q may alias
+ * A.  n <= 256. */
+rclupp_status_t rclupp_trsm_emulated_wellcond(rclupp_handle_t handle, int64_t m, int64_t n,
+                                              const double *A, int64_t lda, const double *R,
+                                              int64_t ldr, double *Q, int64_t ldq, int32_t *form);
 
 /* Q = A R^{-1} by substitution (eq. (ewy), C3, C7) and, when G != NULL,
  * G = Q^T Q (C1, C5) in the same pass.  R: n x n upper, nonzero diagonal.

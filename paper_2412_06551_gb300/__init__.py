@@ -28,7 +28,8 @@ __all__ = [
     "load", "library_path", "exported_symbols", "workspace_size", "colmajor", "empty_colmajor", "Handle",
     "rclupp_factor", "rclupp_r_factor", "cholqr2_factor", "lc2_factor", "rcholqr_factor",
     "scholqr3_factor", "ALGO_RCHOLQR", "ALGO_SCHOLQR3",
-    "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
+    "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated",
+    "rclupp_trsm_emulated_wellcond", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
     "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
     "rclupp_set_batch_policy", "rclupp_get_batch_policy",
@@ -107,6 +108,8 @@ _SIGNATURES = {
     "rclupp_sketch_rows": ([_P, _I64, _I64, _P, _I64, _I64, _I32, _P, _P, _I64], _I32),
     "rclupp_workspace_size": ([_I32, _I64, _I64, _P, _I32, _P], _I32),
     "rclupp_trsm_emulated": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
+    "rclupp_trsm_emulated_wellcond": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64,
+                                       ctypes.POINTER(ctypes.c_int32)], _I32),
     "rclupp_trsm_gram": ([_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
     "rclupp_cholesky": ([_P, _I64, _P, _I64, _P, _I64, ctypes.POINTER(ctypes.c_int64)], _I32),
     "rclupp_trmm_upper": ([_P, _I64, _P, _I64, _P, _I64, _P, _I64], _I32),
@@ -463,6 +466,22 @@ def rclupp_trsm_emulated(A, R, *, Q=None):
     st = load().rclupp_trsm_emulated(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(R), ldr, _ptr(Q), ldq)
     _raise("rclupp_trsm_emulated", st)
     return Q
+
+
+def rclupp_trsm_emulated_wellcond(A, R, *, Q=None):
+    """Q = A R^{-1} for a well-conditioned R: the emulated product with R^{-1}
+    when ||R||_1 ||R^{-1}||_1 <= 100, else the emulated substitution.
+    Returns (Q, form) with form 1 for the product, 0 for the substitution."""
+    A, lda = colmajor(A)
+    m, n = A.shape
+    R, ldr = colmajor(R)
+    Q = empty_colmajor(m, n, A.device) if Q is None else Q
+    Q, ldq = colmajor(Q)
+    form = ctypes.c_int32(-1)
+    st = load().rclupp_trsm_emulated_wellcond(_handle(A).bind(), m, n, _ptr(A), lda, _ptr(R), ldr, _ptr(Q),
+                                              ldq, ctypes.byref(form))
+    _raise("rclupp_trsm_emulated_wellcond", st)
+    return Q, int(form.value)
 
 
 ALGO_RCLUPP, ALGO_RCLUPPR, ALGO_CHOLQR2, ALGO_LC2, ALGO_RCHOLQR, ALGO_SCHOLQR3 = 0, 1, 2, 3, 4, 5

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "librclupp.so")
 OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = ["tall.cu", "lu.cu", "small.cu", "api.cu", "prof.cu", "noalloc.cu", "tc_sketch.cu",
-           "emu_gram.cu", "emu_trsm.cu", "emu_trsm32.cu", "small_cluster.cu", "srht.cu"]
+           "emu_gram.cu", "emu_trsm.cu", "emu_trsm32.cu", "emu_wprod.cu", "small_cluster.cu", "srht.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-expt-relaxed-constexpr",
          "-I" + INCLUDE]

@@ -134,7 +134,7 @@ Bufs carve(void *base, int64_t m, int n, int64_t s, bool need_lu_copy, size_t *t
     const int n_pad = pad16(n);
     const size_t part = std::max({gram_partials_doubles(m, n), sketch_partials_doubles(m, n, s, 0),
                                   sketch_digits_partials_doubles(s, n), gram_emu_partials_doubles(n),
-                                  trsm_emu_scratch_bytes(n) / 8 + 1});
+                                  wellcond_scratch_bytes(n) / 8 + 1});
     b.part = c.take<double>(part);
     b.Y = c.take<double>(size_t(std::max<int64_t>(s, 1)) * n);
     b.W = c.take<double>(std::max(size_t(2) * std::max<int64_t>(s, n) * n, size_t(n) * n));
@@ -384,7 +384,9 @@ rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, 
     const int np = pad16(n);
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, b.RP[2], np, s));  // R3 = R2 R1
     if (emulated) {
-        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, st, s));
+        // R2 has the condition number of Q1 (that of the sketch's embedding):
+        // the product with R2^{-1} unless the estimate says otherwise
+        RQ_TRY(launch_trsm_emu_wellcond(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, st, s));
         if (emu_final_gram)
             RQ_TRY(launch_gram_emu(Q, ldq, m, n, b.G, n, b.part, st, s));
         else
@@ -394,8 +396,8 @@ rclupp_status_t rest_cholqr2(Ctx c, const Bufs &b, int64_t m, int n, double *Q, 
     }
     RQ_TRY(launch_cholesky(b.G, n, n, b.W, b.RP[3], b.rinv[3], nullptr, 0, st, 4, s));
     RQ_TRY(launch_trmm_upper(b.RP[3], np, b.RP[2], np, n, R, ldr, s));  // R = R4 R3
-    if (emulated)
-        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, b.part, st, s));
+    if (emulated)  // R4 = I + O(u kappa(Q1)^2)
+        RQ_TRY(launch_trsm_emu_wellcond(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, b.part, st, s));
     else
         RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[3], b.rinv[3], Q, ldq, nullptr, 0, b.part, st, s));
     return RCLUPP_OK;
@@ -526,7 +528,7 @@ rclupp_status_t enqueue_rcholqr(Ctx c, const Bufs &b, const rclupp_opts_t &o, in
     if (st != RCLUPP_OK) return st;
     RQ_TRY(launch_trmm_upper(b.RP[1], np, b.RP[0], np, n, R, ldr, c.s));
     if (emu)
-        RQ_TRY(launch_trsm_emu(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, c.st, c.s));
+        RQ_TRY(launch_trsm_emu_wellcond(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, b.part, c.st, c.s));
     else
         RQ_TRY(launch_trsm_gram(Q, ldq, m, n, b.RP[1], b.rinv[1], Q, ldq, nullptr, 0, b.part, c.st,
                                 c.s));
@@ -1113,6 +1115,24 @@ rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t h, int64_t m, int64_t n, co
         e = launch_trsm_emu(A, lda, m, int(n), b.RP[0], b.rinv[0], Q, ldq, b.part, h->d_status,
                             h->stream);
     return finish(h, from_cuda(e), nullptr, nullptr);
+}
+
+rclupp_status_t rclupp_trsm_emulated_wellcond(rclupp_handle_t h, int64_t m, int64_t n, const double *A,
+                                              int64_t lda, const double *R, int64_t ldr, double *Q,
+                                              int64_t ldq, int32_t *form) {
+    if (!h || !A || !R || !Q || n < 1 || m < 1 || bad_ld(lda, m) || bad_ld(ldr, n) || bad_ld(ldq, m))
+        return RCLUPP_ERR_ARG;
+    if (n > kMaxN || m >= (int64_t(1) << 31)) return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st;
+    Bufs b = prepare(h, m, int(n), n, false, &st);
+    if (st != RCLUPP_OK) return st;
+    cudaError_t e = launch_pad_upper(R, ldr, int(n), b.RP[0], b.rinv[0], h->stream);
+    if (e == cudaSuccess)
+        e = launch_trsm_emu_wellcond(A, lda, m, int(n), b.RP[0], b.rinv[0], Q, ldq, b.part, h->d_status,
+                                     h->stream);
+    const rclupp_status_t r = finish(h, from_cuda(e), nullptr, nullptr);
+    if (form) *form = r == RCLUPP_OK ? wellcond_used_product(b.part, int(n), h->stream) : -1;
+    return r;
 }
 
 rclupp_status_t rclupp_cholesky(rclupp_handle_t h, int64_t n, const double *G, int64_t ldg,

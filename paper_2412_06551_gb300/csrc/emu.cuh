@@ -73,6 +73,18 @@ __device__ __forceinline__ uint32_t small_int_bf16(int d) {
     return __float_as_uint(f) >> 16;
 }
 
+// Selection between the two forms of an emulated solve by a well-conditioned
+// factor: the product with R^{-1} runs when the 1-norm condition estimate
+// ||R||_1 ||R^{-1}||_1 (both maxima stored as the bits of non-negative
+// doubles) is at most kWprodMaxCond, the substitution otherwise.
+constexpr double kWprodMaxCond = 100.0;
+
+__device__ __forceinline__ bool wprod_selected(const unsigned long long *norms) {
+    const double nr = __longlong_as_double(static_cast<long long>(norms[0]));
+    const double nw = __longlong_as_double(static_cast<long long>(norms[1]));
+    return nr * nw <= kWprodMaxCond;
+}
+
 // Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.
 __device__ __forceinline__ int emu_exponent(int bits) { return bits - 1022; }
 

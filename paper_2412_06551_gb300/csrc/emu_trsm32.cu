@@ -64,7 +64,9 @@ __host__ __device__ __forceinline__ size_t te_rtile(int J, int kc) {
 // Column exponents of R over rows < 32J for each target block J >= 1, and the
 // digit tiles of R[32 kc .. 32 kc + 31][32J .. 32J + 31].  One CTA per J.
 __global__ void k_trsm_emu32_prep(const double *__restrict__ RP, int ldr, int n,
-                                unsigned char *__restrict__ rdig, int *__restrict__ rbits) {
+                                unsigned char *__restrict__ rdig, int *__restrict__ rbits,
+                                const unsigned long long *skip_if) {
+    if (skip_if != nullptr && wprod_selected(skip_if)) return;
     const int J = blockIdx.x + 1;
     const int j0 = kTeB * J;
     __shared__ int cb[kTeB];
@@ -99,7 +101,9 @@ __global__ void __launch_bounds__(kTeThreads, 2)
     k_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, int n_pad, int64_t chunk,
                const double *__restrict__ RT, const double *__restrict__ rinv,
                const unsigned char *__restrict__ rdig, const int *__restrict__ rbits, double *Q,
-               int64_t ldq, DevStatus *st) {
+               int64_t ldq, DevStatus *st,
+               const unsigned long long *skip_if) {
+    if (skip_if != nullptr && wprod_selected(skip_if)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_mma[kTeStages];
     __shared__ __align__(8) uint64_t bar_r;  // bulk copy of R's digit tiles
@@ -331,7 +335,8 @@ size_t trsm_emu32_scratch_bytes(int n) {
 
 cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, const double *RP,
                               const double *rinv, double *Q, int64_t ldq, void *scratch,
-                              DevStatus *st, cudaStream_t stream) {
+                              DevStatus *st, cudaStream_t stream,
+                            const unsigned long long *skip_if) {
     if (n < 1 || n > 256 || m < 1) return cudaErrorInvalidValue;
     const int n_pad = pad16(n);
     const int nblk = (n + kTeB - 1) / kTeB;
@@ -340,7 +345,7 @@ cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, co
     cudaError_t e;
     if (nblk > 1) {
         RQ_LAUNCH(KID_EMU_AUX, stream,
-                  k_trsm_emu32_prep<<<nblk - 1, 256, 0, stream>>>(RP, n_pad, n, rdig, rbits));
+                  k_trsm_emu32_prep<<<nblk - 1, 256, 0, stream>>>(RP, n_pad, n, rdig, rbits, skip_if));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t tiles = ceil_div(m, kTeM);
@@ -352,7 +357,7 @@ cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, co
     RQ_LAUNCH(KID_TRSM_EMU, stream,
               k_trsm_emu32<<<g, kTeThreads, smem, stream>>>(A, lda, m, n, n_pad, chunk,
                                                           RP + size_t(n_pad) * n_pad, rinv, rdig,
-                                                          rbits, Q, ldq, st));
+                                                          rbits, Q, ldq, st, skip_if));
     return cudaGetLastError();
 }
 

@@ -1,0 +1,387 @@
+// Triangular solve Q = A R^{-1} for a well-conditioned upper-triangular R as
+// one binary64-emulating product Q = A W with W = R^{-1} (the precision form
+// of the second and final solves of CholeskyQR2, C3 and C7, whose factors R2
+// and R4 have the condition number of Q1 and of Q2: a few units after a
+// sketch that embeds).
+//
+// W is formed once in binary64 by substitution (k_tri_inverse, one warp per
+// column), and the 1-norm condition estimate ||R||_1 ||W||_1 is taken on the
+// way.  Both this product and the substitution kernel of emu_trsm.cu are
+// launched; each reads the estimate and only one of them runs: the product
+// when the estimate is at most kWprodMaxCond (the product's backward error
+// carries a factor kappa(R)), the substitution otherwise.  No host round trip,
+// so the pair can be captured in a graph.
+//
+// The product: digits of A's rows (one exponent per row over all n columns of
+// A, known before anything is written) and of W's columns (one exponent per
+// column), levels s + t <= 7 summed exactly in fp32 over at most 128
+// K-columns, drained into int64 (units 2^-40 of level 0), scaled into
+// binary64.  A CTA of 256 threads owns 128 rows (two threads per row: each
+// splits half of a 16-column K-chunk and drains half of a 32-column pass);
+// passes of 32 output columns run from the last to the first, so that a pass
+// reads only columns of A below the ones it writes and Q may alias A.  Per
+// K-chunk the threads split their values into eight K-major digit tiles while
+// the tensor core works on the previous chunk; one thread bulk-copies W's
+// precomputed digit tiles and issues the 36 level products (kind::f16,
+// M = 128, N = 32, K = 16).  No binary64 arithmetic remains on the rows.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "emu.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace rq {
+namespace {
+
+constexpr int kWpThreads = 256;
+constexpr int kWpM = 128;            // rows per tile
+constexpr int kWpK = 16;             // K-columns per chunk
+constexpr int kWpN = 32;             // output columns per pass
+constexpr int kWpWinChunks = 8;      // K-chunks per exact window (128 K-columns)
+constexpr int kWpStages = 2;
+constexpr int kWpTileA = kWpM * kWpK * 2;   // one digit tile of A: 4 KB
+constexpr int kWpTileB = kWpN * kWpK * 2;   // one digit tile of W: 1 KB
+constexpr int kWpStageA = kEmuDigits * kWpTileA;
+constexpr int kWpStageB = kEmuDigits * kWpTileB;
+constexpr int kWpStageBytes = kWpStageA + kWpStageB;
+constexpr int kWpTmemCols = 256;     // eight 32-column level accumulators
+constexpr int kWpUnit = 16;          // drain units: 2^-(24 + 16) of level 0
+
+// Byte offset of element (row, k) of a K-major tile of 16 K-columns laid
+// out as [row/8][k/8][row%8][k%8] (bf16).
+__host__ __device__ __forceinline__ uint32_t wp_off(int row, int k) {
+    return static_cast<uint32_t>(((row >> 3) * 2 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Index of W's digit tiles for (pass g, K-chunk kc), kc <= 2g + 1.
+__host__ __device__ __forceinline__ size_t wp_tile(int g, int kc) {
+    return size_t(g) * (g + 1) + kc;
+}
+
+// Scratch layout (bytes from its start): the two norm maxima (as ordered
+// bits), then W's column exponents, then W (n_pad x n_pad binary64), then the
+// digit tiles.
+struct WpLayout {
+    size_t norms, cbits, w, tiles, total;
+};
+
+__host__ __device__ __forceinline__ WpLayout wp_layout(int n) {
+    const int n_pad = pad16(n);
+    const int np32 = (n + kWpN - 1) / kWpN * kWpN;
+    const int passes = np32 / kWpN;
+    WpLayout l;
+    l.norms = 0;
+    l.cbits = 256;
+    l.w = l.cbits + ((size_t(np32) * sizeof(int) + 255) / 256) * 256;
+    l.tiles = l.w + ((size_t(n_pad) * n_pad * 8 + 1023) / 1024) * 1024;
+    l.total = l.tiles + wp_tile(passes, 0) * kWpStageB + 256;
+    return l;
+}
+
+// W = R^{-1} (binary64, column-major n_pad x n_pad, zeros below the diagonal
+// and in the padding) by substitution, one warp per column j:
+// w_jj = 1 / r_jj, w_ij = -(sum_{k = i+1..j} r_ik w_kj) / r_ii for i < j,
+// the sum split over the lanes and combined by shuffles; and the column sums
+// of |R| and |W| folded into their maxima (the 1-norms).
+__global__ void k_tri_inverse(const double *__restrict__ RP, const double *__restrict__ rinv, int n,
+                              int n_pad, double *__restrict__ W, unsigned long long *norms) {
+    extern __shared__ double wcol_all[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (j >= n_pad) return;
+    double *wc = wcol_all + size_t(warp) * n_pad;
+    const double *RT = RP + size_t(n_pad) * n_pad;  // row-major copy: RT[i * n_pad + k] = r_ik
+    for (int i = lane; i < n_pad; i += 32) wc[i] = 0.0;
+    __syncwarp();
+    if (j < n) {
+        if (lane == 0) wc[j] = rinv[j];
+        __syncwarp();
+        for (int i = j - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int k = i + 1 + lane; k <= j; k += 32) acc = fma(RT[size_t(i) * n_pad + k], wc[k], acc);
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) wc[i] = -acc * rinv[i];
+            __syncwarp();
+        }
+    }
+    double sw = 0.0, sr = 0.0;
+    for (int i = lane; i < n_pad; i += 32) {
+        W[size_t(j) * n_pad + i] = wc[i];
+        sw += fabs(wc[i]);
+        sr += fabs(RP[size_t(j) * n_pad + i]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, off);
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+    }
+    if (lane == 0) {
+        // non-negative doubles order like their bits; a NaN sum maps to the
+        // largest bits and makes the estimate fail
+        atomicMax(norms, static_cast<unsigned long long>(__double_as_longlong(sr == sr ? sr : INFINITY)));
+        atomicMax(norms + 1, static_cast<unsigned long long>(__double_as_longlong(sw == sw ? sw : INFINITY)));
+    }
+}
+
+// Column exponents of W (over all its rows) and its digit tiles for every
+// (pass g, K-chunk kc <= 2g + 1): one CTA per pass.
+__global__ void k_wprod_prep(const double *__restrict__ W, int n, int n_pad,
+                             const unsigned long long *norms, int *__restrict__ cbits,
+                             unsigned char *__restrict__ tiles) {
+    if (!wprod_selected(norms)) return;
+    const int g = blockIdx.x;
+    const int c0 = kWpN * g;
+    __shared__ int cb[kWpN];
+    if (threadIdx.x < kWpN) {
+        const int c = c0 + threadIdx.x;
+        int e = 0;
+        if (c < n)
+            for (int k = 0; k <= c; ++k) {
+                const unsigned long long b =
+                    static_cast<unsigned long long>(__double_as_longlong(W[size_t(c) * n_pad + k]));
+                e = max(e, static_cast<int>((b >> 52) & 0x7ff));
+            }
+        cb[threadIdx.x] = e;
+        cbits[c] = e;
+    }
+    __syncthreads();
+    const int nk = std::min(2 * g + 2, (n + kWpK - 1) / kWpK);
+    for (int idx = threadIdx.x; idx < nk * kWpK * kWpN; idx += blockDim.x) {
+        const int k = idx % (nk * kWpK), c = idx / (nk * kWpK);
+        const int col = c0 + c;
+        const double w = (col < n && k < n_pad) ? W[size_t(col) * n_pad + k] : 0.0;
+        int d[kEmuDigits];
+        emu_digits(w, emu_exponent(cb[c]), d);
+        unsigned char *tile = tiles + wp_tile(g, k / kWpK) * kWpStageB;
+#pragma unroll
+        for (int s = 0; s < kEmuDigits; ++s)
+            *reinterpret_cast<uint16_t *>(tile + s * kWpTileB + wp_off(c, k % kWpK)) =
+                static_cast<uint16_t>(small_int_bf16(d[s]));
+    }
+}
+
+__global__ void __launch_bounds__(kWpThreads, 2)
+    k_wprod_emu(const double *A, int64_t lda, int64_t m, int n, int64_t chunk,
+                const unsigned long long *norms, const int *__restrict__ cbits,
+                const unsigned char *__restrict__ tiles, double *Q, int64_t ldq, DevStatus *st) {
+    if (!wprod_selected(norms)) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mma[kWpStages];
+    __shared__ __align__(8) uint64_t bar_w[kWpStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int rowbits_half[kWpThreads];
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = tid & (kWpM - 1), h = tid >> 7;  // row of the tile, half of its values
+    if (warp == 0) tmem_alloc(&tmem_slot, kWpTmemCols);
+    if (tid == 0) {
+        for (int q = 0; q < kWpStages; ++q) {
+            mbar_init(&bar_mma[q], 1);
+            mbar_init(&bar_w[q], 1);
+        }
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = idesc_bf16_f32(kWpM, kWpN);
+    const uint32_t sbase = smem_u32(smem_raw);
+    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 = rows, columns 16 (warp / 4) .. +15
+    const uint32_t tl = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                        static_cast<uint32_t>(16 * (warp >> 2));
+    const int nkc = (n + kWpK - 1) / kWpK;
+    const int passes = (n + kWpN - 1) / kWpN;
+
+    const int64_t rb = int64_t(blockIdx.x) * chunk;
+    const int64_t re = std::min<int64_t>(m, rb + chunk);
+    unsigned it = 0;  // K-chunks issued by this CTA (barrier phases of the stages)
+    for (int64_t r0 = rb; r0 < re && !abort_flag; r0 += kWpM) {
+        const int64_t row = r0 + r;
+        const bool live = row < re;
+        // the row's exponent over all n columns of A (each half scans half)
+        int eb = 0;
+        if (live)
+            for (int c = h; c < n; c += 2) {
+                const unsigned long long b = static_cast<unsigned long long>(
+                    __double_as_longlong(__ldcg(A + row + int64_t(c) * lda)));
+                eb = max(eb, static_cast<int>((b >> 52) & 0x7ff));
+            }
+        rowbits_half[tid] = eb;
+        __syncthreads();
+        const int rowbits = max(rowbits_half[r], rowbits_half[r + kWpM]);
+        const int E = emu_exponent(rowbits);
+        for (int g = passes - 1; g >= 0 && !abort_flag; --g) {
+            const int nk = std::min(2 * g + 2, nkc);
+            long long acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int sidx = it % kWpStages;
+                unsigned char *stage = smem_raw + sidx * kWpStageBytes;
+                // this thread's eight values of the chunk (in flight during the wait)
+                double xv[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int col = kWpK * kc + 8 * h + t;
+                    xv[t] = (live && col < n) ? __ldcg(A + row + int64_t(col) * lda) : 0.0;
+                }
+                // the MMAs that last read this stage are done
+                if (it >= kWpStages &&
+                    !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>(((it / kWpStages) - 1) & 1u)))
+                    abort_flag = 1;
+                __syncthreads();
+                if (abort_flag) break;
+                if (tid == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bar_w[sidx], kWpStageB);
+                    bulk_load(stage + kWpStageA, tiles + wp_tile(g, kc) * kWpStageB, kWpStageB, &bar_w[sidx]);
+                }
+                // digits of the eight values, two K-neighbours (one 32-bit word) per
+                // digit tile at a time
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    int d0[kEmuDigits], d1[kEmuDigits];
+                    emu_digits(xv[t], E, d0);
+                    emu_digits(xv[t + 1], E, d1);
+#pragma unroll
+                    for (int s = 0; s < kEmuDigits; ++s)
+                        *reinterpret_cast<uint32_t *>(stage + s * kWpTileA + wp_off(r, 8 * h + t)) =
+                            small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                }
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    const bool have_w = mbar_wait_bounded(&bar_w[sidx], (it / kWpStages) & 1u);
+                    if (!have_w) abort_flag = 1;
+                    tc_fence_after();
+                    const uint32_t sa = sbase + sidx * kWpStageBytes, sb = sa + kWpStageA;
+                    const bool fresh = (kc % kWpWinChunks) == 0;
+#pragma unroll 1
+                    for (int L = 0; L < (have_w ? kEmuDigits : 0); ++L) {
+#pragma unroll 1
+                        for (int s = 0; s <= L; ++s) {
+                            const uint64_t ad = smem_desc(sa + s * kWpTileA, 128, 256);
+                            const uint64_t bd = smem_desc(sb + (L - s) * kWpTileB, 128, 256);
+                            mma_bf16(tmem + static_cast<uint32_t>(L * kWpN), ad, bd, idesc,
+                                     (fresh && s == 0) ? 0u : 1u);
+                        }
+                    }
+                    mma_commit(&bar_mma[sidx]);
+                }
+                if ((kc % kWpWinChunks) == kWpWinChunks - 1 || kc == nk - 1) {
+                    // window end: drain the eight levels of this thread's 16 columns
+                    if (!mbar_wait_bounded(&bar_mma[sidx], (it / kWpStages) & 1u)) abort_flag = 1;
+                    __syncthreads();
+                    if (abort_flag) break;
+                    tc_fence_after();
+                    float v[16];
+#pragma unroll
+                    for (int L = 0; L < kEmuDigits; ++L) {
+                        tmem_ld16(tl + static_cast<uint32_t>(L * kWpN), v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            switch (L) {  // compile-time after unrolling
+                                case 0: acc[q] += emu_level<24 + kWpUnit>(v[q]); break;
+                                case 1: acc[q] += emu_level<16 + kWpUnit>(v[q]); break;
+                                case 2: acc[q] += emu_level<8 + kWpUnit>(v[q]); break;
+                                case 3: acc[q] += emu_level<0 + kWpUnit>(v[q]); break;
+                                case 4: acc[q] += emu_level<-8 + kWpUnit>(v[q]); break;
+                                case 5: acc[q] += emu_level<-16 + kWpUnit>(v[q]); break;
+                                case 6: acc[q] += emu_level<-24 + kWpUnit>(v[q]); break;
+                                default: acc[q] += emu_level<-32 + kWpUnit>(v[q]); break;
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncthreads();  // TMEM read before the next window's MMAs overwrite it
+                }
+            }
+            if (abort_flag) break;
+            // Q[row, 32 g + 16 (warp / 4) + q] = 2^(E + E'_c - 54) acc[q]
+            const int64_t drow = r0 + 32 * (warp & 3) + (tid & 31);
+            const int drb = max(rowbits_half[drow - r0], rowbits_half[drow - r0 + kWpM]);
+            if (drow < re) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = kWpN * g + 16 * (warp >> 2) + q;
+                    if (col < n) {
+                        const int cb = __ldg(cbits + col);
+                        Q[drow + int64_t(col) * ldq] =
+                            (drb == 0x7ff || cb == 0x7ff)
+                                ? __longlong_as_double(0x7ff8000000000000ll)
+                                : emu_i64_scaled(acc[q], emu_exponent(drb) + emu_exponent(cb) - 14 - 24 - kWpUnit);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // rowbits_half reused by the next tile
+    }
+    if (abort_flag && tid == 0) report(st, kErrTimeout, 0, -1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kWpTmemCols);
+}
+
+}  // namespace
+
+size_t wprod_scratch_bytes(int n) { return wp_layout(n).total; }
+
+// After a launch_trsm_emu_wellcond on `stream` with this scratch: 1 if the
+// product form ran, 0 if the substitution did, -1 on a CUDA error
+// (synchronizes the stream).
+int wellcond_used_product(const void *scratch, int n, cudaStream_t stream) {
+    const unsigned char *wp = static_cast<const unsigned char *>(scratch) +
+                              round_up(int64_t(trsm_emu_scratch_bytes(n)), 1024);
+    unsigned long long h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, wp + wp_layout(n).norms, sizeof h, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return -1;
+    double nr, nw;
+    memcpy(&nr, &h[0], sizeof nr);
+    memcpy(&nw, &h[1], sizeof nw);
+    return nr * nw <= kWprodMaxCond ? 1 : 0;
+}
+
+cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                                     const double *rinv, double *Q, int64_t ldq, void *scratch,
+                                     DevStatus *st, cudaStream_t stream) {
+    if (n < 1 || n > 256 || m < 1) return cudaErrorInvalidValue;
+    const int n_pad = pad16(n);
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    unsigned char *wp = base + round_up(int64_t(trsm_emu_scratch_bytes(n)), 1024);
+    const WpLayout l = wp_layout(n);
+    unsigned long long *norms = reinterpret_cast<unsigned long long *>(wp + l.norms);
+    int *cbits = reinterpret_cast<int *>(wp + l.cbits);
+    double *W = reinterpret_cast<double *>(wp + l.w);
+    unsigned char *tiles = wp + l.tiles;
+    cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    constexpr int kWarps = 8;
+    const size_t ism = size_t(kWarps) * n_pad * sizeof(double);
+    RQ_LAUNCH(KID_EMU_AUX, stream,
+              k_tri_inverse<<<static_cast<unsigned>(ceil_div(n_pad, kWarps)), 32 * kWarps, ism, stream>>>(
+                  RP, rinv, n, n_pad, W, norms));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int passes = (n + kWpN - 1) / kWpN;
+    RQ_LAUNCH(KID_EMU_AUX, stream,
+              k_wprod_prep<<<passes, 256, 0, stream>>>(W, n, n_pad, norms, cbits, tiles));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t ntiles = ceil_div(m, kWpM);
+    const int64_t grid = std::min<int64_t>(ntiles, 2 * int64_t(grid_sms()));
+    const int64_t chunk = ceil_div(ntiles, grid) * kWpM;
+    const int g = static_cast<int>(ceil_div(m, chunk));
+    const size_t smem = size_t(kWpStages) * kWpStageBytes;
+    cudaFuncSetAttribute(k_wprod_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    RQ_LAUNCH(KID_TRSM_EMU, stream,
+              k_wprod_emu<<<g, kWpThreads, smem, stream>>>(A, lda, m, n, chunk, norms, cbits, tiles, Q,
+                                                           ldq, st));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the substitution form, which runs only when the estimate rejected the product
+    return launch_trsm_emu(A, lda, m, n, RP, rinv, Q, ldq, scratch, st, stream, norms);
+}
+
+}  // namespace rq

@@ -144,15 +144,33 @@ size_t gram_emu_partials_doubles(int n);
 // int64 drains), the diagonal blocks in binary64.  RP/rinv as for
 // launch_trsm_gram (padded factor followed by its row-major copy); scratch
 // holds R's digit tiles (trsm_emu_scratch_bytes).  Q may alias A.
+// skip_if: when non-null, the kernels return at once if the estimate stored
+// there selects the product form (launch_trsm_emu_wellcond).
 cudaError_t launch_trsm_emu(const double *A, int64_t lda, int64_t m, int n, const double *RP,
                             const double *rinv, double *Q, int64_t ldq, void *scratch,
-                            DevStatus *st, cudaStream_t stream);
+                            DevStatus *st, cudaStream_t stream,
+                            const unsigned long long *skip_if = nullptr);
 size_t trsm_emu_scratch_bytes(int n);
-// The 32-column-block form (emu_trsm32.cu) that launch_trsm_emu uses for n > 128.
+// The 32-column-block form (emu_trsm32.cu) that launch_trsm_emu uses for n > 160.
 cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, const double *RP,
                               const double *rinv, double *Q, int64_t ldq, void *scratch,
-                              DevStatus *st, cudaStream_t stream);
+                              DevStatus *st, cudaStream_t stream,
+                              const unsigned long long *skip_if = nullptr);
 size_t trsm_emu32_scratch_bytes(int n);
+// Q = A R^{-1} for a factor expected to be well conditioned (emu_wprod.cu):
+// W = R^{-1} in binary64 and the estimate ||R||_1 ||W||_1; then either the
+// emulated product Q = A W (estimate <= 100) or the substitution form, chosen
+// on the device.  scratch: wellcond_scratch_bytes(n).  Q may alias A.
+cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, int n, const double *RP,
+                                     const double *rinv, double *Q, int64_t ldq, void *scratch,
+                                     DevStatus *st, cudaStream_t stream);
+size_t wprod_scratch_bytes(int n);
+// Which form the last launch_trsm_emu_wellcond with this scratch ran: 1 the
+// product, 0 the substitution, -1 a CUDA error (synchronizes the stream).
+int wellcond_used_product(const void *scratch, int n, cudaStream_t stream);
+inline size_t wellcond_scratch_bytes(int n) {
+    return size_t(round_up(int64_t(trsm_emu_scratch_bytes(n)), 1024)) + wprod_scratch_bytes(n);
+}
 
 // Padded upper factor: RP = triu(R) padded to n_pad with zeros, rinv = 1/diag.
 cudaError_t launch_pad_upper(const double *R, int64_t ldr, int n, double *RP, double *rinv,

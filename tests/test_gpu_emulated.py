@@ -242,3 +242,75 @@ def test_trsm_emulated_in_place_and_ld(rq):
         rq.rclupp_trsm_emulated(X, dev(r), Q=X)
         assert np.array_equal(host(X), ref)
         assert float(buf.t()[m:].abs().max()) == 0.0
+
+
+# ------------------------------- solve by a well-conditioned factor (C3, C7) ---
+
+def _wellcond_r(n, seed, spread=0.1):
+    g = np.random.default_rng(seed)
+    return np.eye(n) + spread * np.triu(g.standard_normal((n, n)), 1) / math.sqrt(n)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (300, 31), (5000, 64), (4097, 100), (2048, 128), (3001, 129),
+                                 (2100, 256), (70001, 200)])
+def test_wellcond_solve_product_against_oracle(rq, m, n):
+    # kappa_1(R) ~ 1.5: the product Q = X R^{-1} runs; against the oracle's
+    # substitution, both within the rounding of R^{-1} (|W| |R| |W|, the
+    # triangular inverse's error) and the digits' 2^-50 of the row and column
+    # maxima
+    g = np.random.default_rng(m + 7 * n)
+    r = _wellcond_r(n, m + n)
+    x = g.standard_normal((m, n)) * np.logspace(-3, 3, m)[:, None]
+    q, form = rq.rclupp_trsm_emulated_wellcond(dev(x), dev(r))
+    assert form == 1
+    q = host(q)
+    q_ref = oracle.trsm(x, r)
+    w = np.abs(np.linalg.inv(r))
+    tol = (16 * n * U * (np.abs(x) @ (w @ np.abs(r) @ w))
+           + (n + 128) * 2.0 ** -50 * np.max(np.abs(x), axis=1)[:, None] * np.max(w, axis=0)[None, :])
+    assert np.all(np.abs(q - q_ref) <= tol), float(np.max(np.abs(q - q_ref) / tol))
+    assert np.linalg.norm(q @ r - x) <= 100 * n * U * np.linalg.norm(np.abs(q) @ np.abs(r))
+
+
+def test_wellcond_solve_exact_on_integers(rq):
+    # R = I + superdiagonal of ones: R^{-1} has entries (-1)^(j - i) above the
+    # diagonal (kappa_1 = 2n = 80), X = Q0 R with small integers: every digit
+    # product and sum is exact, so Q = Q0
+    n, m = 40, 3000
+    r = np.eye(n) + np.diag(np.ones(n - 1), 1)
+    q0 = np.random.default_rng(3).integers(-9, 10, size=(m, n)).astype(np.float64)
+    x = q0 @ r
+    q, form = rq.rclupp_trsm_emulated_wellcond(dev(x), dev(r))
+    assert form == 1 and np.array_equal(host(q), q0)
+
+
+def test_wellcond_solve_falls_back_to_substitution(rq):
+    # an ill-conditioned factor (kappa_1 far above 100) takes the emulated
+    # substitution, bit for bit the result of rclupp_trsm_emulated
+    n, m = 96, 5000
+    g = np.random.default_rng(11)
+    r = np.triu(g.standard_normal((n, n))) / math.sqrt(n) + np.diag(np.logspace(0, -6, n))
+    x = g.standard_normal((m, n))
+    q, form = rq.rclupp_trsm_emulated_wellcond(dev(x), dev(r))
+    assert form == 0
+    assert torch.equal(q, rq.rclupp_trsm_emulated(dev(x), dev(r)))
+
+
+def test_wellcond_solve_in_place_and_nonfinite(rq):
+    n, m = 150, 4001
+    r = _wellcond_r(n, 5)
+    x = np.random.default_rng(6).standard_normal((m, n))
+    ref, form = rq.rclupp_trsm_emulated_wellcond(dev(x), dev(r))
+    assert form == 1
+    for ld in (4001, 4008):
+        buf = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+        X = buf.t()[:m]
+        X.copy_(dev(x))
+        rq.rclupp_trsm_emulated_wellcond(X, dev(r), Q=X)
+        assert torch.equal(X, ref)
+        assert float(buf.t()[m:].abs().max()) == 0.0
+    xn = x.copy()
+    xn[17, 3] = np.inf
+    q, _ = rq.rclupp_trsm_emulated_wellcond(dev(xn), dev(r))
+    q = host(q)
+    assert np.all(np.isnan(q[17])) and np.all(np.isfinite(np.delete(q, 17, axis=0)))
