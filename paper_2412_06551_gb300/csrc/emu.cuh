@@ -9,6 +9,8 @@
 // dropped ones are below 2^-61 of the scale.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "common.cuh"
@@ -59,6 +61,57 @@ __device__ __forceinline__ void emu_digits_n(double x, int E, int (&d)[ND]) {
     }
     const int top = static_cast<int>((ND > 4 ? (hi >> (8 * (ND - 5))) : (lo >> (8 * (ND - 1)))) + c);
     d[0] = neg ? -top : top;
+}
+
+// The same digits for two values at once, as packed bf16 pairs ready for a
+// K-major tile: w[s] holds digit s of x0 (low half) and of x1 (high half).
+// Adding B = sum_{q < ND-1} 128 256^q to |F| gives G, whose bytes below the
+// top are the balanced digits plus 128 (the carries of the digit-by-digit
+// form happen in the addition) and whose top part is the top digit; a digit
+// becomes an exact binary32 integer by the 1.5 * 2^23 trick, takes the sign
+// of x by one XOR, and two of them are packed by one bf16x2 conversion.  A
+// zero digit of a negative value is -0, which adds like +0.
+template <int ND>
+__device__ __forceinline__ unsigned long long emu_biased_magnitude(double x, int E, uint32_t &sign) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int e = static_cast<int>((b >> 52) & 0x7ff);
+    unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+    if (e != 0) M |= 1ull << 52;
+    const int sh = (e != 0 ? e : 1) - 1076 + 8 * ND - E;
+    unsigned long long F;
+    if (sh >= 0)
+        F = M << (sh & 15);
+    else if (sh > -64)
+        F = (M + (1ull << (-sh - 1))) >> (-sh);
+    else
+        F = 0ull;
+    sign = static_cast<uint32_t>(b >> 63) << 31;
+    constexpr unsigned long long kBias = 0x0080808080808080ull >> (8 * (8 - ND));
+    return F + kBias;
+}
+
+template <int ND>
+__device__ __forceinline__ void emu_digits2_packed(double x0, double x1, int E, uint32_t (&w)[ND]) {
+    uint32_t s0, s1;
+    const unsigned long long g0 = emu_biased_magnitude<ND>(x0, E, s0);
+    const unsigned long long g1 = emu_biased_magnitude<ND>(x1, E, s1);
+#pragma unroll
+    for (int s = 0; s < ND; ++s) {
+        const int q = ND - 1 - s;  // byte of G
+        const uint32_t v0 = static_cast<uint32_t>(g0 >> (8 * q)), v1 = static_cast<uint32_t>(g1 >> (8 * q));
+        float f0, f1;
+        if (q == ND - 1) {  // the top digit, 0 .. 128, no bias
+            f0 = __int_as_float(0x4B400000 + static_cast<int>(v0)) - 12582912.0f;
+            f1 = __int_as_float(0x4B400000 + static_cast<int>(v1)) - 12582912.0f;
+        } else {
+            f0 = __int_as_float(0x4B400000 + static_cast<int>(v0 & 0xffu)) - 12583040.0f;
+            f1 = __int_as_float(0x4B400000 + static_cast<int>(v1 & 0xffu)) - 12583040.0f;
+        }
+        f0 = __int_as_float(__float_as_int(f0) ^ static_cast<int>(s0));
+        f1 = __int_as_float(__float_as_int(f1) ^ static_cast<int>(s1));
+        const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+        w[s] = *reinterpret_cast<const uint32_t *>(&p);
+    }
 }
 
 // The eight digits of the emulated Gram and solve (F = round(x 2^(63 - E))).

@@ -185,13 +185,11 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             // two rows at a time: one 32-bit word (two bf16) per digit
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
-                int d0[kEmuDigits], d1[kEmuDigits];
-                emu_digits(xv[ts][t], E, d0);
-                emu_digits(xv[ts][t + 1], E, d1);
+                uint32_t w[kEmuDigits];
+                emu_digits2_packed<kEmuDigits>(xv[ts][t], xv[ts][t + 1], E, w);
 #pragma unroll
                 for (int s = 0; s < kEmuDigits; ++s)
-                    *reinterpret_cast<uint32_t *>(base + s * tbytes + emu_off(cc, kb * 8 + t)) =
-                        small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                    *reinterpret_cast<uint32_t *>(base + s * tbytes + emu_off(cc, kb * 8 + t)) = w[s];
             }
         }
         fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core

@@ -162,12 +162,10 @@ __global__ void __launch_bounds__(kTeThreads, kTeCtasPerSm)
                     uint32_t w[kEmuDigits][2];
 #pragma unroll
                     for (int t = 0; t < 4; t += 2) {
-                        int d0[kEmuDigits], d1[kEmuDigits];
-                        emu_digits(xv[4 * h + t], E, d0);
-                        emu_digits(xv[4 * h + t + 1], E, d1);
+                        uint32_t wp[kEmuDigits];
+                        emu_digits2_packed<kEmuDigits>(xv[4 * h + t], xv[4 * h + t + 1], E, wp);
 #pragma unroll
-                        for (int s = 0; s < kEmuDigits; ++s)
-                            w[s][t >> 1] = small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                        for (int s = 0; s < kEmuDigits; ++s) w[s][t >> 1] = wp[s];
                     }
 #pragma unroll
                     for (int s = 0; s < kEmuDigits; ++s)

@@ -187,14 +187,12 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                     // two rows at a time: one 32-bit word (two bf16) per digit
 #pragma unroll
                     for (int t = 0; t < 8; t += 2) {
-                        int d0[kEmuDigits], d1[kEmuDigits];
-                        emu_digits(xv[u][t], E, d0);
-                        emu_digits(xv[u][t + 1], E, d1);
+                        uint32_t w[kEmuDigits];
+                        emu_digits2_packed<kEmuDigits>(xv[u][t], xv[u][t + 1], E, w);
 #pragma unroll
                         for (int s = 0; s < kEmuDigits; ++s)
                             *reinterpret_cast<uint32_t *>(stage + s * kTeTileA +
-                                                          emu_off(srow, 8 * skg + t)) =
-                                small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                                                          emu_off(srow, 8 * skg + t)) = w[s];
                     }
                 }
                 fence_proxy_async_smem();

@@ -244,13 +244,11 @@ __global__ void __launch_bounds__(kWpThreads, 2)
                 // digit tile at a time
 #pragma unroll
                 for (int t = 0; t < 8; t += 2) {
-                    int d0[kEmuDigits], d1[kEmuDigits];
-                    emu_digits(xv[t], E, d0);
-                    emu_digits(xv[t + 1], E, d1);
+                    uint32_t w[kEmuDigits];
+                    emu_digits2_packed<kEmuDigits>(xv[t], xv[t + 1], E, w);
 #pragma unroll
                     for (int s = 0; s < kEmuDigits; ++s)
-                        *reinterpret_cast<uint32_t *>(stage + s * kWpTileA + wp_off(r, 8 * h + t)) =
-                            small_int_bf16(d0[s]) | (small_int_bf16(d1[s]) << 16);
+                        *reinterpret_cast<uint32_t *>(stage + s * kWpTileA + wp_off(r, 8 * h + t)) = w[s];
                 }
                 fence_proxy_async_smem();
                 __syncthreads();

@@ -426,14 +426,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int E = expB[xc];
             uint32_t w[kDgDigits][2];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                int d[kDgDigits];
-                emu_digits_n<kDgDigits>(xv[t], E, d);
+            for (int t = 0; t < 4; t += 2) {
+                uint32_t wp[kDgDigits];
+                emu_digits2_packed<kDgDigits>(xv[t], xv[t + 1], E, wp);
 #pragma unroll
-                for (int q = 0; q < kDgDigits; ++q) {
-                    const uint32_t h = small_int_bf16(d[q]) << (16 * (t & 1));
-                    w[q][t >> 1] = (t & 1) ? (w[q][t >> 1] | h) : h;
-                }
+                for (int q = 0; q < kDgDigits; ++q) w[q][t >> 1] = wp[q];
             }
             const uint32_t off = static_cast<uint32_t>(((xc >> 3) * (kTcBK / 8) + (xq >> 1)) * 128 +
                                                        (xc & 7) * 16 + (xq & 1) * 8);
