@@ -1045,7 +1045,13 @@ rclupp_status_t rclupp_sketch_rows(rclupp_handle_t h, int64_t m, int64_t n, cons
     Bufs b = prepare(h, m, int(n), o.s, false, &st);
     if (st != RCLUPP_OK) return st;
     cudaError_t e;
-    if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
+    // the emulated tiers sketch at the digit tier, as their drivers do
+    const bool digits = o.prec == RCLUPP_PREC_SKETCH_DIGITS || o.prec == RCLUPP_PREC_EMULATED ||
+                        o.prec == RCLUPP_PREC_EMULATED_ALL;
+    if (digits && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
+        e = launch_sketch_digits(A, lda, m, int(n), unit_lower, o.s, o.seed, Y, ldy, b.part, h->d_status,
+                                 h->stream, row0);
+    else if (o.prec != RCLUPP_PREC_FP64 && o.kind == RCLUPP_SKETCH_GAUSSIAN && !o.S)
         e = launch_sketch_tc(A, lda, m, int(n), unit_lower, o.s, o.seed,
                              o.prec == RCLUPP_PREC_SKETCH_FP32 ? 3 : 1, Y, ldy, b.part, h->d_status,
                              h->stream, row0);

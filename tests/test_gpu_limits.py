@@ -76,7 +76,7 @@ def test_tensor_core_sketch_at_the_largest_s(rq, prec, nterms):
     x = synth.svd_matrix(m, n, 1e2, 9)
     y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=prec))
     ref = oracle.sketch_bf16(s, seed, nterms, x)
-    S = oracle.bf16_sketch_z(s, m, seed) / np.sqrt(s)
+    S = oracle.tier_sketch_z(s, m, seed) / np.sqrt(s)
     mag = (1 + 2.0 ** -7) * (np.abs(S) @ np.abs(x))
     assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
 

@@ -55,7 +55,7 @@ def test_tc_sketch_matches_definition(rq, prec, nterms, m, n, s):
     seed = 1234 + m
     y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=prec))
     ref = oracle.sketch_bf16(s, seed, nterms, x)
-    S = oracle.bf16_sketch_z(s, m, seed) / np.sqrt(s)  # z_b / sqrt(s) in binary64
+    S = oracle.tier_sketch_z(s, m, seed) / np.sqrt(s)  # z_b / sqrt(s) in binary64
     mag = (1 + 2.0 ** -7) * (np.abs(S) @ np.abs(x))
     assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
     # and close to the same S times the unrounded X: X's rounding (2^-9 for
@@ -84,7 +84,7 @@ def test_tc_sketch_row_block_draws_the_global_entries(rq, row0):
     m, n, s, seed = 300, 5, 64, 17
     x = synth.integer_matrix(m, n, row0 + 1)
     y = host(rq.rclupp_sketch(dev(x), s=s, seed=seed, prec=1, row0=row0))
-    z = oracle.bf16_sketch_z(s, row0 + m, seed)[:, row0:]
+    z = oracle.tier_sketch_z(s, row0 + m, seed)[:, row0:]
     assert np.array_equal(y, (z @ x) * (1.0 / np.sqrt(s)))
 
 
@@ -95,7 +95,7 @@ def test_tc_sketch_unit_lower(rq):
     M = oracle.unit_lower(lu)
     y = host(rq.rclupp_sketch(dev(lu), s=s, seed=4, prec=2, unit_lower=True))
     ref = oracle.sketch_bf16(s, 4, 3, M)
-    S = oracle.bf16_sketch_z(s, m, 4) / np.sqrt(s)
+    S = oracle.tier_sketch_z(s, m, 4) / np.sqrt(s)
     mag = 1.02 * (np.abs(S) @ np.abs(M))
     assert np.all(np.abs(y - ref) <= gamma32(m) * mag + 1e-300)
 
