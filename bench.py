@@ -133,7 +133,7 @@ def parse():
                    help="also report orthogonality/residual at kappa 1e10 and 1e15")
     p.add_argument("--case", choices=["trsm_gram", "trsm", "gram", "gram_emu", "trsm_emu", "sketch_gauss",
                                       "sketch_sparse", "sketch_srht", "precond", "lu", "rclupp",
-                                      "dfma_peak"],
+                                      "dfma_peak", "trsm_wellcond"],
                    help="run one kernel class on an m x n matrix instead (profiler captures)")
     p.add_argument("--workload", choices=["side_by_side", "precision", "batched", "small",
                                           "large_sparse"],
@@ -897,6 +897,8 @@ def run_case(args):
             rq.rclupp_gram_emulated(X)
         elif args.case == "trsm_emu":
             rq.rclupp_trsm_emulated(X, R)
+        elif args.case == "trsm_wellcond":
+            rq.rclupp_trsm_emulated_wellcond(X, R)
         elif args.case == "sketch_gauss":
             rq.rclupp_sketch(X, s=2 * n, seed=1, prec=args.prec)
         elif args.case == "sketch_sparse":
@@ -923,7 +925,7 @@ def run_case(args):
     # (n(n+1)/2 dot products of length m), 2 s m n per sketch, m n^2 - n^3/3
     # per tall LU
     flops = {"trsm_gram": 2.0 * m * n * n, "trsm": 1.0 * m * n * n, "gram": 1.0 * m * n * n,
-             "gram_emu": 1.0 * m * n * n, "trsm_emu": 1.0 * m * n * n,
+             "gram_emu": 1.0 * m * n * n, "trsm_emu": 1.0 * m * n * n, "trsm_wellcond": 1.0 * m * n * n,
              "sketch_gauss": 4.0 * m * n * n, "lu": m * n * n - n ** 3 / 3.0}.get(args.case)
     total = sum(v[1] for v in prof.values()) / args.reps
     line = {"case": args.case, "m": m, "n": n, "reps": args.reps, "ms_per_call": total,
