@@ -308,7 +308,8 @@ def test_wellcond_solve_in_place_and_nonfinite(rq):
         X.copy_(dev(x))
         rq.rclupp_trsm_emulated_wellcond(X, dev(r), Q=X)
         assert torch.equal(X, ref)
-        assert float(buf.t()[m:].abs().max()) == 0.0
+        if ld > m:
+            assert float(buf.t()[m:].abs().max()) == 0.0
     xn = x.copy()
     xn[17, 3] = np.inf
     q, _ = rq.rclupp_trsm_emulated_wellcond(dev(xn), dev(r))
