@@ -18,9 +18,12 @@ int num_sms();
 // leading dimension ld) with a box of box_rows x box_cols.  Returns false
 // when the matrix does not meet TMA's alignment rules (16-byte base address,
 // 16-byte multiple stride) or the encoder is unavailable; callers then use
-// plain loads.
+// plain loads.  With swizzle128 (box_rows = 16, one 128-byte line per
+// column) the box lands with the 128-byte swizzle: the 16-byte chunk j of
+// column c's line is stored at chunk j ^ (c % 8), so that eight threads
+// reading chunk j of eight neighbouring columns hit distinct banks.
 bool make_tma_map(CUtensorMap *map, const double *A, int64_t rows, int64_t cols, int64_t ld,
-                  int box_rows, int box_cols);
+                  int box_rows, int box_cols, bool swizzle128 = false);
 
 // ---- tall passes (tall.cu) ----
 struct TallPlan {

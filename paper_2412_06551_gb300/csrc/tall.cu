@@ -64,20 +64,22 @@ static EncodeTiledFn encode_fn() {
 }
 
 bool make_tma_map(CUtensorMap *map, const double *A, int64_t rows, int64_t cols, int64_t ld,
-                  int box_rows, int box_cols) {
+                  int box_rows, int box_cols, bool swizzle128) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     if (reinterpret_cast<uintptr_t>(A) % 16 != 0) return false;
     if ((ld * 8) % 16 != 0 || ld * 8 >= (int64_t(1) << 40)) return false;
     if ((box_rows * 8) % 16 != 0 || box_rows > 256 || box_cols > 256 || box_rows < 1 || box_cols < 1)
         return false;
+    if (swizzle128 && box_rows * 8 != 128) return false;  // one 128-byte swizzle span per column
     if (rows >= (int64_t(1) << 32) || cols >= (int64_t(1) << 32)) return false;
     cuuint64_t gdim[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
     cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld * 8)};
     cuuint32_t box[2] = {static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_cols)};
     cuuint32_t es[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(A), gdim, gstride, box,
-              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
