@@ -19,10 +19,11 @@
 //
 // Tiles: a CTA owns 128 rows (columns j of A) x 64 columns (k of A) of G and
 // a contiguous chunk of rows of A (split-K).  Its eight 128 x 64 fp32
-// accumulators take the 512 TMEM columns.  Per 32 rows of A the 512 threads
-// split the block into digits (K-major 8 x 8 bf16 core matrices in shared
-// memory), one thread issues the 36 x 2 MMAs (kind::f16, M=128, N=64, K=16)
-// and commits to the stage's mbarrier; stages rotate.
+// accumulators take the 512 TMEM columns.  Per 32 rows of A the 16 producer
+// warps split the block into digits (K-major 8 x 8 bf16 core matrices in
+// shared memory) while the control warp issues the previous blocks' 36 x 2
+// MMAs (kind::f16, M=128, N=64, K=16); mbarriers hand the stages back and
+// forth (see k_gram_emu).
 #include <algorithm>
 #include <climits>
 
@@ -34,11 +35,12 @@
 namespace rq {
 namespace {
 
-constexpr int kEmuThreads = 512;
+constexpr int kEmuProducers = 512;                 // 16 producer warps
+constexpr int kEmuThreads = kEmuProducers + 32;   // plus the control warp
 constexpr int kEmuWinSteps = 4; // stages per exact window (128 rows)
 constexpr int kEmuM = 128;      // rows of G per tile (columns j of A)
 constexpr int kEmuN = 64;       // columns of G per tile (columns k of A)
-constexpr int kEmuMaxStages = 3;  // 3 stages of j digits only, or 2 with k digits
+constexpr int kEmuMaxStages = 2;  // one stage per producer group
 constexpr int kTileA = kEmuM * kEmuBK * 2;  // bytes of one digit tile of the j columns
 constexpr int kTileB = kEmuN * kEmuBK * 2;  // ... of the k columns
 constexpr int kEmuStageBytes = kEmuDigits * (kTileA + kTileB);
@@ -46,7 +48,8 @@ constexpr int kEmuTmemCols = 512;
 constexpr int kEmuSlot = kEmuM * kEmuN;  // elements of one per-CTA partial
 constexpr int kEmuFlushWindows = 16;     // int64 drains between binary64 flushes
 constexpr int kEmuUnit = 12;             // drain units: 2^-(24 + 12) of level 0
-constexpr int kEmuTaskSlots = 2;         // digit tasks per thread and stage (A: 1, B: 1 more)
+constexpr int kEmuGroups = 2;            // producer groups taking alternate blocks
+constexpr int kEmuGroupWarps = kEmuProducers / 32 / kEmuGroups;
 
 // Tile t of the upper triangle of G: rows [128 jb, +128), columns [64 kb, +64),
 // kb >= 2 jb, enumerated jb-major.
@@ -85,30 +88,59 @@ __global__ void k_col_exponent(const double *__restrict__ A, int64_t lda, int64_
     if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(colbits + j, e);
 }
 
+// Warp-specialised: two groups of 8 producer warps take alternate 32-row
+// blocks of A, split each into digit tiles in the block's stage and arrive on
+// the stage's full barrier (one arrival per warp); the control warp's lane 0
+// waits for it,
+// issues the block's 72 MMAs and commits them to the stage's empty barrier.
+// A window's eight accumulators are drained by the producers after they
+// have filled the next block (so that its split overlaps the window's last
+// MMAs); the control lane starts a window only when the previous one is
+// drained (tmem_empty).  No block-wide barrier inside the loop.
+struct GePipe {
+    uint64_t full[kEmuMaxStages], empty[kEmuMaxStages];
+    uint64_t win_done;    // a window's MMAs are complete
+    uint64_t tmem_empty;  // its accumulators are drained
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+
+__device__ __forceinline__ bool ge_wait(GePipe &pp, uint64_t *bar, uint32_t parity) {
+    if (*reinterpret_cast<volatile int *>(&pp.abort_flag)) return false;
+    if (mbar_wait_bounded(bar, parity)) return true;
+    *reinterpret_cast<volatile int *>(&pp.abort_flag) = 1;
+    return false;
+}
+
 __global__ void __launch_bounds__(kEmuThreads, 1)
     k_gram_emu(const double *__restrict__ A, int64_t lda, int64_t m, int n,
                const int *__restrict__ colbits, int64_t chunk, double *__restrict__ part,
                DevStatus *st) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mma[kEmuMaxStages];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
+    __shared__ GePipe pp;
     __shared__ int expA[kEmuM], expB[kEmuN];
 
     int j0, k0;
     emu_tile(blockIdx.x, n, j0, k0);
     const bool b_in_a = (k0 >= j0) && (k0 + kEmuN <= j0 + kEmuM);
-    // the k columns inside the j columns need no digits of their own, which
-    // leaves room for a third stage
-    const int nst = b_in_a ? 3 : 2;
+    // one stage per producer group (block ks in stage ks % 2, so that each
+    // stage's empty barrier is waited on by one group, phase after phase);
+    // the k columns inside the j columns need no digits of their own
+    constexpr int nst = kEmuGroups;
     const int stage_bytes = b_in_a ? kEmuDigits * kTileA : kEmuStageBytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool control = warp == kEmuProducers / 32;
 
-    if (warp == 0) tmem_alloc(&tmem_slot, kEmuTmemCols);
+    if (control) tmem_alloc(&pp.tmem_slot, kEmuTmemCols);
     if (tid == 0) {
-        for (int s = 0; s < kEmuMaxStages; ++s) mbar_init(&bar_mma[s], 1);
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&pp.full[s], kEmuGroupWarps);
+            mbar_init(&pp.empty[s], 1);
+        }
+        mbar_init(&pp.win_done, 1);
+        mbar_init(&pp.tmem_empty, kEmuProducers / 32);
         fence_mbar_init();
-        abort_flag = 0;
+        pp.abort_flag = 0;
     }
     for (int c = tid; c < kEmuM; c += kEmuThreads)
         expA[c] = (j0 + c < n) ? emu_exponent(colbits[j0 + c]) : 0;
@@ -117,119 +149,73 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
-    const uint32_t smem_base = smem_u32(smem_raw);
-
-    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows j of the tile),
-    // columns 16 (warp / 4) .. +15
-    const int lane_base = 32 * (warp & 3);
-    const int cgrp = warp >> 2;
-    long long acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0;
-    // this thread's elements of the CTA's binary64 partial, [col][row]
-    double *mine = part + (size_t(blockIdx.x) * gridDim.y + blockIdx.y) * kEmuSlot +
-                   size_t(16 * cgrp) * kEmuM + lane_base + lane;
-    int windows = 0;
-    bool flushed = false;
-    auto flush = [&]() {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const double v = static_cast<double>(acc[q]);
-            mine[q * kEmuM] = flushed ? mine[q * kEmuM] + v : v;
-            acc[q] = 0;
-        }
-        flushed = true;
-    };
+    const uint32_t tmem = pp.tmem_slot;
 
     const int64_t rb = int64_t(blockIdx.y) * chunk;
     const int64_t re = std::min<int64_t>(m, rb + chunk);
     const int nsteps = re > rb ? static_cast<int>(ceil_div(re - rb, kEmuBK)) : 0;
-    const int ncolsB = b_in_a ? 0 : kEmuN;
-    const int ntasks = (kEmuM + ncolsB) * (kEmuBK / 8);
-    // Load block ks (32 rows) and split it into digits in its stage, once the
-    // MMAs that last read that stage are done.  Runs while the tensor core
-    // works on block ks - 1, also across the drain at a window's end.
-    auto prepare = [&](int ks) {
-        const int sidx = ks % nst;
-        unsigned char *stage = smem_raw + sidx * stage_bytes;
-        const int64_t r0 = rb + int64_t(ks) * kEmuBK;
-        // (1) this thread's blocks of 8 rows x 1 column (in flight during the wait)
-        double xv[kEmuTaskSlots][8];
-#pragma unroll
-        for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
-            const int task = tid + ts * kEmuThreads;
-            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
-            const int col = c < kEmuM ? j0 + c : k0 + (c - kEmuM);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int64_t row = r0 + kb * 8 + t;
-                xv[ts][t] = (task < ntasks && row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
-            }
-        }
-        if (ks >= nst &&
-            !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst - 1) & 1)))
-            abort_flag = 1;
-        // (2) digits, stored as K-major operand tiles
-#pragma unroll
-        for (int ts = 0; ts < kEmuTaskSlots; ++ts) {
-            const int task = tid + ts * kEmuThreads;
-            if (task >= ntasks) break;
-            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
-            const bool isA = c < kEmuM;
-            const int cc = isA ? c : c - kEmuM;
-            const int E = isA ? expA[cc] : expB[cc];
-            unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
-            const int tbytes = isA ? kTileA : kTileB;
-            // two rows at a time: one 32-bit word (two bf16) per digit
-#pragma unroll
-            for (int t = 0; t < 8; t += 2) {
-                uint32_t w[kEmuDigits];
-                emu_digits2_packed<kEmuDigits>(xv[ts][t], xv[ts][t + 1], E, w);
-#pragma unroll
-                for (int s = 0; s < kEmuDigits; ++s)
-                    *reinterpret_cast<uint32_t *>(base + s * tbytes + emu_off(cc, kb * 8 + t)) = w[s];
-            }
-        }
-        fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
-    };
-    if (nsteps > 0) prepare(0);
-    for (int ks = 0; ks < nsteps; ++ks) {
-        const int sidx = ks % nst;
-        // block ks is in its stage; the previous window's drain is complete
-        __syncthreads();
-        if (abort_flag) break;
-        // (3) one thread issues the level products of this block
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t sa = smem_base + sidx * stage_bytes;
-            const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128
-                                       : sa + kEmuDigits * kTileA;
-            const uint32_t tb = b_in_a ? kTileA : kTileB;
-            const bool fresh = (ks % kEmuWinSteps) == 0;
+    int committed = -1;  // the control thread's last commit
+
+    if (control) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
+            for (int ks = 0; ks < nsteps; ++ks) {
+                const int s = ks % nst;
+                const bool fresh = (ks % kEmuWinSteps) == 0;
+                if (fresh && ks > 0 &&
+                    !ge_wait(pp, &pp.tmem_empty, static_cast<uint32_t>((ks / kEmuWinSteps - 1) & 1)))
+                    break;
+                if (!ge_wait(pp, &pp.full[s], static_cast<uint32_t>((ks / nst) & 1))) break;
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem_raw + s * stage_bytes);
+                const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128
+                                           : sa + kEmuDigits * kTileA;
+                const uint32_t tb = b_in_a ? kTileA : kTileB;
 #pragma unroll 1
-            for (int L = 0; L < kEmuDigits; ++L) {
+                for (int L = 0; L < kEmuDigits; ++L) {
 #pragma unroll 1
-                for (int s = 0; s <= L; ++s) {
-                    const int t = L - s;
+                    for (int sd = 0; sd <= L; ++sd) {
+                        const int t = L - sd;
 #pragma unroll
-                    for (int kk = 0; kk < kEmuBK / 16; ++kk) {
-                        const uint64_t ad = smem_desc(sa + s * kTileA + kk * 256, 128, (kEmuBK / 8) * 128);
-                        const uint64_t bd = smem_desc(sb + t * tb + kk * 256, 128, (kEmuBK / 8) * 128);
-                        const uint32_t accum = (fresh && s == 0 && kk == 0) ? 0u : 1u;
-                        mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN), ad, bd, idesc, accum);
+                        for (int kk = 0; kk < kEmuBK / 16; ++kk) {
+                            const uint64_t ad = smem_desc(sa + sd * kTileA + kk * 256, 128, (kEmuBK / 8) * 128);
+                            const uint64_t bd = smem_desc(sb + t * tb + kk * 256, 128, (kEmuBK / 8) * 128);
+                            mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN), ad, bd, idesc,
+                                     (fresh && sd == 0 && kk == 0) ? 0u : 1u);
+                        }
                     }
                 }
+                mma_commit(&pp.empty[s]);
+                if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) mma_commit(&pp.win_done);
+                committed = ks;
             }
-            mma_commit(&bar_mma[sidx]);
         }
-        // the next block's digits while the tensor core works on this one
-        if (ks + 1 < nsteps) prepare(ks + 1);
-        // (4) end of a window: drain the eight level accumulators
-        if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) {
-            if (!mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>((ks / nst) & 1)))
-                abort_flag = 1;
+    } else {
+        // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows j of the
+        // tile), columns 16 (warp / 4) .. +15
+        const int lane_base = 32 * (warp & 3);
+        const int cgrp = warp >> 2;
+        long long acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0;
+        // this thread's elements of the CTA's binary64 partial, [col][row]
+        double *mine = part + (size_t(blockIdx.x) * gridDim.y + blockIdx.y) * kEmuSlot +
+                       size_t(16 * cgrp) * kEmuM + lane_base + lane;
+        int windows = 0;
+        bool flushed = false;
+        auto flush = [&]() {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const double v = static_cast<double>(acc[q]);
+                mine[q * kEmuM] = flushed ? mine[q * kEmuM] + v : v;
+                acc[q] = 0;
+            }
+            flushed = true;
+        };
+        // window w: its MMAs are done; add the eight levels into int64 and
+        // release TMEM (every producer warp drains every window, in order)
+        auto drain = [&](int w) -> bool {
+            if (!ge_wait(pp, &pp.win_done, static_cast<uint32_t>(w & 1))) return false;
             tc_fence_after();
             const uint32_t tl = tmem + (static_cast<uint32_t>(lane_base) << 16) +
                                 static_cast<uint32_t>(16 * cgrp);
@@ -251,22 +237,93 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pp.tmem_empty);
             if (++windows == kEmuFlushWindows) {
                 flush();
                 windows = 0;
             }
-            tc_fence_before();  // the next iteration's barrier orders these reads before its MMAs
+            return true;
+        };
+        const int ncolsB = b_in_a ? 0 : kEmuN;
+        const int ntasks = (kEmuM + ncolsB) * (kEmuBK / 8);
+        // the two groups of eight producer warps take alternate blocks, so that
+        // one group's loads are in flight while the other splits
+        const int grp = warp / kEmuGroupWarps;
+        const int gtid = tid % (kEmuGroupWarps * 32);
+        constexpr int kG = kEmuGroupWarps * 32;
+        // split this thread's task (8 rows x 1 column) held in x into the stage
+        auto split = [&](unsigned char *stage, int task, const double (&x)[8]) {
+            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
+            const bool isA = c < kEmuM;
+            const int cc = isA ? c : c - kEmuM;
+            const int E = isA ? expA[cc] : expB[cc];
+            unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
+            const int tbytes = isA ? kTileA : kTileB;
+            // two rows at a time: one 32-bit word (two bf16) per digit
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                uint32_t w[kEmuDigits];
+                emu_digits2_packed<kEmuDigits>(x[t], x[t + 1], E, w);
+#pragma unroll
+                for (int sd = 0; sd < kEmuDigits; ++sd)
+                    *reinterpret_cast<uint32_t *>(base + sd * tbytes + emu_off(cc, kb * 8 + t)) = w[sd];
+            }
+        };
+        auto load = [&](int64_t r0, int task, double (&x)[8]) {
+            const int kb = task % (kEmuBK / 8), c = task / (kEmuBK / 8);
+            const int col = c < kEmuM ? j0 + c : k0 + (c - kEmuM);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int64_t row = r0 + kb * 8 + t;
+                x[t] = (task < ntasks && row < re && col < n) ? A[row + int64_t(col) * lda] : 0.0;
+            }
+        };
+        bool ok = true;
+        int next_w = 0;  // the next window this warp drains
+        for (int ks = grp; ks < nsteps && ok; ks += kEmuGroups) {
+            const int s = ks % nst;
+            unsigned char *stage = smem_raw + s * stage_bytes;
+            const int64_t r0 = rb + int64_t(ks) * kEmuBK;
+            // (1) this thread's first two blocks of 8 rows x 1 column (in
+            // flight during the wait); a third, for the k columns outside the
+            // j columns, after them
+            double x0[8], x1[8];
+            load(r0, gtid, x0);
+            load(r0, gtid + kG, x1);
+            // the MMAs that last read this stage are done
+            if (ks >= nst && !ge_wait(pp, &pp.empty[s], static_cast<uint32_t>((ks / nst - 1) & 1))) break;
+            // (2) digits, stored as K-major operand tiles
+            split(stage, gtid, x0);
+            if (gtid + kG < ntasks) split(stage, gtid + kG, x1);
+            if (gtid + 2 * kG < ntasks) {
+                load(r0, gtid + 2 * kG, x0);
+                split(stage, gtid + 2 * kG, x0);
+            }
+            fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pp.full[s]);
+            // (3) the window that ended before this block
+            if (kEmuWinSteps * next_w + kEmuWinSteps - 1 < ks) {
+                ok = drain(next_w);
+                ++next_w;
+            }
         }
+        // the windows left (the last one may be short)
+        const int nwin = static_cast<int>(ceil_div(nsteps, kEmuWinSteps));
+        for (; ok && next_w < nwin; ++next_w) ok = drain(next_w);
+        if (ok && nsteps > 0) flush();
     }
     __syncthreads();
-    if (abort_flag) {
+    if (*reinterpret_cast<volatile int *>(&pp.abort_flag)) {
         if (tid == 0) report(st, kErrTimeout, 0, -1);
-    } else {
-        flush();
+        if (control && lane == 0 && committed >= 0)
+            (void)mbar_wait_bounded(&pp.empty[committed % nst], static_cast<uint32_t>((committed / nst) & 1));
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kEmuTmemCols);
+    if (control) tmem_dealloc(tmem, kEmuTmemCols);
 }
 
 // G[j][k] = G[k][j] = 2^(E_j + E_k - 50) times the sum over the tile's CTAs
@@ -328,7 +385,7 @@ cudaError_t launch_gram_emu(const double *A, int64_t lda, int64_t m, int n, doub
     const dim3 gx(n, static_cast<unsigned>(ceil_div(m, cchunk)));
     RQ_LAUNCH(KID_EMU_AUX, stream, k_col_exponent<<<gx, 256, 0, stream>>>(A, lda, m, cchunk, colbits));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t smem = std::max(size_t(2) * kEmuStageBytes, size_t(3) * kEmuDigits * kTileA);
+    const size_t smem = size_t(kEmuMaxStages) * kEmuStageBytes;
     cudaFuncSetAttribute(k_gram_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     RQ_LAUNCH(KID_GRAM_EMU, stream,
               k_gram_emu<<<dim3(tiles, nsplit), kEmuThreads, smem, stream>>>(

@@ -54,6 +54,7 @@ namespace rq {
 namespace {
 
 constexpr int kSkProducers = 512;              // producer threads of the sketch kernels
+constexpr int kSkWarps = kSkProducers / 32;     // producer warps (one barrier arrival each)
 constexpr int kTcThreads = kSkProducers + 32;   // plus one control warp
 constexpr int kSkMaxStages = 4;
 constexpr int kTcBK = 32;      // rows of X per step (two 16-row k-steps of the MMA)
@@ -251,9 +252,11 @@ __device__ __forceinline__ void xring_read8(const unsigned char *box0, const uns
 }
 
 // Pipeline state shared by the sketch kernels' warps: operand stages
-// (full: every producer thread has written it; empty: the MMAs that read it
+// (full: every producer warp has written it; empty: the MMAs that read it
 // are done), ring slots (xfull: the TMA box has landed; xempty: every
-// producer thread has read it) and the abort flag.
+// producer warp has read it) and the abort flag.  A producer warp's lanes
+// fence their stores for the async proxy, meet at __syncwarp, and lane 0
+// arrives for the warp.
 struct SkPipe {
     uint64_t full[kSkMaxStages], empty[kSkMaxStages];
     uint64_t xfull[kXRingMax], xempty[kXRingMax];
@@ -343,12 +346,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (control) tmem_alloc(&pp.tmem_slot, ncols);
     if (tid == 0) {
         for (int q = 0; q < nst; ++q) {
-            mbar_init(&pp.full[q], kSkProducers);
+            mbar_init(&pp.full[q], kSkWarps);
             mbar_init(&pp.empty[q], 1);
         }
         for (int q = 0; q < kx; ++q) {
             mbar_init(&pp.xfull[q], 1);
-            mbar_init(&pp.xempty[q], kSkProducers);
+            mbar_init(&pp.xempty[q], kSkWarps);
         }
         fence_mbar_init();
         pp.abort_flag = 0;
@@ -472,11 +475,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
             fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
-            if (use_tma) {
-                mbar_arrive(&pp.xempty[g0 % kx]);
-                mbar_arrive(&pp.xempty[(g0 + 1) % kx]);
+            __syncwarp();
+            if (lane == 0) {  // one arrival per warp
+                if (use_tma) {
+                    mbar_arrive(&pp.xempty[g0 % kx]);
+                    mbar_arrive(&pp.xempty[(g0 + 1) % kx]);
+                }
+                mbar_arrive(&pp.full[s]);
             }
-            mbar_arrive(&pp.full[s]);
         }
         // the last commit covers every MMA
         if (nsteps > 0) {
@@ -600,14 +606,14 @@ __global__ void __launch_bounds__(kDgThreads, 1)
     if (control) tmem_alloc(&pp.tmem_slot, kDgTmemCols);
     if (tid == 0) {
         for (int q = 0; q < kDgStages; ++q) {
-            mbar_init(&pp.full[q], kSkProducers);
+            mbar_init(&pp.full[q], kSkWarps);
             mbar_init(&pp.empty[q], 1);
         }
         for (int q = 0; q < kDgRing; ++q) {
             mbar_init(&pp.xfull[q], 1);
-            mbar_init(&pp.xempty[q], kSkProducers);
+            mbar_init(&pp.xempty[q], kSkWarps);
         }
-        mbar_init(&pp.tmem_empty, kSkProducers);
+        mbar_init(&pp.tmem_empty, kSkWarps);
         fence_mbar_init();
         pp.abort_flag = 0;
     }
@@ -747,11 +753,14 @@ __global__ void __launch_bounds__(kDgThreads, 1)
                     *reinterpret_cast<uint2 *>(stage + kDgTileA + q * kDgTileB + xoff) = make_uint2(w0[q], w1[q]);
             }
             fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
-            if (use_tma) {
-                mbar_arrive(&pp.xempty[g0 % kDgRing]);
-                mbar_arrive(&pp.xempty[(g0 + 1) % kDgRing]);
+            __syncwarp();
+            if (lane == 0) {  // one arrival per warp
+                if (use_tma) {
+                    mbar_arrive(&pp.xempty[g0 % kDgRing]);
+                    mbar_arrive(&pp.xempty[(g0 + 1) % kDgRing]);
+                }
+                mbar_arrive(&pp.full[s]);
             }
-            mbar_arrive(&pp.full[s]);
             // (3) end of a window: drain the six level accumulators into int64,
             // in units of 2^8 (level 5 rounded to that unit), and release TMEM
             if ((ks % kDgWinSteps) == kDgWinSteps - 1 || ks == nsteps - 1) {
@@ -782,7 +791,8 @@ __global__ void __launch_bounds__(kDgThreads, 1)
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&pp.tmem_empty);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pp.tmem_empty);
                 if (++windows == kDgFlushWindows) {
                     flush();
                     windows = 0;
