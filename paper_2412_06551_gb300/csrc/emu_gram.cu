@@ -157,38 +157,43 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     int committed = -1;  // the control thread's last commit
 
     if (control) {
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
-            for (int ks = 0; ks < nsteps; ++ks) {
-                const int s = ks % nst;
-                const bool fresh = (ks % kEmuWinSteps) == 0;
-                if (fresh && ks > 0 &&
-                    !ge_wait(pp, &pp.tmem_empty, static_cast<uint32_t>((ks / kEmuWinSteps - 1) & 1)))
-                    break;
-                if (!ge_wait(pp, &pp.full[s], static_cast<uint32_t>((ks / nst) & 1))) break;
+        // the whole warp runs the loop, so that the stage addresses and
+        // descriptors are warp-uniform values; lane 0 waits and issues
+        const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
+        const uint32_t tbq = (b_in_a ? kTileA : kTileB) >> 4;  // digit-tile stride of B, in 16 bytes
+        for (int ks = 0; ks < nsteps; ++ks) {
+            const int s = ks % nst;
+            const bool fresh = (ks % kEmuWinSteps) == 0;
+            int okw = 1;
+            if (lane == 0)
+                okw = (!fresh || ks == 0 ||
+                       ge_wait(pp, &pp.tmem_empty, static_cast<uint32_t>((ks / kEmuWinSteps - 1) & 1))) &&
+                      ge_wait(pp, &pp.full[s], static_cast<uint32_t>((ks / nst) & 1));
+            if (!__shfl_sync(0xffffffffu, okw, 0)) break;
+            const uint32_t sa = smem_u32(smem_raw + s * stage_bytes);
+            const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128 : sa + kEmuDigits * kTileA;
+            // descriptors of digit 0, k-step 0; digit d, k-step kk add their
+            // byte offsets / 16 to the start-address field (no carry: shared
+            // addresses stay below 2^18)
+            const uint64_t adA = smem_desc(sa, 128, (kEmuBK / 8) * 128);
+            const uint64_t adB = smem_desc(sb, 128, (kEmuBK / 8) * 128);
+            if (lane == 0) {
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem_raw + s * stage_bytes);
-                const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128
-                                           : sa + kEmuDigits * kTileA;
-                const uint32_t tb = b_in_a ? kTileA : kTileB;
-#pragma unroll 1
-                for (int L = 0; L < kEmuDigits; ++L) {
-#pragma unroll 1
-                    for (int sd = 0; sd <= L; ++sd) {
-                        const int t = L - sd;
 #pragma unroll
-                        for (int kk = 0; kk < kEmuBK / 16; ++kk) {
-                            const uint64_t ad = smem_desc(sa + sd * kTileA + kk * 256, 128, (kEmuBK / 8) * 128);
-                            const uint64_t bd = smem_desc(sb + t * tb + kk * 256, 128, (kEmuBK / 8) * 128);
-                            mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN), ad, bd, idesc,
+                for (int L = 0; L < kEmuDigits; ++L)
+#pragma unroll
+                    for (int sd = 0; sd <= L; ++sd)
+#pragma unroll
+                        for (int kk = 0; kk < kEmuBK / 16; ++kk)
+                            mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN),
+                                     adA + static_cast<uint64_t>(sd * (kTileA >> 4) + kk * 16),
+                                     adB + static_cast<uint64_t>((L - sd) * tbq + kk * 16), idesc,
                                      (fresh && sd == 0 && kk == 0) ? 0u : 1u);
-                        }
-                    }
-                }
                 mma_commit(&pp.empty[s]);
                 if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) mma_commit(&pp.win_done);
                 committed = ks;
             }
+            __syncwarp();
         }
     } else {
         // drain ownership: TMEM lanes 32 (warp % 4) .. +31 (rows j of the
