@@ -16,14 +16,14 @@
 // A, known before anything is written) and of W's columns (one exponent per
 // column), levels s + t <= 7 summed exactly in fp32 over at most 128
 // K-columns, drained into int64 (units 2^-40 of level 0), scaled into
-// binary64.  A CTA of 256 threads owns 128 rows (two threads per row: each
-// splits half of a 16-column K-chunk and drains half of a 32-column pass);
-// passes of 32 output columns run from the last to the first, so that a pass
-// reads only columns of A below the ones it writes and Q may alias A.  Per
-// K-chunk the threads split their values into eight K-major digit tiles while
-// the tensor core works on the previous chunk; one thread bulk-copies W's
-// precomputed digit tiles and issues the 36 level products (kind::f16,
-// M = 128, N = 32, K = 16).  No binary64 arithmetic remains on the rows.
+// binary64.  One CTA per SM owns 128-row tiles; passes of 64 output columns
+// (all 512 TMEM columns: eight levels) run from the last to the first, so
+// that a pass reads only columns of A below the ones it writes and Q may
+// alias A.  Warp-specialised (k_wprod_emu): 16 producer warps split each
+// 32-column K-chunk of their rows into eight K-major digit tiles while the
+// control warp bulk-copies W's precomputed digit tiles and issues the 72
+// level products (kind::f16, M = 128, N = 64, K = 16).  No binary64
+// arithmetic remains on the rows.
 #include <algorithm>
 #include <cstring>
 
@@ -35,24 +35,25 @@
 namespace rq {
 namespace {
 
-constexpr int kWpThreads = 256;
+constexpr int kWpProducers = 512;    // 16 producer warps
+constexpr int kWpThreads = kWpProducers + 32;  // plus the control warp
 constexpr int kWpM = 128;            // rows per tile
-constexpr int kWpK = 16;             // K-columns per chunk
-constexpr int kWpN = 32;             // output columns per pass
-constexpr int kWpWinChunks = 8;      // K-chunks per exact window (128 K-columns)
+constexpr int kWpK = 32;             // K-columns per chunk (two k-steps of the MMA)
+constexpr int kWpN = 64;             // output columns per pass
+constexpr int kWpWinChunks = 4;      // K-chunks per exact window (128 K-columns)
 constexpr int kWpStages = 2;
-constexpr int kWpTileA = kWpM * kWpK * 2;   // one digit tile of A: 4 KB
-constexpr int kWpTileB = kWpN * kWpK * 2;   // one digit tile of W: 1 KB
+constexpr int kWpTileA = kWpM * kWpK * 2;   // one digit tile of A: 8 KB
+constexpr int kWpTileB = kWpN * kWpK * 2;   // one digit tile of W: 4 KB
 constexpr int kWpStageA = kEmuDigits * kWpTileA;
 constexpr int kWpStageB = kEmuDigits * kWpTileB;
 constexpr int kWpStageBytes = kWpStageA + kWpStageB;
-constexpr int kWpTmemCols = 256;     // eight 32-column level accumulators
+constexpr int kWpTmemCols = 512;     // eight 64-column level accumulators
 constexpr int kWpUnit = 16;          // drain units: 2^-(24 + 16) of level 0
 
-// Byte offset of element (row, k) of a K-major tile of 16 K-columns laid
+// Byte offset of element (row, k) of a K-major tile of 32 K-columns laid
 // out as [row/8][k/8][row%8][k%8] (bf16).
 __host__ __device__ __forceinline__ uint32_t wp_off(int row, int k) {
-    return static_cast<uint32_t>(((row >> 3) * 2 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return static_cast<uint32_t>(((row >> 3) * (kWpK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // Index of W's digit tiles for (pass g, K-chunk kc), kc <= 2g + 1.
@@ -69,12 +70,12 @@ struct WpLayout {
 
 __host__ __device__ __forceinline__ WpLayout wp_layout(int n) {
     const int n_pad = pad16(n);
-    const int np32 = (n + kWpN - 1) / kWpN * kWpN;
-    const int passes = np32 / kWpN;
+    const int npn = (n + kWpN - 1) / kWpN * kWpN;
+    const int passes = npn / kWpN;
     WpLayout l;
     l.norms = 0;
     l.cbits = 256;
-    l.w = l.cbits + ((size_t(np32) * sizeof(int) + 255) / 256) * 256;
+    l.w = l.cbits + ((size_t(npn) * sizeof(int) + 255) / 256) * 256;
     l.tiles = l.w + ((size_t(n_pad) * n_pad * 8 + 1023) / 1024) * 1024;
     l.total = l.tiles + wp_tile(passes, 0) * kWpStageB + 256;
     return l;
@@ -161,167 +162,277 @@ __global__ void k_wprod_prep(const double *__restrict__ W, int n, int n_pad,
     }
 }
 
-__global__ void __launch_bounds__(kWpThreads, 2)
+// Pipeline state of k_wprod_emu: per stage, the producers' digit tiles of A
+// are written (full, one arrival per producer warp), W's digit tiles have
+// landed (wfull) and the MMAs that read the stage are done (empty); per
+// window, the MMAs are complete (win_done) and the accumulators are drained
+// (tmem_empty).  Every thread that waits on a barrier waits on each of its
+// completions in order.
+struct WpPipe {
+    uint64_t full[kWpStages], wfull[kWpStages], empty[kWpStages];
+    uint64_t win_done, tmem_empty;
+    uint64_t rowx;  // a tile's row-exponent parts are written
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+
+__device__ __forceinline__ bool wp_aborted(WpPipe &pp) {
+    return *reinterpret_cast<volatile int *>(&pp.abort_flag) != 0;
+}
+
+__device__ __forceinline__ bool wp_wait(WpPipe &pp, uint64_t *bar, uint32_t parity) {
+    if (wp_aborted(pp)) return false;
+    if (mbar_wait_bounded(bar, parity)) return true;
+    *reinterpret_cast<volatile int *>(&pp.abort_flag) = 1;
+    return false;
+}
+
+// Warp-specialised: per 128-row tile and 64-column pass (last first, so
+// that a pass reads only columns of A below the ones it writes and Q may
+// alias A), per 32-column K-chunk the 16 producer warps split their rows'
+// values into eight digit tiles of A (four threads per row, eight K-columns
+// each), while lane 0 of the control warp bulk-copies W's precomputed digit
+// tiles into the same stage and issues the chunk's 72 level products
+// (kind::f16, M = 128, N = 64, K = 16).  After each window (at most four
+// chunks: 128 K-columns) the producers drain the eight levels into int64;
+// at a pass's end they write Q.
+__global__ void __launch_bounds__(kWpThreads, 1)
     k_wprod_emu(const double *A, int64_t lda, int64_t m, int n, int64_t chunk,
                 const unsigned long long *norms, const int *__restrict__ cbits,
                 const unsigned char *__restrict__ tiles, double *Q, int64_t ldq, DevStatus *st) {
     if (!wprod_selected(norms)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_mma[kWpStages];
-    __shared__ __align__(8) uint64_t bar_w[kWpStages];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
-    __shared__ int rowbits_half[kWpThreads];
+    __shared__ WpPipe pp;
+    __shared__ int rowbits_part[kWpProducers / kWpM][kWpM];
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int r = tid & (kWpM - 1), h = tid >> 7;  // row of the tile, half of its values
-    if (warp == 0) tmem_alloc(&tmem_slot, kWpTmemCols);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool control = warp == kWpProducers / 32;
+    if (control) tmem_alloc(&pp.tmem_slot, kWpTmemCols);
     if (tid == 0) {
         for (int q = 0; q < kWpStages; ++q) {
-            mbar_init(&bar_mma[q], 1);
-            mbar_init(&bar_w[q], 1);
+            mbar_init(&pp.full[q], kWpProducers / 32);
+            mbar_init(&pp.wfull[q], 1);
+            mbar_init(&pp.empty[q], 1);
         }
+        mbar_init(&pp.win_done, 1);
+        mbar_init(&pp.tmem_empty, kWpProducers / 32);
+        mbar_init(&pp.rowx, kWpProducers / 32);
         fence_mbar_init();
-        abort_flag = 0;
+        pp.abort_flag = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(kWpM, kWpN);
-    const uint32_t sbase = smem_u32(smem_raw);
-    // drain ownership: TMEM lanes 32 (warp % 4) .. +31 = rows, columns 16 (warp / 4) .. +15
-    const uint32_t tl = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                        static_cast<uint32_t>(16 * (warp >> 2));
+    const uint32_t tmem = pp.tmem_slot;
     const int nkc = (n + kWpK - 1) / kWpK;
     const int passes = (n + kWpN - 1) / kWpN;
-
     const int64_t rb = int64_t(blockIdx.x) * chunk;
     const int64_t re = std::min<int64_t>(m, rb + chunk);
-    unsigned it = 0;  // K-chunks issued by this CTA (barrier phases of the stages)
-    for (int64_t r0 = rb; r0 < re && !abort_flag; r0 += kWpM) {
-        const int64_t row = r0 + r;
-        const bool live = row < re;
-        // the row's exponent over all n columns of A (each half scans half)
-        int eb = 0;
-        if (live)
-            for (int c = h; c < n; c += 2) {
-                const unsigned long long b = static_cast<unsigned long long>(
-                    __double_as_longlong(__ldcg(A + row + int64_t(c) * lda)));
-                eb = max(eb, static_cast<int>((b >> 52) & 0x7ff));
+    const int ntiles = re > rb ? static_cast<int>(ceil_div(re - rb, kWpM)) : 0;
+    int committed = -1, wcopies = 0;  // the control thread's last commit, W copies issued
+
+    if (control) {
+        const uint32_t idesc = idesc_bf16_f32(kWpM, kWpN);
+        // W's tiles of chunk `it` (pass g, K-chunk kc) into its stage, once
+        // the MMAs that last read the stage are done (lane 0)
+        auto copy_w = [&](int it, int g, int kc) -> bool {
+            const int s = it % kWpStages;
+            if (it >= kWpStages &&
+                !wp_wait(pp, &pp.empty[s], static_cast<uint32_t>((it / kWpStages - 1) & 1)))
+                return false;
+            mbar_arrive_expect_tx(&pp.wfull[s], kWpStageB);
+            bulk_load(smem_raw + s * kWpStageBytes + kWpStageA, tiles + wp_tile(g, kc) * kWpStageB,
+                      kWpStageB, &pp.wfull[s]);
+            wcopies = it + 1;
+            return true;
+        };
+        int it = 0, win = 0;
+        bool ok = true;
+        // the chunk after (it, g, kc) in the schedule, for the copy one ahead
+        int ng = passes - 1, nkn = 0, ntile = 0;
+        auto advance = [&]() {
+            if (++nkn == std::min(2 * ng + 2, nkc)) {
+                nkn = 0;
+                if (--ng < 0) {
+                    ng = passes - 1;
+                    ++ntile;
+                }
             }
-        rowbits_half[tid] = eb;
-        __syncthreads();
-        const int rowbits = max(rowbits_half[r], rowbits_half[r + kWpM]);
-        const int E = emu_exponent(rowbits);
-        for (int g = passes - 1; g >= 0 && !abort_flag; --g) {
-            const int nk = std::min(2 * g + 2, nkc);
-            long long acc[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = 0;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-                const int sidx = it % kWpStages;
-                unsigned char *stage = smem_raw + sidx * kWpStageBytes;
-                // this thread's eight values of the chunk (in flight during the wait)
-                double xv[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int col = kWpK * kc + 8 * h + t;
-                    xv[t] = (live && col < n) ? __ldcg(A + row + int64_t(col) * lda) : 0.0;
-                }
-                // the MMAs that last read this stage are done
-                if (it >= kWpStages &&
-                    !mbar_wait_bounded(&bar_mma[sidx], static_cast<uint32_t>(((it / kWpStages) - 1) & 1u)))
-                    abort_flag = 1;
-                __syncthreads();
-                if (abort_flag) break;
-                if (tid == 0) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&bar_w[sidx], kWpStageB);
-                    bulk_load(stage + kWpStageA, tiles + wp_tile(g, kc) * kWpStageB, kWpStageB, &bar_w[sidx]);
-                }
-                // digits of the eight values, two K-neighbours (one 32-bit word) per
-                // digit tile at a time
-#pragma unroll
-                for (int t = 0; t < 8; t += 2) {
-                    uint32_t w[kEmuDigits];
-                    emu_digits2_packed<kEmuDigits>(xv[t], xv[t + 1], E, w);
-#pragma unroll
-                    for (int s = 0; s < kEmuDigits; ++s)
-                        *reinterpret_cast<uint32_t *>(stage + s * kWpTileA + wp_off(r, 8 * h + t)) = w[s];
-                }
-                fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    const bool have_w = mbar_wait_bounded(&bar_w[sidx], (it / kWpStages) & 1u);
-                    if (!have_w) abort_flag = 1;
-                    tc_fence_after();
-                    const uint32_t sa = sbase + sidx * kWpStageBytes, sb = sa + kWpStageA;
+        };
+        if (ntiles > 0 && lane == 0) ok = copy_w(0, ng, nkn);
+        advance();
+        for (int t = 0; t < ntiles && ok; ++t)
+            for (int g = passes - 1; g >= 0 && ok; --g) {
+                const int nk = std::min(2 * g + 2, nkc);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kWpStages;
                     const bool fresh = (kc % kWpWinChunks) == 0;
-#pragma unroll 1
-                    for (int L = 0; L < (have_w ? kEmuDigits : 0); ++L) {
-#pragma unroll 1
-                        for (int s = 0; s <= L; ++s) {
-                            const uint64_t ad = smem_desc(sa + s * kWpTileA, 128, 256);
-                            const uint64_t bd = smem_desc(sb + (L - s) * kWpTileB, 128, 256);
-                            mma_bf16(tmem + static_cast<uint32_t>(L * kWpN), ad, bd, idesc,
-                                     (fresh && s == 0) ? 0u : 1u);
-                        }
+                    const bool wend = (kc % kWpWinChunks) == kWpWinChunks - 1 || kc == nk - 1;
+                    int okw = 1;
+                    if (lane == 0)
+                        okw = (!fresh || win == 0 ||
+                               wp_wait(pp, &pp.tmem_empty, static_cast<uint32_t>((win - 1) & 1))) &&
+                              wp_wait(pp, &pp.full[s], static_cast<uint32_t>((it / kWpStages) & 1)) &&
+                              wp_wait(pp, &pp.wfull[s], static_cast<uint32_t>((it / kWpStages) & 1));
+                    if (!__shfl_sync(0xffffffffu, okw, 0)) {
+                        ok = false;
+                        break;
                     }
-                    mma_commit(&bar_mma[sidx]);
+                    const uint32_t sa = smem_u32(smem_raw + s * kWpStageBytes);
+                    const uint64_t adA = smem_desc(sa, 128, (kWpK / 8) * 128);
+                    const uint64_t adB = smem_desc(sa + kWpStageA, 128, (kWpK / 8) * 128);
+                    if (lane == 0) {
+                        tc_fence_after();
+#pragma unroll
+                        for (int L = 0; L < kEmuDigits; ++L)
+#pragma unroll
+                            for (int sd = 0; sd <= L; ++sd)
+#pragma unroll
+                                for (int kk = 0; kk < kWpK / 16; ++kk)
+                                    mma_bf16(tmem + static_cast<uint32_t>(L * kWpN),
+                                             adA + static_cast<uint64_t>(sd * (kWpTileA >> 4) + kk * 16),
+                                             adB + static_cast<uint64_t>((L - sd) * (kWpTileB >> 4) + kk * 16),
+                                             idesc, (fresh && sd == 0 && kk == 0) ? 0u : 1u);
+                        mma_commit(&pp.empty[s]);
+                        if (wend) mma_commit(&pp.win_done);
+                        committed = it;
+                        // the next chunk's W while these products run
+                        if (ntile < ntiles) ok = copy_w(it + 1, ng, nkn);
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
+                    advance();
+                    if (wend) ++win;
                 }
-                if ((kc % kWpWinChunks) == kWpWinChunks - 1 || kc == nk - 1) {
-                    // window end: drain the eight levels of this thread's 16 columns
-                    if (!mbar_wait_bounded(&bar_mma[sidx], (it / kWpStages) & 1u)) abort_flag = 1;
-                    __syncthreads();
-                    if (abort_flag) break;
-                    tc_fence_after();
-                    float v[16];
+            }
+    } else {
+        const int r = 32 * (warp & 3) + lane;                   // this thread's row of the tile
+        const int kb = warp >> 2;                              // its eight K-columns of a chunk
+        const int cgrp = warp >> 2;                            // its 16 drain columns of a pass
+        long long acc[16];
+        int it = 0, win = 0;
+        bool ok = true;
+        for (int t = 0; t < ntiles && ok; ++t) {
+            const int64_t row = rb + int64_t(t) * kWpM + r;
+            const bool live = row < re;
+            // the row's exponent over all n columns of A (its four threads
+            // scan a quarter each)
+            int eb = 0;
+            if (live)
+                for (int c = kb; c < n; c += 4) {
+                    const unsigned long long b = static_cast<unsigned long long>(
+                        __double_as_longlong(__ldcg(A + row + int64_t(c) * lda)));
+                    eb = max(eb, static_cast<int>((b >> 52) & 0x7ff));
+                }
+            rowbits_part[kb][r] = eb;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pp.rowx);
+            if (!wp_wait(pp, &pp.rowx, static_cast<uint32_t>(t & 1))) {
+                ok = false;
+                break;
+            }
+            const int rowbits = max(max(rowbits_part[0][r], rowbits_part[1][r]),
+                                    max(rowbits_part[2][r], rowbits_part[3][r]));
+            const int E = emu_exponent(rowbits);
+            for (int g = passes - 1; g >= 0 && ok; --g) {
+                const int nk = std::min(2 * g + 2, nkc);
 #pragma unroll
-                    for (int L = 0; L < kEmuDigits; ++L) {
-                        tmem_ld16(tl + static_cast<uint32_t>(L * kWpN), v);
+                for (int q = 0; q < 16; ++q) acc[q] = 0;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kWpStages;
+                    unsigned char *stage = smem_raw + s * kWpStageBytes;
+                    // this thread's eight values of the chunk (in flight during the wait)
+                    double xv[8];
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            switch (L) {  // compile-time after unrolling
-                                case 0: acc[q] += emu_level<24 + kWpUnit>(v[q]); break;
-                                case 1: acc[q] += emu_level<16 + kWpUnit>(v[q]); break;
-                                case 2: acc[q] += emu_level<8 + kWpUnit>(v[q]); break;
-                                case 3: acc[q] += emu_level<0 + kWpUnit>(v[q]); break;
-                                case 4: acc[q] += emu_level<-8 + kWpUnit>(v[q]); break;
-                                case 5: acc[q] += emu_level<-16 + kWpUnit>(v[q]); break;
-                                case 6: acc[q] += emu_level<-24 + kWpUnit>(v[q]); break;
-                                default: acc[q] += emu_level<-32 + kWpUnit>(v[q]); break;
+                    for (int u = 0; u < 8; ++u) {
+                        const int col = kWpK * kc + 8 * kb + u;
+                        xv[u] = (live && col < n) ? __ldcg(A + row + int64_t(col) * lda) : 0.0;
+                    }
+                    if (it >= kWpStages &&
+                        !wp_wait(pp, &pp.empty[s], static_cast<uint32_t>((it / kWpStages - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    // digits, two K-neighbours (one 32-bit word) per digit tile at a time
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        uint32_t w[kEmuDigits];
+                        emu_digits2_packed<kEmuDigits>(xv[u], xv[u + 1], E, w);
+#pragma unroll
+                        for (int d = 0; d < kEmuDigits; ++d)
+                            *reinterpret_cast<uint32_t *>(stage + d * kWpTileA + wp_off(r, 8 * kb + u)) = w[d];
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&pp.full[s]);
+                    if ((kc % kWpWinChunks) == kWpWinChunks - 1 || kc == nk - 1) {
+                        // window end: drain the eight levels of this thread's 16 columns
+                        if (!wp_wait(pp, &pp.win_done, static_cast<uint32_t>(win & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        ++win;
+                        tc_fence_after();
+                        const uint32_t tl = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                                            static_cast<uint32_t>(16 * cgrp);
+                        float v[16];
+#pragma unroll
+                        for (int L = 0; L < kEmuDigits; ++L) {
+                            tmem_ld16(tl + static_cast<uint32_t>(L * kWpN), v);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                switch (L) {  // compile-time after unrolling
+                                    case 0: acc[q] += emu_level<24 + kWpUnit>(v[q]); break;
+                                    case 1: acc[q] += emu_level<16 + kWpUnit>(v[q]); break;
+                                    case 2: acc[q] += emu_level<8 + kWpUnit>(v[q]); break;
+                                    case 3: acc[q] += emu_level<0 + kWpUnit>(v[q]); break;
+                                    case 4: acc[q] += emu_level<-8 + kWpUnit>(v[q]); break;
+                                    case 5: acc[q] += emu_level<-16 + kWpUnit>(v[q]); break;
+                                    case 6: acc[q] += emu_level<-24 + kWpUnit>(v[q]); break;
+                                    default: acc[q] += emu_level<-32 + kWpUnit>(v[q]); break;
+                                }
                             }
                         }
-                    }
-                    tc_fence_before();
-                    __syncthreads();  // TMEM read before the next window's MMAs overwrite it
-                }
-            }
-            if (abort_flag) break;
-            // Q[row, 32 g + 16 (warp / 4) + q] = 2^(E + E'_c - 54) acc[q]
-            const int64_t drow = r0 + 32 * (warp & 3) + (tid & 31);
-            const int drb = max(rowbits_half[drow - r0], rowbits_half[drow - r0 + kWpM]);
-            if (drow < re) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&pp.tmem_empty);
+                        if (kc == nk - 1 && live) {
+                            // Q[row, 64 g + 16 cgrp + q] = 2^(E + E'_c - 54) acc[q]
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int col = kWpN * g + 16 * (warp >> 2) + q;
-                    if (col < n) {
-                        const int cb = __ldg(cbits + col);
-                        Q[drow + int64_t(col) * ldq] =
-                            (drb == 0x7ff || cb == 0x7ff)
-                                ? __longlong_as_double(0x7ff8000000000000ll)
-                                : emu_i64_scaled(acc[q], emu_exponent(drb) + emu_exponent(cb) - 14 - 24 - kWpUnit);
+                            for (int q = 0; q < 16; ++q) {
+                                const int col = kWpN * g + 16 * cgrp + q;
+                                if (col < n) {
+                                    const int cb = __ldg(cbits + col);
+                                    Q[row + int64_t(col) * ldq] =
+                                        (rowbits == 0x7ff || cb == 0x7ff)
+                                            ? __longlong_as_double(0x7ff8000000000000ll)
+                                            : emu_i64_scaled(acc[q], E + emu_exponent(cb) - 14 - 24 - kWpUnit);
+                                }
+                            }
+                        }
                     }
                 }
             }
         }
-        __syncthreads();  // rowbits_half reused by the next tile
     }
-    if (abort_flag && tid == 0) report(st, kErrTimeout, 0, -1);
+    __syncthreads();
+    if (wp_aborted(pp)) {
+        if (tid == 0) report(st, kErrTimeout, 0, -1);
+        if (control && lane == 0) {
+            // the copies and products in flight land before the shared
+            // memory and TMEM are released (bounded waits)
+            for (int q = 0; q < kWpStages && q < wcopies; ++q) {
+                const int c = q + ((wcopies - 1 - q) / kWpStages) * kWpStages;
+                (void)mbar_wait_bounded(&pp.wfull[q], static_cast<uint32_t>((c / kWpStages) & 1));
+            }
+            if (committed >= 0)
+                (void)mbar_wait_bounded(&pp.empty[committed % kWpStages],
+                                        static_cast<uint32_t>((committed / kWpStages) & 1));
+        }
+    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kWpTmemCols);
+    if (control) tmem_dealloc(tmem, kWpTmemCols);
 }
 
 }  // namespace
@@ -369,11 +480,13 @@ cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, in
               k_wprod_prep<<<passes, 256, 0, stream>>>(W, n, n_pad, norms, cbits, tiles));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t ntiles = ceil_div(m, kWpM);
-    const int64_t grid = std::min<int64_t>(ntiles, 2 * int64_t(grid_sms()));
+    const int64_t grid = std::min<int64_t>(ntiles, int64_t(grid_sms()));  // one CTA per SM
     const int64_t chunk = ceil_div(ntiles, grid) * kWpM;
     const int g = static_cast<int>(ceil_div(m, chunk));
     const size_t smem = size_t(kWpStages) * kWpStageBytes;
-    cudaFuncSetAttribute(k_wprod_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if ((e = cudaFuncSetAttribute(k_wprod_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
+        cudaSuccess)
+        return e;
     RQ_LAUNCH(KID_TRSM_EMU, stream,
               k_wprod_emu<<<g, kWpThreads, smem, stream>>>(A, lda, m, n, chunk, norms, cbits, tiles, Q,
                                                            ldq, st));
