@@ -21,9 +21,11 @@
 // a contiguous chunk of rows of A (split-K).  Its eight 128 x 64 fp32
 // accumulators take the 512 TMEM columns.  Per 32 rows of A the 16 producer
 // warps split the block into digits (K-major 8 x 8 bf16 core matrices in
-// shared memory) while the control warp issues the previous blocks' 36 x 2
-// MMAs (kind::f16, M=128, N=64, K=16); mbarriers hand the stages back and
-// forth (see k_gram_emu).
+// shared memory; the k columns' eight digit tiles side by side) while the
+// control warp issues the previous blocks' 36 digit-pair products as 12 x 2
+// wide MMAs (kind::f16, M=128, N=64 .. 256, K=16): one digit of the j columns
+// times up to four adjacent digits of the k columns lands in as many adjacent
+// levels; mbarriers hand the stages back and forth (see k_gram_emu).
 #include <algorithm>
 #include <climits>
 
@@ -92,7 +94,7 @@ __global__ void k_col_exponent(const double *__restrict__ A, int64_t lda, int64_
 // blocks of A, split each into digit tiles in the block's stage and arrive on
 // the stage's full barrier (one arrival per warp); the control warp's lane 0
 // waits for it,
-// issues the block's 72 MMAs and commits them to the stage's empty barrier.
+// issues the block's 24 MMAs and commits them to the stage's empty barrier.
 // A window's eight accumulators are drained by the producers after they
 // have filled the next block (so that its split overlaps the window's last
 // MMAs); the control lane starts a window only when the previous one is
@@ -127,7 +129,10 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     // stage's empty barrier is waited on by one group, phase after phase);
     // the k columns inside the j columns need no digits of their own
     constexpr int nst = kEmuGroups;
-    const int stage_bytes = b_in_a ? kEmuDigits * kTileA : kEmuStageBytes;
+    // the k columns' digit tiles sit side by side after the j columns' (when
+    // the k columns lie inside the j columns, their digits are stored twice)
+    const int stage_bytes = kEmuStageBytes;
+    const int kin = b_in_a ? k0 - j0 : -kEmuN;  // first k column inside the j columns
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool control = warp == kEmuProducers / 32;
 
@@ -159,8 +164,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     if (control) {
         // the whole warp runs the loop, so that the stage addresses and
         // descriptors are warp-uniform values; lane 0 waits and issues
-        const uint32_t idesc = idesc_bf16_f32(kEmuM, kEmuN);
-        const uint32_t tbq = (b_in_a ? kTileA : kTileB) >> 4;  // digit-tile stride of B, in 16 bytes
+        // the level products as wide MMAs: the k columns' digit tiles t0 ..
+        // t0 + w - 1 side by side form one operand of N = 64 w, whose product
+        // with digit s of the j columns lands in levels s + t0 .. s + t0 + w - 1
+        // (TMEM columns 64 (s + t0) ..); twelve MMAs per k-step cover the 36
+        // pairs s + t <= 7.  The two with s = 0 come first: they write every
+        // level, so only they start a window afresh.
+        const uint32_t idn[5] = {0u, idesc_bf16_f32(kEmuM, kEmuN), idesc_bf16_f32(kEmuM, 2 * kEmuN),
+                                 idesc_bf16_f32(kEmuM, 3 * kEmuN), idesc_bf16_f32(kEmuM, 4 * kEmuN)};
         for (int ks = 0; ks < nsteps; ++ks) {
             const int s = ks % nst;
             const bool fresh = (ks % kEmuWinSteps) == 0;
@@ -171,24 +182,33 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
                       ge_wait(pp, &pp.full[s], static_cast<uint32_t>((ks / nst) & 1));
             if (!__shfl_sync(0xffffffffu, okw, 0)) break;
             const uint32_t sa = smem_u32(smem_raw + s * stage_bytes);
-            const uint32_t sb = b_in_a ? sa + ((k0 - j0) / 8) * (kEmuBK / 8) * 128 : sa + kEmuDigits * kTileA;
             // descriptors of digit 0, k-step 0; digit d, k-step kk add their
             // byte offsets / 16 to the start-address field (no carry: shared
             // addresses stay below 2^18)
             const uint64_t adA = smem_desc(sa, 128, (kEmuBK / 8) * 128);
-            const uint64_t adB = smem_desc(sb, 128, (kEmuBK / 8) * 128);
+            const uint64_t adB = smem_desc(sa + kEmuDigits * kTileA, 128, (kEmuBK / 8) * 128);
             if (lane == 0) {
                 tc_fence_after();
 #pragma unroll
-                for (int L = 0; L < kEmuDigits; ++L)
+                for (int kk = 0; kk < kEmuBK / 16; ++kk) {
+                    const uint32_t a0 = fresh && kk == 0 ? 0u : 1u;
+                    const uint64_t ak = adA + static_cast<uint64_t>(kk * 16);
+                    const uint64_t bk = adB + static_cast<uint64_t>(kk * 16);
+                    // s = 0: k tiles 0-3 -> levels 0-3, k tiles 4-7 -> levels 4-7
+                    mma_bf16(tmem, ak, bk, idn[4], a0);
+                    mma_bf16(tmem + 4 * kEmuN, ak, bk + static_cast<uint64_t>(4 * (kTileB >> 4)), idn[4], a0);
 #pragma unroll
-                    for (int sd = 0; sd <= L; ++sd)
-#pragma unroll
-                        for (int kk = 0; kk < kEmuBK / 16; ++kk)
-                            mma_bf16(tmem + static_cast<uint32_t>(L * kEmuN),
-                                     adA + static_cast<uint64_t>(sd * (kTileA >> 4) + kk * 16),
-                                     adB + static_cast<uint64_t>((L - sd) * tbq + kk * 16), idesc,
-                                     (fresh && sd == 0 && kk == 0) ? 0u : 1u);
+                    for (int sd = 1; sd < kEmuDigits; ++sd) {
+                        const uint64_t as = ak + static_cast<uint64_t>(sd * (kTileA >> 4));
+                        // k tiles 0 .. min(3, 7 - sd)
+                        mma_bf16(tmem + static_cast<uint32_t>(sd * kEmuN), as, bk,
+                                 idn[(8 - sd) < 4 ? (8 - sd) : 4], 1u);
+                        // k tiles 4 .. 7 - sd
+                        if (sd <= 3)
+                            mma_bf16(tmem + static_cast<uint32_t>((sd + 4) * kEmuN), as,
+                                     bk + static_cast<uint64_t>(4 * (kTileB >> 4)), idn[4 - sd], 1u);
+                    }
+                }
                 mma_commit(&pp.empty[s]);
                 if ((ks % kEmuWinSteps) == kEmuWinSteps - 1 || ks == nsteps - 1) mma_commit(&pp.win_done);
                 committed = ks;
@@ -266,14 +286,20 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             const int E = isA ? expA[cc] : expB[cc];
             unsigned char *base = stage + (isA ? 0 : kEmuDigits * kTileA);
             const int tbytes = isA ? kTileA : kTileB;
+            // a j column that is also a k column: its digits again in the k tiles
+            const int kc = isA ? c - kin : -1;
+            const bool dup = kc >= 0 && kc < kEmuN;
+            unsigned char *bdup = stage + kEmuDigits * kTileA;
             // two rows at a time: one 32-bit word (two bf16) per digit
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
                 uint32_t w[kEmuDigits];
                 emu_digits2_packed<kEmuDigits>(x[t], x[t + 1], E, w);
 #pragma unroll
-                for (int sd = 0; sd < kEmuDigits; ++sd)
+                for (int sd = 0; sd < kEmuDigits; ++sd) {
                     *reinterpret_cast<uint32_t *>(base + sd * tbytes + emu_off(cc, kb * 8 + t)) = w[sd];
+                    if (dup) *reinterpret_cast<uint32_t *>(bdup + sd * kTileB + emu_off(kc, kb * 8 + t)) = w[sd];
+                }
             }
         };
         auto load = [&](int64_t r0, int task, double (&x)[8]) {

@@ -572,8 +572,9 @@ __global__ void k_dg_col_exponent(const double *__restrict__ A, int64_t lda, int
 // part[blockIdx.y][c * s_pad + r].  Warp-specialised like k_sketch_tc: per
 // 32 rows of X the 16 producer warps draw S (integers k) and split X (from
 // the ring) into six digit tiles; the control lane issues the six level
-// products of each 16-row k-step (kind::f16, M = 128, N = 64): level t
-// (digit t of X, weight 256^(5 - t)) in TMEM columns 64 t .. 64 t + 63.
+// products of each 16-row k-step as two MMAs over the side-by-side digit
+// tiles (kind::f16, M = 128, N = 256 and 128): level t (digit t of X,
+// weight 256^(5 - t)) in TMEM columns 64 t .. 64 t + 63.
 // After the last step of each 1024-row window the producers drain the
 // levels into int64 window sums (exact) and release TMEM (tmem_empty) before
 // the control lane starts the next window; every 16 windows the sums go
@@ -631,7 +632,8 @@ __global__ void __launch_bounds__(kDgThreads, 1)
 
     if (control) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(kTcM, kDgNC);
+            const uint32_t idesc4 = idesc_bf16_f32(kTcM, 4 * kDgNC);
+            const uint32_t idesc2 = idesc_bf16_f32(kTcM, 2 * kDgNC);
             if (use_tma) {
                 prefetch_tensormap(&xmap);
                 for (; issued < (nboxes < kDgRing ? nboxes : kDgRing); ++issued)
@@ -647,15 +649,17 @@ __global__ void __launch_bounds__(kDgThreads, 1)
                 if (!sk_wait(pp, &pp.full[s], static_cast<uint32_t>((ks / kDgStages) & 1))) break;
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(smem + s * kDgStageBytes);
+                // the digit tiles lie side by side (K-major, 64 rows each), so
+                // digits 0-3 form one N = 256 operand whose product lands in
+                // levels 0-3 (TMEM columns 0-255) and digits 4-5 one N = 128
+                // operand (columns 256-383): two MMAs per k-step instead of six
 #pragma unroll
                 for (int kk = 0; kk < kTcBK / 16; ++kk) {
                     const uint64_t ad = smem_desc(a0 + kk * 256, 128, kTcBK * 16);
-#pragma unroll
-                    for (int t = 0; t < kDgDigits; ++t) {
-                        const uint64_t bd = smem_desc(a0 + kDgTileA + t * kDgTileB + kk * 256, 128, kTcBK * 16);
-                        mma_bf16(tmem + static_cast<uint32_t>(t * kDgNC), ad, bd, idesc,
-                                 (fresh && kk == 0) ? 0u : 1u);
-                    }
+                    const uint64_t bd = smem_desc(a0 + kDgTileA + kk * 256, 128, kTcBK * 16);
+                    mma_bf16(tmem, ad, bd, idesc4, (fresh && kk == 0) ? 0u : 1u);
+                    mma_bf16(tmem + static_cast<uint32_t>(4 * kDgNC), ad,
+                             bd + static_cast<uint64_t>((4 * kDgTileB) >> 4), idesc2, (fresh && kk == 0) ? 0u : 1u);
                 }
                 mma_commit(&pp.empty[s]);
                 committed = ks;
