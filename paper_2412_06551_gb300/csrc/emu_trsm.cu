@@ -22,8 +22,8 @@
 // K-chunk of 16 columns each thread loads its row's 16 solved values of Q
 // (L2, written by the CTA itself) and splits them into digits (K-major
 // operand tiles), one thread bulk-copies R's precomputed digit tiles and
-// issues 36 MMAs (kind::f16, M=128, N=16, K=16) into eight 16-column
-// accumulators.  The drain, the binary64 update of C_J and the diagonal
+// issues eight MMAs (kind::f16, M=128, N=128 .. 16, K=16: one digit of Q
+// times the side-by-side digits of R) into eight 16-column accumulators.  The drain, the binary64 update of C_J and the diagonal
 // substitution all stay in the owning thread's registers: no shuffles and no
 // barriers between rows.  Four CTAs share an SM (36 KB of shared memory and
 // 128 TMEM columns each), so one CTA's binary64 substitution overlaps the
@@ -123,7 +123,6 @@ __global__ void __launch_bounds__(kTeThreads, kTeCtasPerSm)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(kTeM, kTeB);
     const uint32_t sa = smem_u32(smem_raw);
     const uint32_t sb = sa + kTeStageA;
     const uint32_t tl = tmem + (static_cast<uint32_t>(32 * warp) << 16);  // this warp's lanes
@@ -179,15 +178,20 @@ __global__ void __launch_bounds__(kTeThreads, kTeCtasPerSm)
                     if (!have_r) abort_flag = 1;
                     tc_fence_after();
                     const bool fresh = (kc % kTeWinChunks) == 0;
-#pragma unroll 1
-                    for (int L = 0; L < (have_r ? kEmuDigits : 0); ++L) {
-#pragma unroll 1
-                        for (int s = 0; s <= L; ++s) {
-                            const uint64_t ad = smem_desc(sa + s * kTeTileA, 128, 256);
-                            const uint64_t bd = smem_desc(sb + (L - s) * kTeTileB, 128, 256);
-                            mma_bf16(tmem + static_cast<uint32_t>(L * kTeB), ad, bd, idesc,
+                    if (have_r) {
+                        // R's eight digit tiles lie side by side (16 rows of the
+                        // K-major operand each), so digit s of Q times digits
+                        // 0 .. 7 - s of R is one MMA of N = 16 (8 - s) landing in
+                        // levels s .. 7 (TMEM columns 16 s ..): eight MMAs per
+                        // chunk for the 36 digit pairs; the first writes every
+                        // level, so only it starts a window afresh
+                        const uint64_t bd = smem_desc(sb, 128, 256);
+#pragma unroll
+                        for (int s = 0; s < kEmuDigits; ++s)
+                            mma_bf16(tmem + static_cast<uint32_t>(s * kTeB),
+                                     smem_desc(sa + s * kTeTileA, 128, 256), bd,
+                                     idesc_bf16_f32(kTeM, kTeB * (kEmuDigits - s)),
                                      (fresh && s == 0) ? 0u : 1u);
-                        }
                     }
                     mma_commit(&bar_mma);
                 }

@@ -23,8 +23,9 @@
 // A CTA walks its chunk of rows in tiles of 128 (M = 128, one row per TMEM
 // lane).  Per K-chunk the 256 threads load 128 x 32 solved values of Q (L2,
 // written by the CTA itself), split them into digits (K-major operand tiles),
-// copy R's precomputed digit tiles, and one thread issues 36 x 2 MMAs
-// (kind::f16, M=128, N=32, K=16) into eight 32-column accumulators.  Two CTAs
+// copy R's precomputed digit tiles, and one thread issues 8 x 2 MMAs
+// (kind::f16, M=128, N=256 .. 32, K=16: one digit of Q times the side-by-side
+// digits of R) into eight 32-column accumulators.  Two CTAs
 // share an SM (80 KB of shared memory and 256 TMEM columns each), so one's
 // binary64 diagonal solve overlaps the other's digit split and tensor-core
 // work.  The diagonal-block solve gives each row 2 adjacent lanes of a warp
@@ -126,7 +127,6 @@ __global__ void __launch_bounds__(kTeThreads, 2)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(kTeM, kTeB);
     const uint32_t smem_base = smem_u32(smem_raw);
     const int nblk = (n + kTeB - 1) / kTeB;
 
@@ -204,20 +204,22 @@ __global__ void __launch_bounds__(kTeThreads, 2)
                     const uint32_t sa = smem_base + sidx * kTeStageBytes;
                     const uint32_t sb = sa + kTeStageA;
                     const bool fresh = (kc % kTeWinChunks) == 0;
-#pragma unroll 1
-                    for (int L = 0; L < (have_r ? kEmuDigits : 0); ++L) {
-#pragma unroll 1
-                        for (int s = 0; s <= L; ++s) {
-                            const int t = L - s;
+                    if (have_r) {
+                        // R's eight digit tiles lie side by side (32 rows of the
+                        // K-major operand each): digit s of Q times digits
+                        // 0 .. 7 - s of R is one MMA of N = 32 (8 - s) into
+                        // levels s .. 7 (TMEM columns 32 s ..), eight MMAs per
+                        // 16-column k-step; those with s = 0 write every level
+                        // and come first, so only they start a window afresh
 #pragma unroll
-                            for (int kk = 0; kk < kEmuBK / 16; ++kk) {
-                                const uint64_t ad =
-                                    smem_desc(sa + s * kTeTileA + kk * 256, 128, (kEmuBK / 8) * 128);
-                                const uint64_t bd =
-                                    smem_desc(sb + t * kTeTileB + kk * 256, 128, (kEmuBK / 8) * 128);
-                                mma_bf16(tmem + static_cast<uint32_t>(L * kTeB), ad, bd, idesc,
+                        for (int kk = 0; kk < kEmuBK / 16; ++kk) {
+                            const uint64_t bd = smem_desc(sb + kk * 256, 128, (kEmuBK / 8) * 128);
+#pragma unroll
+                            for (int s = 0; s < kEmuDigits; ++s)
+                                mma_bf16(tmem + static_cast<uint32_t>(s * kTeB),
+                                         smem_desc(sa + s * kTeTileA + kk * 256, 128, (kEmuBK / 8) * 128),
+                                         bd, idesc_bf16_f32(kTeM, kTeB * (kEmuDigits - s)),
                                          (fresh && s == 0 && kk == 0) ? 0u : 1u);
-                            }
                         }
                     }
                     mma_commit(&bar_mma[sidx]);

@@ -21,8 +21,9 @@
 // that a pass reads only columns of A below the ones it writes and Q may
 // alias A.  Warp-specialised (k_wprod_emu): 16 producer warps split each
 // 32-column K-chunk of their rows into eight K-major digit tiles while the
-// control warp bulk-copies W's precomputed digit tiles and issues the 72
-// level products (kind::f16, M = 128, N = 64, K = 16).  No binary64
+// control warp bulk-copies W's precomputed digit tiles and issues the level
+// products as 24 wide MMAs (kind::f16, M = 128, N = 64 .. 256, K = 16: one
+// digit of A times up to four side-by-side digits of W).  No binary64
 // arithmetic remains on the rows.
 #include <algorithm>
 #include <cstring>
@@ -232,7 +233,6 @@ __global__ void __launch_bounds__(kWpThreads, 1)
     int committed = -1, wcopies = 0;  // the control thread's last commit, W copies issued
 
     if (control) {
-        const uint32_t idesc = idesc_bf16_f32(kWpM, kWpN);
         // W's tiles of chunk `it` (pass g, K-chunk kc) into its stage, once
         // the MMAs that last read the stage are done (lane 0)
         auto copy_w = [&](int it, int g, int kc) -> bool {
@@ -283,16 +283,32 @@ __global__ void __launch_bounds__(kWpThreads, 1)
                     const uint64_t adB = smem_desc(sa + kWpStageA, 128, (kWpK / 8) * 128);
                     if (lane == 0) {
                         tc_fence_after();
+                        // W's eight digit tiles lie side by side (64 rows of the
+                        // K-major operand each): digit sd of A times up to four
+                        // adjacent digits t0 .. t0 + w - 1 of W is one MMA of
+                        // N = 64 w into levels sd + t0 .. (TMEM columns
+                        // 64 (sd + t0) ..); twelve MMAs per k-step for the 36
+                        // pairs, the two with sd = 0 first (they write every
+                        // level, so only they start a window afresh)
 #pragma unroll
-                        for (int L = 0; L < kEmuDigits; ++L)
+                        for (int kk = 0; kk < kWpK / 16; ++kk) {
+                            const uint32_t a0 = (fresh && kk == 0) ? 0u : 1u;
+                            const uint64_t ak = adA + static_cast<uint64_t>(kk * 16);
+                            const uint64_t bk = adB + static_cast<uint64_t>(kk * 16);
+                            const uint64_t bk4 = bk + static_cast<uint64_t>(4 * (kWpTileB >> 4));
+                            mma_bf16(tmem, ak, bk, idesc_bf16_f32(kWpM, 4 * kWpN), a0);
+                            mma_bf16(tmem + 4 * kWpN, ak, bk4, idesc_bf16_f32(kWpM, 4 * kWpN), a0);
 #pragma unroll
-                            for (int sd = 0; sd <= L; ++sd)
-#pragma unroll
-                                for (int kk = 0; kk < kWpK / 16; ++kk)
-                                    mma_bf16(tmem + static_cast<uint32_t>(L * kWpN),
-                                             adA + static_cast<uint64_t>(sd * (kWpTileA >> 4) + kk * 16),
-                                             adB + static_cast<uint64_t>((L - sd) * (kWpTileB >> 4) + kk * 16),
-                                             idesc, (fresh && sd == 0 && kk == 0) ? 0u : 1u);
+                            for (int sd = 1; sd < kEmuDigits; ++sd) {
+                                const uint64_t as = ak + static_cast<uint64_t>(sd * (kWpTileA >> 4));
+                                const int w0 = (kEmuDigits - sd) < 4 ? (kEmuDigits - sd) : 4;
+                                mma_bf16(tmem + static_cast<uint32_t>(sd * kWpN), as, bk,
+                                         idesc_bf16_f32(kWpM, w0 * kWpN), 1u);
+                                if (sd < 4)
+                                    mma_bf16(tmem + static_cast<uint32_t>((sd + 4) * kWpN), as, bk4,
+                                             idesc_bf16_f32(kWpM, (4 - sd) * kWpN), 1u);
+                            }
+                        }
                         mma_commit(&pp.empty[s]);
                         if (wend) mma_commit(&pp.win_done);
                         committed = it;
