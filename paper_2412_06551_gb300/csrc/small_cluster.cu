@@ -425,6 +425,257 @@ __global__ void __launch_bounds__(kClThreads)
     }
 }
 
+// ---- preconditioner with one exchange per column step ----------------------
+// The factorizations of k_precond_cluster's modes 0 and 1 (Householder R0),
+// arranged so that each column step needs one cluster barrier and no remote
+// read: before the barrier every CTA stores what the others need into their
+// shared memory (distributed shared-memory stores); after it, every CTA reads
+// only its own.
+//   LU column k: each CTA pushes its pivot candidate (largest |a_gk| over its
+//   rows g >= k, smallest g on ties, NaN never a candidate) with that row in
+//   full, and the owner of row k pushes row k.  After the barrier every
+//   thread picks the same pivot p from the C candidates; the owner of row k
+//   takes the pushed pivot row, the owner of row p takes row k, and the
+//   trailing update reads the pivot row from the exchange buffer.
+//   Householder column k: each CTA pushes P_j = sum over its rows g > k of
+//   a_gk a_gj (j >= k; P_k is its share of sigma) and the owner of row k
+//   pushes row k.  After the barrier every CTA forms sigma = sum_q P_k^q, the
+//   reflector's scalars (eq. (eh), larfg convention) and
+//   u_j = tau (a_kj + scal sum_q P_j^q) = tau (v^T A)_j, v_g = scal a_gk,
+//   v_k = 1, on its own.
+// Two exchange buffers, used alternately: a CTA stores into buffer b only
+// after the barrier that every CTA reaches once it has read buffer b.
+// The slab's leading dimension is odd, so that a warp reading one row of 32
+// columns hits distinct banks.
+constexpr int kPxThreads = 256;
+constexpr int kPxMaxCtas = 8;
+constexpr int kPxWarps = kPxThreads / 32;
+
+// |v| as an order-preserving integer, plus one; 0 for NaN (not a candidate).
+__device__ __forceinline__ unsigned long long px_key(double v) {
+    const unsigned long long b =
+        static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
+    return b <= 0x7ff0000000000000ull ? b + 1ull : 0ull;
+}
+
+__device__ __forceinline__ bool px_better(unsigned long long k1, int g1, unsigned long long k2, int g2) {
+    return k1 > k2 || (k1 == k2 && g1 < g2);
+}
+
+template <bool kCl>
+__global__ void __launch_bounds__(kPxThreads)
+    k_precond_push(const double *__restrict__ Y, int64_t ldy, int s, int n, int h, int ld, int mode,
+                   const double *__restrict__ Nsrc, int64_t ldn, double *Nbuf, double *RP,
+                   double *rinv, double *R1, int64_t ldr, DevStatus *st, int step) {
+    using Cl = ClOps<kCl>;
+    const int C = Cl::size();
+    const int rank = Cl::rank();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *A = reinterpret_cast<double *>(smem_raw);  // slab, h x n, leading dimension ld
+    const size_t xs = size_t(C + 1) * n;               // one exchange buffer: C rows, then row k
+    double *X = A + size_t(ld) * n;
+    double *Ssum = X + 2 * xs;                         // combined partial sums
+    double *U = Ssum + n;                              // u_j of the current reflector
+    __shared__ unsigned long long ckey[2][kPxMaxCtas];
+    __shared__ int cidx[2][kPxMaxCtas];
+    __shared__ double csc[4];                          // sigma, beta, tau, scal
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = rank * h;
+    const int rows = max(0, min(h, s - r0));
+
+    for (int idx = tid; idx < h * n; idx += T) {
+        const int i = idx % h, j = idx / h;
+        A[i + size_t(j) * ld] = i < rows ? Y[(r0 + i) + int64_t(j) * ldy] : 0.0;
+    }
+    __syncthreads();
+    int xc = 0;  // exchanges so far (buffer parity)
+
+    if (mode == 0) {
+        // ---- LU with partial pivoting (eq. (elu))
+        for (int k = 0; k < n; ++k) {
+            const int b = (xc++) & 1;
+            double *xb = X + size_t(b) * xs;
+            const int rk = k / h;
+            // (1) this CTA's candidate, in every warp
+            unsigned long long bk = 0;
+            int bg = INT_MAX;
+            for (int i = lane; i < rows; i += 32) {
+                const int g = r0 + i;
+                if (g >= k) {
+                    const unsigned long long kk = px_key(A[i + size_t(k) * ld]);
+                    if (px_better(kk, g, bk, bg)) {
+                        bk = kk;
+                        bg = g;
+                    }
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, off);
+                const int g2 = __shfl_xor_sync(0xffffffffu, bg, off);
+                if (px_better(k2, g2, bk, bg)) {
+                    bk = k2;
+                    bg = g2;
+                }
+            }
+            // (2) push the candidate row, row k (its owner) and the candidate
+            {
+                const int li = bg - r0;
+                for (int idx = tid; idx < C * n; idx += T) {
+                    const int q = idx / n, j = idx - q * n;
+                    double *dst = Cl::at(xb, q);
+                    if (bg != INT_MAX) dst[size_t(rank) * n + j] = A[li + size_t(j) * ld];
+                    if (rank == rk) dst[size_t(C) * n + j] = A[(k - r0) + size_t(j) * ld];
+                }
+                if (tid < C) {
+                    Cl::at(&ckey[b][0], tid)[rank] = bk;
+                    Cl::at(&cidx[b][0], tid)[rank] = bg;
+                }
+            }
+            Cl::sync();
+            // (3) the pivot: the same in every thread of every CTA
+            unsigned long long pk = 0;
+            int p = INT_MAX, rp = 0;
+            for (int q = 0; q < C; ++q)
+                if (px_better(ckey[b][q], cidx[b][q], pk, p)) {
+                    pk = ckey[b][q];
+                    p = cidx[b][q];
+                    rp = q;
+                }
+            if (pk <= 1ull) {  // key 1: the largest magnitude is 0; key 0: only NaN
+                if (rank == 0 && tid == 0) report(st, pk == 1ull ? kErrLuZeroPivot : kErrNonfinite, step, k);
+                Cl::sync();
+                return;
+            }
+            const double *prow = xb + size_t(rp) * n;  // row p, pushed by its owner
+            const double *krow = xb + size_t(C) * n;   // row k before the swap
+            const double piv = prow[k];
+            // (4) swap; multipliers l_g = a_gk / piv of the rows below k
+            if (rank == rk)
+                for (int j = tid; j < n; j += T) A[(k - r0) + size_t(j) * ld] = prow[j];
+            if (rank == rp && p != k)
+                for (int j = tid; j < n; j += T)
+                    if (j != k) A[(p - r0) + size_t(j) * ld] = krow[j];
+            for (int i = tid; i < rows; i += T) {
+                const int g = r0 + i;
+                if (g > k) A[i + size_t(k) * ld] = (g == p ? krow[k] : A[i + size_t(k) * ld]) / piv;
+            }
+            __syncthreads();
+            // (5) trailing update with the pivot row: rows by lane, columns by warp
+            for (int i = lane; i < rows; i += 32) {
+                if (r0 + i <= k) continue;
+                const double l = A[i + size_t(k) * ld];
+                for (int j = k + 1 + warp; j < n; j += kPxWarps)
+                    A[i + size_t(j) * ld] = fma(-l, prow[j], A[i + size_t(j) * ld]);
+            }
+            __syncthreads();
+        }
+        // N (rows < n, upper part) to global scratch; the slab becomes M
+        for (int idx = tid; idx < rows * n; idx += T) {
+            const int i = idx % rows, j = idx / rows, g = r0 + i;
+            const double a = A[i + size_t(j) * ld];
+            if (g < n) Nbuf[g + size_t(j) * n] = g <= j ? a : 0.0;
+            A[i + size_t(j) * ld] = g > j ? a : (g == j ? 1.0 : 0.0);
+        }
+        __threadfence();
+        __syncthreads();
+    }
+
+    // ---- Householder R of the slab matrix (eq. (eh), larfg convention)
+    for (int k = 0; k < n; ++k) {
+        const int b = (xc++) & 1;
+        double *xb = X + size_t(b) * xs;
+        const int rk = k / h;
+        // (1) partial sums over this CTA's rows g > k; row k from its owner
+        {
+            const int i0 = max(0, k + 1 - r0);
+            for (int j = k + tid; j < n; j += T) {
+                double acc = 0.0;
+                for (int i = i0; i < rows; ++i) acc = fma(A[i + size_t(k) * ld], A[i + size_t(j) * ld], acc);
+                const double akj = rank == rk ? A[(k - r0) + size_t(j) * ld] : 0.0;
+                for (int q = 0; q < C; ++q) {
+                    double *dst = Cl::at(xb, q);
+                    dst[size_t(rank) * n + j] = acc;
+                    if (rank == rk) dst[size_t(C) * n + j] = akj;
+                }
+            }
+        }
+        Cl::sync();
+        // (2) the sums over the CTAs (in rank order) and the reflector's
+        // scalars (one thread: the FP64 pipe is too slow for every thread to
+        // repeat a square root and two divisions)
+        for (int j = k + tid; j < n; j += T) {
+            double sj = 0.0;
+            for (int q = 0; q < C; ++q) sj += xb[size_t(q) * n + j];
+            Ssum[j] = sj;
+            if (j == k) {
+                csc[0] = sj;
+                if (sj != 0.0) {
+                    const double alpha = xb[size_t(C) * n + k];
+                    const double norm = sqrt(alpha * alpha + sj);
+                    const double beta = alpha >= 0.0 ? -norm : norm;
+                    csc[1] = beta;
+                    csc[2] = (beta - alpha) / beta;
+                    csc[3] = 1.0 / (alpha - beta);
+                }
+            }
+        }
+        __syncthreads();
+        if (csc[0] == 0.0) continue;  // the same in every CTA: no reflection
+        const double beta = csc[1], tau = csc[2], scal = csc[3];
+        // (3) u_j, the reflector's vector v_g = scal a_gk in column k, r_kk
+        {
+            const double *krow = xb + size_t(C) * n;
+            for (int j = k + 1 + tid; j < n; j += T) U[j] = tau * fma(scal, Ssum[j], krow[j]);
+            for (int i = tid; i < rows; i += T)
+                if (r0 + i > k) A[i + size_t(k) * ld] *= scal;
+            if (rank == rk && tid == 0) A[(k - r0) + size_t(k) * ld] = beta;
+        }
+        __syncthreads();
+        // (4) a_gj -= v_g u_j, rows g >= k by lane, columns by warp
+        for (int i = lane; i < rows; i += 32) {
+            const int g = r0 + i;
+            if (g < k) continue;
+            const double v = g == k ? 1.0 : A[i + size_t(k) * ld];
+            for (int j = k + 1 + warp; j < n; j += kPxWarps)
+                A[i + size_t(j) * ld] = fma(-v, U[j], A[i + size_t(j) * ld]);
+        }
+        __syncthreads();
+    }
+    Cl::sync();  // Nbuf written by every CTA before any reads it
+
+    // ---- R1 = R0 N (rows of this slab below n), diagonal signs, padded outputs
+    const int n_pad = pad16(n);
+    double *RT = RP + size_t(n_pad) * n_pad;
+    const double *N = mode == 0 ? Nbuf : Nsrc;
+    const int64_t ldN = mode == 0 ? n : ldn;
+    const int own = max(0, min(rows, n - r0));  // rows g < n held here
+    for (int idx = tid; idx < own * n_pad; idx += T) {
+        const int i = idx % own, j = idx / own, g = r0 + i;
+        double acc = 0.0;
+        if (j < n && g <= j) {
+            if (N == nullptr)
+                acc = A[i + size_t(j) * ld];
+            else
+                for (int t = g; t <= j; ++t) acc = fma(A[i + size_t(t) * ld], N[t + int64_t(j) * ldN], acc);
+        }
+        const double dgg =
+            N == nullptr ? A[i + size_t(g) * ld] : A[i + size_t(g) * ld] * N[g + int64_t(g) * ldN];
+        if (dgg < 0.0 && j < n && g <= j) acc = -acc;
+        RP[g + size_t(j) * n_pad] = acc;
+        RT[size_t(g) * n_pad + j] = acc;
+        if (R1 != nullptr && j < n) R1[g + int64_t(j) * ldr] = acc;
+        if (j == g) rinv[g] = 1.0 / acc;
+    }
+    if (rank == 0) {  // padding rows n .. n_pad - 1
+        for (int idx = tid; idx < (n_pad - n) * n_pad; idx += T) {
+            const int g = n + idx % (n_pad - n), j = idx / (n_pad - n);
+            RP[g + size_t(j) * n_pad] = 0.0;
+            RT[size_t(g) * n_pad + j] = 0.0;
+        }
+        for (int g = n + tid; g < n_pad; g += T) rinv[g] = 0.0;
+    }
+}
+
 // Upper Cholesky of G (n x n) by rows over the cluster: step k takes
 // r_kk = sqrt(w_kk) (breakdown if w_kk is not > 0), r_kj = w_kj / r_kk (the
 // owner of row k), then every CTA subtracts r_ki r_kj from its rows i > k,
@@ -508,6 +759,90 @@ __global__ void __launch_bounds__(kClThreads)
     }
 }
 
+// Upper Cholesky of G with one exchange per step, the arithmetic of
+// k_cholesky_cluster: the owner of row k takes r_kk = sqrt(w_kk) (or records
+// the breakdown) and r_kj = w_kj / r_kk, and pushes row k and the verdict into
+// every CTA's shared memory; after the cluster barrier each CTA reads only
+// its own copy and subtracts r_kg r_kj from its rows g > k, j >= g.  Two
+// exchange buffers, used alternately, as in k_precond_push.
+template <bool kCl>
+__global__ void __launch_bounds__(kPxThreads)
+    k_cholesky_push(const double *__restrict__ G, int64_t ldg, int n, int h, int ld, double *RP,
+                    double *rinv, double *R, int64_t ldr, DevStatus *st, int step) {
+    using Cl = ClOps<kCl>;
+    const int C = Cl::size();
+    const int rank = Cl::rank();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *A = reinterpret_cast<double *>(smem_raw);  // rows [r0, r0 + rows), leading dimension ld
+    double *X = A + size_t(ld) * n;                    // two copies of the current row of R
+    __shared__ int cfail[2];
+    __shared__ double rkk_sh;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = rank * h;
+    const int rows = max(0, min(h, n - r0));
+    for (int idx = tid; idx < h * n; idx += T) {
+        const int i = idx % h, j = idx / h, g = r0 + i;
+        A[i + size_t(j) * ld] = (i < rows && g <= j) ? G[g + int64_t(j) * ldg] : 0.0;
+    }
+    __syncthreads();
+    int failed = -1;
+    for (int k = 0; k < n; ++k) {
+        const int b = k & 1;
+        const int rk = k / h;
+        if (rank == rk) {  // the owner of row k (uniform in the CTA)
+            const int lk = k - r0;
+            const double d = A[lk + size_t(k) * ld];
+            const bool ok = d > 0.0;
+            if (tid == 0 && ok) rkk_sh = sqrt(d);  // one square root, shared
+            __syncthreads();
+            if (ok) {
+                const double rkk = rkk_sh;
+                for (int j = k + 1 + tid; j < n; j += T) {
+                    const double r = A[lk + size_t(j) * ld] / rkk;
+                    A[lk + size_t(j) * ld] = r;
+                    for (int q = 0; q < C; ++q) Cl::at(X, q)[size_t(b) * n + j] = r;
+                }
+                if (tid == 0) A[lk + size_t(k) * ld] = rkk;
+            }
+            if (tid < C) Cl::at(&cfail[0], tid)[b] = ok ? -1 : k;
+        }
+        Cl::sync();
+        if (cfail[b] >= 0) {  // the same verdict in every CTA
+            failed = cfail[b];
+            break;
+        }
+        const double *rowk = X + size_t(b) * n;
+        // rows g > k by lane, columns j >= g by warp (all lanes on one column)
+        for (int i = lane; i < rows; i += 32) {
+            const int g = r0 + i;
+            if (g <= k) continue;
+            const double rg = rowk[g];
+            for (int j = k + 1 + warp; j < n; j += kPxWarps)
+                if (j >= g) A[i + size_t(j) * ld] = fma(-rg, rowk[j], A[i + size_t(j) * ld]);
+        }
+        __syncthreads();
+    }
+    if (failed >= 0 && rank == 0 && tid == 0) report(st, kErrCholBreakdown, step, failed);
+    const int n_pad = pad16(n);
+    double *RT = RP + size_t(n_pad) * n_pad;
+    for (int idx = tid; idx < rows * n_pad; idx += T) {
+        const int i = idx % rows, j = idx / rows, g = r0 + i;
+        const double v = (g <= j && j < n) ? A[i + size_t(j) * ld] : 0.0;
+        RP[g + size_t(j) * n_pad] = v;
+        RT[size_t(g) * n_pad + j] = v;
+        if (R != nullptr && j < n) R[g + int64_t(j) * ldr] = v;
+        if (j == g) rinv[g] = (failed < 0) ? 1.0 / v : 0.0;
+    }
+    if (rank == 0) {
+        for (int idx = tid; idx < (n_pad - n) * n_pad; idx += T) {
+            const int g = n + idx % (n_pad - n), j = idx / (n_pad - n);
+            RP[g + size_t(j) * n_pad] = 0.0;
+            RT[size_t(g) * n_pad + j] = 0.0;
+        }
+        for (int g = n + tid; g < n_pad; g += T) rinv[g] = 0.0;
+    }
+}
+
 // Smallest power-of-two cluster whose slabs fit the shared-memory budget,
 // and at least four CTAs from 256 rows on: the column steps' FP64 updates
 // then spread over four SMs (256 x 128: 2.76 -> 2.30 ms on GB300; eight
@@ -525,18 +860,19 @@ bool cl_shape(int rows, int n, int extra_vectors, int &C, int &h, size_t &smem, 
 // One CTA: the kCl == false instance, a plain launch.  Otherwise a cluster
 // of C CTAs (the kCl == true instance).
 template <class K1, class KC, class... Args>
-cudaError_t cl_launch(K1 k1, KC kc, int C, size_t smem, cudaStream_t stream, Args... args) {
+cudaError_t cl_launch_t(K1 k1, KC kc, int C, int threads, size_t smem, cudaStream_t stream,
+                        Args... args) {
     if (C == 1) {
         cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        k1<<<1, kClThreads, smem, stream>>>(args...);
+        k1<<<1, threads, smem, stream>>>(args...);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -547,6 +883,22 @@ cudaError_t cl_launch(K1 k1, KC kc, int C, size_t smem, cudaStream_t stream, Arg
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kc, args...);
+}
+
+template <class K1, class KC, class... Args>
+cudaError_t cl_launch(K1 k1, KC kc, int C, size_t smem, cudaStream_t stream, Args... args) {
+    return cl_launch_t(k1, kc, C, kClThreads, smem, stream, args...);
+}
+
+// Shape of k_precond_push: eight CTAs from 128 rows on (four from 32, else
+// one), each slab with an odd leading dimension, two exchange buffers and two
+// vectors, within the shared-memory budget of the other cluster kernels.
+bool px_shape(int s, int n, int &C, int &h, int &ld, size_t &smem) {
+    C = s >= 128 ? kPxMaxCtas : (s >= 32 ? 4 : 1);
+    h = (s + C - 1) / C;
+    ld = h | 1;
+    smem = (size_t(ld) * n + 2 * size_t(C + 1) * n + 2 * size_t(n)) * sizeof(double);
+    return smem <= kClSmemBudget;
 }
 
 }  // namespace
@@ -561,10 +913,17 @@ cudaError_t launch_precond_cluster(const double *Y, int64_t ldy, int s, int n, i
                                    const double *Nsrc, int64_t ldn, double *Nbuf, double *RP,
                                    double *rinv, double *R1, int64_t ldr, DevStatus *st, int step,
                                    cudaStream_t stream) {
-    int C, h;
+    int C, h, ld;
     size_t smem;
-    if (!cl_shape(s, n, 3, C, h, smem, (mode & kGivensMode) != 0)) return cudaErrorInvalidValue;
     cudaError_t e;
+    if ((mode & kGivensMode) == 0 && px_shape(s, n, C, h, ld, smem)) {
+        RQ_LAUNCH(KID_SMALL_PRECOND, stream,
+                  e = cl_launch_t(k_precond_push<false>, k_precond_push<true>, C, kPxThreads, smem, stream,
+                                  Y, ldy, s, n, h, ld, mode, Nsrc, ldn, Nbuf, RP, rinv, R1, ldr, st, step));
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    if (!cl_shape(s, n, 3, C, h, smem, (mode & kGivensMode) != 0)) return cudaErrorInvalidValue;
     RQ_LAUNCH(KID_SMALL_PRECOND, stream,
               e = cl_launch(k_precond_cluster<false>, k_precond_cluster<true>, C, smem, stream, Y, ldy,
                             s, n, h, mode, Nsrc, ldn, Nbuf, RP, rinv, R1, ldr, st, step));
@@ -583,8 +942,21 @@ cudaError_t launch_cholesky_cluster(const double *G, int64_t ldg, int n, double 
                                     cudaStream_t stream) {
     int C, h;
     size_t smem;
-    if (!cl_shape(n, n, 1, C, h, smem)) return cudaErrorInvalidValue;
     cudaError_t e;
+    {
+        // one exchange per step: eight CTAs from n = 128 on (four from 32)
+        const int Cx = n >= 128 ? kPxMaxCtas : (n >= 32 ? 4 : 1);
+        const int hx = (n + Cx - 1) / Cx, ldx = hx | 1;
+        const size_t sx = (size_t(ldx) * n + 2 * size_t(n)) * sizeof(double);
+        if (sx <= kClSmemBudget) {
+            RQ_LAUNCH(KID_CHOLESKY, stream,
+                      e = cl_launch_t(k_cholesky_push<false>, k_cholesky_push<true>, Cx, kPxThreads, sx,
+                                      stream, G, ldg, n, hx, ldx, RP, rinv, R, ldr, st, step));
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+        }
+    }
+    if (!cl_shape(n, n, 1, C, h, smem)) return cudaErrorInvalidValue;
     RQ_LAUNCH(KID_CHOLESKY, stream,
               e = cl_launch(k_cholesky_cluster<false>, k_cholesky_cluster<true>, C, smem, stream, G,
                             ldg, n, h, RP, rinv, R, ldr, st, step));
