@@ -405,12 +405,13 @@ rclupp_status_t rclupp_trsm_emulated(rclupp_handle_t handle, int64_t m, int64_t 
 /* Q = A R^{-1} for an R expected to be well conditioned, the form the
  * emulated tiers use for the second and final solves of CholeskyQR2 (C3, C7:
  * R2 and R4 have the condition numbers of Q1 and Q2).  W = R^{-1} is formed
- * in binary64 by substitution, with the estimate kappa_1 = ||R||_1 ||W||_1;
- * if kappa_1 <= 100, Q = A W runs as one binary64-emulating product on the
- * tensor cores (digits of A's rows with one exponent per row over all n
- * columns, of W's columns with one per column; levels <= 7 exact in fp32 over
- * <= 128 K-columns, int64 drains), whose backward error carries a factor
- * kappa_1 next to eq. (ewy)'s; else the substitution of
+ * in binary64 by forward substitution along its rows, with Skeel's condition
+ * number cond(R) = || |W| |R| ||_inf; if cond(R) <= max(100, n), Q = A W runs
+ * as one binary64-emulating product on the tensor cores (digits of A's rows
+ * with one exponent per row over all n columns, of W's columns with one per
+ * column; levels <= 7 exact in fp32 over <= 128 K-columns, int64 drains),
+ * whose residual |Q R - A| <= c u |A| |W| |R| then stays within the bound
+ * of eq. (ewy)'s substitution (gamma_n |Q| |R|); else the substitution of
  * rclupp_trsm_emulated runs.  The choice is made on the device.  *form (may
  * be NULL) receives 1 for the product, 0 for the substitution.  Q may alias
  * A.  n <= 256. */

@@ -127,15 +127,16 @@ __device__ __forceinline__ uint32_t small_int_bf16(int d) {
 }
 
 // Selection between the two forms of an emulated solve by a well-conditioned
-// factor: the product with R^{-1} runs when the 1-norm condition estimate
-// ||R||_1 ||R^{-1}||_1 (both maxima stored as the bits of non-negative
-// doubles) is at most kWprodMaxCond, the substitution otherwise.
+// factor: the product with R^{-1} runs when Skeel's condition number
+// cond(R) = || |R^{-1}| |R| ||_inf (norms[0]) is at most the limit in
+// norms[1], max(kWprodMaxCond, n) (both stored as the bits of non-negative
+// doubles), the substitution otherwise.
 constexpr double kWprodMaxCond = 100.0;
 
 __device__ __forceinline__ bool wprod_selected(const unsigned long long *norms) {
-    const double nr = __longlong_as_double(static_cast<long long>(norms[0]));
-    const double nw = __longlong_as_double(static_cast<long long>(norms[1]));
-    return nr * nw <= kWprodMaxCond;
+    const double cond = __longlong_as_double(static_cast<long long>(norms[0]));
+    const double lim = __longlong_as_double(static_cast<long long>(norms[1]));
+    return cond <= lim;
 }
 
 // Exponent E with |a| < 2^E for every a of a column with largest biased exponent bits.

@@ -4,13 +4,15 @@
 // and R4 have the condition number of Q1 and of Q2: a few units after a
 // sketch that embeds).
 //
-// W is formed once in binary64 by substitution (k_tri_inverse, one warp per
-// column), and the 1-norm condition estimate ||R||_1 ||W||_1 is taken on the
-// way.  Both this product and the substitution kernel of emu_trsm.cu are
-// launched; each reads the estimate and only one of them runs: the product
-// when the estimate is at most kWprodMaxCond (the product's backward error
-// carries a factor kappa(R)), the substitution otherwise.  No host round trip,
-// so the pair can be captured in a graph.
+// W is formed once in binary64 by forward substitution along its rows
+// (k_tri_inverse, one warp per row), and Skeel's condition number
+// cond(R) = || |R^{-1}| |R| ||_inf, which bounds the product's residual
+// (|Q R - A| <= c u |A| |W| |R|), is taken on the way.  Both this product and
+// the substitution kernel of emu_trsm.cu are launched; each reads cond(R) and
+// only one of them runs: the product when cond(R) <= max(kWprodMaxCond, n)
+// (its residual bound then stays within the substitution's own, gamma_n
+// |Q| |R| ~ n u), the substitution otherwise.  No host round trip, so the
+// pair can be captured in a graph.
 //
 // The product: digits of A's rows (one exponent per row over all n columns of
 // A, known before anything is written) and of W's columns (one exponent per
@@ -83,47 +85,57 @@ __host__ __device__ __forceinline__ WpLayout wp_layout(int n) {
 }
 
 // W = R^{-1} (binary64, column-major n_pad x n_pad, zeros below the diagonal
-// and in the padding) by substitution, one warp per column j:
-// w_jj = 1 / r_jj, w_ij = -(sum_{k = i+1..j} r_ik w_kj) / r_ii for i < j,
-// the sum split over the lanes and combined by shuffles; and the column sums
-// of |R| and |W| folded into their maxima (the 1-norms).
+// and in the padding) by rows, one warp per row i: w_ii = 1 / r_ii,
+// w_ij = -(sum_{k = i..j-1} w_ik r_kj) / r_jj for j > i (the reciprocal
+// multiplied, as in the binary64 substitution), the sum split over the lanes
+// and combined by shuffles.  Each row is a forward substitution with R, so
+// the left residual is small, |W R - I| <= c_n u |W| |R|, and the product
+// Q = A W then has the residual |Q R - A| <= c u |A| |W| |R|.  Its bound,
+// Skeel's condition number cond(R) = || |W| |R| ||_inf = max_i sum_k |w_ik|
+// rho_k (rho_k = sum_j |r_kj|), is folded into norms[0]; block 0 stores the
+// selection limit max(kWprodMaxCond, n) in norms[1].
 __global__ void k_tri_inverse(const double *__restrict__ RP, const double *__restrict__ rinv, int n,
                               int n_pad, double *__restrict__ W, unsigned long long *norms) {
-    extern __shared__ double wcol_all[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (j >= n_pad) return;
-    double *wc = wcol_all + size_t(warp) * n_pad;
-    const double *RT = RP + size_t(n_pad) * n_pad;  // row-major copy: RT[i * n_pad + k] = r_ik
-    for (int i = lane; i < n_pad; i += 32) wc[i] = 0.0;
+    extern __shared__ double ti_smem[];  // rho (n_pad), then one row of W per warp
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *rho = ti_smem;
+    double *wr = ti_smem + n_pad + size_t(warp) * n_pad;
+    const double *RT = RP + size_t(n_pad) * n_pad;  // row-major copy: RT[k * n_pad + j] = r_kj
+    for (int k = warp; k < n_pad; k += nw) {
+        double a = 0.0;
+        for (int j = lane; j < n_pad; j += 32) a += fabs(RT[size_t(k) * n_pad + j]);
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) rho[k] = a;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double lim = n > kWprodMaxCond ? double(n) : kWprodMaxCond;
+        norms[1] = static_cast<unsigned long long>(__double_as_longlong(lim));
+    }
+    __syncthreads();
+    const int i = blockIdx.x * nw + warp;
+    if (i >= n_pad) return;
+    for (int j = lane; j < n_pad; j += 32) wr[j] = 0.0;
     __syncwarp();
-    if (j < n) {
-        if (lane == 0) wc[j] = rinv[j];
+    if (i < n) {
+        if (lane == 0) wr[i] = rinv[i];
         __syncwarp();
-        for (int i = j - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) {
             double acc = 0.0;
-            for (int k = i + 1 + lane; k <= j; k += 32) acc = fma(RT[size_t(i) * n_pad + k], wc[k], acc);
+            for (int k = i + lane; k < j; k += 32) acc = fma(wr[k], RP[size_t(j) * n_pad + k], acc);
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == 0) wc[i] = -acc * rinv[i];
+            if (lane == 0) wr[j] = -acc * rinv[j];
             __syncwarp();
         }
     }
-    double sw = 0.0, sr = 0.0;
-    for (int i = lane; i < n_pad; i += 32) {
-        W[size_t(j) * n_pad + i] = wc[i];
-        sw += fabs(wc[i]);
-        sr += fabs(RP[size_t(j) * n_pad + i]);
+    double t = 0.0;
+    for (int j = lane; j < n_pad; j += 32) {
+        W[size_t(j) * n_pad + i] = wr[j];
+        t = fma(fabs(wr[j]), rho[j], t);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        sw += __shfl_xor_sync(0xffffffffu, sw, off);
-        sr += __shfl_xor_sync(0xffffffffu, sr, off);
-    }
-    if (lane == 0) {
-        // non-negative doubles order like their bits; a NaN sum maps to the
-        // largest bits and makes the estimate fail
-        atomicMax(norms, static_cast<unsigned long long>(__double_as_longlong(sr == sr ? sr : INFINITY)));
-        atomicMax(norms + 1, static_cast<unsigned long long>(__double_as_longlong(sw == sw ? sw : INFINITY)));
-    }
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    // non-negative doubles order like their bits; a NaN sum maps to the
+    // largest bits and rejects the product
+    if (lane == 0) atomicMax(norms, static_cast<unsigned long long>(__double_as_longlong(t == t ? t : INFINITY)));
 }
 
 // Column exponents of W (over all its rows) and its digit tiles for every
@@ -465,10 +477,10 @@ int wellcond_used_product(const void *scratch, int n, cudaStream_t stream) {
     if (cudaMemcpyAsync(h, wp + wp_layout(n).norms, sizeof h, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
         return -1;
-    double nr, nw;
-    memcpy(&nr, &h[0], sizeof nr);
-    memcpy(&nw, &h[1], sizeof nw);
-    return nr * nw <= kWprodMaxCond ? 1 : 0;
+    double cond, lim;
+    memcpy(&cond, &h[0], sizeof cond);
+    memcpy(&lim, &h[1], sizeof lim);
+    return cond <= lim ? 1 : 0;
 }
 
 cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, int n, const double *RP,
@@ -486,7 +498,7 @@ cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, in
     cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     constexpr int kWarps = 8;
-    const size_t ism = size_t(kWarps) * n_pad * sizeof(double);
+    const size_t ism = size_t(kWarps + 1) * n_pad * sizeof(double);
     RQ_LAUNCH(KID_EMU_AUX, stream,
               k_tri_inverse<<<static_cast<unsigned>(ceil_div(n_pad, kWarps)), 32 * kWarps, ism, stream>>>(
                   RP, rinv, n, n_pad, W, norms));

@@ -254,7 +254,7 @@ def _wellcond_r(n, seed, spread=0.1):
 @pytest.mark.parametrize("m,n", [(1, 1), (300, 31), (5000, 64), (4097, 100), (2048, 128), (3001, 129),
                                  (2100, 256), (70001, 200)])
 def test_wellcond_solve_product_against_oracle(rq, m, n):
-    # kappa_1(R) ~ 1.5: the product Q = X R^{-1} runs; against the oracle's
+    # cond(R) ~ 1.5: the product Q = X R^{-1} runs; against the oracle's
     # substitution, both within the rounding of R^{-1} (|W| |R| |W|, the
     # triangular inverse's error) and the digits' 2^-50 of the row and column
     # maxima
@@ -274,7 +274,7 @@ def test_wellcond_solve_product_against_oracle(rq, m, n):
 
 def test_wellcond_solve_exact_on_integers(rq):
     # R = I + superdiagonal of ones: R^{-1} has entries (-1)^(j - i) above the
-    # diagonal (kappa_1 = 2n = 80), X = Q0 R with small integers: every digit
+    # diagonal (Skeel's cond(R) = 2n - 1 = 79), X = Q0 R with small integers: every digit
     # product and sum is exact, so Q = Q0
     n, m = 40, 3000
     r = np.eye(n) + np.diag(np.ones(n - 1), 1)
@@ -285,7 +285,7 @@ def test_wellcond_solve_exact_on_integers(rq):
 
 
 def test_wellcond_solve_falls_back_to_substitution(rq):
-    # an ill-conditioned factor (kappa_1 far above 100) takes the emulated
+    # an ill-conditioned factor (cond(R) far above max(100, n)) takes the emulated
     # substitution, bit for bit the result of rclupp_trsm_emulated
     n, m = 96, 5000
     g = np.random.default_rng(11)
