@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kTeThreads, kTeCtasPerSm)
 #pragma unroll
                     for (int t = 0; t < 4; t += 2) {
                         uint32_t wp[kEmuDigits];
-                        emu_digits2_packed<kEmuDigits>(xv[4 * h + t], xv[4 * h + t + 1], E, wp);
+                        emu_digits2_packed_shift<kEmuDigits>(xv[4 * h + t], xv[4 * h + t + 1], E, wp);
 #pragma unroll
                         for (int s = 0; s < kEmuDigits; ++s) w[s][t >> 1] = wp[s];
                     }

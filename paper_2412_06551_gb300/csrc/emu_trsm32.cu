@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kTeThreads, 2)
 #pragma unroll
                     for (int t = 0; t < 8; t += 2) {
                         uint32_t w[kEmuDigits];
-                        emu_digits2_packed<kEmuDigits>(xv[u][t], xv[u][t + 1], E, w);
+                        emu_digits2_packed_shift<kEmuDigits>(xv[u][t], xv[u][t + 1], E, w);
 #pragma unroll
                         for (int s = 0; s < kEmuDigits; ++s)
                             *reinterpret_cast<uint32_t *>(stage + s * kTeTileA +
