@@ -302,9 +302,11 @@ typedef enum {
  * problems run concurrently, so the outputs of different problems must not
  * overlap (inputs may be shared).
  * The whole batch is enqueued as one CUDA graph: it forks into B parallel
- * branches (streams; problem i runs on branch i mod B, B set by
- * rclupp_set_batch_branches, default 16) so that small problems fill the GPU
- * together, and joins.  The instantiated graph is cached in the handle and
+ * branches (streams; B set by rclupp_set_batch_branches, default 16) so that
+ * small problems fill the GPU together, and joins.  Problems go to branches
+ * longest first, each to the branch with the least estimated work so far
+ * (m n^2 plus a per-column term for the small factorizations), and each
+ * branch runs its problems largest first.  The instantiated graph is cached in the handle and
  * replayed while the batch is unchanged: sizes, pointers, options, branch
  * count, launch shapes and workspace, compared byte for byte.  The
  * workspace holds B per-branch slices sized for the largest problem.

@@ -799,6 +799,29 @@ rclupp_status_t scholqr3_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
 
 // ---- batched form ------------------------------------------------------------
 
+// Branch of each problem and the order of the captures: longest processing
+// time first -- problems by decreasing estimated time (m n^2 for the tall
+// passes plus 4e6 n for the latency of the n-step small factorizations, in
+// flop-equivalents), each to the branch with the least estimated time so far
+// -- so that the branches end together and each starts with its largest
+// problems.  Ties keep the problems' order.
+void assign_branches(int count, const int64_t *m, const int64_t *n, int branches,
+                     std::vector<int> &branch, std::vector<int> &order) {
+    std::vector<double> w(count);
+    for (int i = 0; i < count; ++i)
+        w[i] = double(m[i]) * double(n[i]) * double(n[i]) + 4e6 * double(n[i]);
+    order.resize(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    std::vector<double> load(branches, 0.0);
+    branch.assign(count, 0);
+    for (int i : order) {
+        const int k = int(std::min_element(load.begin(), load.end()) - load.begin());
+        branch[i] = k;
+        load[k] += w[i];
+    }
+}
+
 rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t count,
                                       const int64_t *m, const int64_t *n, const double *const *X,
                                       const int64_t *ldx, const rclupp_opts_t *opts,
@@ -840,8 +863,9 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
     char *base = static_cast<char *>(h->ws);
     DevStatus *d_st = reinterpret_cast<DevStatus *>(base + per_branch * branches);
 
-    // Graph of the whole batch: fork into `branches` streams, matrix i on
-    // branch i mod branches, join.  Reused while the batch is unchanged.
+    // Graph of the whole batch: fork into `branches` streams, each problem on
+    // the branch assign_branches gives it, join.  Reused while the batch is
+    // unchanged.
     LaunchPolicy pol;
     pol.grid_div = h->batch_grid_div;
     pol.fine_tiles = h->batch_fine_tiles;
@@ -864,8 +888,11 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
             ls = RCLUPP_ERR_CUDA;
         for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
             if (cudaStreamWaitEvent(h->bstreams[k], h->fork, 0) != cudaSuccess) ls = RCLUPP_ERR_CUDA;
-        for (int i = 0; i < count && ls == RCLUPP_OK; ++i) {
-            const int k = i % branches;
+        std::vector<int> branch, order;
+        assign_branches(count, m, n, branches, branch, order);
+        for (int oi = 0; oi < count && ls == RCLUPP_OK; ++oi) {
+            const int i = order[oi];
+            const int k = branch[i];
             const Ctx c{h->bstreams[k], d_st + i};
             const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
             const int64_t s = randomized ? o[i].s : n[i];
