@@ -381,14 +381,21 @@ __global__ void __launch_bounds__(kWpThreads, 1)
                         ok = false;
                         break;
                     }
-                    // digits, two K-neighbours (one 32-bit word) per digit tile at a time
+                    // digits, two K-neighbours per 32-bit word; the eight of a digit
+                    // are one 16-byte row of a core matrix, stored at once
+                    {
+                        uint32_t w[kEmuDigits][4];
 #pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
-                        uint32_t w[kEmuDigits];
-                        emu_digits2_packed<kEmuDigits>(xv[u], xv[u + 1], E, w);
+                        for (int u = 0; u < 8; u += 2) {
+                            uint32_t wp[kEmuDigits];
+                            emu_digits2_packed<kEmuDigits>(xv[u], xv[u + 1], E, wp);
+#pragma unroll
+                            for (int d = 0; d < kEmuDigits; ++d) w[d][u >> 1] = wp[d];
+                        }
 #pragma unroll
                         for (int d = 0; d < kEmuDigits; ++d)
-                            *reinterpret_cast<uint32_t *>(stage + d * kWpTileA + wp_off(r, 8 * kb + u)) = w[d];
+                            *reinterpret_cast<uint4 *>(stage + d * kWpTileA + wp_off(r, 8 * kb)) =
+                                make_uint4(w[d][0], w[d][1], w[d][2], w[d][3]);
                     }
                     fence_proxy_async_smem();
                     __syncwarp();

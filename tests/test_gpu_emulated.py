@@ -315,3 +315,54 @@ def test_wellcond_solve_in_place_and_nonfinite(rq):
     q, _ = rq.rclupp_trsm_emulated_wellcond(dev(xn), dev(r))
     q = host(q)
     assert np.all(np.isnan(q[17])) and np.all(np.isfinite(np.delete(q, 17, axis=0)))
+
+
+def _skeel(r):
+    """Skeel's condition number || |R^-1| |R| ||_inf of an upper-triangular R."""
+    return float(np.max(np.abs(np.linalg.inv(r)) @ np.abs(r).sum(axis=1)))
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_wellcond_solve_selects_by_skeel_condition_of_a_sketch_factor(rq, n):
+    # R2 of the emulated tiers: the Cholesky factor of Q1^T Q1, Q1 = X R1^{-1}
+    # after a Gaussian embedding with s = 2n (kappa(Q1) ~ 6).  Its 1-norm
+    # condition number exceeds 100 from n = 128 on, but Skeel's condition
+    # number, the factor in the product's residual bound, stays below
+    # max(100, n): the product runs, and matches the oracle's substitution
+    # within the bound of the product test above.
+    m = 8 * n
+    g = np.random.default_rng(n)
+    x = synth.svd_matrix(m, n, 1e4, 40 + n)
+    y = (g.standard_normal((2 * n, m)) / math.sqrt(2 * n)) @ x
+    r1 = np.linalg.qr(y, mode="r")
+    q1 = np.linalg.solve(r1.T, x.T).T
+    r = np.linalg.cholesky(q1.T @ q1).T
+    cond = _skeel(r)
+    kappa_1 = np.abs(r).sum(axis=0).max() * np.abs(np.linalg.inv(r)).sum(axis=0).max()
+    assert cond <= max(100.0, n)
+    if n >= 128:
+        assert kappa_1 > 100.0
+    a = g.standard_normal((3001, n))
+    q, form = rq.rclupp_trsm_emulated_wellcond(dev(a), dev(r))
+    assert form == 1
+    q = host(q)
+    q_ref = oracle.trsm(a, r)
+    w = np.abs(np.linalg.inv(r))
+    tol = (16 * n * U * (np.abs(a) @ (w @ np.abs(r) @ w))
+           + (n + 128) * 2.0 ** -50 * np.max(np.abs(a), axis=1)[:, None] * np.max(w, axis=0)[None, :])
+    assert np.all(np.abs(q - q_ref) <= tol), float(np.max(np.abs(q - q_ref) / tol))
+
+
+def test_wellcond_solve_rejects_above_the_skeel_limit(rq):
+    # a factor with Skeel's condition number above max(100, n) = 100 (about
+    # 214 for this unit upper-triangular R with N(0, 4/n) entries above the
+    # diagonal) takes the substitution, bit for bit
+    n, m = 64, 2000
+    g = np.random.default_rng(21)
+    r = np.eye(n) + 2.0 * np.triu(g.standard_normal((n, n)), 1) / math.sqrt(n)
+    cond = _skeel(r)
+    assert 150.0 < cond < 300.0, cond
+    x = g.standard_normal((m, n))
+    q, form = rq.rclupp_trsm_emulated_wellcond(dev(x), dev(r))
+    assert form == 0
+    assert torch.equal(q, rq.rclupp_trsm_emulated(dev(x), dev(r)))
