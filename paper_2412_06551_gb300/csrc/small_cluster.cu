@@ -585,17 +585,31 @@ __global__ void __launch_bounds__(kPxThreads)
         const int b = (xc++) & 1;
         double *xb = X + size_t(b) * xs;
         const int rk = k / h;
-        // (1) partial sums over this CTA's rows g > k; row k from its owner
+        // (1) partial sums over this CTA's rows g > k; row k from its owner.
+        // tpc adjacent lanes share a column, each summing every tpc-th row
+        // (the FP64 work spread over all warps when few columns are left),
+        // combined by shuffles.
         {
             const int i0 = max(0, k + 1 - r0);
-            for (int j = k + tid; j < n; j += T) {
+            const int ncol = n - k;
+            int tpc = 1;
+            while (tpc < 8 && tpc * 2 * ncol <= T) tpc *= 2;
+            for (int base = 0; base < ncol * tpc; base += T) {  // the same trip count in every thread
+                const int idx = base + tid;
+                const int jl = idx / tpc, part = idx - jl * tpc;
+                const int j = k + jl;
                 double acc = 0.0;
-                for (int i = i0; i < rows; ++i) acc = fma(A[i + size_t(k) * ld], A[i + size_t(j) * ld], acc);
-                const double akj = rank == rk ? A[(k - r0) + size_t(j) * ld] : 0.0;
-                for (int q = 0; q < C; ++q) {
-                    double *dst = Cl::at(xb, q);
-                    dst[size_t(rank) * n + j] = acc;
-                    if (rank == rk) dst[size_t(C) * n + j] = akj;
+                if (jl < ncol)
+                    for (int i = i0 + part; i < rows; i += tpc)
+                        acc = fma(A[i + size_t(k) * ld], A[i + size_t(j) * ld], acc);
+                for (int off = tpc >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (part == 0 && jl < ncol) {
+                    const double akj = rank == rk ? A[(k - r0) + size_t(j) * ld] : 0.0;
+                    for (int q = 0; q < C; ++q) {
+                        double *dst = Cl::at(xb, q);
+                        dst[size_t(rank) * n + j] = acc;
+                        if (rank == rk) dst[size_t(C) * n + j] = akj;
+                    }
                 }
             }
         }
