@@ -318,6 +318,29 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t handle, int32_t algo, int3
                                       double *const *Q, const int64_t *ldq, double *const *R,
                                       const int64_t *ldr, int32_t *status);
 
+/* The same batch enqueued on the handle's stream without waiting, for a
+ * caller that captures it into a CUDA graph of its own: no graph of the
+ * library's, no host synchronization, no host read-back.  The problems fork
+ * into the B branch streams and join back into the handle's stream, every
+ * step being a stream operation that a capture records; at the end problem
+ * i's status code is written to d_status[i], a DEVICE array of count int32.
+ * The arrays m .. ldr are read during the call only.  While the handle's
+ * stream captures nothing may be allocated: the handle's workspace and
+ * branch streams must already be large enough, from an earlier call
+ * (batched or async) with the same or larger problems and branch count
+ * outside the capture; otherwise RCLUPP_ERR_UNSUPPORTED.  A graph that
+ * recorded this call keeps pointers into the handle's workspace, so it stays
+ * valid while the handle lives and its workspace is not regrown (a later
+ * call with larger problems would regrow it).  Two such graphs, or this
+ * call and another call on the same handle, must not run concurrently.
+ * Returns RCLUPP_OK once enqueued; argument errors as rclupp_factor_batched. */
+rclupp_status_t rclupp_factor_batched_async(rclupp_handle_t handle, int32_t algo, int32_t count,
+                                            const int64_t *m, const int64_t *n,
+                                            const double *const *X, const int64_t *ldx,
+                                            const rclupp_opts_t *opts, double *const *Q,
+                                            const int64_t *ldq, double *const *R, const int64_t *ldr,
+                                            int32_t *d_status);
+
 /* Number of parallel branches of the batched graph (1 ..64). */
 rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t handle, int32_t branches);
 

@@ -31,7 +31,8 @@ __all__ = [
     "rclupp_sketch", "rclupp_gram", "rclupp_gram_emulated", "rclupp_trsm_emulated",
     "rclupp_trsm_emulated_wellcond", "rclupp_trsm_gram", "rclupp_cholesky", "rclupp_trmm_upper",
     "rclupp_tall_lupp", "rclupp_sketch_precond", "rclupp_householder_r", "rclupp_gram_noalloc",
-    "rclupp_factor_batched", "rclupp_set_batch_branches", "rclupp_autotune_batched",
+    "rclupp_factor_batched", "rclupp_factor_batched_async", "rclupp_set_batch_branches",
+    "rclupp_autotune_batched",
     "rclupp_set_batch_policy", "rclupp_get_batch_policy",
     "ALGO_RCLUPP", "ALGO_RCLUPPR",
     "ALGO_CHOLQR2", "ALGO_LC2",
@@ -122,6 +123,7 @@ _SIGNATURES = {
     "rclupp_sketch_precond_r0": ([_P, _I64, _I64, _P, _I64, _I32, _P, _I64], _I32),
     "rclupp_gram_noalloc": ([_I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "rclupp_factor_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "rclupp_factor_batched_async": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "rclupp_set_batch_branches": ([_P, _I32], _I32),
     "rclupp_autotune_batched": ([_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)], _I32),
@@ -499,6 +501,24 @@ def rclupp_factor_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN,
     st = load().rclupp_factor_batched(a["h"], int(algo), a["count"], *a["args"], a["pst"])
     _raise("rclupp_factor_batched", st, None, check)
     return a["Qs"], a["Rs"], a["status"]
+
+
+def rclupp_factor_batched_async(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8,
+                                seed=0, Qs=None, Rs=None, prec=PREC_FP64, r0=R0_HOUSEHOLDER,
+                                d_status=None):
+    """The batched call enqueued on the current stream without waiting (it can
+    be recorded by a caller's CUDA graph capture): returns (Qs, Rs, d_status),
+    d_status an int32 tensor on the device holding each problem's status once
+    the stream reaches it.  While capturing, the handle's workspace must
+    already fit the batch (an earlier call outside the capture)."""
+    torch = _torch()
+    a = _batch_args(Xs, Qs, Rs, s, kind, zeta, seed, prec, r0)
+    if d_status is None:
+        d_status = torch.zeros(a["count"], dtype=torch.int32, device=a["Qs"][0].device)
+    st = load().rclupp_factor_batched_async(a["h"], int(algo), a["count"], *a["args"],
+                                            _P(d_status.data_ptr()))
+    _raise("rclupp_factor_batched_async", st)
+    return a["Qs"], a["Rs"], d_status
 
 
 def rclupp_autotune_batched(Xs, *, algo=ALGO_RCLUPP, s=None, kind=SKETCH_GAUSSIAN, zeta=8, seed=0,

@@ -799,6 +799,10 @@ rclupp_status_t scholqr3_factor(rclupp_handle_t h, int64_t m, int64_t n, const d
 
 // ---- batched form ------------------------------------------------------------
 
+}  // extern "C"
+
+namespace {
+
 // Branch of each problem and the order of the captures: longest processing
 // time first -- problems by decreasing estimated time (m n^2 for the tall
 // passes plus 4e6 n for the latency of the n-step small factorizations, in
@@ -822,46 +826,144 @@ void assign_branches(int count, const int64_t *m, const int64_t *n, int branches
     }
 }
 
+// What a batch needs before anything is enqueued: every problem validated,
+// its options resolved, the per-branch workspace (sized for the largest
+// problem) and the branch streams.  `may_allocate` false: a workspace or
+// stream set too small is RCLUPP_ERR_UNSUPPORTED instead of allocated.
+struct BatchSetup {
+    std::vector<rclupp_opts_t> o;
+    bool randomized = false;
+    size_t per_branch = 0;
+    int branches = 1;
+    char *base = nullptr;
+    DevStatus *d_st = nullptr;
+};
+
+rclupp_status_t batch_setup(rclupp_handle_t h, int32_t algo, int32_t count, const int64_t *m,
+                            const int64_t *n, const double *const *X, const int64_t *ldx,
+                            const rclupp_opts_t *opts, double *const *Q, const int64_t *ldq,
+                            double *const *R, const int64_t *ldr, bool may_allocate, BatchSetup &bs) {
+    if (!h || count < 0 || (count > 0 && (!m || !n || !X || !ldx || !Q || !ldq || !R || !ldr)))
+        return RCLUPP_ERR_ARG;
+    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_SCHOLQR3) return RCLUPP_ERR_ARG;
+    bs.randomized =
+        algo == RCLUPP_ALGO_RCLUPP || algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_RCHOLQR;
+    if (count == 0) return RCLUPP_OK;
+    // validate every problem and size one branch's workspace for the largest
+    bs.o.assign(count, rclupp_opts_t{});
+    size_t per_branch = 0;
+    for (int i = 0; i < count; ++i) {
+        rclupp_status_t st = check_common(h, m[i], n[i], X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+        if (st != RCLUPP_OK) return st;
+        bs.o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
+        if (bs.randomized) {
+            if ((st = check_opts(bs.o[i], m[i], n[i])) != RCLUPP_OK) return st;
+            // one sketch tier per problem (no escalation inside a graph):
+            // binary64, or the three-term tensor-core sketch for the
+            // RCLUPP_PREC_SKETCH_FP32 and emulated tiers; the bf16 tier needs
+            // the escalation and is refused
+            if (bs.o[i].prec == RCLUPP_PREC_SKETCH_BF16) return RCLUPP_ERR_UNSUPPORTED;
+        }
+        const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
+        const int64_t s = bs.randomized ? bs.o[i].s : n[i];
+        size_t total = 0;
+        carve(nullptr, m[i], int(n[i]), s, own_lu, &total);
+        per_branch = std::max(per_branch, total);
+    }
+    bs.per_branch = (per_branch + 255) & ~size_t(255);
+    bs.branches = std::max(1, std::min<int>(count, h->batch_branches));
+    const size_t status_bytes = (size_t(count) * sizeof(DevStatus) + 255) & ~size_t(255);
+    const size_t need = bs.per_branch * bs.branches + status_bytes;
+    if (!may_allocate && (h->ws_bytes < need || h->nstreams < bs.branches || !h->fork))
+        return RCLUPP_ERR_UNSUPPORTED;
+    rclupp_status_t st = ensure_ws(h, need);
+    if (st != RCLUPP_OK) return st;
+    if (ensure_streams(h, bs.branches) != RCLUPP_OK) return RCLUPP_ERR_CUDA;
+    bs.base = static_cast<char *>(h->ws);
+    bs.d_st = reinterpret_cast<DevStatus *>(bs.base + bs.per_branch * bs.branches);
+    return RCLUPP_OK;
+}
+
+// The batch's work relative to `origin`: statuses cleared, a fork into the
+// branch streams, each problem on the branch assign_branches gives it (each
+// branch's problems largest first), a join back into `origin`.  Every call it
+// makes can be captured.
+rclupp_status_t enqueue_batch(rclupp_handle_t h, int32_t algo, int32_t count, const int64_t *m,
+                              const int64_t *n, const double *const *X, const int64_t *ldx,
+                              double *const *Q, const int64_t *ldq, double *const *R,
+                              const int64_t *ldr, const BatchSetup &bs, cudaStream_t origin) {
+    const int branches = bs.branches;
+    rclupp_status_t ls = RCLUPP_OK;
+    if (cudaMemsetAsync(bs.d_st, 0, size_t(count) * sizeof(DevStatus), origin) != cudaSuccess ||
+        cudaEventRecord(h->fork, origin) != cudaSuccess)
+        ls = RCLUPP_ERR_CUDA;
+    for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
+        if (cudaStreamWaitEvent(h->bstreams[k], h->fork, 0) != cudaSuccess) ls = RCLUPP_ERR_CUDA;
+    std::vector<int> branch, order;
+    assign_branches(count, m, n, branches, branch, order);
+    for (int oi = 0; oi < count && ls == RCLUPP_OK; ++oi) {
+        const int i = order[oi];
+        const int k = branch[i];
+        const Ctx c{h->bstreams[k], bs.d_st + i};
+        const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
+        const int64_t s = bs.randomized ? bs.o[i].s : n[i];
+        size_t total = 0;
+        const Bufs b = carve(bs.base + bs.per_branch * k, m[i], int(n[i]), s, own_lu, &total);
+        double *L = own_lu ? b.LUbuf : Q[i];
+        const int64_t ldl = own_lu ? m[i] : ldq[i];
+        const int ni = int(n[i]);
+        const rclupp_opts_t &oi_opts = bs.o[i];
+        switch (algo) {
+            case RCLUPP_ALGO_RCLUPP:
+                ls = enqueue_rclupp(c, b, oi_opts, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                break;
+            case RCLUPP_ALGO_RCLUPPR:
+                ls = enqueue_rcluppr(c, b, oi_opts, m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i],
+                                     ldr[i]);
+                break;
+            case RCLUPP_ALGO_CHOLQR2:
+                ls = enqueue_cholqr2(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                break;
+            case RCLUPP_ALGO_RCHOLQR:
+                ls = enqueue_rcholqr(c, b, oi_opts, batch_sketch_tier(oi_opts), m[i], ni, X[i], ldx[i],
+                                     Q[i], ldq[i], R[i], ldr[i]);
+                break;
+            case RCLUPP_ALGO_SCHOLQR3:
+                ls = enqueue_scholqr3(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
+                break;
+            default:
+                ls = enqueue_lc2(c, b, m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i], ldr[i]);
+                break;
+        }
+    }
+    for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
+        if (cudaEventRecord(h->join[k], h->bstreams[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(origin, h->join[k], 0) != cudaSuccess)
+            ls = RCLUPP_ERR_CUDA;
+    return ls;
+}
+
+// Problem i's status code into status[i] (device memory).
+__global__ void k_batch_status(const DevStatus *__restrict__ st, int count, int32_t *__restrict__ status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) status[i] = st[i].code;
+}
+
+}  // namespace
+
+extern "C" {
+
 rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t count,
                                       const int64_t *m, const int64_t *n, const double *const *X,
                                       const int64_t *ldx, const rclupp_opts_t *opts,
                                       double *const *Q, const int64_t *ldq, double *const *R,
                                       const int64_t *ldr, int32_t *status) {
-    if (!h || count < 0 || (count > 0 && (!m || !n || !X || !ldx || !Q || !ldq || !R || !ldr)))
-        return RCLUPP_ERR_ARG;
-    if (algo < RCLUPP_ALGO_RCLUPP || algo > RCLUPP_ALGO_SCHOLQR3) return RCLUPP_ERR_ARG;
-    const bool randomized =
-        algo == RCLUPP_ALGO_RCLUPP || algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_RCHOLQR;
-    if (count == 0) return RCLUPP_OK;
-    // validate every problem and size one branch's workspace for the largest
-    std::vector<rclupp_opts_t> o(count);
-    size_t per_branch = 0;
-    for (int i = 0; i < count; ++i) {
-        rclupp_status_t st = check_common(h, m[i], n[i], X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
-        if (st != RCLUPP_OK) return st;
-        o[i] = resolve_opts(opts ? &opts[i] : nullptr, n[i]);
-        if (randomized) {
-            if ((st = check_opts(o[i], m[i], n[i])) != RCLUPP_OK) return st;
-            // one sketch tier per problem (no escalation inside a graph):
-            // binary64, or the three-term tensor-core sketch for the
-            // RCLUPP_PREC_SKETCH_FP32 and emulated tiers; the bf16 tier needs
-            // the escalation and is refused
-            if (o[i].prec == RCLUPP_PREC_SKETCH_BF16) return RCLUPP_ERR_UNSUPPORTED;
-        }
-        const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
-        const int64_t s = randomized ? o[i].s : n[i];
-        size_t total = 0;
-        carve(nullptr, m[i], int(n[i]), s, own_lu, &total);
-        per_branch = std::max(per_branch, total);
-    }
-    per_branch = (per_branch + 255) & ~size_t(255);
-    const int branches = std::max(1, std::min<int>(count, h->batch_branches));
-    const size_t status_bytes = (size_t(count) * sizeof(DevStatus) + 255) & ~size_t(255);
-    rclupp_status_t st = ensure_ws(h, per_branch * branches + status_bytes);
-    if (st != RCLUPP_OK) return st;
-    if (ensure_streams(h, branches) != RCLUPP_OK) return RCLUPP_ERR_CUDA;
-    char *base = static_cast<char *>(h->ws);
-    DevStatus *d_st = reinterpret_cast<DevStatus *>(base + per_branch * branches);
+    BatchSetup bs;
+    rclupp_status_t st = batch_setup(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr, true, bs);
+    if (st != RCLUPP_OK || count == 0) return st;
+    const int branches = bs.branches;
+    const std::vector<rclupp_opts_t> &o = bs.o;
+    DevStatus *d_st = bs.d_st;
 
     // Graph of the whole batch: fork into `branches` streams, each problem on
     // the branch assign_branches gives it, join.  Reused while the batch is
@@ -881,53 +983,11 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         // legacy default stream, which cannot be captured); launch on the caller's
         if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
             return RCLUPP_ERR_CUDA;
-        rclupp_status_t ls = RCLUPP_OK;
-        const LaunchPolicyScope policy_scope(pol);  // launch shapes of the captured kernels
-        if (cudaMemsetAsync(d_st, 0, size_t(count) * sizeof(DevStatus), h->cap) != cudaSuccess ||
-            cudaEventRecord(h->fork, h->cap) != cudaSuccess)
-            ls = RCLUPP_ERR_CUDA;
-        for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
-            if (cudaStreamWaitEvent(h->bstreams[k], h->fork, 0) != cudaSuccess) ls = RCLUPP_ERR_CUDA;
-        std::vector<int> branch, order;
-        assign_branches(count, m, n, branches, branch, order);
-        for (int oi = 0; oi < count && ls == RCLUPP_OK; ++oi) {
-            const int i = order[oi];
-            const int k = branch[i];
-            const Ctx c{h->bstreams[k], d_st + i};
-            const bool own_lu = (algo == RCLUPP_ALGO_RCLUPPR || algo == RCLUPP_ALGO_LC2) && Q[i] == X[i];
-            const int64_t s = randomized ? o[i].s : n[i];
-            size_t total = 0;
-            const Bufs b = carve(base + per_branch * k, m[i], int(n[i]), s, own_lu, &total);
-            double *L = own_lu ? b.LUbuf : Q[i];
-            const int64_t ldl = own_lu ? m[i] : ldq[i];
-            const int ni = int(n[i]);
-            switch (algo) {
-                case RCLUPP_ALGO_RCLUPP:
-                    ls = enqueue_rclupp(c, b, o[i], m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
-                    break;
-                case RCLUPP_ALGO_RCLUPPR:
-                    ls = enqueue_rcluppr(c, b, o[i], m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i],
-                                         ldr[i]);
-                    break;
-                case RCLUPP_ALGO_CHOLQR2:
-                    ls = enqueue_cholqr2(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
-                    break;
-                case RCLUPP_ALGO_RCHOLQR:
-                    ls = enqueue_rcholqr(c, b, o[i], batch_sketch_tier(o[i]), m[i], ni, X[i], ldx[i], Q[i],
-                                         ldq[i], R[i], ldr[i]);
-                    break;
-                case RCLUPP_ALGO_SCHOLQR3:
-                    ls = enqueue_scholqr3(c, b, m[i], ni, X[i], ldx[i], Q[i], ldq[i], R[i], ldr[i]);
-                    break;
-                default:
-                    ls = enqueue_lc2(c, b, m[i], ni, X[i], ldx[i], L, ldl, Q[i], ldq[i], R[i], ldr[i]);
-                    break;
-            }
+        rclupp_status_t ls;
+        {
+            const LaunchPolicyScope policy_scope(pol);  // launch shapes of the captured kernels
+            ls = enqueue_batch(h, algo, count, m, n, X, ldx, Q, ldq, R, ldr, bs, h->cap);
         }
-        for (int k = 0; k < branches && ls == RCLUPP_OK; ++k)
-            if (cudaEventRecord(h->join[k], h->bstreams[k]) != cudaSuccess ||
-                cudaStreamWaitEvent(h->cap, h->join[k], 0) != cudaSuccess)
-                ls = RCLUPP_ERR_CUDA;
         const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
         if (ls != RCLUPP_OK || ec != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -965,6 +1025,36 @@ rclupp_status_t rclupp_factor_batched(rclupp_handle_t h, int32_t algo, int32_t c
         if (first == RCLUPP_OK && hs[i].code != 0) first = static_cast<rclupp_status_t>(hs[i].code);
     }
     return first;
+}
+
+rclupp_status_t rclupp_factor_batched_async(rclupp_handle_t h, int32_t algo, int32_t count,
+                                            const int64_t *m, const int64_t *n,
+                                            const double *const *X, const int64_t *ldx,
+                                            const rclupp_opts_t *opts, double *const *Q,
+                                            const int64_t *ldq, double *const *R, const int64_t *ldr,
+                                            int32_t *d_status) {
+    if (count > 0 && !d_status) return RCLUPP_ERR_ARG;
+    // while the caller's stream captures, nothing may be allocated
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (h && cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return RCLUPP_ERR_CUDA;
+    }
+    BatchSetup bs;
+    rclupp_status_t st = batch_setup(h, algo, count, m, n, X, ldx, opts, Q, ldq, R, ldr,
+                                     cs == cudaStreamCaptureStatusNone, bs);
+    if (st != RCLUPP_OK || count == 0) return st;
+    LaunchPolicy pol;
+    pol.grid_div = h->batch_grid_div;
+    pol.fine_tiles = h->batch_fine_tiles;
+    {
+        const LaunchPolicyScope policy_scope(pol);
+        st = enqueue_batch(h, algo, count, m, n, X, ldx, Q, ldq, R, ldr, bs, h->stream);
+    }
+    if (st != RCLUPP_OK) return st;
+    k_batch_status<<<(count + 255) / 256, 256, 0, h->stream>>>(bs.d_st, count, d_status);
+    if (cudaGetLastError() != cudaSuccess) return RCLUPP_ERR_CUDA;
+    return RCLUPP_OK;
 }
 
 rclupp_status_t rclupp_set_batch_branches(rclupp_handle_t h, int32_t branches) {

@@ -230,3 +230,91 @@ def test_batched_tensor_core_sketch_gates_up_to_kappa_1e12(rq, prec):
         assert np.array_equal(r, np.triu(r)) and np.all(np.diag(r) > 0), i
         assert oracle.orthogonality(q) <= max(10 * oracle.orthogonality(q_o), 1e-13), i
         assert oracle.residual(x, q, r) <= max(10 * oracle.residual(x, q_o, r_o), 1e-13), i
+
+
+# ------------------------------------------- asynchronous, caller-recorded ---
+
+@pytest.mark.parametrize("algo", [0, 1, 3])
+def test_batched_async_matches_the_synchronous_call(rq, algo):
+    # the same kernels and launch shapes as the graph of rclupp_factor_batched,
+    # enqueued straight on the stream: every Q and R bit for bit, and the
+    # statuses on the device
+    xs, _ = _batch(10, 77 + algo, nmax=96)
+    X = [dev(x) for x in xs]
+    qs, rs, st = rq.rclupp_factor_batched(X, algo=algo, seed=5)
+    qa, ra, dst = rq.rclupp_factor_batched_async(X, algo=algo, seed=5)
+    torch.cuda.synchronize()
+    assert dst.dtype == torch.int32 and dst.device.type == "cuda"
+    assert np.array_equal(dst.cpu().numpy(), st)
+    for i in range(len(xs)):
+        assert torch.equal(qa[i], qs[i]) and torch.equal(ra[i], rs[i]), i
+
+
+@pytest.mark.parametrize("mode", ["global", "relaxed"])
+def test_batched_async_recorded_in_a_caller_graph(rq, mode):
+    # a caller captures the call into its own CUDA graph (the workspace sized
+    # by an earlier call outside the capture); replays give the results of
+    # direct calls, also after the inputs change in place
+    xs, _ = _batch(8, 91, nmax=64)
+    X = [dev(x) for x in xs]
+    qa, ra, _ = rq.rclupp_factor_batched_async(X, seed=3)
+    torch.cuda.synchronize()
+    qg = [torch.full_like(q, float("nan")) for q in qa]
+    rg = [torch.full_like(r, float("nan")) for r in ra]
+    dst = torch.full((len(xs),), -1, dtype=torch.int32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode=mode):
+        rq.rclupp_factor_batched_async(X, seed=3, Qs=qg, Rs=rg, d_status=dst)
+    torch.cuda.synchronize()
+    assert int(dst[0]) == -1  # recorded, not run
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(dst.abs().max()) == 0
+    for i in range(len(xs)):
+        assert torch.equal(qg[i], qa[i]) and torch.equal(rg[i], ra[i]), i
+    # new inputs in the same buffers
+    xs2, _ = _batch(8, 92, nmax=64)
+    for i in range(len(xs)):
+        X[i].copy_(dev(synth.svd_matrix(xs[i].shape[0], xs[i].shape[1], 1e3, 500 + i)))
+    g.replay()
+    q2, r2, st2 = rq.rclupp_factor_batched(X, seed=3)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.cpu().numpy(), st2)
+    for i in range(len(xs)):
+        assert torch.equal(qg[i], q2[i]) and torch.equal(rg[i], r2[i]), i
+
+
+def test_batched_async_refuses_to_grow_its_workspace_while_captured(rq):
+    # a thread's first call has no workspace yet, and none can be allocated
+    # inside a capture: RCLUPP_ERR_UNSUPPORTED, nothing enqueued, and the
+    # capture ends cleanly; the same call outside a capture then runs
+    import threading
+    xs, _ = _batch(4, 93, nmax=32)
+    X = [dev(x) for x in xs]
+    torch.cuda.synchronize()
+    out = {}
+
+    def worker():
+        try:
+            rq.rclupp_get_batch_policy()  # this thread's handle, created outside the capture
+            qs = [rq.empty_colmajor(x.shape[0], x.shape[1], "cuda") for x in xs]
+            rs = [rq.empty_colmajor(x.shape[1], x.shape[1], "cuda") for x in xs]
+            dst = torch.full((len(xs),), -1, dtype=torch.int32, device="cuda")
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="thread_local"):
+                try:
+                    rq.rclupp_factor_batched_async(X, seed=2, Qs=qs, Rs=rs, d_status=dst)
+                except rq.RclupError as e:
+                    out["err"] = e
+            _, _, dst = rq.rclupp_factor_batched_async(X, seed=2, Qs=qs, Rs=rs, d_status=dst)
+            torch.cuda.synchronize()
+            out["status"] = dst.cpu().numpy()
+        except Exception as e:  # pragma: no cover - reported below
+            out["exc"] = e
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert "exc" not in out, out.get("exc")
+    assert out["err"].status == rq.Status.ERR_UNSUPPORTED
+    assert np.all(out["status"] == 0)
