@@ -161,9 +161,10 @@ cudaError_t launch_trsm_emu32(const double *A, int64_t lda, int64_t m, int n, co
                               const unsigned long long *skip_if = nullptr);
 size_t trsm_emu32_scratch_bytes(int n);
 // Q = A R^{-1} for a factor expected to be well conditioned (emu_wprod.cu):
-// W = R^{-1} in binary64 and the estimate ||R||_1 ||W||_1; then either the
-// emulated product Q = A W (estimate <= 100) or the substitution form, chosen
-// on the device.  scratch: wellcond_scratch_bytes(n).  Q may alias A.
+// W = R^{-1} in binary64 and Skeel's condition number || |W| |R| ||_inf;
+// then either the emulated product Q = A W (cond <= max(100, n)) or the
+// substitution form, chosen on the device.  scratch: wellcond_scratch_bytes(n).
+// Q may alias A.
 cudaError_t launch_trsm_emu_wellcond(const double *A, int64_t lda, int64_t m, int n, const double *RP,
                                      const double *rinv, double *Q, int64_t ldq, void *scratch,
                                      DevStatus *st, cudaStream_t stream);
