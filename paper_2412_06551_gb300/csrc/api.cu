@@ -1052,7 +1052,8 @@ rclupp_status_t rclupp_factor_batched_async(rclupp_handle_t h, int32_t algo, int
         st = enqueue_batch(h, algo, count, m, n, X, ldx, Q, ldq, R, ldr, bs, h->stream);
     }
     if (st != RCLUPP_OK) return st;
-    k_batch_status<<<(count + 255) / 256, 256, 0, h->stream>>>(bs.d_st, count, d_status);
+    RQ_LAUNCH(KID_REDUCE, h->stream,
+              k_batch_status<<<(count + 255) / 256, 256, 0, h->stream>>>(bs.d_st, count, d_status));
     if (cudaGetLastError() != cudaSuccess) return RCLUPP_ERR_CUDA;
     return RCLUPP_OK;
 }
