@@ -205,8 +205,8 @@ __device__ __forceinline__ bool wp_wait(WpPipe &pp, uint64_t *bar, uint32_t pari
 // alias A), per 32-column K-chunk the 16 producer warps split their rows'
 // values into eight digit tiles of A (four threads per row, eight K-columns
 // each), while lane 0 of the control warp bulk-copies W's precomputed digit
-// tiles into the same stage and issues the chunk's 72 level products
-// (kind::f16, M = 128, N = 64, K = 16).  After each window (at most four
+// tiles into the same stage and issues the chunk's level products as 24 wide
+// MMAs (kind::f16, M = 128, N = 64 .. 256, K = 16).  After each window (at most four
 // chunks: 128 K-columns) the producers drain the eight levels into int64;
 // at a pass's end they write Q.
 __global__ void __launch_bounds__(kWpThreads, 1)
