@@ -138,7 +138,7 @@ def c3(request):
 
 
 def _gate(c3, Q, R, label):
-    """BASELINE gates against the oracle on the same X: orthogonality and
+    """The accuracy gates against the oracle on the same X: orthogonality and
     residual <= max(10 x oracle, 1e-13) for kappa <= 1e12, R within 1e-10 kappa
     of the oracle's R for kappa <= 1e6; beyond the gate a record-level check."""
     kappa, ref, X = c3["kappa"], c3["ref"], c3["X"]
